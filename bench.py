@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 hybrid DH^2 build + matvec.
+
+One step = the whole hot path on one synthetic workload: cluster tree,
+directions, block tree, nearfield, directional interpolation, basis weights,
+total weights (rows and columns), SVD truncation, projection (dh2_build_tree +
+dh2_build_dh2), then one DH^2 matvec (dh2_matvec).
+
+Workload (default): unit sphere, icosahedral refinement to 20480 flat
+triangles, kappa = 16 (kappa h ~ 0.5), leaf <= 32, eta1 = 10, eta2 = 1,
+Chebyshev m = 5 (k = 125), eps = 1e-4, seeded N(0,1) + i N(0,1) vectors.
+
+Prints ONE JSON line (rank 0).  `value` = build seconds per step (device time
+with CUDA events on the launching stream); the matvec throughput (algorithmic
+GB/s: every stored coefficient + the vectors, once) and its error against
+sampled dense Galerkin rows are reported beside it, together with the plain
+FP64 GPU form of the same build.  `--impl reference` times the CPU oracle (the
+reference arm) on a bounded sample of the same workload.
+
+    python bench.py [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (icosphere level, kappa, leaf, eta1, eta2, m, eps)
+    "sphere20480": (5, 16.0, 32, 10.0, 1.0, 5, 1e-4),
+    "sphere1280": (3, 4.0, 32, 10.0, 1.0, 4, 1e-4),
+}
+METRIC = "DH2 build s + matvec GB/s at rel.err≤1e-4 vs dense; vs plain FP64 GPU form"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="sphere20480", choices=list(WORKLOADS))
+    ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form")
+    ap.add_argument("--error-rows", type=int, default=256)
+    return ap.parse_args()
+
+
+def workload_config(name):
+    lvl, kappa, leaf, eta1, eta2, m, eps = WORKLOADS[name]
+    return dict(workload=f"icosphere{20 * 4 ** lvl}", mesh="unit sphere, icosahedral refinement",
+                triangles=20 * 4 ** lvl, kappa=kappa, leaf=leaf, eta1=eta1, eta2=eta2, m=m, k=m ** 3, eps=eps)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                     timeout=5).stdout.strip()
+                if out:
+                    self.samples.append([x.strip() for x in out.split(",")])
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for name, val in zip(names, s[4:8]):
+                if val.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle baseline
+
+def oracle_sample_seconds(name, out_queue=None):
+    """Times the oracle on a bounded sample of the workload (runs in a child process).
+
+    Sample: the full structure phase (cluster tree, directions, block tree) of the
+    workload, plus the complete build (nearfield + interpolation + recompression) of
+    the mesh patch under one level-3 cluster (~1/8 of the triangles, same mesh
+    density, kappa, leaf, m, eps).  The patch costs are scaled to the full workload by
+    its admissible-block and nearfield-entry counts.
+    """
+    import synth
+    from oracle.geometry import Discretisation
+    from oracle.interp import InterpolatedDH2
+    from oracle.recompress import Recompression
+    from oracle.structure import build_block_tree, build_cluster_tree, build_directions
+
+    lvl, kappa, leaf, eta1, eta2, m, eps = WORKLOADS[name]
+    v, f = synth.icosphere(lvl)
+    t0 = time.perf_counter()
+    tr = build_cluster_tree(v, f, leaf)
+    dirs = build_directions(tr, kappa, eta1)
+    bt = build_block_tree(tr, dirs, kappa, eta2)
+    t_struct = time.perf_counter() - t0
+    near_full = int(sum(tr.size[t] * tr.size[s] for t, s in bt.near))
+    nadm_full = len(bt.adm)
+    plevel = min(3, tr.depth)
+    t = tr.level_start[plevel]
+    idx = np.sort(tr.indices(t))
+    used, inv = np.unique(f[idx], return_inverse=True)
+    vs, fs = v[used], inv.reshape(-1, 3).astype(np.int32)
+    t0 = time.perf_counter()
+    tr2 = build_cluster_tree(vs, fs, leaf)
+    d2 = build_directions(tr2, kappa, eta1)
+    b2 = build_block_tree(tr2, d2, kappa, eta2)
+    dh = InterpolatedDH2(Discretisation(vs, fs), tr2, d2, b2, kappa, m)
+    t1 = time.perf_counter()
+    rc = Recompression(dh, eps)
+    t2 = time.perf_counter()
+    for (a, b) in b2.near:
+        dh.nearfield_block(a, b)
+    t3 = time.perf_counter()
+    near_s = int(sum(tr2.size[a] * tr2.size[b] for a, b in b2.near))
+    t_recomp = t2 - t1
+    t_near = t3 - t2
+    est = t_struct + t_recomp * nadm_full / max(len(b2.adm), 1) + t_near * near_full / max(near_s, 1)
+    res = dict(value=est, sample_seconds=t_struct + (t3 - t0), patch_triangles=len(fs),
+               patch_adm=len(b2.adm), patch_near_entries=near_s, full_adm=nadm_full, full_near_entries=near_full,
+               t_struct=t_struct, t_recomp=t_recomp, t_near=t_near)
+    return res
+
+
+def run_oracle_child(name):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample_seconds(%r)))" % (ROOT, name))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(res):
+    return {"value": res["value"], "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"oracle structure phase on the full mesh + full oracle build of a "
+                       f"{res['patch_triangles']}-triangle patch (one level-3 cluster) of the same sphere; "
+                       f"recompression scaled by admissible blocks ({res['patch_adm']} -> {res['full_adm']}), "
+                       f"nearfield by entries ({res['patch_near_entries']} -> {res['full_near_entries']}); "
+                       f"{res['sample_seconds']:.1f} s of single-threaded CPU work")}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def gpu_build(pkg, v, f, cfg, precision, stream):
+    tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
+    mat = pkg.Matrix(tree, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], precision=precision,
+                     eta1=cfg["eta1"], stream=stream)
+    tree.close()
+    return mat
+
+
+def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream):
+    """Device-timed steps: build (tree + DH^2) and one matvec, CUDA events on `stream`."""
+    build_ms, mv_ms = [], []
+    mats = []
+    for i in range(warmup + steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        y = torch.empty_like(x_dev)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mat = gpu_build(pkg, v, f, cfg, precision, stream)
+        e1.record(stream)
+        mat.matvec(x_dev, y, stream=stream)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        if i >= warmup:
+            build_ms.append(e0.elapsed_time(e1))
+            mv_ms.append(e1.elapsed_time(e2))
+            mats.append(mat)
+        else:
+            mat.close()
+    return build_ms, mv_ms, mats
+
+
+def matvec_repeat_ms(torch, mat, x_dev, reps, stream):
+    y = torch.empty_like(x_dev)
+    for _ in range(3):
+        mat.matvec(x_dev, y, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        mat.matvec(x_dev, y, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def sampled_dense_error(mat, torch, v, f, cfg, x, rows_count, seed):
+    from oracle.geometry import Discretisation
+
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(len(f), size=min(rows_count, len(f)), replace=False))
+    dt = torch.complex64 if mat.precision == 1 else torch.complex128
+    y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+    ref = Discretisation(v, f).dense_rows_matvec(rows, x, cfg["kappa"])
+    return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cfg = workload_config(args.workload)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        res = None
+        for i in range(args.warmup + args.steps):
+            res = run_oracle_child(args.workload)
+            if i >= args.warmup:
+                vals.append(res["value"])
+        value = float(np.mean(vals))
+        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": 0, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": dict(cfg, l2="inputs larger than L2"), "impl": "reference",
+                "cpu_baseline": cpu_baseline_obj(dict(res, value=value)),
+                "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+
+    import paper_1809_04384_gb300 as pkg
+    import synth
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    pkg.lib()
+    precision = pkg.DH2_MIXED if args.precision == "mixed" else pkg.DH2_FP64
+    lvl = WORKLOADS[args.workload][0]
+    v, f = synth.icosphere(lvl)
+    n = len(f)
+    x = synth.random_vector(n, 1809_0002)
+    xdt = torch.complex64 if precision == pkg.DH2_MIXED else torch.complex128
+    x_dev = torch.from_numpy(x).to(xdt).cuda()
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up and timed steps (one replica per GPU: the path is not sharded)
+    launches0 = pkg.lib().dh2_kernel_launches()
+    barrier()
+    with ClockSampler(local) as clk:
+        t_wall0 = time.perf_counter()
+        build_ms, mv_ms, mats = time_steps(pkg, torch, v, f, cfg, precision, x_dev, args.steps, args.warmup,
+                                           stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    launches = pkg.lib().dh2_kernel_launches() - launches0
+    launches_per_step = launches / (args.steps + args.warmup)
+    build_s = float(np.mean(build_ms)) / 1e3
+    step_ms = float(np.mean(np.array(build_ms) + np.array(mv_ms)))
+    if world > 1:
+        t = torch.tensor([build_s, step_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        build_s, step_ms = float(t[0]), float(t[1])
+    mat = mats[-1]
+    info = mat.get_info()
+
+    # matvec throughput: algorithmic bytes / device time, repeated launches
+    mv_rep_ms = matvec_repeat_ms(torch, mat, x_dev, 20, stream)
+    mv_gbs = info.matvec_bytes / (mv_rep_ms * 1e-3) / 1e9
+
+    # per-kernel device times summed over the timed builds
+    ktimes = {}
+    for m_ in mats:
+        for name, (ms, cnt) in m_.kernel_times().items():
+            a, b = ktimes.get(name, (0.0, 0))
+            ktimes[name] = (a + ms, b + cnt)
+    # matvec kernels with timing on
+    mat.set_timing(True)
+    for _ in range(10):
+        mat.matvec(x_dev, torch.empty_like(x_dev), stream=stream)
+    torch.cuda.synchronize()
+    mv_kernels = {k: v_ for k, v_ in mat.kernel_times().items() if k.startswith("mv_")}
+    mat.set_timing(False)
+    work = kernel_work(mat, info, cfg)
+    peaks = load_peaks()
+    build_kernels = {k: v_ for k, v_ in ktimes.items() if not k.startswith("mv_") and v_[1] > 0}
+    dom = max(build_kernels, key=lambda k: build_kernels[k][0])
+    roof = roofline_obj(dom, build_kernels[dom], work, peaks, len(mats))
+    leaf_ms, leaf_cnt = mv_kernels.get("mv_leaf_out", (0.0, 0))
+    mv_roof = roofline_obj("mv_leaf_out", (leaf_ms, leaf_cnt), work, peaks, 10)
+
+    # e2e: host mesh in, host vector in/out, through the C ABI
+    xh = np.ascontiguousarray(x.astype(np.complex128))
+    e2e = []
+    for i in range(1 + min(args.steps, 3)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m2 = gpu_build(pkg, v, f, cfg, precision, None)
+        m2.matvec_host(xh)
+        torch.cuda.synchronize()
+        if i > 0:
+            e2e.append(time.perf_counter() - t0)
+        m2.close()
+    h2d = v.nbytes + f.astype(np.int32).nbytes + xh.nbytes
+    d2h = xh.nbytes
+
+    # accuracy against sampled dense rows (outside the timed region)
+    err = sampled_dense_error(mat, torch, v, f, cfg, x, args.error_rows, 1809_0002)
+
+    # plain FP64 GPU form of the same build
+    fp64 = None
+    if precision == pkg.DH2_MIXED and not args.no_fp64:
+        x64 = torch.from_numpy(x).cuda()
+        b64, m64, mats64 = time_steps(pkg, torch, v, f, cfg, pkg.DH2_FP64, x64, 2, 1, stream)
+        mv64 = matvec_repeat_ms(torch, mats64[-1], x64, 10, stream)
+        err64 = sampled_dense_error(mats64[-1], torch, v, f, cfg, x, args.error_rows, 1809_0002)
+        fp64 = {"build_s": float(np.mean(b64)) / 1e3, "matvec_ms": mv64,
+                "matvec_gbs": mats64[-1].get_info().matvec_bytes / (mv64 * 1e-3) / 1e9,
+                "matvec_relerr_sampled_dense": err64,
+                "speedup_build_mixed_vs_fp64": float(np.mean(b64)) / 1e3 / build_s}
+        for m_ in mats64:
+            m_.close()
+
+    baseline = None
+    if rank == 0 and not args.no_baseline:
+        try:
+            baseline = cpu_baseline_obj(run_oracle_child(args.workload))
+        except Exception as e:  # reported, never silently replaced
+            baseline = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": build_s * world / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64+f64" if precision == pkg.DH2_MIXED else "c128",
+            "data": "synthetic",
+            "config": dict(cfg, precision=args.precision, parallelism=f"replicas{world}",
+                           l2="inputs larger than L2 (nearfield alone > 1 GB)"),
+            "build_s": build_s,
+            "matvec": {"gbs": mv_gbs, "ms": mv_rep_ms, "bytes": info.matvec_bytes,
+                       "relerr_sampled_dense": err, "rows_sampled": args.error_rows},
+            "ranks": {"max_row": info.max_rank_row, "mean_row": info.mean_rank_row,
+                      "max_col": info.max_rank_col, "mean_col": info.mean_rank_col},
+            "storage": {"near_entries": info.near_entries, "coupling_entries": info.coupling_entries,
+                        "basis_entries": info.basis_entries, "nadm": info.nadm, "nnear": info.nnear},
+            "stage_ms": {k: round(v_, 3) for k, v_ in mat.stage_ms().items()},
+            "kernel_ms_per_step": {k: round(v_[0] / len(mats), 3) for k, v_ in build_kernels.items()},
+            "roofline": roof,
+            "matvec_roofline": mv_roof,
+            "plain_fp64": fp64,
+            "cpu_baseline": baseline,
+            "e2e": {"value": float(np.mean(e2e)), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clk.summary(),
+            "wall_s_timed_region": t_wall,
+        }
+        print(json.dumps(line))
+    for m_ in mats:
+        m_.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return dict(hbm_gbs=d["hbm_gbs"], bf16=d["bf16_tflops"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, bf16=1900.0, sm_max_mhz=2070.0, source="fallback")
+
+
+def kernel_work(mat, info, cfg):
+    """Algorithmic work per kernel over one build / one matvec (library counters)."""
+    return mat.kernel_work()
+
+
+def roofline_obj(name, timing, work, peaks, nsteps):
+    ms, launches = timing
+    if launches == 0 or ms <= 0:
+        return None
+    w = work.get(name)
+    if w is None:
+        return None
+    kind, amount = w          # amount per build (or per matvec)
+    per_launch_ms = ms / launches
+    launches_per_step = launches / nsteps
+    per_launch_work = amount / launches_per_step
+    if kind == "byte":
+        achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peaks["source"] + " copy bandwidth",
+                "algorithmic_bytes_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
+    # FP32 / FP64 SIMT arithmetic: peak from unit counts and the maximum SM clock
+    lanes = {"flop32": 128, "flop64": 2}[kind]
+    peak = 152 * lanes * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
+    return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_source": f"derived: 152 SMs x {lanes} {'FP32' if lanes == 128 else 'FP64'} FMA lanes x 2 x "
+                           f"{peaks['sm_max_mhz']:.0f} MHz",
+            "algorithmic_flop_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * dh2.h - C ABI of the GB300 hybrid DH^2 library.
+ *
+ * Hybrid compression of the Galerkin matrix of the Helmholtz single layer
+ * operator (Boerm & Boerst, "Hybrid matrix compression for high-frequency
+ * problems"): directional Chebyshev interpolation (Section 2) followed by
+ * algebraic recompression (Section 3.2), and the matrix-vector product of the
+ * resulting DH^2 matrix.
+ *
+ * Conventions for every entry point:
+ *   - The return value is a dh2_status: 0 (DH2_OK) or a negative error code.
+ *     No C++ exception crosses this boundary.  dh2_last_error() returns a
+ *     thread-local, NUL-terminated description of the last failure.
+ *   - Handles (dh2_tree, dh2_matrix) are opaque and owned by the library;
+ *     release them with dh2_free_tree / dh2_free_matrix.  A matrix keeps a
+ *     reference to nothing but its own copies: the tree may be freed first.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device pointers must be valid on the current CUDA device.
+ *   - Invalid arguments are rejected with DH2_EINVAL before any GPU work.
+ *   - Complex vectors are interleaved (re, im) pairs: DH2_C64 = 2 x float,
+ *     DH2_C128 = 2 x double.
+ *   - All index arrays are int32 and 0-based.
+ */
+#ifndef DH2_H
+#define DH2_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DH2_OK = 0,
+    DH2_EINVAL = -1,        /* invalid argument (detected on the host, no GPU work done) */
+    DH2_ENOMEM = -2,        /* device or host allocation failed */
+    DH2_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+    DH2_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
+    DH2_ENUMERIC = -5,      /* NaN/Inf or a non-converged factorisation */
+    DH2_EUNSUPPORTED = -6   /* valid but not supported by this build (e.g. k too large) */
+} dh2_status;
+
+enum { DH2_FP64 = 0, DH2_MIXED = 1 };                 /* dh2_options.precision */
+enum { DH2_C64 = 1, DH2_C128 = 2 };                   /* vector dtypes */
+enum { DH2_RANK_BLOCKREL = 0, DH2_RANK_GLOBAL = 1 };  /* dh2_options.rank_rule */
+
+typedef struct dh2_tree_s* dh2_tree;
+typedef struct dh2_matrix_s* dh2_matrix;
+
+typedef struct {
+    double eta1;            /* direction parameter eta_1 of Eq. (3a)/(4); paper: 10 (Section 5) */
+    int32_t leaf_max;       /* clusters with at most leaf_max elements are leaves; paper: 32 */
+    int32_t precision;      /* DH2_FP64: complex FP64 everywhere.  DH2_MIXED: complex FP32
+                               kernel evaluation, GEMMs, weight QRs and matvec storage; FP64
+                               SVD truncation (Gram + Jacobi) and basis-change matrices */
+    int32_t rank_rule;      /* DH2_RANK_BLOCKREL: sum_{i>k} sigma_i^2 <= eps^2 with every block
+                               weighted by 1/|G_b|_F (blockwise relative Frobenius, Section 5);
+                               DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted */
+    int32_t qr_fp64;        /* DH2_MIXED only: 1 = run the weight QRs (R, Z-hat) in FP64 */
+    int64_t workspace_bytes;/* cap on the stacked weight workspace per level (0 = 16 GiB) */
+} dh2_options;
+
+typedef struct {
+    int64_t n;              /* number of elements (triangles) */
+    int32_t nclusters;
+    int32_t depth;          /* p_I: levels are 0..depth */
+} dh2_tree_info;
+
+typedef struct {
+    int64_t n;
+    int32_t depth;
+    int32_t m, k;           /* Chebyshev points per axis, k = m^3 */
+    int64_t nadm;           /* admissible leaves of the block tree */
+    int64_t nnear;          /* nearfield (inadmissible) leaves */
+    int64_t npairs;         /* pairs (t, c), c in D_level(t) */
+    int64_t nactive;        /* pairs visited by the recompression */
+    int64_t near_entries;   /* stored nearfield coefficients */
+    int64_t coupling_entries; /* stored recompressed coupling coefficients */
+    int64_t basis_entries;  /* stored leaf bases Q and transfers F, rows + columns */
+    int64_t matvec_bytes;   /* algorithmic bytes one matvec streams (matrix + vectors) */
+    int32_t max_rank_row, max_rank_col;
+    double mean_rank_row, mean_rank_col;
+    double stage_ms[16];    /* device time per build stage (see dh2_stage_name) */
+    double kernel_ms[16];   /* summed CUDA-event duration per kernel (see dh2_kernel_name):
+                               build kernels always, matvec kernels while timing is on */
+    int64_t kernel_launches[16]; /* number of timed launches per kernel */
+    double kernel_work[16]; /* algorithmic work of each kernel in one build (build kernels) or
+                               one matvec (matvec kernels), in the unit of kernel_work_kind */
+    int32_t kernel_work_kind[16]; /* 0 none, 1 FP32 flop, 2 FP64 flop, 3 bytes moved */
+} dh2_matrix_info;
+
+/* Fills *opt with the paper's parameters: eta1 = 10, leaf_max = 32, DH2_MIXED,
+ * blockwise relative rank rule, FP32 weight QRs, default workspace. */
+dh2_status dh2_options_default(dh2_options* opt);
+
+/*
+ * Cluster tree (Def. "cluster tree"; Section 5: binary space partitioning to
+ * at most leaf_max elements per leaf) and bounding boxes B_t (Section 2).
+ * vertices: HOST, FP64 [nv][3].  triangles: HOST, int32 [nt][3], vertex ids in
+ * [0, nv); both are copied, the caller keeps ownership.  triangles == NULL
+ * selects point mode: every vertex is one element (used by interpolation
+ * tests).  The tree is built by GPU kernels on `stream`; the call returns
+ * after the tree is complete.  Errors: DH2_EINVAL for nv <= 0, nt < 0, an
+ * out-of-range vertex id or NULL pointers; DH2_ENOMEM; DH2_ECUDA.
+ */
+dh2_status dh2_build_tree(const double* vertices, int64_t nv, const int32_t* triangles,
+                          int64_t nt, const dh2_options* opt, void* stream, dh2_tree* out);
+
+/*
+ * Builds the recompressed DH^2 matrix for the Helmholtz kernel
+ * g(x,y) = exp(i kappa |x-y|)/(4 pi |x-y|) (Eq. 1) with piecewise-constant
+ * Galerkin discretisation (Eq. 2):
+ *   directions D_l and son maps (Remark "construction of directions"),
+ *   block tree with eta = eta_2 of Eq. (3b),(3c) (Def. "block tree"),
+ *   nearfield blocks, leaf bases and transfers of the directional Chebyshev
+ *   interpolation with m points per axis (k = m^3; Eq. matrix_apx,
+ *   nested_apx), then Section 3.2: basis weights, total weights, truncation
+ *   at tolerance eps, projection of the couplings (Lemma "Projections").
+ * The couplings S_b of the interpolation are never stored: they are evaluated
+ * where they are used.  Blocks until the matrix is complete.
+ * Errors: DH2_EINVAL for kappa < 0, m not in [1, 8], eta <= 0, eps <= 0;
+ * DH2_ENOMEM when a level's workspace exceeds opt->workspace_bytes or the
+ * device is full; DH2_ECUDA; DH2_ENUMERIC for NaN/Inf in a factorisation.
+ */
+dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, double eps,
+                         const dh2_options* opt, void* stream, dh2_matrix* out);
+
+/*
+ * y = G~ x with the recompressed DH^2 matrix: forward transform with the
+ * column basis, couplings, backward transform with the row basis, nearfield
+ * (derived from Eq. nested and Eq. vsw).  x, y: DEVICE buffers of n complex
+ * values of type `dtype` (DH2_C64 or DH2_C128) in the ORIGINAL element order,
+ * caller-owned, not aliased.  Asynchronous on `stream`; the library's
+ * internal scratch is per matrix, so concurrent matvecs with one matrix on
+ * different streams race.  Errors: DH2_EINVAL (bad dtype, NULL), DH2_ECUDA.
+ */
+dh2_status dh2_matvec(dh2_matrix mat, const void* x, void* y, int32_t dtype, void* stream);
+
+/*
+ * End-to-end matvec from HOST memory: copies x (n complex128, original order)
+ * to the device, runs dh2_matvec in the matrix precision, copies y back to
+ * the host buffer.  Synchronous.  Pinned host memory gives the fastest copies.
+ */
+dh2_status dh2_matvec_host(dh2_matrix mat, const double* x_host, double* y_host, void* stream);
+
+/* Turns per-launch CUDA-event timing of the matvec kernels on (1) or off (0);
+ * the sums are reported in dh2_matrix_info.kernel_ms / kernel_launches (matvec
+ * entries are reset by this call).  Timing synchronises the stream per launch. */
+dh2_status dh2_set_timing(dh2_matrix mat, int32_t on);
+
+/* Number of kernels this library has launched in this process so far (all
+ * devices, all streams).  Library-internal device-wide scans and sorts are not
+ * counted. */
+int64_t dh2_kernel_launches(void);
+
+/* Waits for `stream` and reports deferred device errors. */
+dh2_status dh2_sync(void* stream);
+
+/* ---- inspection and parity exports (host copies; caller-allocated buffers) ---- */
+
+dh2_status dh2_tree_get_info(dh2_tree tree, dh2_tree_info* out);
+
+/* perm[n]: element index of the i-th position in cluster order.  Cluster
+ * arrays of length nclusters: offset, size, parent (-1 at the root), son0 and
+ * son1 (-1 at leaves), level.  lo, hi: FP64 [nclusters][3] bounding boxes.
+ * Any pointer may be NULL to skip that array. */
+dh2_status dh2_tree_export(dh2_tree tree, int32_t* perm, int32_t* offset, int32_t* size,
+                           int32_t* parent, int32_t* son0, int32_t* son1, int32_t* level,
+                           double* lo, double* hi);
+
+dh2_status dh2_matrix_get_info(dh2_matrix mat, dh2_matrix_info* out);
+
+/* Directions of level l: *count = |D_l|; msplit = m_l (0 if D_l = {0});
+ * dirs FP64 [count][3] and sd int32 [count] (index into D_{l+1}; zeros on the
+ * last level) if non-NULL. */
+dh2_status dh2_export_directions(dh2_matrix mat, int32_t level, int32_t* count, int32_t* msplit,
+                                 double* dirs, int32_t* sd);
+
+/* adm int32 [nadm][3] = (t, s, c), near int32 [nnear][2] = (t, s), in the
+ * breadth-first order of the block-tree recursion; active int8 [npairs]. */
+dh2_status dh2_export_blocks(dh2_matrix mat, int32_t* adm, int32_t* near, int8_t* active);
+
+enum {
+    DH2_X_R = 0,        /* basis weight R_tc, rows x k */
+    DH2_X_ZROW = 1,     /* total weight Z-hat_tc of the row pass */
+    DH2_X_ZCOL = 2,     /* total weight of the column pass */
+    DH2_X_SROW = 3,     /* singular values of the row truncation (1 x count) */
+    DH2_X_SCOL = 4,
+    DH2_X_QROW = 5,     /* leaf: Q_tc (#t x k_tc); non-leaf: [F_t1c; F_t2c] */
+    DH2_X_QCOL = 6,
+    DH2_X_CROW = 7,     /* basis change C_tc = Q_tc^* V_tc, k_tc x k */
+    DH2_X_CCOL = 8
+};
+/* Copies one per-pair matrix as complex128 (interleaved, row-major) into out
+ * (capacity `cap` complex values; singular values are stored as (sigma, 0)).
+ * *rows, *cols receive the shape; a pair that is not active gives 0 x 0. */
+dh2_status dh2_export_pair(dh2_matrix mat, int32_t which, int64_t tc, double* out, int64_t cap,
+                           int32_t* rows, int32_t* cols);
+
+/* Ranks k_tc of the row and column bases, int32 [npairs] (-1 if inactive). */
+dh2_status dh2_export_ranks(dh2_matrix mat, int32_t* rank_row, int32_t* rank_col);
+
+/* Name of build stage i for dh2_matrix_info.stage_ms (NULL past the end). */
+const char* dh2_stage_name(int32_t i);
+
+/* Name of kernel i for dh2_matrix_info.kernel_ms (NULL past the end). */
+const char* dh2_kernel_name(int32_t i);
+
+void dh2_free_tree(dh2_tree tree);
+void dh2_free_matrix(dh2_matrix mat);
+const char* dh2_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DH2_H */

@@ -1,0 +1,318 @@
+"""GB300 hybrid DH^2 compression of the Helmholtz single layer operator.
+
+Thin ctypes binding of ``libdh2.so`` (C ABI in ``include/dh2.h``).  Every step
+of the construction and of the matvec runs in the library's CUDA kernels; this
+module only marshals arguments.  Importing it does not need a GPU; calling into
+the library does, and a missing library raises ``RuntimeError`` (there is no
+fallback path).
+
+The functions keep the C names (``dh2_build_tree``, ``dh2_build_dh2``,
+``dh2_matvec`` ...).  ``Tree`` and ``Matrix`` are small owning wrappers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdh2.so")
+
+DH2_OK, DH2_EINVAL, DH2_ENOMEM, DH2_ECUDA, DH2_ETIMEOUT, DH2_ENUMERIC, DH2_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+DH2_FP64, DH2_MIXED = 0, 1
+DH2_C64, DH2_C128 = 1, 2
+DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL = 0, 1
+(DH2_X_R, DH2_X_ZROW, DH2_X_ZCOL, DH2_X_SROW, DH2_X_SCOL, DH2_X_QROW, DH2_X_QCOL,
+ DH2_X_CROW, DH2_X_CCOL) = range(9)
+
+_STATUS = {DH2_EINVAL: "EINVAL", DH2_ENOMEM: "ENOMEM", DH2_ECUDA: "ECUDA", DH2_ETIMEOUT: "ETIMEOUT",
+           DH2_ENUMERIC: "ENUMERIC", DH2_EUNSUPPORTED: "EUNSUPPORTED"}
+
+
+class dh2_options(C.Structure):
+    _fields_ = [("eta1", C.c_double), ("leaf_max", C.c_int32), ("precision", C.c_int32),
+                ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("workspace_bytes", C.c_int64)]
+
+
+class dh2_tree_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nclusters", C.c_int32), ("depth", C.c_int32)]
+
+
+class dh2_matrix_info(C.Structure):
+    _fields_ = [("n", C.c_int64), ("depth", C.c_int32), ("m", C.c_int32), ("k", C.c_int32),
+                ("nadm", C.c_int64), ("nnear", C.c_int64), ("npairs", C.c_int64), ("nactive", C.c_int64),
+                ("near_entries", C.c_int64), ("coupling_entries", C.c_int64), ("basis_entries", C.c_int64),
+                ("matvec_bytes", C.c_int64), ("max_rank_row", C.c_int32), ("max_rank_col", C.c_int32),
+                ("mean_rank_row", C.c_double), ("mean_rank_col", C.c_double),
+                ("stage_ms", C.c_double * 16), ("kernel_ms", C.c_double * 16),
+                ("kernel_launches", C.c_int64 * 16), ("kernel_work", C.c_double * 16),
+                ("kernel_work_kind", C.c_int32 * 16)]
+
+
+class DH2Error(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+_P = C.c_void_p
+_SIGS = {
+    "dh2_options_default": (C.c_int, [C.POINTER(dh2_options)]),
+    "dh2_build_tree": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.POINTER(dh2_options), _P, C.POINTER(_P)]),
+    "dh2_build_dh2": (C.c_int, [_P, C.c_double, C.c_int32, C.c_double, C.c_double, C.POINTER(dh2_options), _P,
+                                C.POINTER(_P)]),
+    "dh2_matvec": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
+    "dh2_matvec_host": (C.c_int, [_P, _P, _P, _P]),
+    "dh2_set_timing": (C.c_int, [_P, C.c_int32]),
+    "dh2_sync": (C.c_int, [_P]),
+    "dh2_tree_get_info": (C.c_int, [_P, C.POINTER(dh2_tree_info)]),
+    "dh2_tree_export": (C.c_int, [_P] + [_P] * 9),
+    "dh2_matrix_get_info": (C.c_int, [_P, C.POINTER(dh2_matrix_info)]),
+    "dh2_export_directions": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "dh2_export_blocks": (C.c_int, [_P, _P, _P, _P]),
+    "dh2_export_pair": (C.c_int, [_P, C.c_int32, C.c_int64, _P, C.c_int64, _P, _P]),
+    "dh2_export_ranks": (C.c_int, [_P, _P, _P]),
+    "dh2_stage_name": (C.c_char_p, [C.c_int32]),
+    "dh2_kernel_name": (C.c_char_p, [C.c_int32]),
+    "dh2_free_tree": (None, [_P]),
+    "dh2_free_matrix": (None, [_P]),
+    "dh2_last_error": (C.c_char_p, []),
+    "dh2_kernel_launches": (C.c_int64, []),
+}
+
+
+def lib():
+    """Loads libdh2.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libdh2.so not built ({LIB_PATH}); run paper_1809_04384_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _check(status):
+    if status != DH2_OK:
+        raise DH2Error(status, lib().dh2_last_error().decode())
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def options(**kw) -> dh2_options:
+    o = dh2_options()
+    _check(lib().dh2_options_default(C.byref(o)))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+# ----------------------------------------------------------------------------- C names
+
+def dh2_build_tree(vertices, triangles=None, opts=None, stream=None):
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = None if triangles is None else np.ascontiguousarray(triangles, dtype=np.int32)
+    h = C.c_void_p()
+    _check(lib().dh2_build_tree(_ptr(v), len(v), _ptr(t), 0 if t is None else len(t),
+                                C.byref(opts or options()), _stream(stream), C.byref(h)))
+    return h
+
+
+def dh2_build_dh2(tree, kappa, m, eta, eps, opts=None, stream=None):
+    h = C.c_void_p()
+    _check(lib().dh2_build_dh2(tree, float(kappa), int(m), float(eta), float(eps), C.byref(opts or options()),
+                               _stream(stream), C.byref(h)))
+    return h
+
+
+def dh2_matvec(mat, x, y, stream=None):
+    """y = G~ x for CUDA tensors x, y (complex64 or complex128, same dtype)."""
+    import torch
+    if x.dtype != y.dtype or x.dtype not in (torch.complex64, torch.complex128):
+        raise TypeError("x and y must both be complex64 or complex128")
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise TypeError("x and y must be contiguous CUDA tensors")
+    dtype = DH2_C64 if x.dtype == torch.complex64 else DH2_C128
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    _check(lib().dh2_matvec(mat, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), dtype, _stream(stream)))
+    return y
+
+
+def dh2_matvec_host(mat, x, stream=None):
+    """End-to-end matvec on host arrays (complex128, original order)."""
+    x = np.ascontiguousarray(x, dtype=np.complex128)
+    y = np.empty_like(x)
+    _check(lib().dh2_matvec_host(mat, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def dh2_free_tree(tree):
+    lib().dh2_free_tree(tree)
+
+
+def dh2_free_matrix(mat):
+    lib().dh2_free_matrix(mat)
+
+
+# ----------------------------------------------------------------------------- wrappers
+
+class Tree:
+    """Cluster tree and bounding boxes on the GPU (owning handle)."""
+
+    def __init__(self, vertices, triangles=None, leaf_max=32, stream=None):
+        self.handle = dh2_build_tree(vertices, triangles, options(leaf_max=leaf_max), stream)
+        info = dh2_tree_info()
+        _check(lib().dh2_tree_get_info(self.handle, C.byref(info)))
+        self.n, self.nclusters, self.depth = info.n, info.nclusters, info.depth
+
+    def export(self):
+        nc, n = self.nclusters, self.n
+        out = {k: np.empty(nc, dtype=np.int32) for k in ("offset", "size", "parent", "son0", "son1", "level")}
+        perm = np.empty(n, dtype=np.int32)
+        lo = np.empty((nc, 3))
+        hi = np.empty((nc, 3))
+        _check(lib().dh2_tree_export(self.handle, _ptr(perm), _ptr(out["offset"]), _ptr(out["size"]),
+                                     _ptr(out["parent"]), _ptr(out["son0"]), _ptr(out["son1"]),
+                                     _ptr(out["level"]), _ptr(lo), _ptr(hi)))
+        out.update(perm=perm, lo=lo, hi=hi)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dh2_free_tree(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    """Recompressed DH^2 matrix on the GPU (owning handle)."""
+
+    def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
+                 qr_fp64=0, workspace_bytes=0, stream=None):
+        opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
+                       workspace_bytes=workspace_bytes)
+        self.precision = precision
+        self.handle = dh2_build_dh2(tree.handle, kappa, m, eta, eps, opts, stream)
+        self.info = self.get_info()
+        self.n = self.info.n
+
+    def get_info(self):
+        info = dh2_matrix_info()
+        _check(lib().dh2_matrix_get_info(self.handle, C.byref(info)))
+        return info
+
+    def stage_ms(self):
+        info = self.get_info()
+        out = {}
+        for i in range(16):
+            name = lib().dh2_stage_name(i)
+            if name is None:
+                break
+            out[name.decode()] = info.stage_ms[i]
+        return out
+
+    def kernel_times(self):
+        """{kernel name: (summed ms, launches)} from the library's CUDA events."""
+        info = self.get_info()
+        out = {}
+        for i in range(16):
+            name = lib().dh2_kernel_name(i)
+            if name is None:
+                break
+            out[name.decode()] = (info.kernel_ms[i], info.kernel_launches[i])
+        return out
+
+    def kernel_work(self):
+        """{kernel name: (kind, amount)}: kind 'flop32' | 'flop64' | 'byte'."""
+        info = self.get_info()
+        kinds = {1: "flop32", 2: "flop64", 3: "byte"}
+        out = {}
+        for i in range(16):
+            name = lib().dh2_kernel_name(i)
+            if name is None:
+                break
+            if info.kernel_work_kind[i] in kinds:
+                out[name.decode()] = (kinds[info.kernel_work_kind[i]], info.kernel_work[i])
+        return out
+
+    def matvec(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        return dh2_matvec(self.handle, x, y, stream)
+
+    def matvec_host(self, x, stream=None):
+        return dh2_matvec_host(self.handle, x, stream)
+
+    def set_timing(self, on):
+        _check(lib().dh2_set_timing(self.handle, 1 if on else 0))
+
+    def directions(self, level):
+        cnt = C.c_int32()
+        ms = C.c_int32()
+        _check(lib().dh2_export_directions(self.handle, level, C.byref(cnt), C.byref(ms), None, None))
+        dirs = np.empty((cnt.value, 3))
+        sd = np.empty(cnt.value, dtype=np.int32)
+        _check(lib().dh2_export_directions(self.handle, level, C.byref(cnt), C.byref(ms), _ptr(dirs), _ptr(sd)))
+        return ms.value, dirs, sd
+
+    def blocks(self):
+        info = self.info
+        adm = np.empty((info.nadm, 3), dtype=np.int32)
+        near = np.empty((info.nnear, 2), dtype=np.int32)
+        active = np.empty(info.npairs, dtype=np.int8)
+        _check(lib().dh2_export_blocks(self.handle, _ptr(adm), _ptr(near), _ptr(active)))
+        return adm, near, active.astype(bool)
+
+    def pair(self, which, tc):
+        k = self.info.k
+        cap = max(4 * k * k, 1)
+        buf = np.empty(2 * cap)
+        r = C.c_int32()
+        c = C.c_int32()
+        _check(lib().dh2_export_pair(self.handle, which, int(tc), _ptr(buf), cap, C.byref(r), C.byref(c)))
+        return buf[: 2 * r.value * c.value].view(np.complex128).reshape(r.value, c.value)
+
+    def ranks(self):
+        rr = np.empty(self.info.npairs, dtype=np.int32)
+        rc = np.empty(self.info.npairs, dtype=np.int32)
+        _check(lib().dh2_export_ranks(self.handle, _ptr(rr), _ptr(rc)))
+        return rr, rc
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dh2_free_matrix(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

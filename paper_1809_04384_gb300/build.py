@@ -1,0 +1,87 @@
+"""Builds libdh2.so in-tree from csrc/*.cu with nvcc for sm_103a (GB300).
+
+Each translation unit is compiled in parallel; the structural unit
+(structure.cu) is compiled with -fmad=false so that its FP64 decisions are
+bit-identical with any IEEE evaluation of the same expressions.
+
+    python -m paper_1809_04384_gb300.build        # or build() from Python
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+OBJ = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libdh2.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+COMMON = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "--extended-lambda",
+          "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall", "-Xcompiler", "-Wno-unused-function"]
+PER_FILE = {"structure.cu": ["-fmad=false"]}
+
+
+def _nvcc():
+    for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found")
+
+
+def sources():
+    return sorted(f for f in os.listdir(CSRC) if f.endswith(".cu"))
+
+
+def _compile(nvcc, src, extra):
+    obj = os.path.join(OBJ, src[:-3] + ".o")
+    cmd = [nvcc, *ARCH, *COMMON, *PER_FILE.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    return obj, r.stderr
+
+
+def _up_to_date(objs_and_srcs):
+    if not os.path.exists(LIB):
+        return False
+    lib_t = os.path.getmtime(LIB)
+    for f in os.listdir(CSRC):
+        if os.path.getmtime(os.path.join(CSRC, f)) > lib_t:
+            return False
+    inc = os.path.join(os.path.dirname(HERE), "include", "dh2.h")
+    if os.path.exists(inc) and os.path.getmtime(inc) > lib_t:
+        return False
+    if os.path.getmtime(__file__) > lib_t:
+        return False
+    return True
+
+
+def build(force: bool = False, verbose: bool = False, extra=()) -> str:
+    """Compiles every CUDA source and links libdh2.so; returns its path."""
+    if not force and _up_to_date(None):
+        return LIB
+    nvcc = _nvcc()
+    os.makedirs(OBJ, exist_ok=True)
+    srcs = sources()
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(lambda s: _compile(nvcc, s, list(extra)), srcs))
+    if verbose:
+        for _, err in results:
+            if err.strip():
+                print(err, file=sys.stderr)
+    objs = [o for o, _ in results]
+    tmp = LIB + ".tmp"
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    extra = [a for a in sys.argv[1:] if a.startswith("-")]
+    print(build(force=True, verbose=True, extra=extra))

@@ -1,0 +1,364 @@
+// extern "C" entry points of libdh2 (declared in include/dh2.h).
+#include <atomic>
+#include <cstring>
+#include <memory>
+#include <string>
+
+#include "numeric.cuh"
+#include "structure.cuh"
+
+struct dh2_tree_s {
+    dh2::Tree tr;
+};
+
+struct dh2_matrix_s {
+    dh2::Tree tr;                       // the matrix's own copy of the tree
+    dh2::Structure st;
+    dh2::HostStructure hs;
+    dh2::BuildParams bp;
+    std::unique_ptr<dh2::NumBase> num;
+    int32_t depth = 0;
+    double structure_ms = 0;
+};
+
+namespace dh2 {
+
+namespace {
+thread_local std::string g_last_error;
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <class F>
+dh2_status guarded(F&& f) {
+    try {
+        f();
+        return DH2_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return DH2_ENOMEM;
+    } catch (const std::exception& e) {
+        set_error(e.what());
+        return DH2_ECUDA;
+    }
+}
+
+template <class T>
+void copy_dbuf(DBuf<T>& dst, const DBuf<T>& src, cudaStream_t s) {
+    dst.alloc(src.n);
+    if (src.n) DH2_CHECK_CUDA(cudaMemcpyAsync(dst.p, src.p, src.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+}
+
+void clone_tree(Tree& dst, const Tree& src, cudaStream_t s) {
+    dst.n = src.n;
+    dst.nv = src.nv;
+    dst.leaf_max = src.leaf_max;
+    dst.point_mode = src.point_mode;
+    dst.nc = src.nc;
+    dst.depth = src.depth;
+    dst.level_start = src.level_start;
+    copy_dbuf(dst.vert, src.vert, s);
+    copy_dbuf(dst.tri, src.tri, s);
+    copy_dbuf(dst.cent, src.cent, s);
+    copy_dbuf(dst.tlo, src.tlo, s);
+    copy_dbuf(dst.thi, src.thi, s);
+    copy_dbuf(dst.perm, src.perm, s);
+    copy_dbuf(dst.offset, src.offset, s);
+    copy_dbuf(dst.size, src.size, s);
+    copy_dbuf(dst.parent, src.parent, s);
+    copy_dbuf(dst.son0, src.son0, s);
+    copy_dbuf(dst.son1, src.son1, s);
+    copy_dbuf(dst.level, src.level, s);
+    copy_dbuf(dst.lo, src.lo, s);
+    copy_dbuf(dst.hi, src.hi, s);
+    copy_dbuf(dst.area, src.area, s);
+    copy_dbuf(dst.x3, src.x3, s);
+    copy_dbuf(dst.x7, src.x7, s);
+}
+
+const char* kStageNames[] = {"structure",      "nearfield",          "analytic",        "basis_weights",
+                             "total_weights_row", "total_weights_col", "truncate_row",   "truncate_col",
+                             "project",        "matvec_plan"};
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static std::atomic<int64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+}  // namespace dh2
+
+using namespace dh2;
+
+extern "C" {
+
+const char* dh2_last_error(void) { return g_last_error.c_str(); }
+
+int64_t dh2_kernel_launches(void) { return g_launches.load(); }
+
+const char* dh2_stage_name(int32_t i) {
+    if (i < 0 || i >= (int32_t)(sizeof(kStageNames) / sizeof(kStageNames[0]))) return nullptr;
+    return kStageNames[i];
+}
+
+const char* dh2_kernel_name(int32_t i) {
+    if (i < 0 || i >= K_COUNT) return nullptr;
+    return kKernelNames[i];
+}
+
+dh2_status dh2_options_default(dh2_options* opt) {
+    if (!opt) {
+        set_error("dh2_options_default: NULL");
+        return DH2_EINVAL;
+    }
+    std::memset(opt, 0, sizeof(*opt));
+    opt->eta1 = 10.0;
+    opt->leaf_max = 32;
+    opt->precision = DH2_MIXED;
+    opt->rank_rule = DH2_RANK_BLOCKREL;
+    opt->qr_fp64 = 0;
+    opt->workspace_bytes = 0;
+    return DH2_OK;
+}
+
+dh2_status dh2_build_tree(const double* vertices, int64_t nv, const int32_t* triangles, int64_t nt,
+                          const dh2_options* opt, void* stream, dh2_tree* out) {
+    return guarded([&] {
+        DH2_REQUIRE(out != nullptr, "dh2_build_tree: out is NULL");
+        *out = nullptr;
+        DH2_REQUIRE(vertices != nullptr && nv > 0, "dh2_build_tree: no vertices");
+        DH2_REQUIRE(nv < (int64_t(1) << 30), "dh2_build_tree: too many vertices");
+        dh2_options o;
+        if (opt) o = *opt; else dh2_options_default(&o);
+        DH2_REQUIRE(o.leaf_max >= 1, "dh2_build_tree: leaf_max must be >= 1");
+        const bool point_mode = triangles == nullptr;
+        const int64_t n = point_mode ? nv : nt;
+        DH2_REQUIRE(n > 0, "dh2_build_tree: no elements");
+        DH2_REQUIRE(n < (int64_t(1) << 29), "dh2_build_tree: too many elements");
+        for (int64_t i = 0; i < 3 * nv; ++i)
+            DH2_REQUIRE(std::isfinite(vertices[i]), "dh2_build_tree: non-finite vertex coordinate");
+        if (!point_mode)
+            for (int64_t i = 0; i < 3 * nt; ++i)
+                DH2_REQUIRE(triangles[i] >= 0 && triangles[i] < nv, "dh2_build_tree: vertex id out of range");
+        cudaStream_t s = as_stream(stream);
+        auto h = std::make_unique<dh2_tree_s>();
+        Tree& tr = h->tr;
+        tr.n = n;
+        tr.nv = nv;
+        tr.leaf_max = o.leaf_max;
+        tr.point_mode = point_mode;
+        tr.vert.alloc(3 * nv);
+        tr.vert.upload(vertices, 3 * nv, s);
+        if (!point_mode) {
+            tr.tri.alloc(3 * nt);
+            tr.tri.upload(triangles, 3 * nt, s);
+        }
+        build_tree_gpu(tr, s);
+        prepare_quadrature(tr, s);
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        *out = h.release();
+    });
+}
+
+dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, double eps,
+                         const dh2_options* opt, void* stream, dh2_matrix* out) {
+    return guarded([&] {
+        DH2_REQUIRE(out != nullptr, "dh2_build_dh2: out is NULL");
+        *out = nullptr;
+        DH2_REQUIRE(tree != nullptr, "dh2_build_dh2: tree is NULL");
+        DH2_REQUIRE(!tree->tr.point_mode, "dh2_build_dh2: a point-mode tree has no Galerkin elements");
+        DH2_REQUIRE(std::isfinite(kappa) && kappa >= 0.0, "dh2_build_dh2: kappa must be >= 0");
+        DH2_REQUIRE(m >= 1 && m <= 8, "dh2_build_dh2: m must be in [1, 8]");
+        DH2_REQUIRE(std::isfinite(eta) && eta > 0.0, "dh2_build_dh2: eta must be > 0");
+        DH2_REQUIRE(std::isfinite(eps) && eps > 0.0, "dh2_build_dh2: eps must be > 0");
+        dh2_options o;
+        if (opt) o = *opt; else dh2_options_default(&o);
+        DH2_REQUIRE(std::isfinite(o.eta1) && o.eta1 > 0.0, "dh2_build_dh2: eta1 must be > 0");
+        DH2_REQUIRE(o.precision == DH2_FP64 || o.precision == DH2_MIXED, "dh2_build_dh2: bad precision");
+        DH2_REQUIRE(o.rank_rule == DH2_RANK_BLOCKREL || o.rank_rule == DH2_RANK_GLOBAL,
+                    "dh2_build_dh2: bad rank rule");
+        cudaStream_t s = as_stream(stream);
+        auto mat = std::make_unique<dh2_matrix_s>();
+        cudaEvent_t e0, e1;
+        DH2_CHECK_CUDA(cudaEventCreate(&e0));
+        DH2_CHECK_CUDA(cudaEventCreate(&e1));
+        DH2_CHECK_CUDA(cudaEventRecord(e0, s));
+        clone_tree(mat->tr, tree->tr, s);
+        build_structure(mat->tr, mat->st, kappa, o.eta1, eta, s);
+        DH2_CHECK_CUDA(cudaEventRecord(e1, s));
+        download_structure(mat->tr, mat->st, mat->hs, s);
+        float ms = 0;
+        DH2_CHECK_CUDA(cudaEventSynchronize(e1));
+        DH2_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        mat->structure_ms = ms;
+        mat->depth = mat->tr.depth;
+        mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.workspace_bytes};
+        mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
+        mat->num->build(s);
+        mat->num->info.stage_ms[ST_STRUCTURE] += ms;
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        *out = mat.release();
+    });
+}
+
+dh2_status dh2_matvec(dh2_matrix mat, const void* x, void* y, int32_t dtype, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && mat->num, "dh2_matvec: matrix is NULL");
+        DH2_REQUIRE(x != nullptr && y != nullptr, "dh2_matvec: NULL vector");
+        DH2_REQUIRE(dtype == DH2_C64 || dtype == DH2_C128, "dh2_matvec: dtype must be DH2_C64 or DH2_C128");
+        DH2_REQUIRE(x != y, "dh2_matvec: x and y must not alias");
+        mat->num->matvec(x, y, dtype, as_stream(stream));
+    });
+}
+
+dh2_status dh2_matvec_host(dh2_matrix mat, const double* x_host, double* y_host, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && mat->num, "dh2_matvec_host: matrix is NULL");
+        DH2_REQUIRE(x_host != nullptr && y_host != nullptr, "dh2_matvec_host: NULL vector");
+        cudaStream_t s = as_stream(stream);
+        const int64_t n = mat->tr.n;
+        DBuf<double> xd(2 * n), yd(2 * n);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(xd.p, x_host, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s));
+        mat->num->matvec(xd.p, yd.p, DH2_C128, s);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(y_host, yd.p, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+dh2_status dh2_set_timing(dh2_matrix mat, int32_t on) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && mat->num, "dh2_set_timing: matrix is NULL");
+        mat->num->set_timing(on != 0);
+    });
+}
+
+dh2_status dh2_sync(void* stream) {
+    return guarded([&] { DH2_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream))); });
+}
+
+dh2_status dh2_tree_get_info(dh2_tree tree, dh2_tree_info* out) {
+    return guarded([&] {
+        DH2_REQUIRE(tree != nullptr && out != nullptr, "dh2_tree_get_info: NULL");
+        out->n = tree->tr.n;
+        out->nclusters = tree->tr.nc;
+        out->depth = tree->tr.depth;
+    });
+}
+
+dh2_status dh2_tree_export(dh2_tree tree, int32_t* perm, int32_t* offset, int32_t* size, int32_t* parent,
+                           int32_t* son0, int32_t* son1, int32_t* level, double* lo, double* hi) {
+    return guarded([&] {
+        DH2_REQUIRE(tree != nullptr, "dh2_tree_export: NULL tree");
+        const Tree& tr = tree->tr;
+        cudaStream_t s = 0;
+        if (perm) tr.perm.download(perm, tr.n, s);
+        if (offset) tr.offset.download(offset, tr.nc, s);
+        if (size) tr.size.download(size, tr.nc, s);
+        if (parent) tr.parent.download(parent, tr.nc, s);
+        if (son0) tr.son0.download(son0, tr.nc, s);
+        if (son1) tr.son1.download(son1, tr.nc, s);
+        if (level) tr.level.download(level, tr.nc, s);
+        std::vector<double> l = tr.lo.to_host(s), h = tr.hi.to_host(s);
+        for (int32_t t = 0; t < tr.nc; ++t)
+            for (int a = 0; a < 3; ++a) {
+                if (lo) lo[3 * t + a] = l[(size_t)a * tr.nc + t];
+                if (hi) hi[3 * t + a] = h[(size_t)a * tr.nc + t];
+            }
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+dh2_status dh2_matrix_get_info(dh2_matrix mat, dh2_matrix_info* out) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && out != nullptr && mat->num, "dh2_matrix_get_info: NULL");
+        std::memset(out, 0, sizeof(*out));
+        const auto& in = mat->num->info;
+        out->n = mat->tr.n;
+        out->depth = mat->tr.depth;
+        out->m = mat->bp.m;
+        out->k = mat->bp.m * mat->bp.m * mat->bp.m;
+        out->nadm = mat->st.nadm;
+        out->nnear = mat->st.nnear;
+        out->npairs = mat->st.ntc;
+        out->nactive = mat->st.nactive;
+        out->near_entries = in.near_entries;
+        out->coupling_entries = in.coupling_entries;
+        out->basis_entries = in.basis_entries;
+        out->matvec_bytes = in.matvec_bytes;
+        out->max_rank_row = in.max_rank_row;
+        out->max_rank_col = in.max_rank_col;
+        out->mean_rank_row = in.mean_rank_row;
+        out->mean_rank_col = in.mean_rank_col;
+        for (int i = 0; i < 16; ++i) {
+            out->stage_ms[i] = in.stage_ms[i];
+            out->kernel_ms[i] = in.kernel_ms[i];
+            out->kernel_launches[i] = in.kernel_launches[i];
+            out->kernel_work[i] = in.kernel_work[i];
+            out->kernel_work_kind[i] = in.kernel_work_kind[i];
+        }
+    });
+}
+
+dh2_status dh2_export_directions(dh2_matrix mat, int32_t level, int32_t* count, int32_t* msplit, double* dirs,
+                                 int32_t* sd) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && count != nullptr, "dh2_export_directions: NULL");
+        const Structure& st = mat->st;
+        DH2_REQUIRE(level >= 0 && level <= st.depth, "dh2_export_directions: level out of range");
+        *count = st.ndir[level];
+        if (msplit) *msplit = st.msplit[level];
+        cudaStream_t s = 0;
+        if (dirs)
+            DH2_CHECK_CUDA(cudaMemcpyAsync(dirs, st.dirs.p + 3 * (size_t)st.dir_off[level],
+                                           3 * st.ndir[level] * sizeof(double), cudaMemcpyDeviceToHost, s));
+        if (sd)
+            DH2_CHECK_CUDA(cudaMemcpyAsync(sd, st.sd.p + st.dir_off[level], st.ndir[level] * sizeof(int32_t),
+                                           cudaMemcpyDeviceToHost, s));
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    });
+}
+
+dh2_status dh2_export_blocks(dh2_matrix mat, int32_t* adm, int32_t* near, int8_t* active) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr, "dh2_export_blocks: NULL");
+        const HostStructure& h = mat->hs;
+        if (adm)
+            for (size_t b = 0; b < h.adm_t.size(); ++b) {
+                adm[3 * b] = h.adm_t[b];
+                adm[3 * b + 1] = h.adm_s[b];
+                adm[3 * b + 2] = h.adm_c[b];
+            }
+        if (near)
+            for (size_t b = 0; b < h.near_t.size(); ++b) {
+                near[2 * b] = h.near_t[b];
+                near[2 * b + 1] = h.near_s[b];
+            }
+        if (active)
+            for (size_t tc = 0; tc < h.aidx.size(); ++tc) active[tc] = h.aidx[tc] >= 0 ? 1 : 0;
+    });
+}
+
+dh2_status dh2_export_pair(dh2_matrix mat, int32_t which, int64_t tc, double* out, int64_t cap, int32_t* rows,
+                           int32_t* cols) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && mat->num && out != nullptr && rows != nullptr && cols != nullptr,
+                    "dh2_export_pair: NULL");
+        mat->num->export_pair(which, tc, out, cap, rows, cols, 0);
+    });
+}
+
+dh2_status dh2_export_ranks(dh2_matrix mat, int32_t* rank_row, int32_t* rank_col) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && mat->num, "dh2_export_ranks: NULL");
+        mat->num->export_ranks(rank_row, rank_col, 0);
+    });
+}
+
+void dh2_free_tree(dh2_tree tree) { delete tree; }
+void dh2_free_matrix(dh2_matrix mat) { delete mat; }
+
+}  // extern "C"

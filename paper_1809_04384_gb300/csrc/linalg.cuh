@@ -1,0 +1,362 @@
+// CTA-level complex linear algebra used by the recompression kernels:
+//   * cx<T>           complex scalar (T = float or double), interleaved storage
+//   * cta_gemm        C = A * B with functor operands (operands may be generated
+//                     on the fly, e.g. the couplings S_b), 256 threads
+//   * kron_apply      X * (Ex (x) Ey (x) Ez) or X * (...)^* with the transfer
+//                     matrices kept as three m x m factors
+//   * tsqr_chunk      Householder update of an upper-triangular R (global) by
+//                     a block of extra rows held in shared memory
+//   * herm_jacobi     parallel cyclic Jacobi eigensolver for Hermitian matrices
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dh2 {
+
+template <class T>
+struct __align__(2 * sizeof(T)) cx {
+    T x, y;
+};
+
+template <class T> __device__ __forceinline__ cx<T> mk(T a, T b) { return cx<T>{a, b}; }
+template <class T> __device__ __forceinline__ cx<T> operator+(cx<T> a, cx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __device__ __forceinline__ cx<T> operator-(cx<T> a, cx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <class T> __device__ __forceinline__ cx<T> operator*(cx<T> a, cx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T> __device__ __forceinline__ cx<T> operator*(T s, cx<T> a) { return {s * a.x, s * a.y}; }
+template <class T> __device__ __forceinline__ cx<T> conj(cx<T> a) { return {a.x, -a.y}; }
+template <class T> __device__ __forceinline__ T abs2(cx<T> a) { return a.x * a.x + a.y * a.y; }
+// acc += a * b
+template <class T> __device__ __forceinline__ void fma_cx(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(-a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+template <class T> __device__ __forceinline__ void fma_cjx(cx<T>& acc, cx<T> a, cx<T> b) {
+    acc.x = fma(a.x, b.x, acc.x);
+    acc.x = fma(a.y, b.y, acc.x);
+    acc.y = fma(a.x, b.y, acc.y);
+    acc.y = fma(-a.y, b.x, acc.y);
+}
+template <class T> __device__ __forceinline__ cx<T> zero() { return cx<T>{T(0), T(0)}; }
+
+template <class T>
+__device__ __forceinline__ cx<T> shfl_xor(cx<T> v, int o) {
+    return cx<T>{__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o)};
+}
+template <class T>
+__device__ __forceinline__ cx<T> warp_sum(cx<T> v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = v + shfl_xor(v, o);
+    return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_sum_r(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over the CTA (all threads receive the result); smem: >= 32 T
+template <class T>
+__device__ T block_sum(T v, T* smem) {
+    v = warp_sum_r(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    __syncthreads();
+    if (lane == 0) smem[w] = v;
+    __syncthreads();
+    T r = 0;
+    for (int i = 0; i < nw; ++i) r += smem[i];
+    __syncthreads();
+    return r;
+}
+
+// --------------------------------------------------------------------------- operands
+
+// dense row-major complex matrix view (optionally conjugated and/or transposed)
+template <class T>
+struct Dense {
+    const cx<T>* p;
+    int64_t ld;
+    bool trans, conjg;
+    __device__ __forceinline__ cx<T> operator()(int i, int j) const {
+        cx<T> v = trans ? p[(int64_t)j * ld + i] : p[(int64_t)i * ld + j];
+        return conjg ? conj(v) : v;
+    }
+};
+
+// dense view of a matrix of another precision, converted on load
+template <class T, class U>
+struct DenseCvt {
+    const cx<U>* p;
+    int64_t ld;
+    bool trans, conjg;
+    __device__ __forceinline__ cx<T> operator()(int i, int j) const {
+        cx<U> v = trans ? p[(int64_t)j * ld + i] : p[(int64_t)i * ld + j];
+        return cx<T>{T(v.x), conjg ? -T(v.y) : T(v.y)};
+    }
+};
+
+// --------------------------------------------------------------------------- CTA GEMM
+
+// C(i,j) = sum_k A(i,k) B(k,j) for 0<=i<M, 0<=j<N; `store(i, j, value)` is called
+// once per output.  256 threads, 64 x 64 output tiles, 4 x 4 per thread.
+// smem: 2 * 64 * 8 cx<T> = 2 KB (T=float) / 4 KB (double).
+// one staging buffer per element type and kernel, shared by every cta_gemm call
+template <class T>
+__device__ __forceinline__ cx<T>* gemm_smem() {
+    __shared__ cx<T> buf[2 * 8 * 64];
+    return buf;
+}
+
+template <class T, class FA, class FB, class FS>
+__device__ void cta_gemm(int M, int N, int K, const FA& A, const FB& B, const FS& store) {
+    constexpr int BM = 64, BN = 64, BK = 8;
+    cx<T> (*sA)[BM] = reinterpret_cast<cx<T> (*)[BM]>(gemm_smem<T>());
+    cx<T> (*sB)[BN] = reinterpret_cast<cx<T> (*)[BN]>(gemm_smem<T>() + BK * BM);
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;    // 16 x 16 threads
+    for (int i0 = 0; i0 < M; i0 += BM) {
+        for (int j0 = 0; j0 < N; j0 += BN) {
+            cx<T> acc[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+            for (int k0 = 0; k0 < K; k0 += BK) {
+                // 512 elements per tile, 2 per thread
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    int e = tid + r * 256;
+                    int kk = e / BM, ii = e % BM;
+                    int gi = i0 + ii, gk = k0 + kk;
+                    sA[kk][ii] = (gi < M && gk < K) ? A(gi, gk) : zero<T>();
+                    int jj = e % BN;
+                    int gj = j0 + jj;
+                    sB[kk][jj] = (gj < N && gk < K) ? B(gk, gj) : zero<T>();
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    cx<T> av[4], bv[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) av[a] = sA[kk][ty + 16 * a];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) bv[b] = sB[kk][tx + 16 * b];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int b = 0; b < 4; ++b) fma_cx(acc[a][b], av[a], bv[b]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
+                    if (gi < M && gj < N) store(gi, gj, acc[a][b]);
+                }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------- Kronecker transfer
+
+// out[r][nu] = sum_nu' X[r][nu'] E[nu'][nu]          (adjoint = false)
+// out[r][nu'] = sum_nu X[r][nu] conj(E[nu'][nu])      (adjoint = true)
+// with E[nu'][nu] = Ex[nu'x][nux] Ey[nu'y][nuy] Ez[nu'z][nuz], nu = nx + m ny + m^2 nz.
+// fac: 3 consecutive m*m row-major factors (x, y, z).  `buf`: 2 * k cx<T> of shared
+// memory per row in flight (rows are processed one at a time by the whole CTA).
+template <class T, class FX, class FO>
+__device__ void kron_apply(int rows, int m, const cx<T>* fac, bool adjoint, const FX& X,
+                           const FO& out, cx<T>* buf) {
+    const int k = m * m * m, mm = m * m;
+    cx<T>* b0 = buf;
+    cx<T>* b1 = buf + k;
+    for (int r = 0; r < rows; ++r) {
+        for (int v = threadIdx.x; v < k; v += blockDim.x) b0[v] = X(r, v);
+        __syncthreads();
+        // three passes: axis x (stride 1), y (stride m), z (stride m^2)
+        for (int axis = 0; axis < 3; ++axis) {
+            const cx<T>* F = fac + axis * mm;
+            const int stride = axis == 0 ? 1 : (axis == 1 ? m : mm);
+            cx<T>* src = (axis & 1) ? b1 : b0;
+            cx<T>* dst = (axis & 1) ? b0 : b1;
+            for (int v = threadIdx.x; v < k; v += blockDim.x) {
+                int a = (v / stride) % m;          // output index along this axis
+                int base = v - a * stride;
+                cx<T> acc = zero<T>();
+                for (int q = 0; q < m; ++q) {
+                    cx<T> xv = src[base + q * stride];
+                    // forward: sum_q X[q] F[q][a];  adjoint: sum_q X[q] conj(F[a][q])
+                    cx<T> f = adjoint ? conj(F[a * m + q]) : F[q * m + a];
+                    fma_cx(acc, xv, f);
+                }
+                dst[v] = acc;
+            }
+            __syncthreads();
+        }
+        // after three passes the result is in b1
+        for (int v = threadIdx.x; v < k; v += blockDim.x) out(r, v, b1[v]);
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------- Householder TSQR
+
+// R (k x k, row-major, global, upper triangular) <- R-factor of [R; W] where W is
+// the h x k block held column-major in shared memory (ldw = rows per column,
+// rows >= h are zero).  Column reflectors follow LAPACK's xLARFG convention
+// (real beta); W is overwritten.  blockDim.x must be a multiple of 32; each lane
+// owns rows lane + 32 q, q < RPL.
+template <class T, int RPL>
+__device__ void tsqr_chunk(int k, cx<T>* R, cx<T>* W, cx<T>* s_tau, int* s_skip) {
+    constexpr int LDW = 32 * RPL;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int j = 0; j < k; ++j) {
+        if (warp == 0) {
+            cx<T>* wj = W + (int64_t)j * LDW;
+            const cx<T> al = R[(int64_t)j * k + j];   // read before the shuffles below
+            T xn2 = 0;
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) xn2 += abs2(wj[lane + 32 * q]);
+            xn2 = warp_sum_r(xn2);
+            if (xn2 == T(0)) {
+                if (lane == 0) *s_skip = 1;
+            } else {
+                T beta = -copysign(sqrt(abs2(al) + xn2), al.x);
+                cx<T> tauc = mk<T>((beta - al.x) / beta, al.y / beta);
+                cx<T> d = mk<T>(al.x - beta, al.y);
+                T dn = T(1) / abs2(d);
+                cx<T> sc = mk<T>(d.x * dn, -d.y * dn);   // 1 / (alpha - beta)
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) wj[lane + 32 * q] = wj[lane + 32 * q] * sc;
+                if (lane == 0) {
+                    R[(int64_t)j * k + j] = mk<T>(beta, T(0));
+                    *s_tau = tauc;
+                    *s_skip = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (!*s_skip) {
+            const cx<T> tauc = *s_tau;
+            const cx<T>* v = W + (int64_t)j * LDW;
+            cx<T> vr[RPL];
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) vr[q] = v[lane + 32 * q];
+            for (int l = j + 1 + warp; l < k; l += nwarps) {
+                cx<T>* wl = W + (int64_t)l * LDW;
+                const cx<T> rjl = R[(int64_t)j * k + l];   // every lane reads before lane 0 writes
+                cx<T> s = zero<T>();
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) fma_cjx(s, vr[q], wl[lane + 32 * q]);
+                s = warp_sum(s);
+                cx<T> w = rjl + s;
+                cx<T> tw = tauc * w;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) wl[lane + 32 * q] = wl[lane + 32 * q] - vr[q] * tw;
+                if (lane == 0) R[(int64_t)j * k + l] = rjl - tw;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------------------- Hermitian Jacobi
+
+// Parallel cyclic Jacobi (circle schedule) for a Hermitian n x n matrix M
+// (row-major, ld = n, shared or global memory).  On return the diagonal holds
+// the eigenvalues and U (n x n, ld = n) the eigenvectors as columns.  rot:
+// scratch of n/2+1 entries for rotation data.  Returns the number of sweeps.
+template <class T>
+struct JRot {
+    int p, q;
+    T c, s;
+    cx<T> e;
+};
+
+template <class T>
+__device__ int herm_jacobi(int n, cx<T>* M, cx<T>* U, JRot<T>* rot, T* red, int max_sweeps,
+                           T tol) {
+    const int np = n + (n & 1);
+    const int half = np / 2;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+        U[idx] = (idx / n == idx % n) ? mk<T>(T(1), T(0)) : zero<T>();
+    __syncthreads();
+    T fro = 0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) fro += abs2(M[idx]);
+    fro = block_sum(fro, red);
+    if (n <= 1 || fro == T(0)) return 0;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        T off = 0;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+            if (idx / n != idx % n) off += abs2(M[idx]);
+        off = block_sum(off, red);
+        if (off <= tol * tol * fro) break;
+        for (int r = 0; r < np - 1; ++r) {
+            for (int pi = threadIdx.x; pi < half; pi += blockDim.x) {
+                int p, q;
+                if (pi == 0) {
+                    p = r;
+                    q = np - 1;
+                } else {
+                    p = (r + pi) % (np - 1);
+                    q = (r - pi + np - 1) % (np - 1);
+                }
+                JRot<T> j;
+                j.p = p;
+                j.q = q;
+                j.c = 1;
+                j.s = 0;
+                j.e = mk<T>(T(1), T(0));
+                if (p < n && q < n) {
+                    cx<T> apq = M[p * n + q];
+                    T a = sqrt(abs2(apq));
+                    if (a > T(0)) {
+                        j.e = mk<T>(apq.x / a, apq.y / a);
+                        T zeta = (M[q * n + q].x - M[p * n + p].x) / (T(2) * a);
+                        T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+                        j.c = T(1) / sqrt(T(1) + t * t);
+                        j.s = t * j.c;
+                    }
+                }
+                rot[pi] = j;
+            }
+            __syncthreads();
+            // columns of M and U
+            for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
+                const JRot<T> j = rot[idx / n];
+                const int row = idx % n;
+                if (j.p >= n || j.q >= n || j.s == T(0)) continue;
+                cx<T> ce = conj(j.e);
+                cx<T> mp = M[row * n + j.p], mq = M[row * n + j.q];
+                M[row * n + j.p] = j.c * mp - j.s * (ce * mq);
+                M[row * n + j.q] = j.s * mp + j.c * (ce * mq);
+                cx<T> up = U[row * n + j.p], uq = U[row * n + j.q];
+                U[row * n + j.p] = j.c * up - j.s * (ce * uq);
+                U[row * n + j.q] = j.s * up + j.c * (ce * uq);
+            }
+            __syncthreads();
+            // rows of M
+            for (int idx = threadIdx.x; idx < half * n; idx += blockDim.x) {
+                const JRot<T> j = rot[idx / n];
+                const int col = idx % n;
+                if (j.p >= n || j.q >= n || j.s == T(0)) continue;
+                cx<T> mp = M[j.p * n + col], mq = M[j.q * n + col];
+                M[j.p * n + col] = j.c * mp - j.s * (j.e * mq);
+                M[j.q * n + col] = j.s * mp + j.c * (j.e * mq);
+            }
+            __syncthreads();
+        }
+    }
+    return sweep;
+}
+
+}  // namespace dh2

@@ -1,0 +1,1785 @@
+// Numeric stages of the hybrid DH^2 construction and the DH^2 matvec.
+//
+//   analytic stage (Section 2): Chebyshev nodes in the padded boxes, leaf bases
+//     v_{tc,i nu} = int phi_i exp(i kappa <x,c>) L_{t,nu}(x) (3-point rule),
+//     transfer matrices E_{t'c} (Eq. nested_apx) as three m x m factors, the
+//     nearfield blocks (Eq. 2), couplings S_b = g_c(xi_t, xi_s) generated where
+//     they are used (never stored);
+//   Section 3.2: basis weights R (bottom-up QR), block weights 1/|G_b|_F, total
+//     weights Z-hat (top-down QR of the stacked blocks, rows and columns),
+//     truncation (bottom-up SVD: Gram matrix + Hermitian Jacobi in FP64),
+//     projection S~_b = C_tc S_b C_sc^* (Lemma "Projections");
+//   matvec: forward transform (column basis), couplings, backward transform
+//     (row basis), nearfield (derived from Eq. nested and Eq. vsw).
+//
+// T is the working precision: float for DH2_MIXED, double for DH2_FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "numeric.cuh"
+
+namespace dh2 {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kThreads = 256;
+
+// ----------------------------------------------------------------------------- math wrappers
+
+__device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
+
+// exp(i kappa r) / (4 pi r) for a difference vector d
+template <class T>
+__device__ __forceinline__ cx<T> helmholtz_d(T dx, T dy, T dz, T kappa) {
+    T r2 = dx * dx + dy * dy + dz * dz;
+    T r = sqrt(r2);
+    T s, c;
+    sc(kappa * r, &s, &c);
+    T f = T(1) / (T(4.0 * kPi) * r);
+    return cx<T>{c * f, s * f};
+}
+
+// Lagrange polynomial l_j of the m nodes xi at x (product form)
+__device__ __forceinline__ double lagrange1(const double* xi, int m, int j, double x) {
+    double v = 1.0;
+    for (int i = 0; i < m; ++i)
+        if (i != j) v *= (x - xi[i]) / (xi[j] - xi[i]);
+    return v;
+}
+
+// ----------------------------------------------------------------------------- analytic stage
+
+// nodes[t][a][j] = mid_a + half_a cos(pi (2j+1) / (2m)), half padded to >= 1e-3 max half
+__global__ void k_cheb_nodes(const double* __restrict__ lo, const double* __restrict__ hi, int32_t nc,
+                             int m, double* nodes) {
+    int32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc) return;
+    double mid[3], half[3], hmax = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        mid[a] = (lo[a * nc + t] + hi[a * nc + t]) * 0.5;
+        half[a] = (hi[a * nc + t] - lo[a * nc + t]) * 0.5;
+        hmax = fmax(hmax, half[a]);
+    }
+    for (int a = 0; a < 3; ++a) {
+        double h = fmax(half[a], 1e-3 * hmax);
+        for (int j = 0; j < m; ++j)
+            nodes[((int64_t)t * 3 + a) * m + j] = mid[a] + h * cos(kPi * (2 * j + 1) / (2.0 * m));
+    }
+}
+
+struct LeafTask {
+    int32_t t, gdir, off, rows;
+    int64_t voff;
+};
+
+// V_tc for leaf pairs: v_{i nu} = |T_i|/3 sum_q exp(i kappa <x_q, c>) L_{t,nu}(x_q)  (FP64, stored as T)
+template <class T>
+__global__ void k_leaf_basis(const LeafTask* __restrict__ tasks, const int32_t* __restrict__ perm,
+                             const double* __restrict__ area, const double* __restrict__ x3,
+                             const double* __restrict__ nodes, const double* __restrict__ dirs,
+                             int m, double kappa, cx<T>* V) {
+    const LeafTask tk = tasks[blockIdx.x];
+    const int k = m * m * m;
+    __shared__ double xi[3][8];
+    if (threadIdx.x < 3 * m) xi[threadIdx.x / m][threadIdx.x % m] = nodes[((int64_t)tk.t * 3) * m + threadIdx.x];
+    __syncthreads();
+    const double c0 = dirs[3 * tk.gdir], c1 = dirs[3 * tk.gdir + 1], c2 = dirs[3 * tk.gdir + 2];
+    for (int idx = threadIdx.x; idx < tk.rows * k; idx += blockDim.x) {
+        int i = idx / k, nu = idx % k;
+        int nx = nu % m, ny = (nu / m) % m, nz = nu / (m * m);
+        int e = perm[tk.off + i];
+        double w = area[e] / 3.0;
+        double ar = 0.0, ai = 0.0;
+        for (int q = 0; q < 3; ++q) {
+            const double* x = x3 + ((int64_t)e * 3 + q) * 3;
+            double L = lagrange1(xi[0], m, nx, x[0]) * lagrange1(xi[1], m, ny, x[1]) *
+                       lagrange1(xi[2], m, nz, x[2]);
+            double s, c;
+            sincos(kappa * (x[0] * c0 + x[1] * c1 + x[2] * c2), &s, &c);
+            ar += c * L;
+            ai += s * L;
+        }
+        V[tk.voff + idx] = cx<T>{T(w * ar), T(w * ai)};
+    }
+}
+
+struct TransferTask {
+    int32_t t, ts, gdir, gdir_son;
+    int64_t eoff;
+};
+
+// factors of E_{t'c}: E_a[nu'][nu] = exp(i kappa xi_{t',a,nu'} (c_a - c'_a)) l_{t,a,nu}(xi_{t',a,nu'})
+template <class T>
+__global__ void k_transfer(const TransferTask* __restrict__ tasks, const double* __restrict__ nodes,
+                           const double* __restrict__ dirs, int m, double kappa, cx<T>* E) {
+    const TransferTask tk = tasks[blockIdx.x];
+    const int mm = m * m;
+    for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+        int a = idx / mm, r = idx % mm;
+        int nup = r / m, nu = r % m;
+        const double* xt = nodes + ((int64_t)tk.t * 3 + a) * m;
+        double xs = nodes[((int64_t)tk.ts * 3 + a) * m + nup];
+        double dc = dirs[3 * tk.gdir + a] - dirs[3 * tk.gdir_son + a];
+        double L = lagrange1(xt, m, nu, xs);
+        double s, c;
+        sincos(kappa * xs * dc, &s, &c);
+        E[tk.eoff + idx] = cx<T>{T(c * L), T(s * L)};
+    }
+}
+
+// ----------------------------------------------------------------------------- nearfield
+
+struct NearSeg {
+    int32_t rows, cols, roff, coff;   // cluster-order ranges
+    int32_t ld;                       // panel width of the row leaf
+    int32_t pad;
+    int64_t poff;                     // panel offset of (row 0, first column of this segment)
+};
+
+// split of an FP64 coordinate into float hi + lo (for differences in FP32)
+__global__ void k_split_quad(const int32_t* __restrict__ perm, const double* __restrict__ x3, int64_t n,
+                             float* qh, float* ql) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * 9) return;
+    int64_t r = idx / 9, w = idx % 9;
+    double v = x3[(int64_t)perm[r] * 9 + w];
+    float h = (float)v;
+    qh[idx] = h;
+    ql[idx] = (float)(v - (double)h);
+}
+
+__global__ void k_cluster_quad(const int32_t* __restrict__ perm, const double* __restrict__ x3, int64_t n,
+                               double* out) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * 9) return;
+    int64_t r = idx / 9, w = idx % 9;
+    out[idx] = x3[(int64_t)perm[r] * 9 + w];
+}
+
+template <class T>
+struct QuadRows;   // quadrature nodes in cluster order
+
+template <>
+struct QuadRows<float> {
+    const float* h;
+    const float* l;
+    __device__ __forceinline__ void diff(int64_t r, int p, int64_t c, int q, float* d) const {
+        for (int a = 0; a < 3; ++a) {
+            int64_t i = r * 9 + p * 3 + a, j = c * 9 + q * 3 + a;
+            d[a] = (h[i] - h[j]) + (l[i] - l[j]);
+        }
+    }
+};
+template <>
+struct QuadRows<double> {
+    const double* x;      // [n][3][3] cluster order
+    __device__ __forceinline__ void diff(int64_t r, int p, int64_t c, int q, double* d) const {
+        for (int a = 0; a < 3; ++a) d[a] = x[r * 9 + p * 3 + a] - x[c * 9 + q * 3 + a];
+    }
+};
+
+__constant__ double c_w7[7];
+
+template <class T>
+__global__ void k_nearfield(const NearSeg* __restrict__ segs, QuadRows<T> qr,
+                            const int32_t* __restrict__ perm, const double* __restrict__ area,
+                            const double* __restrict__ x3, const double* __restrict__ x7, double kappa,
+                            cx<T>* P) {
+    const NearSeg sg = segs[blockIdx.x];
+    const T kap = (T)kappa;
+    for (int idx = threadIdx.x; idx < sg.rows * sg.cols; idx += blockDim.x) {
+        int i = idx / sg.cols, j = idx % sg.cols;
+        int64_t r = sg.roff + i, c = sg.coff + j;
+        int e = perm[r], f = perm[c];
+        cx<T> v;
+        if (e != f) {
+            T acc_r = 0, acc_i = 0;
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    T d[3];
+                    qr.diff(r, p, c, q, d);
+                    cx<T> g = helmholtz_d<T>(d[0], d[1], d[2], kap);
+                    acc_r += g.x;
+                    acc_i += g.y;
+                }
+            T w = T(area[e] / 3.0 * (area[f] / 3.0));
+            v = cx<T>{w * acc_r, w * acc_i};
+        } else {
+            // 7-point rule in x against the 3-point rule in y, FP64
+            double ar = 0, ai = 0;
+            for (int p = 0; p < 7; ++p)
+                for (int q = 0; q < 3; ++q) {
+                    const double* xp = x7 + ((int64_t)e * 7 + p) * 3;
+                    const double* yq = x3 + ((int64_t)e * 3 + q) * 3;
+                    cx<double> g = helmholtz_d<double>(xp[0] - yq[0], xp[1] - yq[1], xp[2] - yq[2], kappa);
+                    double w = c_w7[p] / 3.0;
+                    ar += w * g.x;
+                    ai += w * g.y;
+                }
+            double a2 = area[e] * area[e];
+            v = cx<T>{T(a2 * ar), T(a2 * ai)};
+        }
+        P[sg.poff + (int64_t)i * sg.ld + j] = v;
+    }
+}
+
+// ----------------------------------------------------------------------------- coupling generator
+
+// S_b[nu][mu] = g_c(xi_{t,nu}, xi_{s,mu}) from per-axis tables in shared memory:
+// D[a][i][j] = xi_{t,a,i} - xi_{s,a,j} and P[a][i][j] = D[a][i][j] c_a (evaluated in FP64).
+template <class T>
+struct SGen {
+    const T* D;
+    const T* P;
+    int m;
+    T kappa;
+    __device__ __forceinline__ cx<T> operator()(int nu, int mu) const {
+        const int mm = m * m;
+        int nx = nu % m, ny = (nu / m) % m, nz = nu / mm;
+        int mx = mu % m, my = (mu / m) % m, mz = mu / mm;
+        int ix = nx * m + mx, iy = mm + ny * m + my, iz = 2 * mm + nz * m + mz;
+        T dx = D[ix], dy = D[iy], dz = D[iz];
+        T r = sqrt(dx * dx + dy * dy + dz * dz);
+        T ph = kappa * (r - (P[ix] + P[iy] + P[iz]));
+        T s, c;
+        sc(ph, &s, &c);
+        T f = T(1) / (T(4.0 * kPi) * r);
+        return cx<T>{c * f, s * f};
+    }
+};
+
+template <class T>
+__device__ void load_sgen_tables(int32_t t, int32_t s, const double* __restrict__ cdir,
+                                 const double* __restrict__ nodes, int m, T* D, T* P) {
+    const int mm = m * m;
+    for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
+        int a = idx / mm, r = idx % mm, i = r / m, j = r % m;
+        double d = nodes[((int64_t)t * 3 + a) * m + i] - nodes[((int64_t)s * 3 + a) * m + j];
+        D[idx] = (T)d;
+        P[idx] = (T)(d * cdir[a]);
+    }
+    __syncthreads();
+}
+
+// ----------------------------------------------------------------------------- stacked rows
+
+struct BlockRowTask {
+    int32_t b;         // admissible block id
+    int32_t other;     // active pair whose weight R multiplies S (rows pass: s, cols pass: t)
+    int32_t own;       // active pair of the other side (rows pass: t; for |G_b|)
+    int32_t pad;
+    int64_t dst;       // element offset of the first row in the stack
+};
+
+// rows pass: R_sc S_b^*, then |G_b|_F = |R_tc S_b R_sc^*|_F, rows scaled by 1/|G_b|.
+// cols pass: R_tc S_b / |G_b|.
+template <class T>
+__global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows_pass,
+                               const int32_t* __restrict__ adm_t, const int32_t* __restrict__ adm_s,
+                               const int32_t* __restrict__ adm_c, const int32_t* __restrict__ tc_level,
+                               const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
+                               const double* __restrict__ nodes, int m, double kappa,
+                               const cx<T>* __restrict__ R, const int64_t* __restrict__ roff,
+                               const int32_t* __restrict__ rrows, double* bnorm, cx<T>* stack) {
+    extern __shared__ unsigned char smraw[];
+    T* D = reinterpret_cast<T*>(smraw);
+    T* P = D + 3 * m * m;
+    __shared__ T red[32];
+    const BlockRowTask tk = tasks[blockIdx.x];
+    const int k = m * m * m;
+    const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
+    const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
+    load_sgen_tables<T>(t, s, cd, nodes, m, D, P);
+    SGen<T> S{D, P, m, (T)kappa};
+    const int ro = rrows[tk.other];
+    const cx<T>* Ro = R + roff[tk.other];
+    cx<T>* out = stack + tk.dst;
+    if (rows_pass) {
+        // out[i][nu] = sum_mu R_s[i][mu] conj(S[nu][mu])
+        cta_gemm<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+                    [&](int mu, int nu) { return conj(S(nu, mu)); },
+                    [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
+        __syncthreads();
+        // |R_t S R_s^*|_F^2 = sum |(R_t Y)_{i' i}|^2 with Y[nu][i] = conj(out[i][nu])
+        const int rt = rrows[tk.own];
+        const cx<T>* Rt = R + roff[tk.own];
+        T acc = 0;
+        T* accp = &acc;
+        cta_gemm<T>(rt, ro, k, Dense<T>{Rt, k, false, false}, Dense<T>{out, k, true, true},
+                    [=](int, int, cx<T> v) { *accp += abs2(v); });
+        T nrm2 = block_sum(acc, red);
+        T nrm = sqrt(nrm2);
+        if (threadIdx.x == 0) bnorm[tk.b] = (double)nrm;
+        T sc_ = nrm > T(0) ? T(1) / nrm : T(0);
+        for (int idx = threadIdx.x; idx < ro * k; idx += blockDim.x) out[idx] = sc_ * out[idx];
+    } else {
+        const T sc_ = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
+        // out[i][nu] = sum_mu R_t[i][mu] S[mu][nu] / |G_b|
+        cta_gemm<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+                    [&](int mu, int nu) { return S(mu, nu); },
+                    [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = sc_ * v; });
+    }
+}
+
+struct KronTask {
+    int64_t src;       // element offset of the first input row
+    int64_t fac;       // element offset of the 3 m x m factors
+    int64_t dst;       // element offset of the first output row
+    int32_t rows;
+    int32_t adjoint;
+};
+
+// out rows = in rows * E (or * E^*), computed in TC, stored as TO
+template <class TI, class TF, class TC, class TO>
+__global__ void k_kron(const KronTask* __restrict__ tasks, int m, const cx<TI>* __restrict__ in,
+                       const cx<TF>* __restrict__ fac, cx<TO>* out) {
+    extern __shared__ unsigned char smraw[];
+    cx<TC>* buf = reinterpret_cast<cx<TC>*>(smraw);
+    const KronTask tk = tasks[blockIdx.x];
+    const int k = m * m * m;
+    cx<TC>* F = buf + 2 * k;
+    for (int i = threadIdx.x; i < 3 * m * m; i += blockDim.x) {
+        cx<TF> f = fac[tk.fac + i];
+        F[i] = cx<TC>{TC(f.x), TC(f.y)};
+    }
+    __syncthreads();
+    const cx<TI>* X = in + tk.src;
+    cx<TO>* O = out + tk.dst;
+    kron_apply<TC>(tk.rows, m, F, tk.adjoint != 0,
+                   [&](int r, int v) {
+                       cx<TI> x = X[(int64_t)r * k + v];
+                       return cx<TC>{TC(x.x), TC(x.y)};
+                   },
+                   [&](int r, int v, cx<TC> val) { O[(int64_t)r * k + v] = cx<TO>{TO(val.x), TO(val.y)}; },
+                   buf);
+}
+
+// ----------------------------------------------------------------------------- TSQR
+
+struct QRTask {
+    int64_t src;       // element offset of the first stacked row
+    int64_t dst;       // element offset of the output rows
+    int32_t nrows;
+    int32_t rout;      // min(nrows, k) rows written to dst
+};
+
+// R-factor of the stacked rows: R scratch (k x k, TQ) per CTA slot, chunks of 32*RPL rows
+template <class TS, class TQ, int RPL>
+__global__ void k_tsqr(const QRTask* __restrict__ tasks, int k, const cx<TS>* __restrict__ src,
+                       cx<TQ>* scratch, cx<TS>* dst) {
+    extern __shared__ unsigned char smraw[];
+    constexpr int LDW = 32 * RPL;
+    cx<TQ>* W = reinterpret_cast<cx<TQ>*>(smraw);
+    __shared__ cx<TQ> s_tau;
+    __shared__ int s_skip;
+    const QRTask tk = tasks[blockIdx.x];
+    cx<TQ>* R = scratch + (int64_t)blockIdx.x * k * k;
+    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) R[idx] = zero<TQ>();
+    __syncthreads();
+    const cx<TS>* S = src + tk.src;
+    for (int r0 = 0; r0 < tk.nrows; r0 += LDW) {
+        const int h = min(LDW, tk.nrows - r0);
+        for (int idx = threadIdx.x; idx < LDW * k; idx += blockDim.x) {
+            int i = idx / k, l = idx % k;     // row-major read, column-major store
+            cx<TQ> v = zero<TQ>();
+            if (i < h) {
+                cx<TS> u = S[(int64_t)(r0 + i) * k + l];
+                v = cx<TQ>{TQ(u.x), TQ(u.y)};
+            }
+            W[(int64_t)l * LDW + i] = v;
+        }
+        __syncthreads();
+        tsqr_chunk<TQ, RPL>(k, R, W, &s_tau, &s_skip);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < tk.rout * k; idx += blockDim.x) {
+        cx<TQ> v = R[idx];
+        dst[tk.dst + idx] = cx<TS>{TS(v.x), TS(v.y)};
+    }
+}
+
+// ----------------------------------------------------------------------------- truncation (FP64)
+
+struct TruncTask {
+    int64_t vsrc;      // leaf: V (T) element offset; non-leaf: V-hat scratch (double) offset
+    int64_t z;         // Z-hat element offset
+    int64_t q;         // output Q / Q-hat (T), row pitch qld
+    int64_t c;         // output C (double and T copies), pitch k
+    int64_t sig;       // singular values (double)
+    int64_t ascratch;  // A = V Z^* scratch (double complex)
+    int32_t rows, rz, qld, leaf, a, pad;
+};
+
+template <class T, class FV>
+__device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<T>* __restrict__ Z,
+                              cx<double>* Ascr, cx<double>* M, cx<double>* U, JRot<double>* rot,
+                              double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct,
+                              double* sig, int32_t* rank, int* s_order, double* s_lam) {
+    __shared__ double red[32];
+    __shared__ int s_rank;
+    const int n = tk.rows, rz = tk.rz;
+    const cx<T>* Zt = Z + tk.z;
+    // A = V Z^*  (n x rz)
+    cta_gemm<double>(n, rz, k, V, [&](int nu, int j) {
+                         cx<T> z = Zt[(int64_t)j * k + nu];
+                         return cx<double>{double(z.x), -double(z.y)};
+                     },
+                     [&](int i, int j, cx<double> v) { Ascr[(int64_t)i * rz + j] = v; });
+    __syncthreads();
+    // M = A A^*  (n x n)
+    cta_gemm<double>(n, n, rz, Dense<double>{Ascr, rz, false, false}, Dense<double>{Ascr, rz, true, true},
+                     [&](int i, int j, cx<double> v) { M[(int64_t)i * n + j] = v; });
+    __syncthreads();
+    herm_jacobi<double>(n, M, U, rot, red, 40, 1e-15);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s_lam[i] = M[(int64_t)i * n + i].x;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double li = s_lam[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += (s_lam[j] > li || (s_lam[j] == li && j < i)) ? 1 : 0;
+        s_order[r] = i;
+    }
+    __syncthreads();
+    const int nsig = min(n, rz);
+    if (threadIdx.x == 0) {
+        double total = 0;
+        for (int r = 0; r < nsig; ++r) total += fmax(s_lam[s_order[r]], 0.0);
+        double bound = (rule == DH2_RANK_GLOBAL) ? eps * eps * total : eps * eps;
+        int kk = nsig;
+        double tail = 0;
+        while (kk > 0) {
+            double l = fmax(s_lam[s_order[kk - 1]], 0.0);
+            if (tail + l <= bound) {
+                tail += l;
+                --kk;
+            } else {
+                break;
+            }
+        }
+        s_rank = kk;
+        rank[tk.a] = kk;
+    }
+    for (int r = threadIdx.x; r < nsig; r += blockDim.x) sig[tk.sig + r] = sqrt(fmax(s_lam[s_order[r]], 0.0));
+    __syncthreads();
+    const int kt = s_rank;
+    for (int idx = threadIdx.x; idx < n * kt; idx += blockDim.x) {
+        int i = idx / kt, r = idx % kt;
+        cx<double> u = U[(int64_t)i * n + s_order[r]];
+        Q[tk.q + (int64_t)i * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
+    }
+    // C = Q^* V  (kt x k)
+    cta_gemm<double>(kt, k, n, [&](int r, int i) { return conj(U[(int64_t)i * n + s_order[r]]); }, V,
+                     [&](int r, int nu, cx<double> v) {
+                         Cd[tk.c + (int64_t)r * k + nu] = v;
+                         Ct[tk.c + (int64_t)r * k + nu] = cx<T>{T(v.x), T(v.y)};
+                     });
+}
+
+template <class T>
+__global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Vleaf,
+                           const cx<double>* __restrict__ Vhat, const cx<T>* __restrict__ Z,
+                           cx<double>* ascr, cx<double>* gscr, int smem_n, double eps, int rule,
+                           cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig, int32_t* rank) {
+    extern __shared__ unsigned char smraw[];
+    const TruncTask tk = tasks[blockIdx.x];
+    const int n = tk.rows;
+    cx<double>* M;
+    cx<double>* U;
+    JRot<double>* rot;
+    int* order;
+    double* lam;
+    if (n <= smem_n) {
+        M = reinterpret_cast<cx<double>*>(smraw);
+        U = M + (int64_t)smem_n * smem_n;
+        rot = reinterpret_cast<JRot<double>*>(U + (int64_t)smem_n * smem_n);
+        lam = reinterpret_cast<double*>(rot + (smem_n / 2 + 1));
+        order = reinterpret_cast<int*>(lam + smem_n);
+    } else {
+        // per-task slot of the level scratch: [A: n*rz][M: n*n][U: n*n][rot][lam][order]
+        M = ascr + tk.ascratch + (int64_t)n * max(tk.rz, 1);
+        U = M + (int64_t)n * n;
+        rot = reinterpret_cast<JRot<double>*>(U + (int64_t)n * n);
+        lam = reinterpret_cast<double*>(rot + (n / 2 + 1));
+        order = reinterpret_cast<int*>(lam + n);
+    }
+    (void)gscr;
+    if (tk.leaf) {
+        truncate_body<T>(tk, DenseCvt<double, T>{Vleaf + tk.vsrc, k, false, false}, k, Z,
+                         ascr + tk.ascratch, M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam);
+    } else {
+        truncate_body<T>(tk, Dense<double>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch,
+                         M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam);
+    }
+}
+
+// ----------------------------------------------------------------------------- projection
+
+struct ProjTask {
+    int32_t b, kt, ks, pad;
+    int64_t crow, ccol, dst;
+};
+
+template <class T>
+__global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
+                          const int32_t* __restrict__ adm_t, const int32_t* __restrict__ adm_s,
+                          const int32_t* __restrict__ adm_c, const int32_t* __restrict__ tc_level,
+                          const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
+                          const double* __restrict__ nodes, int m, double kappa,
+                          const cx<T>* __restrict__ Crow, const cx<T>* __restrict__ Ccol,
+                          cx<T>* scratch, cx<T>* Stilde) {
+    extern __shared__ unsigned char smraw[];
+    T* D = reinterpret_cast<T*>(smraw);
+    T* P = D + 3 * m * m;
+    const int k = m * m * m;
+    cx<T>* T1 = scratch + (int64_t)blockIdx.x * k * k;
+    for (int64_t w = blockIdx.x; w < ntasks; w += gridDim.x) {
+        const ProjTask tk = tasks[w];
+        if (tk.kt == 0 || tk.ks == 0) continue;
+        const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
+        const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
+        __syncthreads();
+        load_sgen_tables<T>(t, s, cd, nodes, m, D, P);
+        SGen<T> S{D, P, m, (T)kappa};
+        // T1 = C_t S_b  (kt x k)
+        cta_gemm<T>(tk.kt, k, k, Dense<T>{Crow + tk.crow, k, false, false},
+                    [&](int mu, int nu) { return S(mu, nu); },
+                    [&](int i, int nu, cx<T> v) { T1[(int64_t)i * k + nu] = v; });
+        __syncthreads();
+        // S~ = T1 C_s^*  (kt x ks)
+        cx<T>* out = Stilde + tk.dst;
+        const int ks = tk.ks;
+        cta_gemm<T>(tk.kt, ks, k, Dense<T>{T1, k, false, false}, Dense<T>{Ccol + tk.ccol, k, true, true},
+                    [&](int i, int j, cx<T> v) { out[(int64_t)i * ks + j] = v; });
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------- matvec kernels
+
+template <class T, class TX>
+__global__ void k_gather(const int32_t* __restrict__ perm, int64_t n, const cx<TX>* __restrict__ x,
+                         cx<T>* xt) {
+    int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    cx<TX> v = x[perm[r]];
+    xt[r] = cx<T>{T(v.x), T(v.y)};
+}
+
+struct FwdLeaf {
+    int64_t q, xh;
+    int32_t ld, rows, off, k;
+};
+
+// x^_sc = Q_sc^* x|_s for leaf pairs of the column basis
+template <class T>
+__global__ void k_fwd_leaf(const FwdLeaf* __restrict__ tasks, int64_t ntasks, const cx<T>* __restrict__ Q,
+                           const cx<T>* __restrict__ xt, cx<T>* xh) {
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (w >= ntasks) return;
+    const FwdLeaf tk = tasks[w];
+    for (int r = 0; r < tk.k; ++r) {
+        cx<T> acc = zero<T>();
+        for (int i = lane; i < tk.rows; i += 32) fma_cjx(acc, Q[tk.q + (int64_t)i * tk.ld + r], xt[tk.off + i]);
+        acc = warp_sum(acc);
+        if (lane == 0) xh[tk.xh + r] = acc;
+    }
+}
+
+struct FwdUp {
+    int64_t q, xh, xh0, xh1;
+    int32_t ld, k0, k1, k;
+};
+
+// x^_sc = F_{s1 c}^* x^_{s1 c'} + F_{s2 c}^* x^_{s2 c'}
+template <class T>
+__global__ void k_fwd_up(const FwdUp* __restrict__ tasks, int64_t ntasks, const cx<T>* __restrict__ Q,
+                         cx<T>* xh) {
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (w >= ntasks) return;
+    const FwdUp tk = tasks[w];
+    const int rows = tk.k0 + tk.k1;
+    for (int r = 0; r < tk.k; ++r) {
+        cx<T> acc = zero<T>();
+        for (int i = lane; i < rows; i += 32) {
+            cx<T> xv = i < tk.k0 ? xh[tk.xh0 + i] : xh[tk.xh1 + (i - tk.k0)];
+            fma_cjx(acc, Q[tk.q + (int64_t)i * tk.ld + r], xv);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) xh[tk.xh + r] = acc;
+    }
+}
+
+struct Coup {
+    int64_t st, xh;     // S~ offset, x^ offset of the column pair
+    int32_t kt, ks;
+};
+
+// y^_tc = sum_{b in row(t,c)} S~_b x^_sc ; one warp per row pair, blocks in CSR order
+template <class T>
+__global__ void k_coupling(const int32_t* __restrict__ ptr, const Coup* __restrict__ items,
+                           const int64_t* __restrict__ yh_off, const int32_t* __restrict__ krow,
+                           int64_t npairs, const cx<T>* __restrict__ St, const cx<T>* __restrict__ xh,
+                           cx<T>* yh) {
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    int64_t a = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (a >= npairs) return;
+    const int kt = krow[a];
+    for (int i = 0; i < kt; ++i) {
+        cx<T> acc = zero<T>();
+        for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
+            const Coup it = items[e];
+            const cx<T>* row = St + it.st + (int64_t)i * it.ks;
+            for (int j = lane; j < it.ks; j += 32) fma_cx(acc, row[j], xh[it.xh + j]);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) yh[yh_off[a] + i] = acc;
+    }
+}
+
+struct Bwd {
+    int64_t q, yhp;      // parent Q-hat offset (at this son's first row), parent y^ offset
+    int32_t ld, kp;      // parent pitch and rank
+};
+
+// y^_{t'c'} += sum over parent directions c+ with sd(c+) = c' of F_{t'c+} y^_{t c+}
+template <class T>
+__global__ void k_backward(const int32_t* __restrict__ pairs, const int32_t* __restrict__ ptr,
+                           const Bwd* __restrict__ items, const int64_t* __restrict__ yh_off,
+                           const int32_t* __restrict__ krow, int64_t ntasks, const cx<T>* __restrict__ Q,
+                           cx<T>* yh) {
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    int64_t w = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (w >= ntasks) return;
+    const int32_t a = pairs[w];
+    const int k = krow[a];
+    for (int i0 = 0; i0 < k; i0 += 32) {
+        int i = i0 + lane;
+        cx<T> acc = zero<T>();
+        if (i < k) {
+            for (int e = ptr[w]; e < ptr[w + 1]; ++e) {
+                const Bwd it = items[e];
+                const cx<T>* row = Q + it.q + (int64_t)i * it.ld;
+                for (int r = 0; r < it.kp; ++r) fma_cx(acc, row[r], yh[it.yhp + r]);
+            }
+            yh[yh_off[a] + i] = yh[yh_off[a] + i] + acc;
+        }
+    }
+}
+
+struct LeafOut {
+    int32_t off, rows;
+    int32_t qbeg, qend;      // range in the far-field item list
+    int32_t sbeg, send;      // range in the nearfield segment list
+};
+struct LeafQ {
+    int64_t q, yh;
+    int32_t ld, k;
+};
+struct LeafSeg {
+    int64_t p;               // panel offset of (row 0, first column)
+    int32_t ld, xoff, cols, pad;
+};
+
+// y[perm[r]] = sum_c Q_tc y^_tc + nearfield rows, one CTA per leaf, one warp per row
+template <class T, class TY>
+__global__ void k_leaf_out(const LeafOut* __restrict__ leaves, const LeafQ* __restrict__ qitems,
+                           const LeafSeg* __restrict__ segs, const cx<T>* __restrict__ Q,
+                           const cx<T>* __restrict__ yh, const cx<T>* __restrict__ Pn,
+                           const cx<T>* __restrict__ xt, const int32_t* __restrict__ perm, cx<TY>* y) {
+    const LeafOut lf = leaves[blockIdx.x];
+    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x >> 5; i < lf.rows; i += warps) {
+        cx<T> acc = zero<T>();
+        for (int e = lf.qbeg; e < lf.qend; ++e) {
+            const LeafQ it = qitems[e];
+            const cx<T>* row = Q + it.q + (int64_t)i * it.ld;
+            for (int r = lane; r < it.k; r += 32) fma_cx(acc, row[r], yh[it.yh + r]);
+        }
+        for (int e = lf.sbeg; e < lf.send; ++e) {
+            const LeafSeg sg = segs[e];
+            const cx<T>* row = Pn + sg.p + (int64_t)i * sg.ld;
+            const cx<T>* xv = xt + sg.xoff;
+            for (int j = lane; j < sg.cols; j += 32) fma_cx(acc, row[j], xv[j]);
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) y[perm[lf.off + i]] = cx<TY>{TY(acc.x), TY(acc.y)};
+    }
+}
+
+// ----------------------------------------------------------------------------- helpers
+
+template <class T>
+void upload_vec(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
+    d.alloc(h.size());
+    d.upload(h.data(), h.size(), s);
+}
+
+struct StageTimer {
+    cudaStream_t s;
+    cudaEvent_t ev[2 * ST_COUNT];
+    bool used[ST_COUNT] = {false};
+    explicit StageTimer(cudaStream_t st) : s(st) {
+        for (auto& e : ev) DH2_CHECK_CUDA(cudaEventCreate(&e));
+    }
+    ~StageTimer() {
+        for (auto& e : ev) cudaEventDestroy(e);
+    }
+    void begin(int i) {
+        DH2_CHECK_CUDA(cudaEventRecord(ev[2 * i], s));
+        used[i] = true;
+    }
+    void end(int i) { DH2_CHECK_CUDA(cudaEventRecord(ev[2 * i + 1], s)); }
+    void collect(double* out) {
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int i = 0; i < ST_COUNT; ++i)
+            if (used[i]) {
+                float ms = 0;
+                DH2_CHECK_CUDA(cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]));
+                out[i] += ms;
+            }
+    }
+};
+
+}  // namespace
+
+const char* const kKernelNames[K_COUNT] = {
+    "nearfield", "leaf_basis", "transfer", "kron", "stack_blocks", "tsqr", "truncate", "project",
+    "mv_gather", "mv_forward", "mv_coupling", "mv_backward", "mv_leaf_out"};
+
+namespace {
+// CUDA-event pairs around individual launches, summed per kernel id on collect().
+struct EventLog {
+    struct Rec {
+        int id;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    void begin(int id, cudaStream_t s) {
+        Rec r{id, nullptr, nullptr};
+        DH2_CHECK_CUDA(cudaEventCreate(&r.a));
+        DH2_CHECK_CUDA(cudaEventCreate(&r.b));
+        DH2_CHECK_CUDA(cudaEventRecord(r.a, s));
+        recs.push_back(r);
+    }
+    void end(cudaStream_t s) { DH2_CHECK_CUDA(cudaEventRecord(recs.back().b, s)); }
+    void collect(MatrixInfoAcc& info) {
+        for (auto& r : recs) {
+            DH2_CHECK_CUDA(cudaEventSynchronize(r.b));
+            float ms = 0;
+            DH2_CHECK_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+            info.kernel_ms[r.id] += ms;
+            info.kernel_launches[r.id] += 1;
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        recs.clear();
+    }
+    ~EventLog() {
+        for (auto& r : recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+    }
+};
+}  // namespace
+
+// ============================================================================= structure download
+
+void download_structure(const Tree& tr, const Structure& st, HostStructure& hs, cudaStream_t s) {
+    hs.nc = tr.nc;
+    hs.depth = tr.depth;
+    hs.offset = tr.offset.to_host(s);
+    hs.size = tr.size.to_host(s);
+    hs.parent = tr.parent.to_host(s);
+    hs.son0 = tr.son0.to_host(s);
+    hs.son1 = tr.son1.to_host(s);
+    hs.level = tr.level.to_host(s);
+    hs.level_start = tr.level_start;
+    hs.tc_base = st.tc_base.to_host(s);
+    hs.aidx = st.aidx.to_host(s);
+    hs.a_t = st.a_t.to_host(s);
+    hs.a_c = st.a_c.to_host(s);
+    hs.alevel_start = st.alevel_start;
+    hs.row_ptr = st.row_ptr.to_host(s);
+    hs.row_idx = st.row_idx.to_host(s);
+    hs.col_ptr = st.col_ptr.to_host(s);
+    hs.col_idx = st.col_idx.to_host(s);
+    hs.adm_t = st.adm_t.to_host(s);
+    hs.adm_s = st.adm_s.to_host(s);
+    hs.adm_c = st.adm_c.to_host(s);
+    hs.near_t = st.near_t.to_host(s);
+    hs.near_s = st.near_s.to_host(s);
+    hs.sd = st.sd.to_host(s);
+    hs.dir_off = st.dir_off;
+    hs.isd_ptr = st.isd_ptr.to_host(s);
+    hs.isd_idx = st.isd_idx.to_host(s);
+    hs.nactive = st.nactive;
+}
+
+// ============================================================================= Num<T>
+
+template <class T>
+class Num : public NumBase {
+public:
+    Num(const Tree& tr, Structure& st, const HostStructure& hs, const BuildParams& bp)
+        : tr_(tr), st_(st), hs_(hs), bp_(bp) {}
+
+    void build(cudaStream_t s) override;
+    void matvec(const void* x, void* y, int dtype, cudaStream_t s) override;
+    void export_pair(int which, int64_t tc, double* out, int64_t cap, int32_t* rows, int32_t* cols,
+                     cudaStream_t s) override;
+    void export_ranks(int32_t* rr, int32_t* rc, cudaStream_t s) override;
+    void set_timing(bool on) override {
+        timing_on_ = on;
+        for (int i = K_MV_GATHER; i < K_COUNT; ++i) {
+            info.kernel_ms[i] = 0;
+            info.kernel_launches[i] = 0;
+        }
+    }
+
+private:
+    const Tree& tr_;
+    Structure& st_;
+    const HostStructure& hs_;
+    BuildParams bp_;
+    int m_ = 0, k_ = 0;
+    int64_t n_ = 0, na_ = 0;
+
+    // per active pair (host)
+    std::vector<int32_t> lvl_, leaf_, sons_[2], rows_;      // rows_ = #t
+    std::vector<int32_t> rR_, rZ_[2], ub_[2], rank_[2];
+    std::vector<int64_t> offV_, offE_, offR_, offZ_[2], offQ_[2], offC_[2], offSig_[2], ldQ_[2];
+    std::vector<std::vector<std::pair<int32_t, int32_t>>> parents_;   // (parent pair, son slot)
+
+    // device data
+    DBuf<int32_t> tc_level_;
+    DBuf<double> nodes_;
+    DBuf<cx<T>> V_, E_, R_, Z_[2], Q_[2], Ct_[2], St_, near_;
+    DBuf<cx<double>> Cd_[2];
+    DBuf<double> sig_[2], bnorm_;
+    DBuf<int64_t> offR_d_;
+    DBuf<int32_t> rR_d_, rank_d_[2];
+    DBuf<float> qh_, ql_;
+    DBuf<double> x3c_;
+
+    // matvec plan
+    DBuf<cx<T>> xt_, xh_, yh_;
+    DBuf<FwdLeaf> fwd_leaf_;
+    std::vector<std::pair<int64_t, int64_t>> fwd_up_lv_;      // per level range in fwd_up_
+    DBuf<FwdUp> fwd_up_;
+    DBuf<int32_t> coup_ptr_, krow_d_;
+    DBuf<Coup> coup_;
+    DBuf<int64_t> yh_off_;
+    std::vector<std::pair<int64_t, int64_t>> bwd_lv_;
+    DBuf<int32_t> bwd_pairs_, bwd_ptr_;
+    DBuf<Bwd> bwd_;
+    DBuf<LeafOut> leaf_out_;
+    DBuf<LeafQ> leaf_q_;
+    DBuf<LeafSeg> leaf_seg_;
+    int64_t n_fwd_leaf_ = 0, n_leaves_ = 0;
+    std::vector<int64_t> bwd_level_counts_;
+    std::vector<int64_t> fwd_up_level_counts_;
+    std::vector<std::vector<NearSeg>> leaf_segs_;
+    std::vector<int32_t> leaf_order_;
+
+    bool timing_on_ = false;
+    EventLog ev_;
+    double work_[K_COUNT] = {0};     // algorithmic work accumulated while planning launches
+    static constexpr double kEvalFlops = 20.0;   // flop-equivalents per kernel evaluation
+    // brackets one launch with CUDA events when `on`
+    template <class F>
+    void timed(bool on, int id, cudaStream_t s, F&& launch) {
+        if (on) ev_.begin(id, s);
+        launch();
+        if (on) ev_.end(s);
+    }
+
+    void layout();
+    void analytic(cudaStream_t s);
+    void nearfield(cudaStream_t s);
+    void basis_weights(cudaStream_t s);
+    void total_weights(int pass, cudaStream_t s);
+    void truncate(int pass, cudaStream_t s);
+    void project(cudaStream_t s);
+    void plan_matvec(cudaStream_t s);
+    template <int RPL, class TQ>
+    void run_tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s);
+    void tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s);
+};
+
+// ----------------------------------------------------------------------------- layout
+
+template <class T>
+void Num<T>::layout() {
+    const auto& h = hs_;
+    m_ = bp_.m;
+    k_ = m_ * m_ * m_;
+    n_ = tr_.n;
+    na_ = h.nactive;
+    lvl_.resize(na_);
+    leaf_.resize(na_);
+    rows_.resize(na_);
+    sons_[0].assign(na_, -1);
+    sons_[1].assign(na_, -1);
+    parents_.assign(na_, {});
+    for (int64_t a = 0; a < na_; ++a) {
+        int32_t t = h.a_t[a], c = h.a_c[a];
+        lvl_[a] = h.level[t];
+        leaf_[a] = h.son0[t] < 0;
+        rows_[a] = h.size[t];
+        if (!leaf_[a]) {
+            int32_t c1 = h.son_dir(t, c);
+            sons_[0][a] = h.pair_of(h.son0[t], c1);
+            sons_[1][a] = h.pair_of(h.son1[t], c1);
+            if (sons_[0][a] < 0 || sons_[1][a] < 0) throw Error{DH2_ECUDA, "active set not closed"};
+            parents_[sons_[0][a]].push_back({(int32_t)a, 0});
+            parents_[sons_[1][a]].push_back({(int32_t)a, 1});
+        }
+    }
+    // parent lists in ascending parent direction (sd^{-1} order): parents were visited in
+    // active order, which is (t, c) order, so they are already sorted.
+    // basis weight rows, bottom-up
+    rR_.assign(na_, 0);
+    for (int64_t a = na_ - 1; a >= 0; --a) {
+        if (leaf_[a])
+            rR_[a] = std::min(rows_[a], k_);
+        else
+            rR_[a] = std::min(rR_[sons_[0][a]] + rR_[sons_[1][a]], k_);
+    }
+    // total weight rows, top-down
+    for (int pass = 0; pass < 2; ++pass) {
+        const auto& ptr = pass == 0 ? h.row_ptr : h.col_ptr;
+        const auto& idx = pass == 0 ? h.row_idx : h.col_idx;
+        rZ_[pass].assign(na_, 0);
+        for (int64_t a = 0; a < na_; ++a) {
+            int32_t t = h.a_t[a], c = h.a_c[a];
+            int32_t tc = h.tc_base[t] + c;
+            int64_t rows = 0;
+            for (int32_t e = ptr[tc]; e < ptr[tc + 1]; ++e) {
+                int32_t b = idx[e];
+                int32_t other = pass == 0 ? h.adm_s[b] : h.adm_t[b];
+                rows += rR_[h.pair_of(other, c)];
+            }
+            for (auto& pr : parents_[a]) rows += rZ_[pass][pr.first];
+            rZ_[pass][a] = (int32_t)std::min<int64_t>(rows, k_);
+        }
+        ub_[pass].assign(na_, 0);
+        for (int64_t a = na_ - 1; a >= 0; --a) {
+            int32_t rows = leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
+            ub_[pass][a] = std::min(rows, rZ_[pass][a]);
+        }
+    }
+    // offsets
+    auto scan = [&](std::vector<int64_t>& off, auto sizef) {
+        off.resize(na_ + 1);
+        int64_t acc = 0;
+        for (int64_t a = 0; a < na_; ++a) {
+            off[a] = acc;
+            acc += sizef(a);
+        }
+        off[na_] = acc;
+    };
+    scan(offV_, [&](int64_t a) -> int64_t { return leaf_[a] ? (int64_t)rows_[a] * k_ : 0; });
+    scan(offE_, [&](int64_t a) -> int64_t { return leaf_[a] ? 0 : 2 * 3 * m_ * m_; });
+    scan(offR_, [&](int64_t a) -> int64_t { return (int64_t)rR_[a] * k_; });
+    for (int pass = 0; pass < 2; ++pass) {
+        scan(offZ_[pass], [&](int64_t a) -> int64_t { return (int64_t)rZ_[pass][a] * k_; });
+        ldQ_[pass].resize(na_);
+        for (int64_t a = 0; a < na_; ++a) ldQ_[pass][a] = std::max(ub_[pass][a], 1);
+        scan(offQ_[pass], [&](int64_t a) -> int64_t {
+            int64_t rows = leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
+            return rows * ldQ_[pass][a];
+        });
+        scan(offC_[pass], [&](int64_t a) -> int64_t { return (int64_t)ub_[pass][a] * k_; });
+        scan(offSig_[pass], [&](int64_t a) -> int64_t {
+            return leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
+        });
+        rank_[pass].assign(na_, 0);
+    }
+}
+
+// ----------------------------------------------------------------------------- analytic stage
+
+template <class T>
+void Num<T>::analytic(cudaStream_t s) {
+    const auto& h = hs_;
+    const int32_t nc = tr_.nc;
+    nodes_.alloc((size_t)nc * 3 * m_);
+    k_cheb_nodes<<<grid_for(nc, kThreads), kThreads, 0, s>>>(tr_.lo.p, tr_.hi.p, nc, m_, nodes_.p);
+    DH2_CHECK_LAUNCH("k_cheb_nodes");
+    std::vector<int32_t> tcl(hs_.level);
+    upload_vec(tc_level_, tcl, s);
+    // leaf bases
+    std::vector<LeafTask> lt;
+    std::vector<TransferTask> tt;
+    for (int64_t a = 0; a < na_; ++a) {
+        int32_t t = h.a_t[a], c = h.a_c[a];
+        int32_t g = h.dir_off[h.level[t]] + c;
+        if (leaf_[a]) {
+            lt.push_back(LeafTask{t, g, h.offset[t], h.size[t], offV_[a]});
+        } else {
+            int32_t c1 = h.son_dir(t, c);
+            int32_t g1 = h.dir_off[h.level[t] + 1] + c1;
+            tt.push_back(TransferTask{t, h.son0[t], g, g1, offE_[a]});
+            tt.push_back(TransferTask{t, h.son1[t], g, g1, offE_[a] + 3 * m_ * m_});
+        }
+    }
+    V_.alloc(std::max<int64_t>(offV_[na_], 1));
+    E_.alloc(std::max<int64_t>(offE_[na_], 1));
+    if (!lt.empty()) {
+        DBuf<LeafTask> d;
+        upload_vec(d, lt, s);
+        ev_.begin(K_LEAF_BASIS, s);
+        k_leaf_basis<T><<<(unsigned)lt.size(), 128, 0, s>>>(d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p,
+                                                            st_.dirs.p, m_, bp_.kappa, V_.p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_leaf_basis");
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+    if (!tt.empty()) {
+        DBuf<TransferTask> d;
+        upload_vec(d, tt, s);
+        ev_.begin(K_TRANSFER, s);
+        k_transfer<T><<<(unsigned)tt.size(), 128, 0, s>>>(d.p, nodes_.p, st_.dirs.p, m_, bp_.kappa, E_.p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_transfer");
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+// ----------------------------------------------------------------------------- nearfield
+
+template <class T>
+void Num<T>::nearfield(cudaStream_t s) {
+    const auto& h = hs_;
+    // leaves in offset order: the leaves below a cluster form a contiguous range
+    leaf_order_.clear();
+    for (int32_t t = 0; t < h.nc; ++t)
+        if (h.son0[t] < 0) leaf_order_.push_back(t);
+    std::sort(leaf_order_.begin(), leaf_order_.end(),
+              [&](int32_t a, int32_t b) { return h.offset[a] < h.offset[b]; });
+    std::vector<int32_t> leaf_off(leaf_order_.size());
+    for (size_t i = 0; i < leaf_order_.size(); ++i) leaf_off[i] = h.offset[leaf_order_[i]];
+    n_leaves_ = (int64_t)leaf_order_.size();
+    leaf_segs_.assign(leaf_order_.size(), {});
+    for (size_t b = 0; b < h.near_t.size(); ++b) {
+        int32_t t = h.near_t[b], s2 = h.near_s[b];
+        int32_t lo = h.offset[t], hi = h.offset[t] + h.size[t];
+        size_t i0 = std::lower_bound(leaf_off.begin(), leaf_off.end(), lo) - leaf_off.begin();
+        for (size_t i = i0; i < leaf_order_.size() && leaf_off[i] < hi; ++i) {
+            NearSeg sg{};
+            sg.rows = h.size[leaf_order_[i]];
+            sg.cols = h.size[s2];
+            sg.roff = h.offset[leaf_order_[i]];
+            sg.coff = h.offset[s2];
+            leaf_segs_[i].push_back(sg);
+        }
+    }
+    // one dense row panel per leaf: its segments side by side, sorted by column offset
+    std::vector<NearSeg> all;
+    int64_t poff = 0;
+    for (size_t i = 0; i < leaf_order_.size(); ++i) {
+        auto& v = leaf_segs_[i];
+        std::sort(v.begin(), v.end(), [](const NearSeg& a, const NearSeg& b) { return a.coff < b.coff; });
+        int32_t width = 0;
+        for (auto& sg : v) width += sg.cols;
+        int32_t col = 0;
+        for (auto& sg : v) {
+            sg.ld = width;
+            sg.poff = poff + col;
+            col += sg.cols;
+            all.push_back(sg);
+        }
+        poff += (int64_t)h.size[leaf_order_[i]] * width;
+    }
+    info.near_entries = poff;
+    near_.alloc(std::max<int64_t>(poff, 1));
+    const double s15 = std::sqrt(15.0);
+    const double w7[7] = {9.0 / 40.0,           (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0,
+                          (155.0 - s15) / 1200.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0,
+                          (155.0 + s15) / 1200.0};
+    DH2_CHECK_CUDA(cudaMemcpyToSymbol(c_w7, w7, sizeof(w7)));
+    QuadRows<T> qr{};
+    if constexpr (std::is_same<T, float>::value) {
+        qh_.alloc(9 * n_);
+        ql_.alloc(9 * n_);
+        k_split_quad<<<grid_for(9 * n_, kThreads), kThreads, 0, s>>>(tr_.perm.p, tr_.x3.p, n_, qh_.p, ql_.p);
+        DH2_CHECK_LAUNCH("k_split_quad");
+        qr.h = qh_.p;
+        qr.l = ql_.p;
+    } else {
+        x3c_.alloc(9 * n_);
+        k_cluster_quad<<<grid_for(9 * n_, kThreads), kThreads, 0, s>>>(tr_.perm.p, tr_.x3.p, n_, x3c_.p);
+        DH2_CHECK_LAUNCH("k_cluster_quad");
+        qr.x = x3c_.p;
+    }
+    const int64_t chunk = 1 << 22;
+    for (int64_t b0 = 0; b0 < (int64_t)all.size(); b0 += chunk) {
+        int64_t cnt = std::min<int64_t>(chunk, (int64_t)all.size() - b0);
+        std::vector<NearSeg> part(all.begin() + b0, all.begin() + b0 + cnt);
+        DBuf<NearSeg> d;
+        upload_vec(d, part, s);
+        ev_.begin(K_NEARFIELD, s);
+        k_nearfield<T><<<(unsigned)cnt, kThreads, 0, s>>>(d.p, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
+                                                          tr_.x7.p, bp_.kappa, near_.p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_nearfield");
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+// ----------------------------------------------------------------------------- TSQR dispatch
+
+template <class T>
+template <int RPL, class TQ>
+void Num<T>::run_tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s) {
+    if (tasks.empty()) return;
+    const size_t smem = (size_t)k_ * 32 * RPL * sizeof(cx<TQ>);
+    auto kern = k_tsqr<T, TQ, RPL>;
+    DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int64_t per = (int64_t)k_ * k_;
+    const int64_t max_tasks = std::max<int64_t>(1, (int64_t(1) << 31) / (per * (int64_t)sizeof(cx<TQ>)));
+    DBuf<cx<TQ>> scratch;
+    for (size_t b0 = 0; b0 < tasks.size(); b0 += (size_t)max_tasks) {
+        size_t cnt = std::min<size_t>((size_t)max_tasks, tasks.size() - b0);
+        std::vector<QRTask> part(tasks.begin() + b0, tasks.begin() + b0 + cnt);
+        DBuf<QRTask> d;
+        upload_vec(d, part, s);
+        scratch.reserve(cnt * per);
+        ev_.begin(K_TSQR, s);
+        kern<<<(unsigned)cnt, kThreads, smem, s>>>(d.p, k_, src, scratch.p, dst);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_tsqr");
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
+template <class T>
+void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s) {
+    const bool fp64 = std::is_same<T, double>::value || bp_.qr_fp64;
+    if (fp64) {
+        if ((size_t)k_ * 32 * sizeof(cx<double>) > 200 * 1024)
+            throw Error{DH2_EUNSUPPORTED, "FP64 weight QR needs k <= 400 (m <= 7)"};
+        run_tsqr<1, double>(tasks, src, dst, s);
+    } else if ((size_t)k_ * 64 * sizeof(cx<float>) <= 120 * 1024) {
+        run_tsqr<2, float>(tasks, src, dst, s);
+    } else {
+        run_tsqr<1, float>(tasks, src, dst, s);
+    }
+}
+
+// ----------------------------------------------------------------------------- basis weights
+
+template <class T>
+void Num<T>::basis_weights(cudaStream_t s) {
+    R_.alloc(std::max<int64_t>(offR_[na_], 1));
+    DBuf<cx<T>> stack;
+    const int kk = k_;
+    for (int l = hs_.depth; l >= 0; --l) {
+        std::vector<QRTask> leafq, innerq;
+        std::vector<KronTask> kron;
+        int64_t srow = 0;
+        for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a) {
+            if (leaf_[a]) {
+                leafq.push_back(QRTask{offV_[a], offR_[a], rows_[a], rR_[a]});
+                work_[K_TSQR] += 8.0 * rows_[a] * kk * kk;
+            } else {
+                int32_t s0 = sons_[0][a], s1 = sons_[1][a];
+                kron.push_back(KronTask{offR_[s0], offE_[a], srow * kk, rR_[s0], 0});
+                kron.push_back(KronTask{offR_[s1], offE_[a] + 3 * m_ * m_, (srow + rR_[s0]) * kk, rR_[s1], 0});
+                innerq.push_back(QRTask{srow * kk, offR_[a], rR_[s0] + rR_[s1], rR_[a]});
+                work_[K_TSQR] += 8.0 * (rR_[s0] + rR_[s1]) * kk * kk;
+                work_[K_KRON] += 24.0 * m_ * kk * (rR_[s0] + rR_[s1]);
+                srow += rR_[s0] + rR_[s1];
+            }
+        }
+        tsqr(leafq, V_.p, R_.p, s);
+        if (!kron.empty()) {
+            stack.reserve(std::max<int64_t>(srow * kk, 1));
+            DBuf<KronTask> d;
+            upload_vec(d, kron, s);
+            size_t smem = (2 * (size_t)kk + 3 * m_ * m_) * sizeof(cx<T>);
+            ev_.begin(K_KRON, s);
+            k_kron<T, T, T, T><<<(unsigned)kron.size(), kThreads, smem, s>>>(d.p, m_, R_.p, E_.p, stack.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_kron");
+            tsqr(innerq, stack.p, R_.p, s);
+        }
+    }
+    std::vector<int32_t> rr(rR_.begin(), rR_.end());
+    upload_vec(rR_d_, rr, s);
+    upload_vec(offR_d_, offR_, s);
+}
+
+// ----------------------------------------------------------------------------- total weights
+
+template <class T>
+void Num<T>::total_weights(int pass, cudaStream_t s) {
+    const auto& h = hs_;
+    const auto& ptr = pass == 0 ? h.row_ptr : h.col_ptr;
+    const auto& idx = pass == 0 ? h.row_idx : h.col_idx;
+    Z_[pass].alloc(std::max<int64_t>(offZ_[pass][na_], 1));
+    if (pass == 0) bnorm_.alloc(std::max<int64_t>((int64_t)h.adm_t.size(), 1));
+    const int kk = k_;
+    const int64_t cap_rows = std::max<int64_t>(
+        64, (bp_.workspace_bytes > 0 ? bp_.workspace_bytes : (int64_t(16) << 30)) / ((int64_t)kk * sizeof(cx<T>)));
+    DBuf<cx<T>> stack;
+    for (int l = 0; l <= h.depth; ++l) {
+        int64_t a = h.alevel_start[l];
+        const int64_t aend = h.alevel_start[l + 1];
+        while (a < aend) {
+            std::vector<BlockRowTask> btasks;
+            std::vector<KronTask> ptasks;
+            std::vector<QRTask> qtasks;
+            int64_t srow = 0;
+            for (; a < aend; ++a) {
+                int32_t t = h.a_t[a], c = h.a_c[a], tc = h.tc_base[t] + c;
+                int64_t rows = 0;
+                for (int32_t e = ptr[tc]; e < ptr[tc + 1]; ++e) {
+                    int32_t other = pass == 0 ? h.adm_s[idx[e]] : h.adm_t[idx[e]];
+                    rows += rR_[h.pair_of(other, c)];
+                }
+                for (auto& pr : parents_[a]) rows += rZ_[pass][pr.first];
+                if (srow > 0 && srow + rows > cap_rows) break;   // next group
+                int64_t r0 = srow;
+                for (int32_t e = ptr[tc]; e < ptr[tc + 1]; ++e) {
+                    int32_t b = idx[e];
+                    int32_t other = pass == 0 ? h.adm_s[b] : h.adm_t[b];
+                    int32_t ao = h.pair_of(other, c);
+                    btasks.push_back(BlockRowTask{b, ao, (int32_t)a, 0, srow * kk});
+                    work_[K_STACK_BLOCKS] += kEvalFlops * kk * kk + 8.0 * rR_[ao] * kk * kk +
+                                             (pass == 0 ? 8.0 * rR_[a] * kk * rR_[ao] : 0.0);
+                    srow += rR_[ao];
+                }
+                for (auto& pr : parents_[a]) {
+                    int32_t ap = pr.first;
+                    if (rZ_[pass][ap] == 0) continue;
+                    ptasks.push_back(KronTask{offZ_[pass][ap], offE_[ap] + (int64_t)pr.second * 3 * m_ * m_,
+                                              srow * kk, rZ_[pass][ap], 1});
+                    work_[K_KRON] += 24.0 * m_ * kk * rZ_[pass][ap];
+                    srow += rZ_[pass][ap];
+                }
+                qtasks.push_back(QRTask{r0 * kk, offZ_[pass][a], (int32_t)(srow - r0), rZ_[pass][a]});
+                work_[K_TSQR] += 8.0 * (srow - r0) * kk * kk;
+            }
+            stack.reserve(std::max<int64_t>(srow * kk, 1));
+            if (!btasks.empty()) {
+                DBuf<BlockRowTask> d;
+                upload_vec(d, btasks, s);
+                size_t smem = 2 * 3 * (size_t)m_ * m_ * sizeof(T);
+                ev_.begin(K_STACK_BLOCKS, s);
+                k_stack_blocks<T><<<(unsigned)btasks.size(), kThreads, smem, s>>>(
+                    d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p, st_.dir_off_d.p,
+                    st_.dirs.p, nodes_.p, m_, bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack.p);
+                ev_.end(s);
+                DH2_CHECK_LAUNCH("k_stack_blocks");
+            }
+            if (!ptasks.empty()) {
+                DBuf<KronTask> d;
+                upload_vec(d, ptasks, s);
+                size_t smem = (2 * (size_t)kk + 3 * m_ * m_) * sizeof(cx<T>);
+                ev_.begin(K_KRON, s);
+                k_kron<T, T, T, T><<<(unsigned)ptasks.size(), kThreads, smem, s>>>(d.p, m_, Z_[pass].p, E_.p,
+                                                                                   stack.p);
+                ev_.end(s);
+                DH2_CHECK_LAUNCH("k_kron");
+            }
+            tsqr(qtasks, stack.p, Z_[pass].p, s);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- truncation
+
+template <class T>
+void Num<T>::truncate(int pass, cudaStream_t s) {
+    const auto& h = hs_;
+    const int kk = k_;
+    Q_[pass].alloc(std::max<int64_t>(offQ_[pass][na_], 1));
+    Cd_[pass].alloc(std::max<int64_t>(offC_[pass][na_], 1));
+    if constexpr (std::is_same<T, float>::value) Ct_[pass].alloc(std::max<int64_t>(offC_[pass][na_], 1));
+    sig_[pass].alloc(std::max<int64_t>(offSig_[pass][na_], 1));
+    rank_d_[pass].alloc(std::max<int64_t>(na_, 1));
+    cx<T>* Ct = nullptr;
+    if constexpr (std::is_same<T, float>::value) Ct = Ct_[pass].p;
+    else Ct = reinterpret_cast<cx<T>*>(Cd_[pass].p);
+    DBuf<cx<double>> vhat, ascr;
+    for (int l = h.depth; l >= 0; --l) {
+        const int64_t a0 = h.alevel_start[l], a1 = h.alevel_start[l + 1];
+        if (a1 == a0) continue;
+        std::vector<KronTask> kron;
+        std::vector<TruncTask> tt;
+        int64_t vrow = 0, aoff = 0;
+        int smem_n = 0;
+        for (int64_t a = a0; a < a1; ++a) {
+            TruncTask tk{};
+            tk.leaf = leaf_[a];
+            tk.a = (int32_t)a;
+            tk.rz = rZ_[pass][a];
+            tk.z = offZ_[pass][a];
+            tk.q = offQ_[pass][a];
+            tk.qld = (int32_t)ldQ_[pass][a];
+            tk.c = offC_[pass][a];
+            tk.sig = offSig_[pass][a];
+            if (leaf_[a]) {
+                tk.rows = rows_[a];
+                tk.vsrc = offV_[a];
+            } else {
+                int32_t s0 = sons_[0][a], s1 = sons_[1][a];
+                int32_t k0 = rank_[pass][s0], k1 = rank_[pass][s1];
+                tk.rows = k0 + k1;
+                tk.vsrc = vrow * kk;
+                if (k0) kron.push_back(KronTask{offC_[pass][s0], offE_[a], vrow * kk, k0, 0});
+                if (k1) kron.push_back(KronTask{offC_[pass][s1], offE_[a] + 3 * m_ * m_, (vrow + k0) * kk, k1, 0});
+                vrow += k0 + k1;
+            }
+            tk.ascratch = aoff;
+            smem_n = std::max(smem_n, std::min(tk.rows, 64));
+            tt.push_back(tk);
+            // A = V Z^* and M = A A^* (the Jacobi sweeps and C = Q^* V are not counted)
+            work_[K_TRUNCATE] += 8.0 * tk.rows * tk.rz * kk + 8.0 * tk.rows * tk.rows * tk.rz;
+        }
+        // scratch per task: A (rows x rz), plus M, U, rotations, eigenvalues, order when rows > smem_n
+        for (auto& tk : tt) {
+            tk.ascratch = aoff;
+            int64_t need = (int64_t)tk.rows * std::max(tk.rz, 1);
+            if (tk.rows > smem_n) {
+                int64_t extra_bytes = 2 * (int64_t)tk.rows * tk.rows * sizeof(cx<double>) +
+                                      (tk.rows / 2 + 1) * sizeof(JRot<double>) + tk.rows * (sizeof(double) + sizeof(int));
+                need += (extra_bytes + sizeof(cx<double>) - 1) / sizeof(cx<double>) + 4;
+            }
+            aoff += (need + 3) & ~int64_t(3);
+        }
+        vhat.reserve(std::max<int64_t>(vrow * kk, 1));
+        ascr.reserve(std::max<int64_t>(aoff, 1));
+        if (!kron.empty()) {
+            DBuf<KronTask> d;
+            upload_vec(d, kron, s);
+            size_t smem = (2 * (size_t)kk + 3 * m_ * m_) * sizeof(cx<double>);
+            ev_.begin(K_KRON, s);
+            k_kron<double, T, double, double><<<(unsigned)kron.size(), kThreads, smem, s>>>(
+                d.p, m_, Cd_[pass].p, E_.p, vhat.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_kron");
+        }
+        DBuf<TruncTask> d;
+        upload_vec(d, tt, s);
+        size_t smem = smem_n > 0 ? 2 * (size_t)smem_n * smem_n * sizeof(cx<double>) +
+                                       (smem_n / 2 + 1) * sizeof(JRot<double>) +
+                                       smem_n * (sizeof(double) + sizeof(int)) + 64
+                                 : 64;
+        auto kern = k_truncate<T>;
+        DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ev_.begin(K_TRUNCATE, s);
+        kern<<<(unsigned)tt.size(), kThreads, smem, s>>>(d.p, kk, V_.p, vhat.p, Z_[pass].p, ascr.p, nullptr,
+                                                          smem_n, bp_.eps, bp_.rank_rule, Q_[pass].p,
+                                                          Cd_[pass].p, Ct, sig_[pass].p, rank_d_[pass].p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_truncate");
+        std::vector<int32_t> rk(a1 - a0);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(rk.data(), rank_d_[pass].p + a0, (a1 - a0) * sizeof(int32_t),
+                                       cudaMemcpyDeviceToHost, s));
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t a = a0; a < a1; ++a) rank_[pass][a] = rk[a - a0];
+    }
+}
+
+// ----------------------------------------------------------------------------- projection
+
+template <class T>
+void Num<T>::project(cudaStream_t s) {
+    const auto& h = hs_;
+    const int64_t nb = (int64_t)h.adm_t.size();
+    std::vector<ProjTask> pt(nb);
+    int64_t off = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        int32_t c = h.adm_c[b];
+        int32_t at = h.pair_of(h.adm_t[b], c), as = h.pair_of(h.adm_s[b], c);
+        ProjTask p{};
+        p.b = (int32_t)b;
+        p.kt = rank_[0][at];
+        p.ks = rank_[1][as];
+        p.crow = offC_[0][at];
+        p.ccol = offC_[1][as];
+        p.dst = off;
+        off += (int64_t)p.kt * p.ks;
+        pt[b] = p;
+        if (p.kt && p.ks)
+            work_[K_PROJECT] += kEvalFlops * k_ * k_ + 8.0 * p.kt * k_ * k_ + 8.0 * p.kt * k_ * p.ks;
+    }
+    info.coupling_entries = off;
+    St_.alloc(std::max<int64_t>(off, 1));
+    if (nb == 0) return;
+    DBuf<ProjTask> d;
+    upload_vec(d, pt, s);
+    const int64_t grid = std::min<int64_t>(nb, 152 * 8);
+    DBuf<cx<T>> scratch((size_t)grid * k_ * k_);
+    const cx<T>* Crow;
+    const cx<T>* Ccol;
+    if constexpr (std::is_same<T, float>::value) {
+        Crow = Ct_[0].p;
+        Ccol = Ct_[1].p;
+    } else {
+        Crow = reinterpret_cast<const cx<T>*>(Cd_[0].p);
+        Ccol = reinterpret_cast<const cx<T>*>(Cd_[1].p);
+    }
+    size_t smem = 2 * 3 * (size_t)m_ * m_ * sizeof(T);
+    ev_.begin(K_PROJECT, s);
+    k_project<T><<<(unsigned)grid, kThreads, smem, s>>>(d.p, nb, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
+                                                        tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
+                                                        bp_.kappa, Crow, Ccol, scratch.p, St_.p);
+    ev_.end(s);
+    DH2_CHECK_LAUNCH("k_project");
+    DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------------------------- matvec plan
+
+template <class T>
+void Num<T>::plan_matvec(cudaStream_t s) {
+    const auto& h = hs_;
+    std::vector<int64_t> xh_off(na_ + 1), yh_off(na_ + 1);
+    for (int64_t a = 0; a < na_; ++a) {
+        xh_off[a + 1] = xh_off[a] + rank_[1][a];
+        yh_off[a + 1] = yh_off[a] + rank_[0][a];
+    }
+    xt_.alloc(std::max<int64_t>(n_, 1));
+    xh_.alloc(std::max<int64_t>(xh_off[na_], 1));
+    yh_.alloc(std::max<int64_t>(yh_off[na_], 1));
+    int64_t basis_entries = 0;
+    // forward transform
+    std::vector<FwdLeaf> fl;
+    std::vector<FwdUp> fu;
+    fwd_up_level_counts_.assign(h.depth + 1, 0);
+    for (int l = h.depth; l >= 0; --l) {
+        for (int64_t a = h.alevel_start[l]; a < h.alevel_start[l + 1]; ++a) {
+            const int k = rank_[1][a];
+            if (leaf_[a]) {
+                basis_entries += (int64_t)rows_[a] * k;
+                if (k) fl.push_back(FwdLeaf{offQ_[1][a], xh_off[a], (int32_t)ldQ_[1][a], rows_[a], h.offset[h.a_t[a]], k});
+            } else {
+                int32_t s0 = sons_[0][a], s1 = sons_[1][a];
+                basis_entries += (int64_t)(rank_[1][s0] + rank_[1][s1]) * k;
+                if (k) {
+                    fu.push_back(FwdUp{offQ_[1][a], xh_off[a], xh_off[s0], xh_off[s1], (int32_t)ldQ_[1][a],
+                                       rank_[1][s0], rank_[1][s1], k});
+                    fwd_up_level_counts_[l]++;
+                }
+            }
+        }
+    }
+    n_fwd_leaf_ = (int64_t)fl.size();
+    upload_vec(fwd_leaf_, fl, s);
+    upload_vec(fwd_up_, fu, s);
+    // couplings: S~ offsets in block order
+    std::vector<int64_t> st_off(h.adm_t.size() + 1, 0);
+    for (size_t b = 0; b < h.adm_t.size(); ++b) {
+        int32_t c = h.adm_c[b];
+        st_off[b + 1] = st_off[b] + (int64_t)rank_[0][h.pair_of(h.adm_t[b], c)] * rank_[1][h.pair_of(h.adm_s[b], c)];
+    }
+    std::vector<int32_t> cptr(na_ + 1, 0);
+    std::vector<Coup> items;
+    for (int64_t a = 0; a < na_; ++a) {
+        int32_t t = h.a_t[a], c = h.a_c[a], tc = h.tc_base[t] + c;
+        for (int32_t e = h.row_ptr[tc]; e < h.row_ptr[tc + 1]; ++e) {
+            int32_t b = h.row_idx[e];
+            int32_t as = h.pair_of(h.adm_s[b], c);
+            if (rank_[0][a] == 0 || rank_[1][as] == 0) continue;
+            items.push_back(Coup{st_off[b], xh_off[as], rank_[0][a], rank_[1][as]});
+        }
+        cptr[a + 1] = (int32_t)items.size();
+    }
+    upload_vec(coup_ptr_, cptr, s);
+    upload_vec(coup_, items, s);
+    std::vector<int32_t> kr(rank_[0].begin(), rank_[0].end());
+    upload_vec(krow_d_, kr, s);
+    std::vector<int64_t> yo(yh_off.begin(), yh_off.end() - 1);
+    upload_vec(yh_off_, yo, s);
+    // backward transform, top-down
+    std::vector<int32_t> bp, bptr{0};
+    std::vector<Bwd> bitems;
+    bwd_level_counts_.assign(h.depth + 1, 0);
+    for (int l = 1; l <= h.depth; ++l) {
+        for (int64_t a = h.alevel_start[l]; a < h.alevel_start[l + 1]; ++a) {
+            if (rank_[0][a] == 0) continue;
+            bool any = false;
+            for (auto& pr : parents_[a]) {
+                int32_t ap = pr.first;
+                if (rank_[0][ap] == 0) continue;
+                int64_t rowoff = pr.second == 0 ? 0 : rank_[0][sons_[0][ap]];
+                bitems.push_back(Bwd{offQ_[0][ap] + rowoff * ldQ_[0][ap], yh_off[ap], (int32_t)ldQ_[0][ap], rank_[0][ap]});
+                any = true;
+            }
+            if (any) {
+                bp.push_back((int32_t)a);
+                bptr.push_back((int32_t)bitems.size());
+                bwd_level_counts_[l]++;
+            }
+        }
+        if (!leaf_.empty()) {
+            for (int64_t a = h.alevel_start[l - 1]; a < h.alevel_start[l]; ++a)
+                if (!leaf_[a]) basis_entries += 0;
+        }
+    }
+    upload_vec(bwd_pairs_, bp, s);
+    upload_vec(bwd_ptr_, bptr, s);
+    upload_vec(bwd_, bitems, s);
+    // row basis storage (leaf Q and transfers F)
+    for (int64_t a = 0; a < na_; ++a) {
+        if (leaf_[a])
+            basis_entries += (int64_t)rows_[a] * rank_[0][a];
+        else
+            basis_entries += (int64_t)(rank_[0][sons_[0][a]] + rank_[0][sons_[1][a]]) * rank_[0][a];
+    }
+    info.basis_entries = basis_entries;
+    // leaf output: far-field Q items and nearfield segments per leaf
+    std::vector<int32_t> leaf_index(h.nc, -1);
+    for (size_t i = 0; i < leaf_order_.size(); ++i) leaf_index[leaf_order_[i]] = (int32_t)i;
+    std::vector<std::vector<LeafQ>> per_leaf(leaf_order_.size());
+    for (int64_t a = 0; a < na_; ++a) {
+        if (!leaf_[a] || rank_[0][a] == 0) continue;
+        per_leaf[leaf_index[h.a_t[a]]].push_back(LeafQ{offQ_[0][a], yh_off[a], (int32_t)ldQ_[0][a], rank_[0][a]});
+    }
+    std::vector<LeafOut> lo;
+    std::vector<LeafQ> lq;
+    std::vector<LeafSeg> ls;
+    for (size_t i = 0; i < leaf_order_.size(); ++i) {
+        LeafOut o{};
+        o.off = h.offset[leaf_order_[i]];
+        o.rows = h.size[leaf_order_[i]];
+        o.qbeg = (int32_t)lq.size();
+        for (auto& q : per_leaf[i]) lq.push_back(q);
+        o.qend = (int32_t)lq.size();
+        o.sbeg = (int32_t)ls.size();
+        for (auto& sg : leaf_segs_[i]) ls.push_back(LeafSeg{sg.poff, sg.ld, sg.coff, sg.cols, 0});
+        o.send = (int32_t)ls.size();
+        lo.push_back(o);
+    }
+    upload_vec(leaf_out_, lo, s);
+    upload_vec(leaf_q_, lq, s);
+    upload_vec(leaf_seg_, ls, s);
+    const int64_t cs = sizeof(cx<T>);
+    info.matvec_bytes = (info.near_entries + info.coupling_entries + info.basis_entries) * cs +
+                        2 * n_ * cs + 2 * (xh_off[na_] + yh_off[na_]) * cs;
+    // ranks summary
+    int64_t cnt = 0;
+    double sr = 0, sc_ = 0;
+    for (int64_t a = 0; a < na_; ++a) {
+        info.max_rank_row = std::max(info.max_rank_row, rank_[0][a]);
+        info.max_rank_col = std::max(info.max_rank_col, rank_[1][a]);
+        sr += rank_[0][a];
+        sc_ += rank_[1][a];
+        ++cnt;
+    }
+    info.mean_rank_row = cnt ? sr / cnt : 0;
+    info.mean_rank_col = cnt ? sc_ / cnt : 0;
+    DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+// ----------------------------------------------------------------------------- build
+
+template <class T>
+void Num<T>::build(cudaStream_t s) {
+    StageTimer tm(s);
+    layout();
+    tm.begin(ST_ANALYTIC);
+    analytic(s);
+    tm.end(ST_ANALYTIC);
+    tm.begin(ST_NEARFIELD);
+    nearfield(s);
+    tm.end(ST_NEARFIELD);
+    tm.begin(ST_BASIS_WEIGHTS);
+    basis_weights(s);
+    tm.end(ST_BASIS_WEIGHTS);
+    tm.begin(ST_TOTAL_WEIGHTS_ROW);
+    total_weights(0, s);
+    tm.end(ST_TOTAL_WEIGHTS_ROW);
+    tm.begin(ST_TOTAL_WEIGHTS_COL);
+    total_weights(1, s);
+    tm.end(ST_TOTAL_WEIGHTS_COL);
+    tm.begin(ST_TRUNCATE_ROW);
+    truncate(0, s);
+    tm.end(ST_TRUNCATE_ROW);
+    tm.begin(ST_TRUNCATE_COL);
+    truncate(1, s);
+    tm.end(ST_TRUNCATE_COL);
+    tm.begin(ST_PROJECT);
+    project(s);
+    tm.end(ST_PROJECT);
+    tm.begin(ST_MATVEC_PLAN);
+    plan_matvec(s);
+    tm.end(ST_MATVEC_PLAN);
+    tm.collect(info.stage_ms);
+    ev_.collect(info);
+    const int32_t w32 = std::is_same<T, float>::value ? W_FLOP32 : W_FLOP64;
+    const int32_t wqr = (std::is_same<T, double>::value || bp_.qr_fp64) ? W_FLOP64 : W_FLOP32;
+    for (int i = 0; i < K_COUNT; ++i) info.kernel_work[i] = work_[i];
+    info.kernel_work[K_NEARFIELD] = 9.0 * kEvalFlops * info.near_entries;
+    info.kernel_work_kind[K_NEARFIELD] = w32;
+    info.kernel_work_kind[K_KRON] = w32;
+    info.kernel_work_kind[K_STACK_BLOCKS] = w32;
+    info.kernel_work_kind[K_TSQR] = wqr;
+    info.kernel_work_kind[K_TRUNCATE] = W_FLOP64;
+    info.kernel_work_kind[K_PROJECT] = w32;
+    // matvec leaf kernel: nearfield panels + leaf row bases streamed once, x and y once
+    int64_t qleaf = 0;
+    for (int64_t a = 0; a < na_; ++a)
+        if (leaf_[a]) qleaf += (int64_t)rows_[a] * rank_[0][a];
+    info.kernel_work[K_MV_LEAF_OUT] = (double)(info.near_entries + qleaf + 2 * n_) * sizeof(cx<T>);
+    info.kernel_work_kind[K_MV_LEAF_OUT] = W_BYTES;
+}
+
+// ----------------------------------------------------------------------------- matvec
+
+template <class T>
+void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
+    const unsigned g = grid_for(n_, kThreads);
+    if (dtype == DH2_C64) {
+        if (timing_on_) ev_.begin(K_MV_GATHER, s);
+        k_gather<T, float><<<g, kThreads, 0, s>>>(tr_.perm.p, n_, (const cx<float>*)x, xt_.p);
+        if (timing_on_) ev_.end(s);
+    }
+    else {
+        if (timing_on_) ev_.begin(K_MV_GATHER, s);
+        k_gather<T, double><<<g, kThreads, 0, s>>>(tr_.perm.p, n_, (const cx<double>*)x, xt_.p);
+        if (timing_on_) ev_.end(s);
+    }
+    DH2_CHECK_LAUNCH("k_gather");
+    constexpr int WPB = 8;   // warps per CTA of the transform kernels
+    if (n_fwd_leaf_) {
+        if (timing_on_) ev_.begin(K_MV_FORWARD, s);
+        k_fwd_leaf<T><<<grid_for(n_fwd_leaf_, WPB), WPB * 32, 0, s>>>(fwd_leaf_.p, n_fwd_leaf_, Q_[1].p, xt_.p, xh_.p);
+        if (timing_on_) ev_.end(s);
+        DH2_CHECK_LAUNCH("k_fwd_leaf");
+    }
+    int64_t off = 0;
+    for (int l = hs_.depth; l >= 0; --l) {
+        int64_t cnt = fwd_up_level_counts_[l];
+        if (cnt) {
+            if (timing_on_) ev_.begin(K_MV_FORWARD, s);
+            k_fwd_up<T><<<grid_for(cnt, WPB), WPB * 32, 0, s>>>(fwd_up_.p + off, cnt, Q_[1].p, xh_.p);
+            if (timing_on_) ev_.end(s);
+            DH2_CHECK_LAUNCH("k_fwd_up");
+        }
+        off += cnt;
+    }
+    if (na_) {
+        if (timing_on_) ev_.begin(K_MV_COUPLING, s);
+        k_coupling<T><<<grid_for(na_, WPB), WPB * 32, 0, s>>>(coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, na_,
+                                                              St_.p, xh_.p, yh_.p);
+        if (timing_on_) ev_.end(s);
+        DH2_CHECK_LAUNCH("k_coupling");
+    }
+    off = 0;
+    for (int l = 1; l <= hs_.depth; ++l) {
+        int64_t cnt = bwd_level_counts_[l];
+        if (cnt) {
+            if (timing_on_) ev_.begin(K_MV_BACKWARD, s);
+            k_backward<T><<<grid_for(cnt, WPB), WPB * 32, 0, s>>>(bwd_pairs_.p + off, bwd_ptr_.p + off, bwd_.p,
+                                                                  yh_off_.p, krow_d_.p, cnt, Q_[0].p, yh_.p);
+            if (timing_on_) ev_.end(s);
+            DH2_CHECK_LAUNCH("k_backward");
+        }
+        off += cnt;
+    }
+    if (n_leaves_) {
+        if (dtype == DH2_C64) {
+            if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);
+            k_leaf_out<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+                                                                    yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
+            if (timing_on_) ev_.end(s);
+        }
+        else {
+            if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);
+            k_leaf_out<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+                                                                     yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
+            if (timing_on_) ev_.end(s);
+        }
+        DH2_CHECK_LAUNCH("k_leaf_out");
+    }
+    if (timing_on_) ev_.collect(info);
+}
+
+// ----------------------------------------------------------------------------- exports
+
+template <class T>
+void Num<T>::export_pair(int which, int64_t tc, double* out, int64_t cap, int32_t* rows, int32_t* cols,
+                         cudaStream_t s) {
+    *rows = 0;
+    *cols = 0;
+    if (tc < 0 || tc >= (int64_t)hs_.aidx.size()) throw Error{DH2_EINVAL, "pair index out of range"};
+    const int32_t a = hs_.aidx[tc];
+    if (a < 0) return;
+    const int pass = (which == DH2_X_ZCOL || which == DH2_X_SCOL || which == DH2_X_QCOL || which == DH2_X_CCOL) ? 1 : 0;
+    int64_t r = 0, c = 0, ld = 0, off = 0;
+    const void* src = nullptr;
+    bool is_double = std::is_same<T, double>::value, is_real = false;
+    const int rowsA = leaf_[a] ? rows_[a] : rank_[pass][sons_[0][a]] + rank_[pass][sons_[1][a]];
+    switch (which) {
+        case DH2_X_R: r = rR_[a]; c = k_; ld = k_; off = offR_[a]; src = R_.p; break;
+        case DH2_X_ZROW: case DH2_X_ZCOL: r = rZ_[pass][a]; c = k_; ld = k_; off = offZ_[pass][a]; src = Z_[pass].p; break;
+        case DH2_X_SROW: case DH2_X_SCOL:
+            r = 1; c = std::min(rowsA, rZ_[pass][a]); ld = c; off = offSig_[pass][a]; src = sig_[pass].p;
+            is_real = true; is_double = true; break;
+        case DH2_X_QROW: case DH2_X_QCOL: r = rowsA; c = rank_[pass][a]; ld = ldQ_[pass][a]; off = offQ_[pass][a]; src = Q_[pass].p; break;
+        case DH2_X_CROW: case DH2_X_CCOL: r = rank_[pass][a]; c = k_; ld = k_; off = offC_[pass][a]; src = Cd_[pass].p; is_double = true; break;
+        default: throw Error{DH2_EINVAL, "unknown export"};
+    }
+    if (r * c > cap) throw Error{DH2_EINVAL, "export buffer too small"};
+    *rows = (int32_t)r;
+    *cols = (int32_t)c;
+    if (r * c == 0) return;
+    const int64_t span = (r - 1) * ld + c;
+    if (is_real) {
+        std::vector<double> hbuf(span);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(hbuf.data(), (const double*)src + off, span * sizeof(double), cudaMemcpyDeviceToHost, s));
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t j = 0; j < c; ++j) {
+            out[2 * j] = hbuf[j];
+            out[2 * j + 1] = 0.0;
+        }
+    } else if (is_double) {
+        std::vector<cx<double>> hbuf(span);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(hbuf.data(), (const cx<double>*)src + off, span * sizeof(cx<double>), cudaMemcpyDeviceToHost, s));
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < r; ++i)
+            for (int64_t j = 0; j < c; ++j) {
+                out[2 * (i * c + j)] = hbuf[i * ld + j].x;
+                out[2 * (i * c + j) + 1] = hbuf[i * ld + j].y;
+            }
+    } else {
+        std::vector<cx<float>> hbuf(span);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(hbuf.data(), (const cx<float>*)src + off, span * sizeof(cx<float>), cudaMemcpyDeviceToHost, s));
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        for (int64_t i = 0; i < r; ++i)
+            for (int64_t j = 0; j < c; ++j) {
+                out[2 * (i * c + j)] = hbuf[i * ld + j].x;
+                out[2 * (i * c + j) + 1] = hbuf[i * ld + j].y;
+            }
+    }
+}
+
+template <class T>
+void Num<T>::export_ranks(int32_t* rr, int32_t* rc, cudaStream_t) {
+    const int64_t ntc = (int64_t)hs_.aidx.size();
+    for (int64_t tc = 0; tc < ntc; ++tc) {
+        int32_t a = hs_.aidx[tc];
+        if (rr) rr[tc] = a < 0 ? -1 : rank_[0][a];
+        if (rc) rc[tc] = a < 0 ? -1 : rank_[1][a];
+    }
+}
+
+std::unique_ptr<NumBase> make_numeric(const Tree& tr, Structure& st, const HostStructure& hs,
+                                      const BuildParams& bp) {
+    if (bp.precision == DH2_FP64) return std::unique_ptr<NumBase>(new Num<double>(tr, st, hs, bp));
+    return std::unique_ptr<NumBase>(new Num<float>(tr, st, hs, bp));
+}
+
+}  // namespace dh2

@@ -1,0 +1,71 @@
+// Numeric part of the DH^2 matrix: analytic stage, recompression, matvec.
+#pragma once
+
+#include <memory>
+
+#include "common.cuh"
+#include "linalg.cuh"
+#include "structure.cuh"
+
+namespace dh2 {
+
+// Structure arrays copied to the host once, for scheduling and memory layout.
+struct HostStructure {
+    int32_t nc = 0, depth = 0;
+    std::vector<int32_t> offset, size, parent, son0, son1, level, level_start;
+    std::vector<int32_t> tc_base, aidx, a_t, a_c, alevel_start;
+    std::vector<int32_t> row_ptr, row_idx, col_ptr, col_idx;
+    std::vector<int32_t> adm_t, adm_s, adm_c, near_t, near_s;
+    std::vector<int32_t> sd, dir_off, isd_ptr, isd_idx;
+    int64_t nactive = 0;
+    int32_t pair_of(int32_t t, int32_t c) const { return aidx[tc_base[t] + c]; }
+    int32_t son_dir(int32_t t, int32_t c) const { return sd[dir_off[level[t]] + c]; }
+};
+
+enum Stage {
+    ST_STRUCTURE = 0, ST_NEARFIELD, ST_ANALYTIC, ST_BASIS_WEIGHTS, ST_TOTAL_WEIGHTS_ROW,
+    ST_TOTAL_WEIGHTS_COL, ST_TRUNCATE_ROW, ST_TRUNCATE_COL, ST_PROJECT, ST_MATVEC_PLAN, ST_COUNT
+};
+
+struct BuildParams {
+    double kappa, eta, eps;
+    int32_t m, precision, rank_rule, qr_fp64;
+    int64_t workspace_bytes;
+};
+
+enum KernelId {
+    K_NEARFIELD = 0, K_LEAF_BASIS, K_TRANSFER, K_KRON, K_STACK_BLOCKS, K_TSQR, K_TRUNCATE, K_PROJECT,
+    K_MV_GATHER, K_MV_FORWARD, K_MV_COUPLING, K_MV_BACKWARD, K_MV_LEAF_OUT, K_COUNT
+};
+extern const char* const kKernelNames[K_COUNT];
+
+struct MatrixInfoAcc {
+    int64_t near_entries = 0, coupling_entries = 0, basis_entries = 0, matvec_bytes = 0;
+    int32_t max_rank_row = 0, max_rank_col = 0;
+    double mean_rank_row = 0, mean_rank_col = 0;
+    double stage_ms[16] = {0};
+    double kernel_ms[16] = {0};
+    int64_t kernel_launches[16] = {0};
+    double kernel_work[16] = {0};
+    int32_t kernel_work_kind[16] = {0};
+};
+enum WorkKind { W_NONE = 0, W_FLOP32 = 1, W_FLOP64 = 2, W_BYTES = 3 };
+
+class NumBase {
+public:
+    virtual ~NumBase() = default;
+    virtual void build(cudaStream_t s) = 0;
+    virtual void matvec(const void* x, void* y, int dtype, cudaStream_t s) = 0;
+    virtual void export_pair(int which, int64_t tc, double* out, int64_t cap, int32_t* rows,
+                             int32_t* cols, cudaStream_t s) = 0;
+    virtual void export_ranks(int32_t* rr, int32_t* rc, cudaStream_t s) = 0;
+    virtual void set_timing(bool on) = 0;
+    MatrixInfoAcc info;
+};
+
+std::unique_ptr<NumBase> make_numeric(const Tree& tr, Structure& st, const HostStructure& hs,
+                                      const BuildParams& bp);
+
+void download_structure(const Tree& tr, const Structure& st, HostStructure& hs, cudaStream_t s);
+
+}  // namespace dh2

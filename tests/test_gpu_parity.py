@@ -1,0 +1,183 @@
+"""GPU path (through the C ABI) against the CPU oracle.
+
+Integer structure (cluster tree, boxes, directions, son maps, block tree, active
+pairs) must be bit-exact.  Floating point is compared on the invariants the
+paper fixes (QR and SVD factors are unique only up to phases): R^*R, Z^*Z,
+singular values, ranks (ties at the threshold excused), and the matvec.
+"""
+import numpy as np
+import pytest
+
+from tests.cases import mesh, params
+from tests.gpu_common import TOL, gpu_matrix, oracle_recompression, oracle_structure, rel, x_vector
+
+pytestmark = pytest.mark.gpu
+
+STRUCT_CASES = ["plain1280", "laplace1280", "lowfreq1280", "dir320", "mixed1280", "dir1280"]
+NUM_CASES = ["dir320", "mixed1280", "lowfreq1280"]
+PRECISIONS = ["fp64", "mixed"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_04384_gb300.build import build
+
+    build()
+
+
+@pytest.mark.parametrize("name", STRUCT_CASES)
+def test_cluster_tree_bit_exact(name):
+    import paper_1809_04384_gb300 as dh2
+
+    v, f, p, tr, *_ = oracle_structure(name)
+    g = dh2.Tree(v, f, leaf_max=p["leaf"]).export()
+    assert np.array_equal(g["perm"], tr.perm)
+    for key in ("offset", "size", "parent", "son0", "son1", "level"):
+        assert np.array_equal(g[key], getattr(tr, key)), key
+    assert np.array_equal(g["lo"], tr.lo) and np.array_equal(g["hi"], tr.hi)
+
+
+def test_point_mode_tree_bit_exact():
+    import paper_1809_04384_gb300 as dh2
+    import synth
+    from oracle.structure import point_cluster_tree
+
+    pts = synth.point_cloud(3000, 5)
+    ref = point_cluster_tree(pts, 16)
+    g = dh2.Tree(pts, None, leaf_max=16).export()
+    assert np.array_equal(g["perm"], ref.perm)
+    assert np.array_equal(g["son0"], ref.son0) and np.array_equal(g["lo"], ref.lo)
+
+
+def test_degenerate_split_median_rule():
+    """All centroids equal along every axis: the median rule splits by index."""
+    import paper_1809_04384_gb300 as dh2
+    from oracle.structure import point_cluster_tree
+
+    pts = np.zeros((37, 3))
+    ref = point_cluster_tree(pts, 4)
+    g = dh2.Tree(pts, None, leaf_max=4).export()
+    assert np.array_equal(g["perm"], ref.perm) and np.array_equal(g["size"], ref.size)
+
+
+@pytest.mark.parametrize("name", STRUCT_CASES)
+def test_directions_and_blocks_bit_exact(name):
+    v, f, p, tr, dirs, bt = oracle_structure(name)
+    _, mat = gpu_matrix(name, "mixed")
+    for l in range(tr.depth + 1):
+        ms, D, sd = mat.directions(l)
+        assert ms == dirs.msplit[l]
+        assert np.array_equal(D, dirs.dirs[l])
+        if l < tr.depth:
+            assert np.array_equal(sd, dirs.sd[l])
+    adm, near, active = mat.blocks()
+    assert np.array_equal(adm, bt.adm)
+    assert np.array_equal(near, bt.near)
+    from oracle.structure import PairIndex
+
+    assert np.array_equal(active, PairIndex(tr, dirs, bt).active)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_dense_case_equals_galerkin_matrix(precision):
+    """1280 triangles with the paper's parameters: no admissible block, DH^2 = G."""
+    import torch
+
+    rc = oracle_recompression("plain1280")
+    _, mat = gpu_matrix("plain1280", precision)
+    x = x_vector(rc.tree.n)
+    G = rc.dh2.disc.dense(rc.dh2.kappa)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+    assert rel(y, G @ x) <= TOL[precision]["near"]
+
+
+@pytest.mark.parametrize("name", NUM_CASES)
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_weights_and_singular_values(name, precision):
+    import paper_1809_04384_gb300 as dh2
+
+    rc = oracle_recompression(name)
+    _, mat = gpu_matrix(name, precision)
+    tol = TOL[precision]
+    P = rc.pairs
+    for tc in np.nonzero(P.active)[0]:
+        R = mat.pair(dh2.DH2_X_R, tc)
+        Ro = rc.R[tc]
+        assert R.shape == Ro.shape
+        go = Ro.conj().T @ Ro
+        assert rel(R.conj().T @ R, go) <= tol["gram"], ("R", tc)
+        for which, Zo in ((dh2.DH2_X_ZROW, rc.ZR[tc]), (dh2.DH2_X_ZCOL, rc.ZC[tc])):
+            Z = mat.pair(which, tc)
+            assert Z.shape == Zo.shape
+            if Zo.size:
+                assert rel(Z.conj().T @ Z, Zo.conj().T @ Zo) <= tol["gram"], ("Z", which, tc)
+        for which, so in ((dh2.DH2_X_SROW, rc.row["sigma"][tc]), (dh2.DH2_X_SCOL, rc.col["sigma"][tc])):
+            s = mat.pair(which, tc).real.ravel()
+            n = min(len(s), len(so))
+            if n:
+                scale = max(so[0], 1e-300) ** 2
+                assert np.abs(s[:n] ** 2 - so[:n] ** 2).max() <= tol["sigma2"] * scale, ("sigma", which, tc)
+
+
+@pytest.mark.parametrize("name", NUM_CASES)
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_ranks_match_except_threshold_ties(name, precision):
+    rc = oracle_recompression(name)
+    _, mat = gpu_matrix(name, precision)
+    rr, rcl = mat.ranks()
+    eps2 = rc.eps ** 2
+    slack = TOL[precision]["rank_slack"]
+    P = rc.pairs
+    mismatches = 0
+    for tc in np.nonzero(P.active)[0]:
+        for got, basis in ((rr[tc], rc.row), (rcl[tc], rc.col)):
+            want = basis["rank"][tc]
+            if got == want:
+                continue
+            mismatches += 1
+            s2 = basis["sigma"][tc] ** 2
+            tail_at = float(s2[min(got, want):].sum())
+            tail_next = float(s2[max(got, want):].sum())
+            # the threshold lies between the two tails: a tie within rounding
+            assert abs(tail_at - eps2) <= slack * eps2 or abs(tail_next - eps2) <= slack * eps2, (tc, got, want)
+    assert mismatches <= max(2, 0.01 * 2 * P.active.sum())
+
+
+@pytest.mark.parametrize("name", NUM_CASES)
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_matvec_matches_oracle(name, precision):
+    import torch
+
+    rc = oracle_recompression(name)
+    _, mat = gpu_matrix(name, precision)
+    x = x_vector(rc.tree.n)
+    y_ref = rc.matvec(x)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+    rr, rcl = mat.ranks()
+    P = rc.pairs
+    same = all(rr[tc] == rc.row["rank"][tc] and rcl[tc] == rc.col["rank"][tc] for tc in np.nonzero(P.active)[0])
+    tol = TOL[precision]["matvec_same_ranks"] if same else 2 * rc.eps
+    assert rel(y, y_ref) <= tol
+    # both are equally close to the dense Galerkin matrix
+    G = rc.dh2.disc.dense(rc.dh2.kappa)
+    e_gpu, e_ref = rel(y, G @ x), rel(y_ref, G @ x)
+    assert e_gpu <= e_ref * 1.05 + 1e-6
+    # the host entry point gives the same product (complex128 in and out)
+    yh = mat.matvec_host(x)
+    assert rel(yh, y) <= TOL[precision]["matvec_same_ranks"]
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_matvec_dtypes_agree(precision):
+    import torch
+
+    _, mat = gpu_matrix("mixed1280", precision)
+    x = x_vector(mat.n)
+    y64 = mat.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy()
+    y128 = mat.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert rel(y64.astype(np.complex128), y128) <= 1e-5
