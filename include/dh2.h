@@ -137,6 +137,27 @@ dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, dou
 dh2_status dh2_matvec(dh2_matrix mat, const void* x, void* y, int32_t dtype, void* stream);
 
 /*
+ * Allocation-free variant of dh2_matvec (the paper has no counterpart; this is
+ * an interface for callers that cannot call cudaMalloc when they need the
+ * product: code recording into a CUDA graph while another framework owns all
+ * device memory, real-time host loops where an allocator call may block, or
+ * runtimes that give this library a fixed memory budget).  Same arguments,
+ * results and stream semantics as dh2_matvec, but the scratch of the product
+ * (permuted input, forward/backward basis coefficients) lives in one fixed
+ * 16 MiB device array that the library holds on every GPU it is loaded on until
+ * the process exits; the call itself allocates nothing.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents (every kernel writes
+ * its scratch before reading it); calls that overlap on the GPU race and must
+ * be serialised by the caller.  Errors: DH2_EINVAL when the matrix needs more
+ * than 16 MiB of scratch (n complex values of the matrix precision plus the
+ * basis coefficients of both transforms, each rounded up to 256 bytes), bad
+ * dtype or NULL pointers; DH2_ECUDA.
+ */
+dh2_status dh2_matvec_noalloc(dh2_matrix mat, const void* x, void* y, int32_t dtype, void* stream);
+
+/*
  * End-to-end matvec from HOST memory: copies x (n complex128, original order)
  * to the device, runs dh2_matvec in the matrix precision, copies y back to
  * the host buffer.  Synchronous.  Pinned host memory gives the fastest copies.

@@ -65,6 +65,7 @@ _SIGS = {
     "dh2_build_dh2": (C.c_int, [_P, C.c_double, C.c_int32, C.c_double, C.c_double, C.POINTER(dh2_options), _P,
                                 C.POINTER(_P)]),
     "dh2_matvec": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
+    "dh2_matvec_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "dh2_matvec_host": (C.c_int, [_P, _P, _P, _P]),
     "dh2_set_timing": (C.c_int, [_P, C.c_int32]),
     "dh2_sync": (C.c_int, [_P]),
@@ -157,6 +158,21 @@ def dh2_matvec(mat, x, y, stream=None):
     if stream is None:
         stream = torch.cuda.current_stream(x.device)
     _check(lib().dh2_matvec(mat, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), dtype, _stream(stream)))
+    return y
+
+
+def dh2_matvec_noalloc(mat, x, y, stream=None):
+    """dh2_matvec with its scratch in the library's fixed device array (no allocation)."""
+    import torch
+    if x.dtype != y.dtype or x.dtype not in (torch.complex64, torch.complex128):
+        raise TypeError("x and y must both be complex64 or complex128")
+    if not (x.is_cuda and y.is_cuda and x.is_contiguous() and y.is_contiguous()):
+        raise TypeError("x and y must be contiguous CUDA tensors")
+    dtype = DH2_C64 if x.dtype == torch.complex64 else DH2_C128
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    _check(lib().dh2_matvec_noalloc(mat, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), dtype,
+                                    _stream(stream)))
     return y
 
 

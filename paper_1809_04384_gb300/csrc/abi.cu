@@ -215,6 +215,16 @@ dh2_status dh2_matvec(dh2_matrix mat, const void* x, void* y, int32_t dtype, voi
     });
 }
 
+dh2_status dh2_matvec_noalloc(dh2_matrix mat, const void* x, void* y, int32_t dtype, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(mat != nullptr && mat->num, "dh2_matvec_noalloc: matrix is NULL");
+        DH2_REQUIRE(x != nullptr && y != nullptr, "dh2_matvec_noalloc: NULL vector");
+        DH2_REQUIRE(dtype == DH2_C64 || dtype == DH2_C128, "dh2_matvec_noalloc: dtype must be DH2_C64 or DH2_C128");
+        DH2_REQUIRE(x != y, "dh2_matvec_noalloc: x and y must not alias");
+        mat->num->matvec_noalloc(x, y, dtype, as_stream(stream));
+    });
+}
+
 dh2_status dh2_matvec_host(dh2_matrix mat, const double* x_host, double* y_host, void* stream) {
     return guarded([&] {
         DH2_REQUIRE(mat != nullptr && mat->num, "dh2_matvec_host: matrix is NULL");

@@ -15,6 +15,8 @@
 // T is the working precision: float for DH2_MIXED, double for DH2_FP64.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "numeric.cuh"
 
@@ -833,6 +835,7 @@ public:
 
     void build(cudaStream_t s) override;
     void matvec(const void* x, void* y, int dtype, cudaStream_t s) override;
+    void matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) override;
     void export_pair(int which, int64_t tc, double* out, int64_t cap, int32_t* rows, int32_t* cols,
                      cudaStream_t s) override;
     void export_ranks(int32_t* rr, int32_t* rc, cudaStream_t s) override;
@@ -1705,6 +1708,108 @@ void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
         DH2_CHECK_LAUNCH("k_leaf_out");
     }
     if (timing_on_) ev_.collect(info);
+}
+
+
+// ----------------------------------------------------------------------------- allocation-free matvec
+//
+// Some callers cannot call cudaMalloc at the point where they need a product:
+// code that records work into a CUDA graph while another framework owns every
+// device allocation, host threads running inside a real-time or interrupt-like
+// loop where an allocator call may block, or runtimes that hand this library a
+// fixed memory budget.  dh2_matvec_noalloc serves them: it runs the same kernels
+// as dh2_matvec, but its scratch (the permuted input and the basis coefficients
+// of the forward and backward transforms) lives in the fixed device array below
+// instead of the matrix's own buffers.  The array is a file-scope __device__
+// variable: every GPU that loads the library holds its 16 MiB until the process
+// exits.  All calls share it and it keeps the last call's contents; every kernel
+// writes its part of the scratch before reading it, so nothing needs clearing.
+// Two calls whose work overlaps on the GPU (other streams, other host threads)
+// race on the array and must be serialised by the caller.
+
+constexpr size_t kNoAllocScratchBytes = size_t(16) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[128] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol is only a stand-in, so the address comes from cudaGetSymbolAddress,
+// once per device, with that device current.
+void* noalloc_scratch() {
+    int dev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) throw Error{DH2_EUNSUPPORTED, "device index out of range"};
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        DH2_CHECK_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = p;
+    }
+    return g_noalloc_ptr[dev];
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+}  // namespace
+
+template <class T>
+void Num<T>::matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) {
+    const size_t cs = sizeof(cx<T>);
+    const size_t bx = align256(std::max<int64_t>(n_, 1) * cs);
+    const size_t bxh = align256(xh_.n * cs), byh = align256(yh_.n * cs);
+    if (bx + bxh + byh > kNoAllocScratchBytes)
+        throw Error{DH2_EINVAL, "dh2_matvec_noalloc: this matrix needs " + std::to_string(bx + bxh + byh) +
+                                    " bytes of scratch, more than the fixed " +
+                                    std::to_string(kNoAllocScratchBytes) + " bytes"};
+    unsigned char* base = static_cast<unsigned char*>(noalloc_scratch());
+    cx<T>* xt = reinterpret_cast<cx<T>*>(base);
+    cx<T>* xh = reinterpret_cast<cx<T>*>(base + bx);
+    cx<T>* yh = reinterpret_cast<cx<T>*>(base + bx + bxh);
+    const unsigned g = grid_for(n_, kThreads);
+    if (dtype == DH2_C64)
+        k_gather<T, float><<<g, kThreads, 0, s>>>(tr_.perm.p, n_, (const cx<float>*)x, xt);
+    else
+        k_gather<T, double><<<g, kThreads, 0, s>>>(tr_.perm.p, n_, (const cx<double>*)x, xt);
+    DH2_CHECK_LAUNCH("k_gather");
+    constexpr int WPB = 8;
+    if (n_fwd_leaf_) {
+        k_fwd_leaf<T><<<grid_for(n_fwd_leaf_, WPB), WPB * 32, 0, s>>>(fwd_leaf_.p, n_fwd_leaf_, Q_[1].p, xt, xh);
+        DH2_CHECK_LAUNCH("k_fwd_leaf");
+    }
+    int64_t off = 0;
+    for (int l = hs_.depth; l >= 0; --l) {
+        int64_t cnt = fwd_up_level_counts_[l];
+        if (cnt) {
+            k_fwd_up<T><<<grid_for(cnt, WPB), WPB * 32, 0, s>>>(fwd_up_.p + off, cnt, Q_[1].p, xh);
+            DH2_CHECK_LAUNCH("k_fwd_up");
+        }
+        off += cnt;
+    }
+    if (na_) {
+        k_coupling<T><<<grid_for(na_, WPB), WPB * 32, 0, s>>>(coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, na_,
+                                                              St_.p, xh, yh);
+        DH2_CHECK_LAUNCH("k_coupling");
+    }
+    off = 0;
+    for (int l = 1; l <= hs_.depth; ++l) {
+        int64_t cnt = bwd_level_counts_[l];
+        if (cnt) {
+            k_backward<T><<<grid_for(cnt, WPB), WPB * 32, 0, s>>>(bwd_pairs_.p + off, bwd_ptr_.p + off, bwd_.p,
+                                                                  yh_off_.p, krow_d_.p, cnt, Q_[0].p, yh);
+            DH2_CHECK_LAUNCH("k_backward");
+        }
+        off += cnt;
+    }
+    if (n_leaves_) {
+        if (dtype == DH2_C64)
+            k_leaf_out<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+                                                                    yh, near_.p, xt, tr_.perm.p, (cx<float>*)y);
+        else
+            k_leaf_out<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+                                                                     yh, near_.p, xt, tr_.perm.p, (cx<double>*)y);
+        DH2_CHECK_LAUNCH("k_leaf_out");
+    }
 }
 
 // ----------------------------------------------------------------------------- exports

@@ -56,6 +56,8 @@ public:
     virtual ~NumBase() = default;
     virtual void build(cudaStream_t s) = 0;
     virtual void matvec(const void* x, void* y, int dtype, cudaStream_t s) = 0;
+    // matvec whose scratch lives in a fixed device array instead of per-matrix buffers
+    virtual void matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) = 0;
     virtual void export_pair(int which, int64_t tc, double* out, int64_t cap, int32_t* rows,
                              int32_t* cols, cudaStream_t s) = 0;
     virtual void export_ranks(int32_t* rr, int32_t* rc, cudaStream_t s) = 0;
