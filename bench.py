@@ -40,6 +40,7 @@ WORKLOADS = {
     # name: (icosphere level, kappa, leaf, eta1, eta2, m, eps)
     "sphere20480": (5, 16.0, 32, 10.0, 1.0, 5, 1e-4),
     "sphere1280": (3, 4.0, 32, 10.0, 1.0, 4, 1e-4),
+    "sphere5120": (4, 8.0, 32, 10.0, 1.0, 5, 1e-4),     # same kappa h, for profiling captures
 }
 METRIC = "DH2 build s + matvec GB/s at rel.err≤1e-4 vs dense; vs plain FP64 GPU form"
 
@@ -389,7 +390,9 @@ def main():
                            l2="inputs larger than L2 (nearfield alone > 1 GB)"),
             "build_s": build_s,
             "matvec": {"gbs": mv_gbs, "ms": mv_rep_ms, "bytes": info.matvec_bytes,
-                       "relerr_sampled_dense": err, "rows_sampled": args.error_rows},
+                       "relerr_sampled_dense": err, "rows_sampled": args.error_rows,
+                       "kernel_ms": {k: round(v_[0] / max(v_[1], 1) * (v_[1] / 10), 4)
+                                     for k, v_ in mv_kernels.items()}},
             "ranks": {"max_row": info.max_rank_row, "mean_row": info.mean_rank_row,
                       "max_col": info.max_rank_col, "mean_col": info.mean_rank_col},
             "storage": {"near_entries": info.near_entries, "coupling_entries": info.coupling_entries,

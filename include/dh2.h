@@ -57,6 +57,8 @@ typedef struct {
                                weighted by 1/|G_b|_F (blockwise relative Frobenius, Section 5);
                                DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted */
     int32_t qr_fp64;        /* DH2_MIXED only: 1 = run the weight QRs (R, Z-hat) in FP64 */
+    int32_t qr_group_rows;  /* stacks taller than this are factored in row groups whose R
+                               factors are merged by a second QR (0 = 1024) */
     int64_t workspace_bytes;/* cap on the stacked weight workspace per level (0 = 16 GiB) */
 } dh2_options;
 

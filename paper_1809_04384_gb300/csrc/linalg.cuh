@@ -43,6 +43,10 @@ template <class T> __device__ __forceinline__ void fma_cjx(cx<T>& acc, cx<T> a, 
     acc.y = fma(-a.y, b.x, acc.y);
 }
 template <class T> __device__ __forceinline__ cx<T> zero() { return cx<T>{T(0), T(0)}; }
+// smallest positive normal number
+template <class T> __device__ __forceinline__ T tiny_normal();
+template <> __device__ __forceinline__ float tiny_normal<float>() { return 1.17549435e-38f; }
+template <> __device__ __forceinline__ double tiny_normal<double>() { return 2.2250738585072014e-308; }
 
 template <class T>
 __device__ __forceinline__ cx<T> shfl_xor(cx<T> v, int o) {
@@ -209,60 +213,152 @@ __device__ void kron_apply(int rows, int m, const cx<T>* fac, bool adjoint, cons
 
 // --------------------------------------------------------------------------- Householder TSQR
 
-// R (k x k, row-major, global, upper triangular) <- R-factor of [R; W] where W is
-// the h x k block held column-major in shared memory (ldw = rows per column,
-// rows >= h are zero).  Column reflectors follow LAPACK's xLARFG convention
-// (real beta); W is overwritten.  blockDim.x must be a multiple of 32; each lane
-// owns rows lane + 32 q, q < RPL.
-template <class T, int RPL>
-__device__ void tsqr_chunk(int k, cx<T>* R, cx<T>* W, cx<T>* s_tau, int* s_skip) {
-    constexpr int LDW = 32 * RPL;
+// R (k x k, row-major, global, upper triangular) <- R-factor of [R; W] where W is the
+// block of H = 32*RPL extra rows held column-major in shared memory with leading
+// dimension LDW = H + 1 (odd, so that lanes reading different columns hit different
+// banks); rows >= h are zero.  Column reflectors follow LAPACK's xLARFG convention (real
+// beta); the reflector of column j is e_j on the R side and its W part overwrites W[:, j].
+// Blocked by NB columns: the panel is factored by warp 0 (warp-synchronous), the panel's
+// reflectors are combined in compact WY form (T upper triangular, LAPACK xLARFT forward
+// columnwise), and the trailing columns are updated with two small shared-memory GEMMs:
+// Wm = U^H A, Wm <- T^H Wm, A <- A - U Wm.  Scratch: s_tau[NB], s_skip[NB], s_T[NB*NB],
+// s_G[NB*NB], s_Wm[NB*k].
+template <class T, int RPL, int NB>
+__device__ void tsqr_chunk(int k, cx<T>* R, cx<T>* W, cx<T>* s_tau, int* s_skip, cx<T>* s_T,
+                           cx<T>* s_G, cx<T>* s_Wm) {
+    constexpr int H = 32 * RPL, LDW = H + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int j = 0; j < k; ++j) {
+    for (int j0 = 0; j0 < k; j0 += NB) {
+        const int nbc = min(NB, k - j0);
+        // ---- panel factorisation (warp 0)
         if (warp == 0) {
-            cx<T>* wj = W + (int64_t)j * LDW;
-            const cx<T> al = R[(int64_t)j * k + j];   // read before the shuffles below
-            T xn2 = 0;
+            for (int jj = 0; jj < nbc; ++jj) {
+                const int j = j0 + jj;
+                cx<T>* wj = W + (int64_t)j * LDW;
+                const cx<T> al = R[(int64_t)j * k + j];   // read before the shuffles below
+                // The column is scaled by its largest entry before squaring (as LAPACK's
+                // xLARFG rescales): rank-deficient columns of a merged stack hold rounding
+                // remainders whose squares are denormal, and 1/|alpha - beta|^2 would overflow.
+                T xmax = 0;
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) xn2 += abs2(wj[lane + 32 * q]);
-            xn2 = warp_sum_r(xn2);
-            if (xn2 == T(0)) {
-                if (lane == 0) *s_skip = 1;
-            } else {
-                T beta = -copysign(sqrt(abs2(al) + xn2), al.x);
-                cx<T> tauc = mk<T>((beta - al.x) / beta, al.y / beta);
-                cx<T> d = mk<T>(al.x - beta, al.y);
-                T dn = T(1) / abs2(d);
-                cx<T> sc = mk<T>(d.x * dn, -d.y * dn);   // 1 / (alpha - beta)
+                for (int q = 0; q < RPL; ++q) {
+                    const cx<T> x = wj[lane + 32 * q];
+                    xmax = fmax(xmax, fmax(fabs(x.x), fabs(x.y)));
+                }
 #pragma unroll
-                for (int q = 0; q < RPL; ++q) wj[lane + 32 * q] = wj[lane + 32 * q] * sc;
+                for (int o = 16; o > 0; o >>= 1) xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+                if (!(xmax >= tiny_normal<T>())) {   // uniform over the warp: a numerically zero column
+                    if (lane == 0) {
+                        s_skip[jj] = 1;
+                        s_tau[jj] = zero<T>();
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                const T amax = fmax(xmax, fmax(fabs(al.x), fabs(al.y)));
+                const T inv = T(1) / amax;
+                T xn2 = 0;
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) xn2 += abs2(inv * wj[lane + 32 * q]);
+                xn2 = warp_sum_r(xn2);
+                const cx<T> als = inv * al;
+                const T betas = -copysign(sqrt(abs2(als) + xn2), als.x);   // beta / amax, O(1)
+                const cx<T> tauc = mk<T>((betas - als.x) / betas, als.y / betas);
+                const cx<T> d = mk<T>(als.x - betas, als.y);
+                const T dn = inv / abs2(d);
+                const cx<T> sc = mk<T>(d.x * dn, -d.y * dn);   // 1 / (alpha - beta)
+                cx<T> v[RPL];
+#pragma unroll
+                for (int q = 0; q < RPL; ++q) {
+                    v[q] = wj[lane + 32 * q] * sc;
+                    wj[lane + 32 * q] = v[q];
+                }
                 if (lane == 0) {
-                    R[(int64_t)j * k + j] = mk<T>(beta, T(0));
-                    *s_tau = tauc;
-                    *s_skip = 0;
+                    R[(int64_t)j * k + j] = mk<T>(betas * amax, T(0));
+                    s_tau[jj] = tauc;
+                    s_skip[jj] = 0;
+                }
+                for (int l = j + 1; l < j0 + nbc; ++l) {
+                    cx<T>* wl = W + (int64_t)l * LDW;
+                    const cx<T> rjl = R[(int64_t)j * k + l];
+                    cx<T> s = zero<T>();
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) fma_cjx(s, v[q], wl[lane + 32 * q]);
+                    s = warp_sum(s);
+                    const cx<T> tw = tauc * (rjl + s);
+#pragma unroll
+                    for (int q = 0; q < RPL; ++q) wl[lane + 32 * q] = wl[lane + 32 * q] - v[q] * tw;
+                    if (lane == 0) R[(int64_t)j * k + l] = rjl - tw;
+                }
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        const int l0 = j0 + nbc, nl = k - l0;
+        if (nl <= 0) break;
+        // ---- T of the compact WY form; G[p][i] = v_p^H v_i (p < i)
+        for (int pr = warp; pr < nbc * nbc; pr += nwarps) {
+            const int p = pr / nbc, i = pr - p * nbc;
+            if (p >= i) continue;
+            const cx<T>* vp = W + (int64_t)(j0 + p) * LDW;
+            const cx<T>* vi = W + (int64_t)(j0 + i) * LDW;
+            cx<T> s = zero<T>();
+#pragma unroll
+            for (int q = 0; q < RPL; ++q) fma_cjx(s, vp[lane + 32 * q], vi[lane + 32 * q]);
+            s = warp_sum(s);
+            if (lane == 0) s_G[p * NB + i] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int i = 0; i < nbc; ++i) {
+                const cx<T> tau = s_skip[i] ? zero<T>() : conj(s_tau[i]);
+                s_T[i * NB + i] = tau;
+                for (int p = 0; p < i; ++p) {
+                    cx<T> acc = zero<T>();
+                    for (int q = p; q < i; ++q) fma_cx(acc, s_T[p * NB + q], s_G[q * NB + i]);
+                    s_T[p * NB + i] = zero<T>() - tau * acc;
                 }
             }
         }
         __syncthreads();
-        if (!*s_skip) {
-            const cx<T> tauc = *s_tau;
-            const cx<T>* v = W + (int64_t)j * LDW;
-            cx<T> vr[RPL];
+        // ---- Wm = U^H A over the trailing columns
+        for (int idx = threadIdx.x; idx < nbc * nl; idx += blockDim.x) {
+            const int p = idx / nl, l = idx - p * nl;
+            const cx<T>* vp = W + (int64_t)(j0 + p) * LDW;
+            const cx<T>* wl = W + (int64_t)(l0 + l) * LDW;
+            cx<T> acc = R[(int64_t)(j0 + p) * k + l0 + l];
+#pragma unroll 8
+            for (int r = 0; r < H; ++r) fma_cjx(acc, vp[r], wl[r]);
+            s_Wm[p * k + l] = acc;
+        }
+        __syncthreads();
+        // ---- Wm <- T^H Wm and the R rows of the panel
+        for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+            cx<T> col[NB];
 #pragma unroll
-            for (int q = 0; q < RPL; ++q) vr[q] = v[lane + 32 * q];
-            for (int l = j + 1 + warp; l < k; l += nwarps) {
-                cx<T>* wl = W + (int64_t)l * LDW;
-                const cx<T> rjl = R[(int64_t)j * k + l];   // every lane reads before lane 0 writes
-                cx<T> s = zero<T>();
+            for (int p = 0; p < NB; ++p) col[p] = p < nbc ? s_Wm[p * k + l] : zero<T>();
 #pragma unroll
-                for (int q = 0; q < RPL; ++q) fma_cjx(s, vr[q], wl[lane + 32 * q]);
-                s = warp_sum(s);
-                cx<T> w = rjl + s;
-                cx<T> tw = tauc * w;
-#pragma unroll
-                for (int q = 0; q < RPL; ++q) wl[lane + 32 * q] = wl[lane + 32 * q] - vr[q] * tw;
-                if (lane == 0) R[(int64_t)j * k + l] = rjl - tw;
+            for (int p = NB - 1; p >= 0; --p) {
+                if (p >= nbc) continue;
+                cx<T> acc = zero<T>();
+                for (int q = 0; q <= p; ++q) fma_cjx(acc, s_T[q * NB + p], col[q]);
+                col[p] = acc;
             }
+#pragma unroll
+            for (int p = 0; p < NB; ++p) {
+                if (p >= nbc) continue;
+                s_Wm[p * k + l] = col[p];
+                cx<T>* rp = R + (int64_t)(j0 + p) * k + l0 + l;
+                *rp = *rp - col[p];
+            }
+        }
+        __syncthreads();
+        // ---- W <- W - U_W Wm
+        for (int idx = threadIdx.x; idx < H * nl; idx += blockDim.x) {
+            const int l = idx / H, r = idx - l * H;
+            cx<T> acc = W[(int64_t)(l0 + l) * LDW + r];
+            for (int p = 0; p < nbc; ++p) acc = acc - W[(int64_t)(j0 + p) * LDW + r] * s_Wm[p * k + l];
+            W[(int64_t)(l0 + l) * LDW + r] = acc;
         }
         __syncthreads();
     }

@@ -27,6 +27,14 @@ namespace {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kThreads = 256;
 
+// Device error word: kernels that meet a non-finite value set a bit instead of trapping;
+// the host reads the word after each stage and returns DH2_ENUMERIC.
+enum : unsigned {
+    ERR_TSQR_NONFINITE = 1u, ERR_TRUNC_NONFINITE = 2u, ERR_TSQR_INPUT = 4u, ERR_STACK_NONFINITE = 8u,
+    ERR_KRON_NONFINITE = 16u
+};
+__device__ __forceinline__ void raise_err(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+
 // ----------------------------------------------------------------------------- math wrappers
 
 __device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
@@ -286,7 +294,8 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
                                const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
                                const double* __restrict__ nodes, int m, double kappa,
                                const cx<T>* __restrict__ R, const int64_t* __restrict__ roff,
-                               const int32_t* __restrict__ rrows, double* bnorm, cx<T>* stack) {
+                               const int32_t* __restrict__ rrows, double* bnorm, cx<T>* stack,
+                               unsigned* err) {
     extern __shared__ unsigned char smraw[];
     T* D = reinterpret_cast<T*>(smraw);
     T* P = D + 3 * m * m;
@@ -317,7 +326,11 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
         T nrm = sqrt(nrm2);
         if (threadIdx.x == 0) bnorm[tk.b] = (double)nrm;
         T sc_ = nrm > T(0) ? T(1) / nrm : T(0);
-        for (int idx = threadIdx.x; idx < ro * k; idx += blockDim.x) out[idx] = sc_ * out[idx];
+        for (int idx = threadIdx.x; idx < ro * k; idx += blockDim.x) {
+            cx<T> v = sc_ * out[idx];
+            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+            out[idx] = v;
+        }
     } else {
         const T sc_ = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
         // out[i][nu] = sum_mu R_t[i][mu] S[mu][nu] / |G_b|
@@ -369,39 +382,54 @@ struct QRTask {
     int32_t rout;      // min(nrows, k) rows written to dst
 };
 
-// R-factor of the stacked rows: R scratch (k x k, TQ) per CTA slot, chunks of 32*RPL rows
-template <class TS, class TQ, int RPL>
-__global__ void k_tsqr(const QRTask* __restrict__ tasks, int k, const cx<TS>* __restrict__ src,
-                       cx<TQ>* scratch, cx<TS>* dst) {
+constexpr int kQRNB = 8;   // panel width of the blocked Householder update
+
+// R-factor of the stacked rows: R scratch (k x k, TQ) per CTA, chunks of 32*RPL rows.
+// Reads TSrc, writes the rout leading rows of R as TDst.
+template <class TSrc, class TQ, class TDst, int RPL>
+__global__ void __launch_bounds__(256) k_tsqr(const QRTask* __restrict__ tasks, int k,
+                                              const cx<TSrc>* __restrict__ src, cx<TQ>* scratch,
+                                              cx<TDst>* dst, unsigned* err) {
     extern __shared__ unsigned char smraw[];
-    constexpr int LDW = 32 * RPL;
+    constexpr int H = 32 * RPL, LDW = H + 1;
     cx<TQ>* W = reinterpret_cast<cx<TQ>*>(smraw);
-    __shared__ cx<TQ> s_tau;
-    __shared__ int s_skip;
+    cx<TQ>* s_Wm = W + (int64_t)k * LDW;
+    cx<TQ>* s_T = s_Wm + (int64_t)kQRNB * k;
+    cx<TQ>* s_G = s_T + kQRNB * kQRNB;
+    cx<TQ>* s_tau = s_G + kQRNB * kQRNB;
+    int* s_skip = reinterpret_cast<int*>(s_tau + kQRNB);
     const QRTask tk = tasks[blockIdx.x];
     cx<TQ>* R = scratch + (int64_t)blockIdx.x * k * k;
     for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) R[idx] = zero<TQ>();
     __syncthreads();
-    const cx<TS>* S = src + tk.src;
-    for (int r0 = 0; r0 < tk.nrows; r0 += LDW) {
-        const int h = min(LDW, tk.nrows - r0);
-        for (int idx = threadIdx.x; idx < LDW * k; idx += blockDim.x) {
-            int i = idx / k, l = idx % k;     // row-major read, column-major store
+    const cx<TSrc>* S = src + tk.src;
+    for (int r0 = 0; r0 < tk.nrows; r0 += H) {
+        const int h = min(H, tk.nrows - r0);
+        for (int idx = threadIdx.x; idx < H * k; idx += blockDim.x) {
+            const int i = idx / k, l = idx - i * k;     // row-major read, column-major store
             cx<TQ> v = zero<TQ>();
             if (i < h) {
-                cx<TS> u = S[(int64_t)(r0 + i) * k + l];
+                cx<TSrc> u = S[(int64_t)(r0 + i) * k + l];
+                if (!isfinite(u.x) || !isfinite(u.y)) raise_err(err, ERR_TSQR_INPUT);
                 v = cx<TQ>{TQ(u.x), TQ(u.y)};
             }
             W[(int64_t)l * LDW + i] = v;
         }
         __syncthreads();
-        tsqr_chunk<TQ, RPL>(k, R, W, &s_tau, &s_skip);
+        tsqr_chunk<TQ, RPL, kQRNB>(k, R, W, s_tau, s_skip, s_T, s_G, s_Wm);
     }
     __syncthreads();
     for (int idx = threadIdx.x; idx < tk.rout * k; idx += blockDim.x) {
         cx<TQ> v = R[idx];
-        dst[tk.dst + idx] = cx<TS>{TS(v.x), TS(v.y)};
+        if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_TSQR_NONFINITE);
+        dst[tk.dst + idx] = cx<TDst>{TDst(v.x), TDst(v.y)};
     }
+}
+
+template <class TQ, int RPL>
+size_t tsqr_smem_bytes(int k) {
+    return ((size_t)k * (32 * RPL + 1) + (size_t)kQRNB * k + 2 * kQRNB * kQRNB + kQRNB) * sizeof(cx<TQ>) +
+           kQRNB * sizeof(int) + 16;
 }
 
 // ----------------------------------------------------------------------------- truncation (FP64)
@@ -420,7 +448,7 @@ template <class T, class FV>
 __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<T>* __restrict__ Z,
                               cx<double>* Ascr, cx<double>* M, cx<double>* U, JRot<double>* rot,
                               double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct,
-                              double* sig, int32_t* rank, int* s_order, double* s_lam) {
+                              double* sig, int32_t* rank, int* s_order, double* s_lam, unsigned* err) {
     __shared__ double red[32];
     __shared__ int s_rank;
     const int n = tk.rows, rz = tk.rz;
@@ -438,8 +466,16 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
     __syncthreads();
     herm_jacobi<double>(n, M, U, rot, red, 40, 1e-15);
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s_lam[i] = M[(int64_t)i * n + i].x;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double li = M[(int64_t)i * n + i].x;
+        if (!isfinite(li)) {      // never happens for finite input; keeps every index in range
+            raise_err(err, ERR_TRUNC_NONFINITE);
+            li = -INFINITY;
+        }
+        s_lam[i] = li;
+    }
     __syncthreads();
+    // rank of each eigenvalue (descending, ties by index): a permutation of 0..n-1
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double li = s_lam[i];
         int r = 0;
@@ -486,7 +522,7 @@ template <class T>
 __global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Vleaf,
                            const cx<double>* __restrict__ Vhat, const cx<T>* __restrict__ Z,
                            cx<double>* ascr, cx<double>* gscr, int smem_n, double eps, int rule,
-                           cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig, int32_t* rank) {
+                           cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig, int32_t* rank, unsigned* err) {
     extern __shared__ unsigned char smraw[];
     const TruncTask tk = tasks[blockIdx.x];
     const int n = tk.rows;
@@ -512,10 +548,10 @@ __global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<
     (void)gscr;
     if (tk.leaf) {
         truncate_body<T>(tk, DenseCvt<double, T>{Vleaf + tk.vsrc, k, false, false}, k, Z,
-                         ascr + tk.ascratch, M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam);
+                         ascr + tk.ascratch, M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam, err);
     } else {
         truncate_body<T>(tk, Dense<double>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch,
-                         M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam);
+                         M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam, err);
     }
 }
 
@@ -715,6 +751,114 @@ __global__ void k_leaf_out(const LeafOut* __restrict__ leaves, const LeafQ* __re
     }
 }
 
+// y^_tc = sum_{b in row(t,c)} S~_b x^_sc: one CTA per row pair, one thread per (block, row)
+// dot product, partial sums reduced per row in a fixed order (deterministic).  The couplings
+// of one row pair are contiguous (stored in row-list order).
+template <class T>
+__global__ void k_coupling2(const int32_t* __restrict__ ptr, const Coup* __restrict__ items,
+                            const int64_t* __restrict__ yh_off, const int32_t* __restrict__ krow,
+                            const cx<T>* __restrict__ St, const cx<T>* __restrict__ xh, cx<T>* yh) {
+    extern __shared__ unsigned char smraw[];
+    cx<T>* part = reinterpret_cast<cx<T>*>(smraw);
+    const int a = blockIdx.x;
+    const int kt = krow[a];
+    if (kt == 0) return;
+    const int e_begin = ptr[a], e_end = ptr[a + 1];
+    const int cb = max(1, (int)blockDim.x / kt);       // blocks per round
+    cx<T> acc0 = zero<T>(), acc1 = zero<T>();
+    for (int e0 = e_begin; e0 < e_end; e0 += cb) {
+        const int nb = min(cb, e_end - e0);
+        for (int w = threadIdx.x; w < nb * kt; w += blockDim.x) {
+            const int q = w / kt, i = w - q * kt;
+            const Coup it = items[e0 + q];
+            const cx<T>* row = St + it.st + (int64_t)i * it.ks;
+            const cx<T>* xv = xh + it.xh;
+            cx<T> d = zero<T>();
+#pragma unroll 4
+            for (int j = 0; j < it.ks; ++j) fma_cx(d, row[j], xv[j]);
+            part[w] = d;
+        }
+        __syncthreads();
+        for (int q = 0; q < nb; ++q) {
+            if (threadIdx.x < kt) acc0 = acc0 + part[q * kt + threadIdx.x];
+            if (threadIdx.x + blockDim.x < kt) acc1 = acc1 + part[q * kt + threadIdx.x + blockDim.x];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < kt) yh[yh_off[a] + threadIdx.x] = acc0;
+    if (threadIdx.x + blockDim.x < kt) yh[yh_off[a] + threadIdx.x + blockDim.x] = acc1;
+}
+
+struct LeafOut2 {
+    int64_t poff;            // panel offset (row 0, column 0); even
+    int64_t coff;            // offset of the panel's column -> x~ index list
+    int32_t off, rows, ld;   // cluster-order row offset, rows, panel width (even)
+    int32_t qbeg, qend, pad;
+};
+
+// y[perm[r]] = sum_c Q_tc y^_tc + nearfield row panel: one CTA per leaf.  The x~ values of a
+// chunk of panel columns are gathered into shared memory once; each warp then streams its rows
+// with 16-byte loads (lane-partial sums kept in registers for up to 8 rows per warp).
+template <class T, class TY>
+__global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ leaves,
+                                                   const LeafQ* __restrict__ qitems,
+                                                   const int32_t* __restrict__ colidx,
+                                                   const cx<T>* __restrict__ Q, const cx<T>* __restrict__ yh,
+                                                   const cx<T>* __restrict__ Pn, const cx<T>* __restrict__ xt,
+                                                   const int32_t* __restrict__ perm, cx<TY>* y) {
+    constexpr int CH = 2048;
+    constexpr int RW = 8;                    // rows per warp per row tile
+    __shared__ cx<T> xg[CH];
+    const LeafOut2 lf = leaves[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int r0 = 0; r0 < lf.rows; r0 += 8 * RW) {
+        cx<T> acc[RW];
+#pragma unroll
+        for (int q = 0; q < RW; ++q) acc[q] = zero<T>();
+        for (int c0 = 0; c0 < lf.ld; c0 += CH) {
+            const int w = min(CH, lf.ld - c0);
+            for (int j = threadIdx.x; j < w; j += blockDim.x) xg[j] = xt[colidx[lf.coff + c0 + j]];
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < RW; ++q) {
+                const int i = r0 + warp + 8 * q;
+                if (i >= lf.rows) break;
+                const cx<T>* row = Pn + lf.poff + (int64_t)i * lf.ld + c0;
+                cx<T> a = acc[q];
+                if constexpr (sizeof(cx<T>) == 8) {
+                    const float4* r4 = reinterpret_cast<const float4*>(row);
+                    const int w2 = w >> 1;
+#pragma unroll 4
+                    for (int j = lane; j < w2; j += 32) {
+                        float4 v = __ldg(r4 + j);
+                        cx<T> x0 = xg[2 * j], x1 = xg[2 * j + 1];
+                        fma_cx(a, cx<T>{(T)v.x, (T)v.y}, x0);
+                        fma_cx(a, cx<T>{(T)v.z, (T)v.w}, x1);
+                    }
+                } else {
+#pragma unroll 4
+                    for (int j = lane; j < w; j += 32) fma_cx(a, row[j], xg[j]);
+                }
+                acc[q] = a;
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < RW; ++q) {
+            const int i = r0 + warp + 8 * q;
+            if (i >= lf.rows) break;
+            cx<T> a = acc[q];
+            for (int e = lf.qbeg; e < lf.qend; ++e) {
+                const LeafQ it = qitems[e];
+                const cx<T>* row = Q + it.q + (int64_t)i * it.ld;
+                for (int r = lane; r < it.k; r += 32) fma_cx(a, row[r], yh[it.yh + r]);
+            }
+            a = warp_sum(a);
+            if (lane == 0) y[perm[lf.off + i]] = cx<TY>{TY(a.x), TY(a.y)};
+        }
+    }
+}
+
 // ----------------------------------------------------------------------------- helpers
 
 template <class T>
@@ -891,9 +1035,20 @@ private:
     std::vector<int64_t> fwd_up_level_counts_;
     std::vector<std::vector<NearSeg>> leaf_segs_;
     std::vector<int32_t> leaf_order_;
+    std::vector<int64_t> leaf_poff_, leaf_coff_;     // per leaf: panel offset, column-list offset
+    std::vector<int32_t> leaf_ld_;                   // per leaf: panel width (even)
+    std::vector<int64_t> st_off_;                    // per admissible block: S~ offset (row-list order)
+    DBuf<int32_t> colidx_;
+    DBuf<LeafOut2> leaf_out2_;
+    int32_t kmax_row_ = 0;
 
     bool timing_on_ = false;
     EventLog ev_;
+    DBuf<unsigned> err_;
+    void check_err(cudaStream_t s, const char* where) {
+        unsigned e = read_scalar(err_.p, s);
+        if (e) throw Error{DH2_ENUMERIC, std::string("non-finite value in ") + where + " (code " + std::to_string(e) + ")"};
+    }
     double work_[K_COUNT] = {0};     // algorithmic work accumulated while planning launches
     static constexpr double kEvalFlops = 20.0;   // flop-equivalents per kernel evaluation
     // brackets one launch with CUDA events when `on`
@@ -912,9 +1067,7 @@ private:
     void truncate(int pass, cudaStream_t s);
     void project(cudaStream_t s);
     void plan_matvec(cudaStream_t s);
-    template <int RPL, class TQ>
-    void run_tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s);
-    void tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s);
+    void tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s, const char* where);
 };
 
 // ----------------------------------------------------------------------------- layout
@@ -1085,25 +1238,39 @@ void Num<T>::nearfield(cudaStream_t s) {
             leaf_segs_[i].push_back(sg);
         }
     }
-    // one dense row panel per leaf: its segments side by side, sorted by column offset
+    // one dense row panel per leaf: its segments side by side, sorted by column offset; the
+    // width is padded to even (zero column) so that every row starts on 16 bytes
     std::vector<NearSeg> all;
-    int64_t poff = 0;
+    std::vector<int32_t> colidx;
+    int64_t poff = 0, real = 0;
+    leaf_poff_.assign(leaf_order_.size(), 0);
+    leaf_coff_.assign(leaf_order_.size(), 0);
+    leaf_ld_.assign(leaf_order_.size(), 0);
     for (size_t i = 0; i < leaf_order_.size(); ++i) {
         auto& v = leaf_segs_[i];
         std::sort(v.begin(), v.end(), [](const NearSeg& a, const NearSeg& b) { return a.coff < b.coff; });
         int32_t width = 0;
         for (auto& sg : v) width += sg.cols;
+        const int32_t ld = width + (width & 1);
+        leaf_poff_[i] = poff;
+        leaf_coff_[i] = (int64_t)colidx.size();
+        leaf_ld_[i] = ld;
         int32_t col = 0;
         for (auto& sg : v) {
-            sg.ld = width;
+            sg.ld = ld;
             sg.poff = poff + col;
             col += sg.cols;
             all.push_back(sg);
+            for (int32_t j = 0; j < sg.cols; ++j) colidx.push_back(sg.coff + j);
         }
-        poff += (int64_t)h.size[leaf_order_[i]] * width;
+        if (ld > width) colidx.push_back(0);
+        poff += (int64_t)h.size[leaf_order_[i]] * ld;
+        real += (int64_t)h.size[leaf_order_[i]] * width;
     }
-    info.near_entries = poff;
+    info.near_entries = real;
     near_.alloc(std::max<int64_t>(poff, 1));
+    near_.zero(s);
+    upload_vec(colidx_, colidx, s);
     const double s15 = std::sqrt(15.0);
     const double w7[7] = {9.0 / 40.0,           (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0,
                           (155.0 - s15) / 1200.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0,
@@ -1140,42 +1307,75 @@ void Num<T>::nearfield(cudaStream_t s) {
 
 // ----------------------------------------------------------------------------- TSQR dispatch
 
-template <class T>
-template <int RPL, class TQ>
-void Num<T>::run_tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s) {
+template <class TSrc, class TQ, class TDst, int RPL>
+void launch_tsqr(const std::vector<QRTask>& tasks, int k, const cx<TSrc>* src, cx<TDst>* dst,
+                 DBuf<cx<TQ>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err) {
     if (tasks.empty()) return;
-    const size_t smem = (size_t)k_ * 32 * RPL * sizeof(cx<TQ>);
-    auto kern = k_tsqr<T, TQ, RPL>;
+    const size_t smem = tsqr_smem_bytes<TQ, RPL>(k);
+    auto kern = k_tsqr<TSrc, TQ, TDst, RPL>;
     DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t per = (int64_t)k_ * k_;
+    const int64_t per = (int64_t)k * k;
     const int64_t max_tasks = std::max<int64_t>(1, (int64_t(1) << 31) / (per * (int64_t)sizeof(cx<TQ>)));
-    DBuf<cx<TQ>> scratch;
     for (size_t b0 = 0; b0 < tasks.size(); b0 += (size_t)max_tasks) {
         size_t cnt = std::min<size_t>((size_t)max_tasks, tasks.size() - b0);
         std::vector<QRTask> part(tasks.begin() + b0, tasks.begin() + b0 + cnt);
         DBuf<QRTask> d;
         upload_vec(d, part, s);
         scratch.reserve(cnt * per);
-        ev_.begin(K_TSQR, s);
-        kern<<<(unsigned)cnt, kThreads, smem, s>>>(d.p, k_, src, scratch.p, dst);
-        ev_.end(s);
+        ev.begin(K_TSQR, s);
+        kern<<<(unsigned)cnt, kThreads, smem, s>>>(d.p, k, src, scratch.p, dst, err);
+        ev.end(s);
         DH2_CHECK_LAUNCH("k_tsqr");
         DH2_CHECK_CUDA(cudaStreamSynchronize(s));
     }
 }
 
+// Stacks taller than `group` rows are split into row groups: the R factors of the groups
+// (pass 1) are stacked and factored again (pass 2).  This gives every level enough CTAs.
+template <class T, class TQ, int RPL>
+void tsqr_grouped(const std::vector<QRTask>& tasks, int k, int group, const cx<T>* src, cx<T>* dst,
+                  cudaStream_t s, EventLog& ev, unsigned* err) {
+    const int32_t kQRGroup = group;
+    std::vector<QRTask> direct, groups, merges;
+    int64_t mrow = 0;
+    for (const QRTask& t : tasks) {
+        if (t.nrows <= kQRGroup) {
+            direct.push_back(t);
+            continue;
+        }
+        const int64_t m0 = mrow;
+        for (int32_t r0 = 0; r0 < t.nrows; r0 += kQRGroup) {
+            const int32_t h = std::min(kQRGroup, t.nrows - r0);
+            const int32_t ro = std::min(h, k);
+            groups.push_back(QRTask{t.src + (int64_t)r0 * k, mrow * k, h, ro});
+            mrow += ro;
+        }
+        merges.push_back(QRTask{m0 * k, t.dst, (int32_t)(mrow - m0), t.rout});
+    }
+    DBuf<cx<TQ>> scratch, merge;
+    launch_tsqr<T, TQ, T, RPL>(direct, k, src, dst, scratch, s, ev, err);
+    if (!groups.empty()) {
+        merge.alloc((size_t)mrow * k);
+        launch_tsqr<T, TQ, TQ, RPL>(groups, k, src, merge.p, scratch, s, ev, err);
+        launch_tsqr<TQ, TQ, T, RPL>(merges, k, merge.p, dst, scratch, s, ev, err);
+    }
+}
+
 template <class T>
-void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s) {
+void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s,
+                  const char* where) {
+    check_err(s, where);   // inputs of this QR
     const bool fp64 = std::is_same<T, double>::value || bp_.qr_fp64;
     if (fp64) {
-        if ((size_t)k_ * 32 * sizeof(cx<double>) > 200 * 1024)
-            throw Error{DH2_EUNSUPPORTED, "FP64 weight QR needs k <= 400 (m <= 7)"};
-        run_tsqr<1, double>(tasks, src, dst, s);
-    } else if ((size_t)k_ * 64 * sizeof(cx<float>) <= 120 * 1024) {
-        run_tsqr<2, float>(tasks, src, dst, s);
+        if (tsqr_smem_bytes<double, 1>(k_) > 200 * 1024)
+            throw Error{DH2_EUNSUPPORTED, "FP64 weight QR supports m <= 6"};
+        tsqr_grouped<T, double, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+    } else if (tsqr_smem_bytes<float, 2>(k_) <= 100 * 1024) {
+        tsqr_grouped<T, float, 2>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
     } else {
-        run_tsqr<1, float>(tasks, src, dst, s);
+        tsqr_grouped<T, float, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
     }
+    check_err(s, where);
 }
 
 // ----------------------------------------------------------------------------- basis weights
@@ -1203,7 +1403,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
                 srow += rR_[s0] + rR_[s1];
             }
         }
-        tsqr(leafq, V_.p, R_.p, s);
+        tsqr(leafq, V_.p, R_.p, s, "basis weights (leaves)");
         if (!kron.empty()) {
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             DBuf<KronTask> d;
@@ -1213,7 +1413,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
             k_kron<T, T, T, T><<<(unsigned)kron.size(), kThreads, smem, s>>>(d.p, m_, R_.p, E_.p, stack.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_kron");
-            tsqr(innerq, stack.p, R_.p, s);
+            tsqr(innerq, stack.p, R_.p, s, "basis weights");
         }
     }
     std::vector<int32_t> rr(rR_.begin(), rR_.end());
@@ -1280,7 +1480,7 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                 ev_.begin(K_STACK_BLOCKS, s);
                 k_stack_blocks<T><<<(unsigned)btasks.size(), kThreads, smem, s>>>(
                     d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p, st_.dir_off_d.p,
-                    st_.dirs.p, nodes_.p, m_, bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack.p);
+                    st_.dirs.p, nodes_.p, m_, bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack.p, err_.p);
                 ev_.end(s);
                 DH2_CHECK_LAUNCH("k_stack_blocks");
             }
@@ -1294,7 +1494,7 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                 ev_.end(s);
                 DH2_CHECK_LAUNCH("k_kron");
             }
-            tsqr(qtasks, stack.p, Z_[pass].p, s);
+            tsqr(qtasks, stack.p, Z_[pass].p, s, pass == 0 ? "total weights (rows)" : "total weights (columns)");
         }
     }
 }
@@ -1383,7 +1583,7 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
         ev_.begin(K_TRUNCATE, s);
         kern<<<(unsigned)tt.size(), kThreads, smem, s>>>(d.p, kk, V_.p, vhat.p, Z_[pass].p, ascr.p, nullptr,
                                                           smem_n, bp_.eps, bp_.rank_rule, Q_[pass].p,
-                                                          Cd_[pass].p, Ct, sig_[pass].p, rank_d_[pass].p);
+                                                          Cd_[pass].p, Ct, sig_[pass].p, rank_d_[pass].p, err_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_truncate");
         std::vector<int32_t> rk(a1 - a0);
@@ -1391,6 +1591,7 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
                                        cudaMemcpyDeviceToHost, s));
         DH2_CHECK_CUDA(cudaStreamSynchronize(s));
         for (int64_t a = a0; a < a1; ++a) rank_[pass][a] = rk[a - a0];
+        check_err(s, "truncation");
     }
 }
 
@@ -1401,6 +1602,21 @@ void Num<T>::project(cudaStream_t s) {
     const auto& h = hs_;
     const int64_t nb = (int64_t)h.adm_t.size();
     std::vector<ProjTask> pt(nb);
+    // S~ storage in row-list order: the couplings of one row pair are contiguous
+    st_off_.assign(nb + 1, 0);
+    {
+        int64_t o = 0;
+        for (int64_t a = 0; a < na_; ++a) {
+            int32_t tc = h.tc_base[h.a_t[a]] + h.a_c[a];
+            for (int32_t e = h.row_ptr[tc]; e < h.row_ptr[tc + 1]; ++e) {
+                int32_t b = h.row_idx[e];
+                int32_t c = h.adm_c[b];
+                st_off_[b] = o;
+                o += (int64_t)rank_[0][h.pair_of(h.adm_t[b], c)] * rank_[1][h.pair_of(h.adm_s[b], c)];
+            }
+        }
+        st_off_[nb] = o;
+    }
     int64_t off = 0;
     for (int64_t b = 0; b < nb; ++b) {
         int32_t c = h.adm_c[b];
@@ -1411,7 +1627,7 @@ void Num<T>::project(cudaStream_t s) {
         p.ks = rank_[1][as];
         p.crow = offC_[0][at];
         p.ccol = offC_[1][as];
-        p.dst = off;
+        p.dst = st_off_[b];
         off += (int64_t)p.kt * p.ks;
         pt[b] = p;
         if (p.kt && p.ks)
@@ -1481,12 +1697,8 @@ void Num<T>::plan_matvec(cudaStream_t s) {
     n_fwd_leaf_ = (int64_t)fl.size();
     upload_vec(fwd_leaf_, fl, s);
     upload_vec(fwd_up_, fu, s);
-    // couplings: S~ offsets in block order
-    std::vector<int64_t> st_off(h.adm_t.size() + 1, 0);
-    for (size_t b = 0; b < h.adm_t.size(); ++b) {
-        int32_t c = h.adm_c[b];
-        st_off[b + 1] = st_off[b] + (int64_t)rank_[0][h.pair_of(h.adm_t[b], c)] * rank_[1][h.pair_of(h.adm_s[b], c)];
-    }
+    // couplings: S~ offsets from the projection (row-list order)
+    const std::vector<int64_t>& st_off = st_off_;
     std::vector<int32_t> cptr(na_ + 1, 0);
     std::vector<Coup> items;
     for (int64_t a = 0; a < na_; ++a) {
@@ -1568,6 +1780,21 @@ void Num<T>::plan_matvec(cudaStream_t s) {
     upload_vec(leaf_out_, lo, s);
     upload_vec(leaf_q_, lq, s);
     upload_vec(leaf_seg_, ls, s);
+    std::vector<LeafOut2> lo2;
+    for (size_t i = 0; i < leaf_order_.size(); ++i) {
+        LeafOut2 o{};
+        o.poff = leaf_poff_[i];
+        o.coff = leaf_coff_[i];
+        o.off = lo[i].off;
+        o.rows = lo[i].rows;
+        o.ld = leaf_ld_[i];
+        o.qbeg = lo[i].qbeg;
+        o.qend = lo[i].qend;
+        lo2.push_back(o);
+    }
+    upload_vec(leaf_out2_, lo2, s);
+    kmax_row_ = 0;
+    for (int64_t a = 0; a < na_; ++a) kmax_row_ = std::max(kmax_row_, rank_[0][a]);
     const int64_t cs = sizeof(cx<T>);
     info.matvec_bytes = (info.near_entries + info.coupling_entries + info.basis_entries) * cs +
                         2 * n_ * cs + 2 * (xh_off[na_] + yh_off[na_]) * cs;
@@ -1591,6 +1818,8 @@ void Num<T>::plan_matvec(cudaStream_t s) {
 template <class T>
 void Num<T>::build(cudaStream_t s) {
     StageTimer tm(s);
+    err_.alloc(1);
+    err_.zero(s);
     layout();
     tm.begin(ST_ANALYTIC);
     analytic(s);
@@ -1675,8 +1904,8 @@ void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
     }
     if (na_) {
         if (timing_on_) ev_.begin(K_MV_COUPLING, s);
-        k_coupling<T><<<grid_for(na_, WPB), WPB * 32, 0, s>>>(coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, na_,
-                                                              St_.p, xh_.p, yh_.p);
+        k_coupling2<T><<<(unsigned)na_, 256, std::max(256, kmax_row_) * sizeof(cx<T>), s>>>(
+            coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, St_.p, xh_.p, yh_.p);
         if (timing_on_) ev_.end(s);
         DH2_CHECK_LAUNCH("k_coupling");
     }
@@ -1695,13 +1924,13 @@ void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
     if (n_leaves_) {
         if (dtype == DH2_C64) {
             if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);
-            k_leaf_out<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+            k_leaf_out2<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                     yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
             if (timing_on_) ev_.end(s);
         }
         else {
             if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);
-            k_leaf_out<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+            k_leaf_out2<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                      yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
             if (timing_on_) ev_.end(s);
         }
@@ -1787,8 +2016,8 @@ void Num<T>::matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) {
         off += cnt;
     }
     if (na_) {
-        k_coupling<T><<<grid_for(na_, WPB), WPB * 32, 0, s>>>(coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, na_,
-                                                              St_.p, xh, yh);
+        k_coupling2<T><<<(unsigned)na_, 256, std::max(256, kmax_row_) * sizeof(cx<T>), s>>>(
+            coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, St_.p, xh, yh);
         DH2_CHECK_LAUNCH("k_coupling");
     }
     off = 0;
@@ -1803,10 +2032,10 @@ void Num<T>::matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) {
     }
     if (n_leaves_) {
         if (dtype == DH2_C64)
-            k_leaf_out<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+            k_leaf_out2<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                     yh, near_.p, xt, tr_.perm.p, (cx<float>*)y);
         else
-            k_leaf_out<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out_.p, leaf_q_.p, leaf_seg_.p, Q_[0].p,
+            k_leaf_out2<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                      yh, near_.p, xt, tr_.perm.p, (cx<double>*)y);
         DH2_CHECK_LAUNCH("k_leaf_out");
     }

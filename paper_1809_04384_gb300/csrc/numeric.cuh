@@ -29,7 +29,7 @@ enum Stage {
 
 struct BuildParams {
     double kappa, eta, eps;
-    int32_t m, precision, rank_rule, qr_fp64;
+    int32_t m, precision, rank_rule, qr_fp64, qr_group_rows;
     int64_t workspace_bytes;
 };
 

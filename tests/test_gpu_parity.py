@@ -181,3 +181,30 @@ def test_matvec_dtypes_agree(precision):
     y64 = mat.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy()
     y128 = mat.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     assert rel(y64.astype(np.complex128), y128) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["mixed1280", "lowfreq1280"])
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_grouped_weight_qr_matches_oracle(name, precision):
+    """Stacks split into row groups (forced to 40 rows) whose R factors are merged by a
+    second QR give the same total weights and matvec as the oracle."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    v, f, p, *_ = oracle_structure(name)
+    rc = oracle_recompression(name)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    prec = dh2.DH2_FP64 if precision == "fp64" else dh2.DH2_MIXED
+    mat = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], precision=prec, eta1=p["eta1"],
+                     qr_group_rows=40)
+    tol = TOL[precision]
+    for tc in np.nonzero(rc.pairs.active)[0]:
+        for which, Zo in ((dh2.DH2_X_ZROW, rc.ZR[tc]), (dh2.DH2_X_ZCOL, rc.ZC[tc])):
+            Z = mat.pair(which, tc)
+            if Zo.size:
+                assert rel(Z.conj().T @ Z, Zo.conj().T @ Zo) <= tol["gram"], (which, tc)
+    x = x_vector(rc.tree.n)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+    assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision == "mixed" else 0)
