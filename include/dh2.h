@@ -205,14 +205,17 @@ dh2_status dh2_export_blocks(dh2_matrix mat, int32_t* adm, int32_t* near, int8_t
 
 enum {
     DH2_X_R = 0,        /* basis weight R_tc, rows x k */
-    DH2_X_ZROW = 1,     /* total weight Z-hat_tc of the row pass */
-    DH2_X_ZCOL = 2,     /* total weight of the column pass */
+    DH2_X_ZROW = 1,     /* total weight Z-hat_tc of the row pass (r_z x k); for a leaf pair in the
+                           coordinates of its orthonormal basis P (r_z x r_t, Z' with
+                           Z'^* Z' = R Z-hat^* Z-hat R^*) */
+    DH2_X_ZCOL = 2,     /* total weight of the column pass (same conventions) */
     DH2_X_SROW = 3,     /* singular values of the row truncation (1 x count) */
     DH2_X_SCOL = 4,
     DH2_X_QROW = 5,     /* leaf: Q_tc (#t x k_tc); non-leaf: [F_t1c; F_t2c] */
     DH2_X_QCOL = 6,
     DH2_X_CROW = 7,     /* basis change C_tc = Q_tc^* V_tc, k_tc x k */
-    DH2_X_CCOL = 8
+    DH2_X_CCOL = 8,
+    DH2_X_P = 9         /* leaf pair: orthonormal P with V_tc = P R_tc (#t x r_t) */
 };
 /* Copies one per-pair matrix as complex128 (interleaved, row-major) into out
  * (capacity `cap` complex values; singular values are stored as (sigma, 0)).

@@ -24,7 +24,7 @@ DH2_FP64, DH2_MIXED = 0, 1
 DH2_C64, DH2_C128 = 1, 2
 DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL = 0, 1
 (DH2_X_R, DH2_X_ZROW, DH2_X_ZCOL, DH2_X_SROW, DH2_X_SCOL, DH2_X_QROW, DH2_X_QCOL,
- DH2_X_CROW, DH2_X_CCOL) = range(9)
+ DH2_X_CROW, DH2_X_CCOL, DH2_X_P) = range(10)
 
 _STATUS = {DH2_EINVAL: "EINVAL", DH2_ENOMEM: "ENOMEM", DH2_ECUDA: "ECUDA", DH2_ETIMEOUT: "ETIMEOUT",
            DH2_ENUMERIC: "ENUMERIC", DH2_EUNSUPPORTED: "EUNSUPPORTED"}

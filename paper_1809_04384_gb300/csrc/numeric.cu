@@ -281,8 +281,9 @@ struct BlockRowTask {
     int32_t b;         // admissible block id
     int32_t other;     // active pair whose weight R multiplies S (rows pass: s, cols pass: t)
     int32_t own;       // active pair of the other side (rows pass: t; for |G_b|)
-    int32_t pad;
+    int32_t own_leaf;  // rows pass: the row cluster is a leaf (rows projected onto its basis)
     int64_t dst;       // element offset of the first row in the stack
+    int64_t koff;      // rows pass: where K_b = R_t S_b R_s^* is stored
 };
 
 // rows pass: R_sc S_b^*, then |G_b|_F = |R_tc S_b R_sc^*|_F, rows scaled by 1/|G_b|.
@@ -295,7 +296,7 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
                                const double* __restrict__ nodes, int m, double kappa,
                                const cx<T>* __restrict__ R, const int64_t* __restrict__ roff,
                                const int32_t* __restrict__ rrows, double* bnorm, cx<T>* stack,
-                               unsigned* err) {
+                               cx<T>* Kst, unsigned* err) {
     extern __shared__ unsigned char smraw[];
     T* D = reinterpret_cast<T*>(smraw);
     T* P = D + 3 * m * m;
@@ -315,21 +316,36 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
                     [&](int mu, int nu) { return conj(S(nu, mu)); },
                     [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
         __syncthreads();
-        // |R_t S R_s^*|_F^2 = sum |(R_t Y)_{i' i}|^2 with Y[nu][i] = conj(out[i][nu])
+        // K_b = R_t S R_s^* = R_t Y with Y[nu][i] = conj(out[i][nu]); |G_b|_F = |K_b|_F
         const int rt = rrows[tk.own];
         const cx<T>* Rt = R + roff[tk.own];
+        cx<T>* Kb = Kst + tk.koff;
         T acc = 0;
         T* accp = &acc;
         cta_gemm<T>(rt, ro, k, Dense<T>{Rt, k, false, false}, Dense<T>{out, k, true, true},
-                    [=](int, int, cx<T> v) { *accp += abs2(v); });
+                    [=](int i, int j, cx<T> v) {
+                        *accp += abs2(v);
+                        Kb[(int64_t)i * ro + j] = v;
+                    });
         T nrm2 = block_sum(acc, red);
         T nrm = sqrt(nrm2);
         if (threadIdx.x == 0) bnorm[tk.b] = (double)nrm;
         T sc_ = nrm > T(0) ? T(1) / nrm : T(0);
-        for (int idx = threadIdx.x; idx < ro * k; idx += blockDim.x) {
-            cx<T> v = sc_ * out[idx];
-            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
-            out[idx] = v;
+        __syncthreads();
+        if (tk.own_leaf) {
+            // rows projected onto the leaf's orthonormal basis: w K_b^*  (ro x rt, pitch k)
+            for (int idx = threadIdx.x; idx < ro * rt; idx += blockDim.x) {
+                const int i = idx / rt, j = idx - i * rt;
+                cx<T> v = sc_ * conj(Kb[(int64_t)j * ro + i]);
+                if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                out[(int64_t)i * k + j] = v;
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < ro * k; idx += blockDim.x) {
+                cx<T> v = sc_ * out[idx];
+                if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                out[idx] = v;
+            }
         }
     } else {
         const T sc_ = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
@@ -377,9 +393,11 @@ __global__ void k_kron(const KronTask* __restrict__ tasks, int m, const cx<TI>* 
 
 struct QRTask {
     int64_t src;       // element offset of the first stacked row
-    int64_t dst;       // element offset of the output rows
+    int64_t dst;       // element offset of the output rows (compact, ncols per row)
     int32_t nrows;
-    int32_t rout;      // min(nrows, k) rows written to dst
+    int32_t rout;      // min(nrows, ncols) rows written to dst
+    int32_t ncols;     // columns of this task (<= the launch's k)
+    int32_t ld;        // row pitch of the source rows
 };
 
 constexpr int kQRNB = 8;   // panel width of the blocked Householder update
@@ -399,27 +417,28 @@ __global__ void __launch_bounds__(256) k_tsqr(const QRTask* __restrict__ tasks, 
     cx<TQ>* s_tau = s_G + kQRNB * kQRNB;
     int* s_skip = reinterpret_cast<int*>(s_tau + kQRNB);
     const QRTask tk = tasks[blockIdx.x];
+    const int nc = tk.ncols;
     cx<TQ>* R = scratch + (int64_t)blockIdx.x * k * k;
-    for (int idx = threadIdx.x; idx < k * k; idx += blockDim.x) R[idx] = zero<TQ>();
+    for (int idx = threadIdx.x; idx < nc * nc; idx += blockDim.x) R[idx] = zero<TQ>();
     __syncthreads();
     const cx<TSrc>* S = src + tk.src;
     for (int r0 = 0; r0 < tk.nrows; r0 += H) {
         const int h = min(H, tk.nrows - r0);
-        for (int idx = threadIdx.x; idx < H * k; idx += blockDim.x) {
-            const int i = idx / k, l = idx - i * k;     // row-major read, column-major store
+        for (int idx = threadIdx.x; idx < H * nc; idx += blockDim.x) {
+            const int i = idx / nc, l = idx - i * nc;     // row-major read, column-major store
             cx<TQ> v = zero<TQ>();
             if (i < h) {
-                cx<TSrc> u = S[(int64_t)(r0 + i) * k + l];
+                cx<TSrc> u = S[(int64_t)(r0 + i) * tk.ld + l];
                 if (!isfinite(u.x) || !isfinite(u.y)) raise_err(err, ERR_TSQR_INPUT);
                 v = cx<TQ>{TQ(u.x), TQ(u.y)};
             }
             W[(int64_t)l * LDW + i] = v;
         }
         __syncthreads();
-        tsqr_chunk<TQ, RPL, kQRNB>(k, R, W, s_tau, s_skip, s_T, s_G, s_Wm);
+        tsqr_chunk<TQ, RPL, kQRNB>(nc, R, W, s_tau, s_skip, s_T, s_G, s_Wm);
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < tk.rout * k; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < tk.rout * nc; idx += blockDim.x) {
         cx<TQ> v = R[idx];
         if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_TSQR_NONFINITE);
         dst[tk.dst + idx] = cx<TDst>{TDst(v.x), TDst(v.y)};
@@ -434,55 +453,100 @@ size_t tsqr_smem_bytes(int k) {
 
 // ----------------------------------------------------------------------------- truncation (FP64)
 
+// ----------------------------------------------------------------------------- leaf orthogonalisation
+
+// Hermitian eigensolver + descending order (NaN-safe): on return lam[i] are the
+// eigenvalues of M, order[r] the index of the r-th largest, U the eigenvectors.
+template <class T>
+__device__ void eig_desc(int n, cx<double>* M, cx<double>* U, JRot<double>* rot, double* red, double* lam,
+                         int* order, unsigned* err) {
+    herm_jacobi<double>(n, M, U, rot, red, 40, 1e-15);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double li = M[(int64_t)i * n + i].x;
+        if (!isfinite(li)) {
+            raise_err(err, ERR_TRUNC_NONFINITE);
+            li = -INFINITY;
+        }
+        lam[i] = li;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double li = lam[i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += (lam[j] > li || (lam[j] == li && j < i)) ? 1 : 0;
+        order[r] = i;
+    }
+    __syncthreads();
+}
+
+// Jacobi workspace of one CTA: shared memory when n <= smem_n, else a global slot
+struct EigSpace {
+    cx<double>* M;
+    cx<double>* U;
+    JRot<double>* rot;
+    double* lam;
+    int* order;
+};
+
+__device__ __forceinline__ EigSpace eig_space(int n, int smem_n, unsigned char* smraw, cx<double>* gslot) {
+    EigSpace e;
+    if (n <= smem_n) {
+        e.M = reinterpret_cast<cx<double>*>(smraw);
+        e.U = e.M + (int64_t)smem_n * smem_n;
+        e.rot = reinterpret_cast<JRot<double>*>(e.U + (int64_t)smem_n * smem_n);
+        e.lam = reinterpret_cast<double*>(e.rot + (smem_n / 2 + 1));
+        e.order = reinterpret_cast<int*>(e.lam + smem_n);
+    } else {
+        e.M = gslot;
+        e.U = e.M + (int64_t)n * n;
+        e.rot = reinterpret_cast<JRot<double>*>(e.U + (int64_t)n * n);
+        e.lam = reinterpret_cast<double*>(e.rot + (n / 2 + 1));
+        e.order = reinterpret_cast<int*>(e.lam + n);
+    }
+    return e;
+}
+
+inline size_t eig_smem_bytes(int smem_n) {
+    return smem_n > 0 ? 2 * (size_t)smem_n * smem_n * sizeof(cx<double>) + (smem_n / 2 + 1) * sizeof(JRot<double>) +
+                            smem_n * (sizeof(double) + sizeof(int)) + 64
+                      : 64;
+}
+inline int64_t eig_global_elems(int n) {   // cx<double> elements of a global Jacobi slot
+    int64_t bytes = 2 * (int64_t)n * n * sizeof(cx<double>) + (n / 2 + 1) * sizeof(JRot<double>) +
+                    n * (sizeof(double) + sizeof(int));
+    return (bytes + sizeof(cx<double>) - 1) / sizeof(cx<double>) + 4;
+}
+
 struct TruncTask {
     int64_t vsrc;      // leaf: V (T) element offset; non-leaf: V-hat scratch (double) offset
     int64_t z;         // Z-hat element offset
     int64_t q;         // output Q / Q-hat (T), row pitch qld
     int64_t c;         // output C (double and T copies), pitch k
     int64_t sig;       // singular values (double)
-    int64_t ascratch;  // A = V Z^* scratch (double complex)
+    int64_t ascratch;  // A = V Z^* scratch (working precision)
+    int64_t gslot;     // global Jacobi slot (FP64) when rows exceed the shared-memory size
     int32_t rows, rz, qld, leaf, a, pad;
 };
 
 template <class T, class FV>
 __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<T>* __restrict__ Z,
-                              cx<double>* Ascr, cx<double>* M, cx<double>* U, JRot<double>* rot,
+                              cx<T>* Ascr, cx<double>* M, cx<double>* U, JRot<double>* rot,
                               double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct,
                               double* sig, int32_t* rank, int* s_order, double* s_lam, unsigned* err) {
     __shared__ double red[32];
     __shared__ int s_rank;
     const int n = tk.rows, rz = tk.rz;
     const cx<T>* Zt = Z + tk.z;
-    // A = V Z^*  (n x rz)
-    cta_gemm<double>(n, rz, k, V, [&](int nu, int j) {
-                         cx<T> z = Zt[(int64_t)j * k + nu];
-                         return cx<double>{double(z.x), -double(z.y)};
-                     },
-                     [&](int i, int j, cx<double> v) { Ascr[(int64_t)i * rz + j] = v; });
+    // A = V Z^*  (n x rz), working precision (a perturbation of A at the square-root level)
+    cta_gemm<T>(n, rz, k, V, [&](int nu, int j) { return conj(Zt[(int64_t)j * k + nu]); },
+                [&](int i, int j, cx<T> v) { Ascr[(int64_t)i * rz + j] = v; });
     __syncthreads();
-    // M = A A^*  (n x n)
-    cta_gemm<double>(n, n, rz, Dense<double>{Ascr, rz, false, false}, Dense<double>{Ascr, rz, true, true},
+    // M = A A^*  (n x n), FP64: its eigenvalues are the squared singular values
+    cta_gemm<double>(n, n, rz, DenseCvt<double, T>{Ascr, rz, false, false}, DenseCvt<double, T>{Ascr, rz, true, true},
                      [&](int i, int j, cx<double> v) { M[(int64_t)i * n + j] = v; });
     __syncthreads();
-    herm_jacobi<double>(n, M, U, rot, red, 40, 1e-15);
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double li = M[(int64_t)i * n + i].x;
-        if (!isfinite(li)) {      // never happens for finite input; keeps every index in range
-            raise_err(err, ERR_TRUNC_NONFINITE);
-            li = -INFINITY;
-        }
-        s_lam[i] = li;
-    }
-    __syncthreads();
-    // rank of each eigenvalue (descending, ties by index): a permutation of 0..n-1
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        double li = s_lam[i];
-        int r = 0;
-        for (int j = 0; j < n; ++j) r += (s_lam[j] > li || (s_lam[j] == li && j < i)) ? 1 : 0;
-        s_order[r] = i;
-    }
-    __syncthreads();
+    eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err);
     const int nsig = min(n, rz);
     if (threadIdx.x == 0) {
         double total = 0;
@@ -511,55 +575,197 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
         Q[tk.q + (int64_t)i * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
     }
     // C = Q^* V  (kt x k)
-    cta_gemm<double>(kt, k, n, [&](int r, int i) { return conj(U[(int64_t)i * n + s_order[r]]); }, V,
-                     [&](int r, int nu, cx<double> v) {
-                         Cd[tk.c + (int64_t)r * k + nu] = v;
-                         Ct[tk.c + (int64_t)r * k + nu] = cx<T>{T(v.x), T(v.y)};
-                     });
+    cta_gemm<T>(kt, k, n,
+                [&](int r, int i) {
+                    const cx<double> u = U[(int64_t)i * n + s_order[r]];
+                    return cx<T>{T(u.x), T(-u.y)};
+                },
+                V,
+                [&](int r, int nu, cx<T> v) {
+                    Cd[tk.c + (int64_t)r * k + nu] = cx<double>{double(v.x), double(v.y)};
+                    Ct[tk.c + (int64_t)r * k + nu] = v;
+                });
 }
 
+// Truncation of a non-leaf pair: V-hat = [C_t1 E_t1c; C_t2 E_t2c] (working precision),
+// A = V-hat Z^*, SVD of A through the FP64 Gram A A^* and a Hermitian Jacobi eigensolver.
 template <class T>
-__global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Vleaf,
-                           const cx<double>* __restrict__ Vhat, const cx<T>* __restrict__ Z,
-                           cx<double>* ascr, cx<double>* gscr, int smem_n, double eps, int rule,
-                           cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig, int32_t* rank, unsigned* err) {
+__global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Vhat,
+                           const cx<T>* __restrict__ Z, cx<T>* ascr, cx<double>* gscr, int smem_n, double eps,
+                           int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig, int32_t* rank,
+                           unsigned* err) {
     extern __shared__ unsigned char smraw[];
     const TruncTask tk = tasks[blockIdx.x];
     const int n = tk.rows;
-    cx<double>* M;
-    cx<double>* U;
-    JRot<double>* rot;
-    int* order;
-    double* lam;
-    if (n <= smem_n) {
-        M = reinterpret_cast<cx<double>*>(smraw);
-        U = M + (int64_t)smem_n * smem_n;
-        rot = reinterpret_cast<JRot<double>*>(U + (int64_t)smem_n * smem_n);
-        lam = reinterpret_cast<double*>(rot + (smem_n / 2 + 1));
-        order = reinterpret_cast<int*>(lam + smem_n);
-    } else {
-        // per-task slot of the level scratch: [A: n*rz][M: n*n][U: n*n][rot][lam][order]
-        M = ascr + tk.ascratch + (int64_t)n * max(tk.rz, 1);
-        U = M + (int64_t)n * n;
-        rot = reinterpret_cast<JRot<double>*>(U + (int64_t)n * n);
-        lam = reinterpret_cast<double*>(rot + (n / 2 + 1));
-        order = reinterpret_cast<int*>(lam + n);
+    EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.gslot);
+    truncate_body<T>(tk, Dense<T>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch, e.M, e.U, e.rot,
+                     eps, rule, Q, Cd, Ct, sig, rank, e.order, e.lam, err);
+}
+
+struct OrthTask {
+    int64_t v, p, r, scr;   // offsets: leaf basis V, output P, output R, global Jacobi slot
+    int32_t n, rt;          // rows of V (#t), kept columns of P (min(#t, k))
+};
+
+// Leaf basis weights with an explicit orthonormal factor: V V^* = U diag(lam) U^* (FP64
+// Gram, Hermitian Jacobi); P = U[:, :rt] (descending eigenvalues), R = P^* V, so V = P R
+// and R^* R = V^* V (Eq. basis_weights_def up to a unitary left factor).
+template <class T>
+__global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, const cx<T>* __restrict__ V,
+                            cx<double>* gscr, int smem_n, cx<T>* P, cx<T>* R, unsigned* err) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32];
+    const OrthTask tk = tasks[blockIdx.x];
+    const int n = tk.n, rt = tk.rt;
+    EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.scr);
+    const cx<T>* Vt = V + tk.v;
+    cta_gemm<double>(n, n, k, DenseCvt<double, T>{Vt, k, false, false}, DenseCvt<double, T>{Vt, k, true, true},
+                     [&](int i, int j, cx<double> v) { e.M[(int64_t)i * n + j] = v; });
+    __syncthreads();
+    eig_desc<T>(n, e.M, e.U, e.rot, red, e.lam, e.order, err);
+    for (int idx = threadIdx.x; idx < n * rt; idx += blockDim.x) {
+        const int i = idx / rt, j = idx - i * rt;
+        const cx<double> u = e.U[(int64_t)i * n + e.order[j]];
+        P[tk.p + idx] = cx<T>{T(u.x), T(u.y)};
     }
-    (void)gscr;
-    if (tk.leaf) {
-        truncate_body<T>(tk, DenseCvt<double, T>{Vleaf + tk.vsrc, k, false, false}, k, Z,
-                         ascr + tk.ascratch, M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam, err);
-    } else {
-        truncate_body<T>(tk, Dense<double>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch,
-                         M, U, rot, eps, rule, Q, Cd, Ct, sig, rank, order, lam, err);
+    cta_gemm<T>(rt, k, n,
+                [&](int j, int i) {
+                    const cx<double> u = e.U[(int64_t)i * n + e.order[j]];
+                    return cx<T>{T(u.x), T(-u.y)};
+                },
+                Dense<T>{Vt, k, false, false}, [&](int j, int nu, cx<T> v) { R[tk.r + (int64_t)j * k + nu] = v; });
+}
+
+struct LeafTruncTask {
+    int64_t z, p, r, q, c, sig, scr;   // offsets: Z' (rz x rt), P (n x rt), R (rt x k), Q, C, sigma, slot
+    int64_t up;                        // U'[:, :k_tc] (rt x k_tc, pitch qld), kept for the projection
+    int32_t rz, rt, n, qld, a, pad;
+};
+
+// Truncation of a leaf pair in the coordinates of its orthonormal basis P: with V = P R,
+// A = V Z^* has the left singular vectors P U' and the singular values of Z' R-projected,
+// where Z'^* Z' = R Z Z^* R^*.  Q = P U'[:, :k_tc], C = Q^* V = U'[:, :k_tc]^* R.
+template <class T>
+__global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Z,
+                             const cx<T>* __restrict__ P, const cx<T>* __restrict__ R, cx<double>* gscr,
+                             int smem_n, double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig,
+                             int32_t* rank, cx<T>* Up, unsigned* err) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ double red[32];
+    __shared__ int s_rank;
+    const LeafTruncTask tk = tasks[blockIdx.x];
+    const int rt = tk.rt, rz = tk.rz, n = tk.n;
+    EigSpace e = eig_space(rt, smem_n, smraw, gscr + tk.scr);
+    const cx<T>* Zt = Z + tk.z;
+    // M' = Z'^* Z'  (rt x rt)
+    cta_gemm<double>(rt, rt, rz,
+                     [&](int i, int j) {
+                         cx<T> z = Zt[(int64_t)j * rt + i];
+                         return cx<double>{double(z.x), -double(z.y)};
+                     },
+                     DenseCvt<double, T>{Zt, rt, false, false},
+                     [&](int i, int j, cx<double> v) { e.M[(int64_t)i * rt + j] = v; });
+    __syncthreads();
+    eig_desc<T>(rt, e.M, e.U, e.rot, red, e.lam, e.order, err);
+    const int nsig = min(rt, rz);
+    if (threadIdx.x == 0) {
+        double total = 0;
+        for (int r = 0; r < nsig; ++r) total += fmax(e.lam[e.order[r]], 0.0);
+        const double bound = (rule == DH2_RANK_GLOBAL) ? eps * eps * total : eps * eps;
+        int kk = nsig;
+        double tail = 0;
+        while (kk > 0) {
+            const double l = fmax(e.lam[e.order[kk - 1]], 0.0);
+            if (tail + l <= bound) {
+                tail += l;
+                --kk;
+            } else {
+                break;
+            }
+        }
+        s_rank = kk;
+        rank[tk.a] = kk;
+    }
+    for (int r = threadIdx.x; r < nsig; r += blockDim.x) sig[tk.sig + r] = sqrt(fmax(e.lam[e.order[r]], 0.0));
+    __syncthreads();
+    const int kt = s_rank;
+    for (int idx = threadIdx.x; idx < rt * kt; idx += blockDim.x) {
+        const int j = idx / kt, r = idx - j * kt;
+        const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
+        Up[tk.up + (int64_t)j * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
+    }
+    // Q = P U'[:, :kt]  (n x kt)
+    cta_gemm<T>(n, kt, rt, Dense<T>{P + tk.p, rt, false, false},
+                [&](int j, int r) {
+                    const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
+                    return cx<T>{T(u.x), T(u.y)};
+                },
+                [&](int i, int r, cx<T> v) { Q[tk.q + (int64_t)i * tk.qld + r] = v; });
+    // C = U'[:, :kt]^* R  (kt x k)
+    cta_gemm<T>(kt, k, rt,
+                [&](int r, int j) {
+                    const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
+                    return cx<T>{T(u.x), T(-u.y)};
+                },
+                Dense<T>{R + tk.r, k, false, false},
+                [&](int r, int nu, cx<T> v) {
+                    Cd[tk.c + (int64_t)r * k + nu] = cx<double>{double(v.x), double(v.y)};
+                    Ct[tk.c + (int64_t)r * k + nu] = v;
+                });
+}
+
+struct KRowTask {
+    int64_t koff, dst;
+    int32_t b, rt, rs, pad;
+};
+
+// column pass rows of a leaf column cluster: w_b K_b (r_t x r_s), K_b = R_t S_b R_s^*
+template <class T>
+__global__ void k_stack_from_K(const KRowTask* __restrict__ tasks, int k, const cx<T>* __restrict__ K,
+                               const double* __restrict__ bnorm, cx<T>* stack) {
+    const KRowTask tk = tasks[blockIdx.x];
+    const T w = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
+    for (int idx = threadIdx.x; idx < tk.rt * tk.rs; idx += blockDim.x) {
+        const int i = idx / tk.rs, j = idx - i * tk.rs;
+        stack[tk.dst + (int64_t)i * k + j] = w * K[tk.koff + idx];
+    }
+}
+
+struct RhTask {
+    int64_t rows_off, r;   // stacked rows (pitch k), R_t
+    int32_t rows, rt;
+};
+
+// rows <- rows R_t^* in place (first r_t columns): parent rows of a leaf pair projected
+// onto its orthonormal basis
+template <class T>
+__global__ void k_rows_rh(const RhTask* __restrict__ tasks, int k, const cx<T>* __restrict__ R, cx<T>* stack) {
+    extern __shared__ unsigned char smraw[];
+    cx<T>* row = reinterpret_cast<cx<T>*>(smraw);
+    const RhTask tk = tasks[blockIdx.x];
+    for (int i = 0; i < tk.rows; ++i) {
+        cx<T>* x = stack + tk.rows_off + (int64_t)i * k;
+        for (int v = threadIdx.x; v < k; v += blockDim.x) row[v] = x[v];
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int j = warp; j < tk.rt; j += nw) {
+            const cx<T>* rj = R + tk.r + (int64_t)j * k;
+            cx<T> acc = zero<T>();
+            for (int v = lane; v < k; v += 32) fma_cjx(acc, rj[v], row[v]);
+            acc = warp_sum(acc);
+            if (lane == 0) x[j] = acc;
+        }
+        __syncthreads();
     }
 }
 
 // ----------------------------------------------------------------------------- projection
 
 struct ProjTask {
-    int32_t b, kt, ks, pad;
+    int32_t b, kt, ks, leafpair;      // leafpair: both clusters are leaves, S~ = U'_t^* K_b U'_s
     int64_t crow, ccol, dst;
+    int64_t koff, upt, ups;           // leaf pairs: K_b and the two U' matrices
+    int32_t rt, rs, ldt, lds;
 };
 
 template <class T>
@@ -569,7 +775,8 @@ __global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
                           const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
                           const double* __restrict__ nodes, int m, double kappa,
                           const cx<T>* __restrict__ Crow, const cx<T>* __restrict__ Ccol,
-                          cx<T>* scratch, cx<T>* Stilde) {
+                          const cx<T>* __restrict__ Kst, const cx<T>* __restrict__ Upr,
+                          const cx<T>* __restrict__ Upc, cx<T>* scratch, cx<T>* Stilde) {
     extern __shared__ unsigned char smraw[];
     T* D = reinterpret_cast<T*>(smraw);
     T* P = D + 3 * m * m;
@@ -578,6 +785,20 @@ __global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
     for (int64_t w = blockIdx.x; w < ntasks; w += gridDim.x) {
         const ProjTask tk = tasks[w];
         if (tk.kt == 0 || tk.ks == 0) continue;
+        if (tk.leafpair) {
+            // S~ = C_t S_b C_s^* with C = U'^* R for leaves: U'_t^* (R_t S_b R_s^*) U'_s
+            __syncthreads();
+            cta_gemm<T>(tk.kt, tk.rs, tk.rt, [&](int i, int j) { return conj(Upr[tk.upt + (int64_t)j * tk.ldt + i]); },
+                        Dense<T>{Kst + tk.koff, tk.rs, false, false},
+                        [&](int i, int j, cx<T> v) { T1[(int64_t)i * k + j] = v; });
+            __syncthreads();
+            cx<T>* out = Stilde + tk.dst;
+            const int ks = tk.ks;
+            cta_gemm<T>(tk.kt, ks, tk.rs, Dense<T>{T1, k, false, false}, Dense<T>{Upc + tk.ups, tk.lds, false, false},
+                        [&](int i, int j, cx<T> v) { out[(int64_t)i * ks + j] = v; });
+            __syncthreads();
+            continue;
+        }
         const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
         const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
         __syncthreads();
@@ -1002,13 +1223,16 @@ private:
     // per active pair (host)
     std::vector<int32_t> lvl_, leaf_, sons_[2], rows_;      // rows_ = #t
     std::vector<int32_t> rR_, rZ_[2], ub_[2], rank_[2];
-    std::vector<int64_t> offV_, offE_, offR_, offZ_[2], offQ_[2], offC_[2], offSig_[2], ldQ_[2];
+    std::vector<int64_t> offV_, offE_, offR_, offP_, offK_, offZ_[2], offQ_[2], offC_[2], offSig_[2], ldQ_[2],
+        offUp_[2];
+    // columns of a pair's total weight: r_t (orthonormal leaf coordinates) or k
+    int32_t zcols(int64_t a) const { return leaf_[a] ? rR_[a] : k_; }
     std::vector<std::vector<std::pair<int32_t, int32_t>>> parents_;   // (parent pair, son slot)
 
     // device data
     DBuf<int32_t> tc_level_;
     DBuf<double> nodes_;
-    DBuf<cx<T>> V_, E_, R_, Z_[2], Q_[2], Ct_[2], St_, near_;
+    DBuf<cx<T>> V_, E_, R_, P_, K_, Z_[2], Q_[2], Ct_[2], Up_[2], St_, near_;
     DBuf<cx<double>> Cd_[2];
     DBuf<double> sig_[2], bnorm_;
     DBuf<int64_t> offR_d_;
@@ -1124,7 +1348,9 @@ void Num<T>::layout() {
                 rows += rR_[h.pair_of(other, c)];
             }
             for (auto& pr : parents_[a]) rows += rZ_[pass][pr.first];
-            rZ_[pass][a] = (int32_t)std::min<int64_t>(rows, k_);
+            // leaf pairs keep their total weight in the coordinates of their orthonormal
+            // basis (zcols = r_t columns), the others in the interpolation basis (k columns)
+            rZ_[pass][a] = (int32_t)std::min<int64_t>(rows, zcols(a));
         }
         ub_[pass].assign(na_, 0);
         for (int64_t a = na_ - 1; a >= 0; --a) {
@@ -1145,8 +1371,17 @@ void Num<T>::layout() {
     scan(offV_, [&](int64_t a) -> int64_t { return leaf_[a] ? (int64_t)rows_[a] * k_ : 0; });
     scan(offE_, [&](int64_t a) -> int64_t { return leaf_[a] ? 0 : 2 * 3 * m_ * m_; });
     scan(offR_, [&](int64_t a) -> int64_t { return (int64_t)rR_[a] * k_; });
+    scan(offP_, [&](int64_t a) -> int64_t { return leaf_[a] ? (int64_t)rows_[a] * rR_[a] : 0; });
+    {
+        const int64_t nb = (int64_t)h.adm_t.size();
+        offK_.assign(nb + 1, 0);
+        for (int64_t b = 0; b < nb; ++b) {
+            const int32_t c = h.adm_c[b];
+            offK_[b + 1] = offK_[b] + (int64_t)rR_[h.pair_of(h.adm_t[b], c)] * rR_[h.pair_of(h.adm_s[b], c)];
+        }
+    }
     for (int pass = 0; pass < 2; ++pass) {
-        scan(offZ_[pass], [&](int64_t a) -> int64_t { return (int64_t)rZ_[pass][a] * k_; });
+        scan(offZ_[pass], [&](int64_t a) -> int64_t { return (int64_t)rZ_[pass][a] * zcols(a); });
         ldQ_[pass].resize(na_);
         for (int64_t a = 0; a < na_; ++a) ldQ_[pass][a] = std::max(ub_[pass][a], 1);
         scan(offQ_[pass], [&](int64_t a) -> int64_t {
@@ -1154,6 +1389,7 @@ void Num<T>::layout() {
             return rows * ldQ_[pass][a];
         });
         scan(offC_[pass], [&](int64_t a) -> int64_t { return (int64_t)ub_[pass][a] * k_; });
+        scan(offUp_[pass], [&](int64_t a) -> int64_t { return leaf_[a] ? (int64_t)rR_[a] * ldQ_[pass][a] : 0; });
         scan(offSig_[pass], [&](int64_t a) -> int64_t {
             return leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
         });
@@ -1337,25 +1573,27 @@ void tsqr_grouped(const std::vector<QRTask>& tasks, int k, int group, const cx<T
                   cudaStream_t s, EventLog& ev, unsigned* err) {
     const int32_t kQRGroup = group;
     std::vector<QRTask> direct, groups, merges;
-    int64_t mrow = 0;
+    int64_t mel = 0;   // elements of the merge buffer used so far (group R factors, compact rows)
     for (const QRTask& t : tasks) {
         if (t.nrows <= kQRGroup) {
             direct.push_back(t);
             continue;
         }
-        const int64_t m0 = mrow;
+        const int64_t m0 = mel;
+        int32_t mrows = 0;
         for (int32_t r0 = 0; r0 < t.nrows; r0 += kQRGroup) {
             const int32_t h = std::min(kQRGroup, t.nrows - r0);
-            const int32_t ro = std::min(h, k);
-            groups.push_back(QRTask{t.src + (int64_t)r0 * k, mrow * k, h, ro});
-            mrow += ro;
+            const int32_t ro = std::min(h, t.ncols);
+            groups.push_back(QRTask{t.src + (int64_t)r0 * t.ld, mel, h, ro, t.ncols, t.ld});
+            mel += (int64_t)ro * t.ncols;
+            mrows += ro;
         }
-        merges.push_back(QRTask{m0 * k, t.dst, (int32_t)(mrow - m0), t.rout});
+        merges.push_back(QRTask{m0, t.dst, mrows, t.rout, t.ncols, t.ncols});
     }
     DBuf<cx<TQ>> scratch, merge;
     launch_tsqr<T, TQ, T, RPL>(direct, k, src, dst, scratch, s, ev, err);
     if (!groups.empty()) {
-        merge.alloc((size_t)mrow * k);
+        merge.alloc((size_t)mel);
         launch_tsqr<T, TQ, TQ, RPL>(groups, k, src, merge.p, scratch, s, ev, err);
         launch_tsqr<TQ, TQ, T, RPL>(merges, k, merge.p, dst, scratch, s, ev, err);
     }
@@ -1383,27 +1621,47 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
 template <class T>
 void Num<T>::basis_weights(cudaStream_t s) {
     R_.alloc(std::max<int64_t>(offR_[na_], 1));
+    P_.alloc(std::max<int64_t>(offP_[na_], 1));
     DBuf<cx<T>> stack;
+    DBuf<cx<double>> gscr;
     const int kk = k_;
     for (int l = hs_.depth; l >= 0; --l) {
-        std::vector<QRTask> leafq, innerq;
+        std::vector<OrthTask> leafo;
+        std::vector<QRTask> innerq;
         std::vector<KronTask> kron;
-        int64_t srow = 0;
+        int64_t srow = 0, gel = 0;
+        int smem_n = 0;
+        for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a)
+            if (leaf_[a]) smem_n = std::max(smem_n, std::min(rows_[a], 64));
         for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a) {
             if (leaf_[a]) {
-                leafq.push_back(QRTask{offV_[a], offR_[a], rows_[a], rR_[a]});
-                work_[K_TSQR] += 8.0 * rows_[a] * kk * kk;
+                OrthTask o{offV_[a], offP_[a], offR_[a], gel, rows_[a], rR_[a]};
+                if (rows_[a] > smem_n) gel += eig_global_elems(rows_[a]);
+                leafo.push_back(o);
+                work_[K_TRUNCATE] += 8.0 * rows_[a] * rows_[a] * kk + 8.0 * rR_[a] * kk * rows_[a];
             } else {
                 int32_t s0 = sons_[0][a], s1 = sons_[1][a];
                 kron.push_back(KronTask{offR_[s0], offE_[a], srow * kk, rR_[s0], 0});
                 kron.push_back(KronTask{offR_[s1], offE_[a] + 3 * m_ * m_, (srow + rR_[s0]) * kk, rR_[s1], 0});
-                innerq.push_back(QRTask{srow * kk, offR_[a], rR_[s0] + rR_[s1], rR_[a]});
+                innerq.push_back(QRTask{srow * kk, offR_[a], rR_[s0] + rR_[s1], rR_[a], kk, kk});
                 work_[K_TSQR] += 8.0 * (rR_[s0] + rR_[s1]) * kk * kk;
                 work_[K_KRON] += 24.0 * m_ * kk * (rR_[s0] + rR_[s1]);
                 srow += rR_[s0] + rR_[s1];
             }
         }
-        tsqr(leafq, V_.p, R_.p, s, "basis weights (leaves)");
+        if (!leafo.empty()) {
+            gscr.reserve(std::max<int64_t>(gel, 1));
+            DBuf<OrthTask> d;
+            upload_vec(d, leafo, s);
+            const size_t smem = eig_smem_bytes(smem_n);
+            auto kern = k_leaf_orth<T>;
+            DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ev_.begin(K_TRUNCATE, s);
+            kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, V_.p, gscr.p, smem_n, P_.p, R_.p, err_.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_leaf_orth");
+            check_err(s, "leaf basis weights");
+        }
         if (!kron.empty()) {
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             DBuf<KronTask> d;
@@ -1429,7 +1687,10 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
     const auto& ptr = pass == 0 ? h.row_ptr : h.col_ptr;
     const auto& idx = pass == 0 ? h.row_idx : h.col_idx;
     Z_[pass].alloc(std::max<int64_t>(offZ_[pass][na_], 1));
-    if (pass == 0) bnorm_.alloc(std::max<int64_t>((int64_t)h.adm_t.size(), 1));
+    if (pass == 0) {
+        bnorm_.alloc(std::max<int64_t>((int64_t)h.adm_t.size(), 1));
+        K_.alloc(std::max<int64_t>(offK_.back(), 1));
+    }
     const int kk = k_;
     const int64_t cap_rows = std::max<int64_t>(
         64, (bp_.workspace_bytes > 0 ? bp_.workspace_bytes : (int64_t(16) << 30)) / ((int64_t)kk * sizeof(cx<T>)));
@@ -1438,12 +1699,14 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
         int64_t a = h.alevel_start[l];
         const int64_t aend = h.alevel_start[l + 1];
         while (a < aend) {
-            std::vector<BlockRowTask> btasks;
-            std::vector<KronTask> ptasks;
+            std::vector<BlockRowTask> btasks;   // rows generated from S_b
+            std::vector<KRowTask> ktasks;       // column pass, leaf column cluster: rows from K_b
+            std::vector<KronTask> ptasks;       // rows inherited from the father
+            std::vector<RhTask> rhtasks;        // father rows of leaf pairs, projected
             std::vector<QRTask> qtasks;
             int64_t srow = 0;
             for (; a < aend; ++a) {
-                int32_t t = h.a_t[a], c = h.a_c[a], tc = h.tc_base[t] + c;
+                const int32_t t = h.a_t[a], c = h.a_c[a], tc = h.tc_base[t] + c;
                 int64_t rows = 0;
                 for (int32_t e = ptr[tc]; e < ptr[tc + 1]; ++e) {
                     int32_t other = pass == 0 ? h.adm_s[idx[e]] : h.adm_t[idx[e]];
@@ -1451,26 +1714,34 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                 }
                 for (auto& pr : parents_[a]) rows += rZ_[pass][pr.first];
                 if (srow > 0 && srow + rows > cap_rows) break;   // next group
-                int64_t r0 = srow;
+                const int64_t r0 = srow;
+                const int32_t zc = zcols(a);
                 for (int32_t e = ptr[tc]; e < ptr[tc + 1]; ++e) {
-                    int32_t b = idx[e];
-                    int32_t other = pass == 0 ? h.adm_s[b] : h.adm_t[b];
-                    int32_t ao = h.pair_of(other, c);
-                    btasks.push_back(BlockRowTask{b, ao, (int32_t)a, 0, srow * kk});
-                    work_[K_STACK_BLOCKS] += kEvalFlops * kk * kk + 8.0 * rR_[ao] * kk * kk +
-                                             (pass == 0 ? 8.0 * rR_[a] * kk * rR_[ao] : 0.0);
+                    const int32_t b = idx[e];
+                    const int32_t other = pass == 0 ? h.adm_s[b] : h.adm_t[b];
+                    const int32_t ao = h.pair_of(other, c);
+                    if (pass == 1 && leaf_[a]) {
+                        // rows w K_b (r_t x r_s) from the row pass, no coupling evaluation
+                        ktasks.push_back(KRowTask{offK_[b], srow * kk, b, rR_[ao], rR_[a], 0});
+                    } else {
+                        btasks.push_back(BlockRowTask{b, ao, (int32_t)a, pass == 0 ? (int32_t)leaf_[a] : 0,
+                                                      srow * kk, pass == 0 ? offK_[b] : 0});
+                        work_[K_STACK_BLOCKS] += kEvalFlops * kk * kk + 8.0 * rR_[ao] * kk * kk +
+                                                 (pass == 0 ? 8.0 * rR_[a] * kk * rR_[ao] : 0.0);
+                    }
                     srow += rR_[ao];
                 }
                 for (auto& pr : parents_[a]) {
-                    int32_t ap = pr.first;
+                    const int32_t ap = pr.first;
                     if (rZ_[pass][ap] == 0) continue;
                     ptasks.push_back(KronTask{offZ_[pass][ap], offE_[ap] + (int64_t)pr.second * 3 * m_ * m_,
                                               srow * kk, rZ_[pass][ap], 1});
+                    if (leaf_[a]) rhtasks.push_back(RhTask{srow * kk, offR_[a], rZ_[pass][ap], rR_[a]});
                     work_[K_KRON] += 24.0 * m_ * kk * rZ_[pass][ap];
                     srow += rZ_[pass][ap];
                 }
-                qtasks.push_back(QRTask{r0 * kk, offZ_[pass][a], (int32_t)(srow - r0), rZ_[pass][a]});
-                work_[K_TSQR] += 8.0 * (srow - r0) * kk * kk;
+                qtasks.push_back(QRTask{r0 * kk, offZ_[pass][a], (int32_t)(srow - r0), rZ_[pass][a], zc, kk});
+                work_[K_TSQR] += 8.0 * (srow - r0) * zc * zc;
             }
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             if (!btasks.empty()) {
@@ -1480,9 +1751,16 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                 ev_.begin(K_STACK_BLOCKS, s);
                 k_stack_blocks<T><<<(unsigned)btasks.size(), kThreads, smem, s>>>(
                     d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p, st_.dir_off_d.p,
-                    st_.dirs.p, nodes_.p, m_, bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack.p, err_.p);
+                    st_.dirs.p, nodes_.p, m_, bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack.p, K_.p,
+                    err_.p);
                 ev_.end(s);
                 DH2_CHECK_LAUNCH("k_stack_blocks");
+            }
+            if (!ktasks.empty()) {
+                DBuf<KRowTask> d;
+                upload_vec(d, ktasks, s);
+                k_stack_from_K<T><<<(unsigned)ktasks.size(), 128, 0, s>>>(d.p, kk, K_.p, bnorm_.p, stack.p);
+                DH2_CHECK_LAUNCH("k_stack_from_K");
             }
             if (!ptasks.empty()) {
                 DBuf<KronTask> d;
@@ -1493,6 +1771,13 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                                                                                    stack.p);
                 ev_.end(s);
                 DH2_CHECK_LAUNCH("k_kron");
+            }
+            if (!rhtasks.empty()) {
+                DBuf<RhTask> d;
+                upload_vec(d, rhtasks, s);
+                k_rows_rh<T><<<(unsigned)rhtasks.size(), kThreads, (size_t)kk * sizeof(cx<T>), s>>>(d.p, kk, R_.p,
+                                                                                                   stack.p);
+                DH2_CHECK_LAUNCH("k_rows_rh");
             }
             tsqr(qtasks, stack.p, Z_[pass].p, s, pass == 0 ? "total weights (rows)" : "total weights (columns)");
         }
@@ -1506,6 +1791,7 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
     const auto& h = hs_;
     const int kk = k_;
     Q_[pass].alloc(std::max<int64_t>(offQ_[pass][na_], 1));
+    Up_[pass].alloc(std::max<int64_t>(offUp_[pass][na_], 1));
     Cd_[pass].alloc(std::max<int64_t>(offC_[pass][na_], 1));
     if constexpr (std::is_same<T, float>::value) Ct_[pass].alloc(std::max<int64_t>(offC_[pass][na_], 1));
     sig_[pass].alloc(std::max<int64_t>(offSig_[pass][na_], 1));
@@ -1513,17 +1799,38 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
     cx<T>* Ct = nullptr;
     if constexpr (std::is_same<T, float>::value) Ct = Ct_[pass].p;
     else Ct = reinterpret_cast<cx<T>*>(Cd_[pass].p);
-    DBuf<cx<double>> vhat, ascr;
+    DBuf<cx<T>> vhat, ascr;
+    DBuf<cx<double>> gscr, lscr;
     for (int l = h.depth; l >= 0; --l) {
         const int64_t a0 = h.alevel_start[l], a1 = h.alevel_start[l + 1];
         if (a1 == a0) continue;
         std::vector<KronTask> kron;
         std::vector<TruncTask> tt;
-        int64_t vrow = 0, aoff = 0;
-        int smem_n = 0;
+        std::vector<LeafTruncTask> lt;
+        int64_t vrow = 0, aoff = 0, gel = 0;
+        int smem_n = 0, smem_l = 0;
         for (int64_t a = a0; a < a1; ++a) {
+            if (leaf_[a]) {
+                LeafTruncTask t{};
+                t.z = offZ_[pass][a];
+                t.p = offP_[a];
+                t.r = offR_[a];
+                t.q = offQ_[pass][a];
+                t.c = offC_[pass][a];
+                t.sig = offSig_[pass][a];
+                t.rz = rZ_[pass][a];
+                t.rt = rR_[a];
+                t.n = rows_[a];
+                t.qld = (int32_t)ldQ_[pass][a];
+                t.up = offUp_[pass][a];
+                t.a = (int32_t)a;
+                smem_l = std::max(smem_l, std::min(t.rt, 64));
+                lt.push_back(t);
+                work_[K_TRUNCATE] += 8.0 * t.rt * t.rt * t.rz + 8.0 * t.n * t.rt * t.rt + 8.0 * t.rt * t.rt * kk;
+                continue;
+            }
             TruncTask tk{};
-            tk.leaf = leaf_[a];
+            tk.leaf = 0;
             tk.a = (int32_t)a;
             tk.rz = rZ_[pass][a];
             tk.z = offZ_[pass][a];
@@ -1531,61 +1838,70 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
             tk.qld = (int32_t)ldQ_[pass][a];
             tk.c = offC_[pass][a];
             tk.sig = offSig_[pass][a];
-            if (leaf_[a]) {
-                tk.rows = rows_[a];
-                tk.vsrc = offV_[a];
-            } else {
-                int32_t s0 = sons_[0][a], s1 = sons_[1][a];
-                int32_t k0 = rank_[pass][s0], k1 = rank_[pass][s1];
-                tk.rows = k0 + k1;
-                tk.vsrc = vrow * kk;
-                if (k0) kron.push_back(KronTask{offC_[pass][s0], offE_[a], vrow * kk, k0, 0});
-                if (k1) kron.push_back(KronTask{offC_[pass][s1], offE_[a] + 3 * m_ * m_, (vrow + k0) * kk, k1, 0});
-                vrow += k0 + k1;
-            }
-            tk.ascratch = aoff;
+            int32_t s0 = sons_[0][a], s1 = sons_[1][a];
+            int32_t k0 = rank_[pass][s0], k1 = rank_[pass][s1];
+            tk.rows = k0 + k1;
+            tk.vsrc = vrow * kk;
+            if (k0) kron.push_back(KronTask{offC_[pass][s0], offE_[a], vrow * kk, k0, 0});
+            if (k1) kron.push_back(KronTask{offC_[pass][s1], offE_[a] + 3 * m_ * m_, (vrow + k0) * kk, k1, 0});
+            vrow += k0 + k1;
             smem_n = std::max(smem_n, std::min(tk.rows, 64));
             tt.push_back(tk);
             // A = V Z^* and M = A A^* (the Jacobi sweeps and C = Q^* V are not counted)
             work_[K_TRUNCATE] += 8.0 * tk.rows * tk.rz * kk + 8.0 * tk.rows * tk.rows * tk.rz;
         }
-        // scratch per task: A (rows x rz), plus M, U, rotations, eigenvalues, order when rows > smem_n
+        for (auto& t : lt) {
+            t.scr = gel;
+            if (t.rt > smem_l) gel += eig_global_elems(t.rt);
+        }
+        // scratch per task: A (rows x rz, working precision) and, when rows > smem_n, a
+        // global FP64 Jacobi slot
+        int64_t goff = 0;
         for (auto& tk : tt) {
             tk.ascratch = aoff;
-            int64_t need = (int64_t)tk.rows * std::max(tk.rz, 1);
-            if (tk.rows > smem_n) {
-                int64_t extra_bytes = 2 * (int64_t)tk.rows * tk.rows * sizeof(cx<double>) +
-                                      (tk.rows / 2 + 1) * sizeof(JRot<double>) + tk.rows * (sizeof(double) + sizeof(int));
-                need += (extra_bytes + sizeof(cx<double>) - 1) / sizeof(cx<double>) + 4;
-            }
-            aoff += (need + 3) & ~int64_t(3);
+            aoff += ((int64_t)tk.rows * std::max(tk.rz, 1) + 3) & ~int64_t(3);
+            tk.gslot = goff;
+            if (tk.rows > smem_n) goff += eig_global_elems(tk.rows);
         }
         vhat.reserve(std::max<int64_t>(vrow * kk, 1));
         ascr.reserve(std::max<int64_t>(aoff, 1));
+        gscr.reserve(std::max<int64_t>(goff, 1));
+        lscr.reserve(std::max<int64_t>(gel, 1));
+        if (!lt.empty()) {
+            DBuf<LeafTruncTask> d;
+            upload_vec(d, lt, s);
+            const size_t smem = eig_smem_bytes(smem_l);
+            auto kern = k_trunc_leaf<T>;
+            DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ev_.begin(K_TRUNCATE, s);
+            kern<<<(unsigned)lt.size(), kThreads, smem, s>>>(d.p, kk, Z_[pass].p, P_.p, R_.p, lscr.p, smem_l,
+                                                              bp_.eps, bp_.rank_rule, Q_[pass].p, Cd_[pass].p, Ct,
+                                                              sig_[pass].p, rank_d_[pass].p, Up_[pass].p, err_.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_trunc_leaf");
+        }
         if (!kron.empty()) {
             DBuf<KronTask> d;
             upload_vec(d, kron, s);
-            size_t smem = (2 * (size_t)kk + 3 * m_ * m_) * sizeof(cx<double>);
+            size_t smem = (2 * (size_t)kk + 3 * m_ * m_) * sizeof(cx<T>);
             ev_.begin(K_KRON, s);
-            k_kron<double, T, double, double><<<(unsigned)kron.size(), kThreads, smem, s>>>(
-                d.p, m_, Cd_[pass].p, E_.p, vhat.p);
+            k_kron<T, T, T, T><<<(unsigned)kron.size(), kThreads, smem, s>>>(d.p, m_, Ct, E_.p, vhat.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_kron");
         }
-        DBuf<TruncTask> d;
-        upload_vec(d, tt, s);
-        size_t smem = smem_n > 0 ? 2 * (size_t)smem_n * smem_n * sizeof(cx<double>) +
-                                       (smem_n / 2 + 1) * sizeof(JRot<double>) +
-                                       smem_n * (sizeof(double) + sizeof(int)) + 64
-                                 : 64;
-        auto kern = k_truncate<T>;
-        DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        ev_.begin(K_TRUNCATE, s);
-        kern<<<(unsigned)tt.size(), kThreads, smem, s>>>(d.p, kk, V_.p, vhat.p, Z_[pass].p, ascr.p, nullptr,
-                                                          smem_n, bp_.eps, bp_.rank_rule, Q_[pass].p,
-                                                          Cd_[pass].p, Ct, sig_[pass].p, rank_d_[pass].p, err_.p);
-        ev_.end(s);
-        DH2_CHECK_LAUNCH("k_truncate");
+        if (!tt.empty()) {
+            DBuf<TruncTask> d;
+            upload_vec(d, tt, s);
+            size_t smem = eig_smem_bytes(smem_n);
+            auto kern = k_truncate<T>;
+            DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ev_.begin(K_TRUNCATE, s);
+            kern<<<(unsigned)tt.size(), kThreads, smem, s>>>(d.p, kk, vhat.p, Z_[pass].p, ascr.p, gscr.p, smem_n,
+                                                              bp_.eps, bp_.rank_rule, Q_[pass].p, Cd_[pass].p, Ct,
+                                                              sig_[pass].p, rank_d_[pass].p, err_.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_truncate");
+        }
         std::vector<int32_t> rk(a1 - a0);
         DH2_CHECK_CUDA(cudaMemcpyAsync(rk.data(), rank_d_[pass].p + a0, (a1 - a0) * sizeof(int32_t),
                                        cudaMemcpyDeviceToHost, s));
@@ -1628,10 +1944,21 @@ void Num<T>::project(cudaStream_t s) {
         p.crow = offC_[0][at];
         p.ccol = offC_[1][as];
         p.dst = st_off_[b];
+        p.leafpair = leaf_[at] && leaf_[as];
+        if (p.leafpair) {
+            p.koff = offK_[b];
+            p.upt = offUp_[0][at];
+            p.ups = offUp_[1][as];
+            p.rt = rR_[at];
+            p.rs = rR_[as];
+            p.ldt = (int32_t)ldQ_[0][at];
+            p.lds = (int32_t)ldQ_[1][as];
+        }
         off += (int64_t)p.kt * p.ks;
         pt[b] = p;
         if (p.kt && p.ks)
-            work_[K_PROJECT] += kEvalFlops * k_ * k_ + 8.0 * p.kt * k_ * k_ + 8.0 * p.kt * k_ * p.ks;
+            work_[K_PROJECT] += p.leafpair ? 8.0 * p.kt * p.rt * p.rs + 8.0 * p.kt * p.rs * p.ks
+                                           : kEvalFlops * k_ * k_ + 8.0 * p.kt * k_ * k_ + 8.0 * p.kt * k_ * p.ks;
     }
     info.coupling_entries = off;
     St_.alloc(std::max<int64_t>(off, 1));
@@ -1653,7 +1980,8 @@ void Num<T>::project(cudaStream_t s) {
     ev_.begin(K_PROJECT, s);
     k_project<T><<<(unsigned)grid, kThreads, smem, s>>>(d.p, nb, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
                                                         tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
-                                                        bp_.kappa, Crow, Ccol, scratch.p, St_.p);
+                                                        bp_.kappa, Crow, Ccol, K_.p, Up_[0].p, Up_[1].p, scratch.p,
+                                                        St_.p);
     ev_.end(s);
     DH2_CHECK_LAUNCH("k_project");
     DH2_CHECK_CUDA(cudaStreamSynchronize(s));
@@ -2058,7 +2386,11 @@ void Num<T>::export_pair(int which, int64_t tc, double* out, int64_t cap, int32_
     const int rowsA = leaf_[a] ? rows_[a] : rank_[pass][sons_[0][a]] + rank_[pass][sons_[1][a]];
     switch (which) {
         case DH2_X_R: r = rR_[a]; c = k_; ld = k_; off = offR_[a]; src = R_.p; break;
-        case DH2_X_ZROW: case DH2_X_ZCOL: r = rZ_[pass][a]; c = k_; ld = k_; off = offZ_[pass][a]; src = Z_[pass].p; break;
+        case DH2_X_ZROW: case DH2_X_ZCOL:
+            r = rZ_[pass][a]; c = zcols(a); ld = c; off = offZ_[pass][a]; src = Z_[pass].p; break;
+        case DH2_X_P:
+            if (!leaf_[a]) return;
+            r = rows_[a]; c = rR_[a]; ld = c; off = offP_[a]; src = P_.p; break;
         case DH2_X_SROW: case DH2_X_SCOL:
             r = 1; c = std::min(rowsA, rZ_[pass][a]); ld = c; off = offSig_[pass][a]; src = sig_[pass].p;
             is_real = true; is_double = true; break;

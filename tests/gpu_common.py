@@ -57,3 +57,30 @@ def rel(a, b):
 
 def x_vector(n):
     return synth.random_vector(n, 1809_0001)
+
+
+def check_total_weight(mat, rc, tc, which, Zo, tol):
+    """Z^*Z of the GPU total weight against the oracle's, on the invariant the paper fixes.
+
+    Leaf pairs keep their total weight in the coordinates of the orthonormal basis P of
+    V_tc = P R_tc, so P Z'^* Z' P^* is compared with V Z^* Z V^*; other pairs compare
+    Z^* Z directly (k x k).
+    """
+    import paper_1809_04384_gb300 as dh2
+
+    P_ = rc.pairs
+    t = int(np.searchsorted(P_.base, tc, side="right") - 1)
+    c = int(tc - P_.base[t])
+    Z = mat.pair(which, tc)
+    if rc.tree.is_leaf(t):
+        Pm = mat.pair(dh2.DH2_X_P, tc)
+        V = rc.dh2.leaf_basis(t, c)
+        lhs = Pm @ (Z.conj().T @ Z) @ Pm.conj().T
+        rhs = V @ (Zo.conj().T @ Zo) @ V.conj().T
+    else:
+        assert Z.shape == Zo.shape
+        lhs, rhs = Z.conj().T @ Z, Zo.conj().T @ Zo
+    if np.linalg.norm(rhs) == 0:
+        assert np.linalg.norm(lhs) == 0
+        return
+    assert rel(lhs, rhs) <= tol, (which, tc, rel(lhs, rhs))

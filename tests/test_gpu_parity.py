@@ -9,7 +9,8 @@ import numpy as np
 import pytest
 
 from tests.cases import mesh, params
-from tests.gpu_common import TOL, gpu_matrix, oracle_recompression, oracle_structure, rel, x_vector
+from tests.gpu_common import (TOL, check_total_weight, gpu_matrix, oracle_recompression, oracle_structure,
+                              rel, x_vector)
 
 pytestmark = pytest.mark.gpu
 
@@ -111,10 +112,7 @@ def test_weights_and_singular_values(name, precision):
         go = Ro.conj().T @ Ro
         assert rel(R.conj().T @ R, go) <= tol["gram"], ("R", tc)
         for which, Zo in ((dh2.DH2_X_ZROW, rc.ZR[tc]), (dh2.DH2_X_ZCOL, rc.ZC[tc])):
-            Z = mat.pair(which, tc)
-            assert Z.shape == Zo.shape
-            if Zo.size:
-                assert rel(Z.conj().T @ Z, Zo.conj().T @ Zo) <= tol["gram"], ("Z", which, tc)
+            check_total_weight(mat, rc, tc, which, Zo, tol["gram"])
         for which, so in ((dh2.DH2_X_SROW, rc.row["sigma"][tc]), (dh2.DH2_X_SCOL, rc.col["sigma"][tc])):
             s = mat.pair(which, tc).real.ravel()
             n = min(len(s), len(so))
@@ -201,9 +199,7 @@ def test_grouped_weight_qr_matches_oracle(name, precision):
     tol = TOL[precision]
     for tc in np.nonzero(rc.pairs.active)[0]:
         for which, Zo in ((dh2.DH2_X_ZROW, rc.ZR[tc]), (dh2.DH2_X_ZCOL, rc.ZC[tc])):
-            Z = mat.pair(which, tc)
-            if Zo.size:
-                assert rel(Z.conj().T @ Z, Zo.conj().T @ Zo) <= tol["gram"], (which, tc)
+            check_total_weight(mat, rc, tc, which, Zo, tol["gram"])
     x = x_vector(rc.tree.n)
     dt = torch.complex128 if precision == "fp64" else torch.complex64
     y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
