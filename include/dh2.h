@@ -58,7 +58,8 @@ typedef struct {
                                DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted */
     int32_t qr_fp64;        /* DH2_MIXED only: 1 = run the weight QRs (R, Z-hat) in FP64 */
     int32_t qr_group_rows;  /* stacks taller than this are factored in row groups whose R
-                               factors are merged by a second QR (0 = 1024) */
+                               factors are merged by a second QR (0 = 1024 rows, 8192 for
+                               stacks of at most 32 columns) */
     int64_t workspace_bytes;/* cap on the stacked weight workspace per level (0 = 16 GiB) */
 } dh2_options;
 

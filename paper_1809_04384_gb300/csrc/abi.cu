@@ -198,8 +198,8 @@ dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, dou
         mat->structure_ms = ms;
         mat->depth = mat->tr.depth;
         DH2_REQUIRE(o.qr_group_rows >= 0, "dh2_build_dh2: qr_group_rows must be >= 0");
-        mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64,
-                              o.qr_group_rows > 0 ? o.qr_group_rows : 1024, o.workspace_bytes};
+        mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
+                              o.workspace_bytes};
         mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
         mat->num->build(s);
         mat->num->info.stage_ms[ST_STRUCTURE] += ms;

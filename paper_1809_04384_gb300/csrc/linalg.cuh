@@ -108,64 +108,109 @@ struct DenseCvt {
 // --------------------------------------------------------------------------- CTA GEMM
 
 // C(i,j) = sum_k A(i,k) B(k,j) for 0<=i<M, 0<=j<N; `store(i, j, value)` is called
-// once per output.  256 threads, 64 x 64 output tiles, 4 x 4 per thread.
-// smem: 2 * 64 * 8 cx<T> = 2 KB (T=float) / 4 KB (double).
-// one staging buffer per element type and kernel, shared by every cta_gemm call
+// once per output.  256 threads as 16 x 16, BM x BN output tiles, (BM/16) x (BN/16)
+// outputs per thread (rows ty + 16a, columns tx + 16b), K in steps of 8.  The operands
+// of the next K step are fetched (or generated) into registers while the current step
+// is multiplied out of shared memory.
+// One staging buffer per element type and kernel, shared by every cta_gemm call:
+// 8 * (64 + 128) cx<T> = 12 KB (T=float) / 24 KB (double).
 template <class T>
 __device__ __forceinline__ cx<T>* gemm_smem() {
-    __shared__ cx<T> buf[2 * 8 * 64];
+    __shared__ cx<T> buf[8 * (64 + 128)];
     return buf;
 }
 
-template <class T, class FA, class FB, class FS>
-__device__ void cta_gemm(int M, int N, int K, const FA& A, const FB& B, const FS& store) {
-    constexpr int BM = 64, BN = 64, BK = 8;
+template <class T, int BM, int BN, class FA, class FB, class FS>
+__device__ void cta_gemm_t(int M, int N, int K, const FA& A, const FB& B, const FS& store) {
+    constexpr int BK = 8, TM = BM / 16, TN = BN / 16;
+    constexpr int LA = BM * BK / 256, LB = BN * BK / 256;   // staged elements per thread
+    static_assert(BM % 32 == 0 && BN % 32 == 0 && BM <= 64 && BN <= 128, "tile shape");
     cx<T> (*sA)[BM] = reinterpret_cast<cx<T> (*)[BM]>(gemm_smem<T>());
     cx<T> (*sB)[BN] = reinterpret_cast<cx<T> (*)[BN]>(gemm_smem<T>() + BK * BM);
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;    // 16 x 16 threads
+    const int tx = tid & 15, ty = tid >> 4;
     for (int i0 = 0; i0 < M; i0 += BM) {
         for (int j0 = 0; j0 < N; j0 += BN) {
-            cx<T> acc[4][4];
+            cx<T> acc[TM][TN];
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < TM; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) acc[a][b] = zero<T>();
+                for (int b = 0; b < TN; ++b) acc[a][b] = zero<T>();
+            cx<T> ra[LA], rb[LB];
+            // A is read along k (consecutive threads take consecutive k of one row),
+            // B along j.
+            auto fetch = [&](int k0) {
+#pragma unroll
+                for (int r = 0; r < LA; ++r) {
+                    const int e = tid + r * 256, kk = e % BK, ii = e / BK;
+                    const int gi = i0 + ii, gk = k0 + kk;
+                    ra[r] = (gi < M && gk < K) ? A(gi, gk) : zero<T>();
+                }
+#pragma unroll
+                for (int r = 0; r < LB; ++r) {
+                    const int e = tid + r * 256, kk = e / BN, jj = e % BN;
+                    const int gj = j0 + jj, gk = k0 + kk;
+                    rb[r] = (gj < N && gk < K) ? B(gk, gj) : zero<T>();
+                }
+            };
+            fetch(0);
             for (int k0 = 0; k0 < K; k0 += BK) {
-                // 512 elements per tile, 2 per thread
+                __syncthreads();   // the previous step's reads of sA/sB are done
 #pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    int e = tid + r * 256;
-                    int kk = e / BM, ii = e % BM;
-                    int gi = i0 + ii, gk = k0 + kk;
-                    sA[kk][ii] = (gi < M && gk < K) ? A(gi, gk) : zero<T>();
-                    int jj = e % BN;
-                    int gj = j0 + jj;
-                    sB[kk][jj] = (gj < N && gk < K) ? B(gk, gj) : zero<T>();
+                for (int r = 0; r < LA; ++r) {
+                    const int e = tid + r * 256;
+                    sA[e % BK][e / BK] = ra[r];
+                }
+#pragma unroll
+                for (int r = 0; r < LB; ++r) {
+                    const int e = tid + r * 256;
+                    sB[e / BN][e % BN] = rb[r];
                 }
                 __syncthreads();
+                if (k0 + BK < K) fetch(k0 + BK);
 #pragma unroll
                 for (int kk = 0; kk < BK; ++kk) {
-                    cx<T> av[4], bv[4];
+                    cx<T> av[TM], bv[TN];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a) av[a] = sA[kk][ty + 16 * a];
+                    for (int a = 0; a < TM; ++a) av[a] = sA[kk][ty + 16 * a];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) bv[b] = sB[kk][tx + 16 * b];
+                    for (int b = 0; b < TN; ++b) bv[b] = sB[kk][tx + 16 * b];
 #pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                    for (int a = 0; a < TM; ++a)
 #pragma unroll
-                        for (int b = 0; b < 4; ++b) fma_cx(acc[a][b], av[a], bv[b]);
+                        for (int b = 0; b < TN; ++b) fma_cx(acc[a][b], av[a], bv[b]);
                 }
-                __syncthreads();
             }
+            __syncthreads();   // sA/sB free for the next tile or the caller
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < TM; ++a)
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
+                for (int b = 0; b < TN; ++b) {
+                    const int gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
                     if (gi < M && gj < N) store(gi, gj, acc[a][b]);
                 }
         }
+    }
+}
+
+// 64 x 64 tiles: the general shape
+template <class T, class FA, class FB, class FS>
+__device__ void cta_gemm(int M, int N, int K, const FA& A, const FB& B, const FS& store) {
+    cta_gemm_t<T, 64, 64>(M, N, K, A, B, store);
+}
+
+// Tile shape from the sizes: 32-row tiles when M <= 32 (most leaf ranks), 128-wide (FP32)
+// when N > 64 (the k columns of a coupling matrix).
+template <class T, class FA, class FB, class FS>
+__device__ void cta_gemm_fit(int M, int N, int K, const FA& A, const FB& B, const FS& store) {
+    constexpr int WIDE = sizeof(T) == 4 ? 128 : 64;   // FP64 accumulators: at most 64 wide
+    if (M <= 32) {
+        if (N <= 32) cta_gemm_t<T, 32, 32>(M, N, K, A, B, store);
+        else if (N <= 64) cta_gemm_t<T, 32, 64>(M, N, K, A, B, store);
+        else cta_gemm_t<T, 32, WIDE>(M, N, K, A, B, store);
+    } else {
+        if (N <= 64) cta_gemm_t<T, 64, 64>(M, N, K, A, B, store);
+        else cta_gemm_t<T, 64, WIDE>(M, N, K, A, B, store);
     }
 }
 

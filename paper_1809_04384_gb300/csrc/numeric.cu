@@ -240,39 +240,81 @@ __global__ void k_nearfield(const NearSeg* __restrict__ segs, QuadRows<T> qr,
 // ----------------------------------------------------------------------------- coupling generator
 
 // S_b[nu][mu] = g_c(xi_{t,nu}, xi_{s,mu}) from per-axis tables in shared memory:
-// D[a][i][j] = xi_{t,a,i} - xi_{s,a,j} and P[a][i][j] = D[a][i][j] c_a (evaluated in FP64).
+// D[a][i][j] = xi_{t,a,i} - xi_{s,a,j} and P[a][i][j] = D[a][i][j] c_a (evaluated in FP64),
+// and index tables dn[nu], dm[mu] that hold the three per-axis table offsets of a node in
+// 10-bit fields, so that dn[nu] + dm[mu] packs the offsets of the pair (no division by m).
 template <class T>
 struct SGen {
     const T* D;
     const T* P;
-    int m;
+    const uint32_t* dn;
+    const uint32_t* dm;
     T kappa;
     __device__ __forceinline__ cx<T> operator()(int nu, int mu) const {
-        const int mm = m * m;
-        int nx = nu % m, ny = (nu / m) % m, nz = nu / mm;
-        int mx = mu % m, my = (mu / m) % m, mz = mu / mm;
-        int ix = nx * m + mx, iy = mm + ny * m + my, iz = 2 * mm + nz * m + mz;
-        T dx = D[ix], dy = D[iy], dz = D[iz];
-        T r = sqrt(dx * dx + dy * dy + dz * dz);
-        T ph = kappa * (r - (P[ix] + P[iy] + P[iz]));
-        T s, c;
-        sc(ph, &s, &c);
-        T f = T(1) / (T(4.0 * kPi) * r);
-        return cx<T>{c * f, s * f};
+        const uint32_t u = dn[nu] + dm[mu];
+        const int ix = u & 1023u, iy = (u >> 10) & 1023u, iz = u >> 20;
+        return value(D[ix], D[iy], D[iz], P[ix] + P[iy] + P[iz]);
     }
+    // exp(i kappa (r - p)) / (4 pi r), r = |d|
+    __device__ __forceinline__ cx<T> value(T dx, T dy, T dz, T p) const;
 };
 
+// FP32: r from the reciprocal square root; the phase is brought to [-pi, pi] by Cody and
+// Waite's two-constant reduction (2 pi split into a float head and the float of the
+// remainder), after which the hardware sine and cosine are accurate to about 4e-7.
+template <>
+__device__ __forceinline__ cx<float> SGen<float>::value(float dx, float dy, float dz, float p) const {
+    constexpr double k2pi = 2.0 * kPi;
+    constexpr float hi = (float)k2pi;
+    constexpr float lo = (float)(k2pi - (double)hi);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = rsqrtf(r2);
+    const float ph = kappa * (r2 * ri - p);
+    const float j = rintf(ph * (float)(1.0 / k2pi));
+    float red = fmaf(-j, hi, ph);
+    red = fmaf(-j, lo, red);
+    float s, c;
+    __sincosf(red, &s, &c);
+    const float f = ri * (float)(1.0 / (4.0 * kPi));
+    return cx<float>{c * f, s * f};
+}
+
+template <>
+__device__ __forceinline__ cx<double> SGen<double>::value(double dx, double dy, double dz, double p) const {
+    const double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double s, c;
+    sincos(kappa * (r - p), &s, &c);
+    const double f = 1.0 / (4.0 * kPi * r);
+    return cx<double>{c * f, s * f};
+}
+
+// shared memory of the generator tables: D, P (3 m^2 each), dn, dm (m^3 each)
 template <class T>
-__device__ void load_sgen_tables(int32_t t, int32_t s, const double* __restrict__ cdir,
-                                 const double* __restrict__ nodes, int m, T* D, T* P) {
-    const int mm = m * m;
+__host__ __device__ inline size_t sgen_smem_bytes(int m) {
+    return 2 * 3 * (size_t)m * m * sizeof(T) + 2 * (size_t)m * m * m * sizeof(uint32_t);
+}
+
+template <class T>
+__device__ SGen<T> load_sgen_tables(int32_t t, int32_t s, const double* __restrict__ cdir,
+                                    const double* __restrict__ nodes, int m, double kappa, unsigned char* sm) {
+    const int mm = m * m, k = mm * m;
+    T* D = reinterpret_cast<T*>(sm);
+    T* P = D + 3 * mm;
+    uint32_t* dn = reinterpret_cast<uint32_t*>(P + 3 * mm);
+    uint32_t* dm = dn + k;
     for (int idx = threadIdx.x; idx < 3 * mm; idx += blockDim.x) {
         int a = idx / mm, r = idx % mm, i = r / m, j = r % m;
         double d = nodes[((int64_t)t * 3 + a) * m + i] - nodes[((int64_t)s * 3 + a) * m + j];
         D[idx] = (T)d;
         P[idx] = (T)(d * cdir[a]);
     }
+    for (int nu = threadIdx.x; nu < k; nu += blockDim.x) {
+        const uint32_t nx = nu % m, ny = (nu / m) % m, nz = nu / mm;
+        dn[nu] = nx * m | (mm + ny * m) << 10 | (2 * mm + nz * m) << 20;
+        dm[nu] = nx | ny << 10 | nz << 20;
+    }
     __syncthreads();
+    return SGen<T>{D, P, dn, dm, (T)kappa};
 }
 
 // ----------------------------------------------------------------------------- stacked rows
@@ -289,7 +331,7 @@ struct BlockRowTask {
 // rows pass: R_sc S_b^*, then |G_b|_F = |R_tc S_b R_sc^*|_F, rows scaled by 1/|G_b|.
 // cols pass: R_tc S_b / |G_b|.
 template <class T>
-__global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows_pass,
+__global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows_pass,
                                const int32_t* __restrict__ adm_t, const int32_t* __restrict__ adm_s,
                                const int32_t* __restrict__ adm_c, const int32_t* __restrict__ tc_level,
                                const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
@@ -298,21 +340,18 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
                                const int32_t* __restrict__ rrows, double* bnorm, cx<T>* stack,
                                cx<T>* Kst, unsigned* err) {
     extern __shared__ unsigned char smraw[];
-    T* D = reinterpret_cast<T*>(smraw);
-    T* P = D + 3 * m * m;
     __shared__ T red[32];
     const BlockRowTask tk = tasks[blockIdx.x];
     const int k = m * m * m;
     const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
     const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
-    load_sgen_tables<T>(t, s, cd, nodes, m, D, P);
-    SGen<T> S{D, P, m, (T)kappa};
+    const SGen<T> S = load_sgen_tables<T>(t, s, cd, nodes, m, kappa, smraw);
     const int ro = rrows[tk.other];
     const cx<T>* Ro = R + roff[tk.other];
     cx<T>* out = stack + tk.dst;
     if (rows_pass) {
         // out[i][nu] = sum_mu R_s[i][mu] conj(S[nu][mu])
-        cta_gemm<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+        cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
                     [&](int mu, int nu) { return conj(S(nu, mu)); },
                     [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
         __syncthreads();
@@ -322,7 +361,7 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
         cx<T>* Kb = Kst + tk.koff;
         T acc = 0;
         T* accp = &acc;
-        cta_gemm<T>(rt, ro, k, Dense<T>{Rt, k, false, false}, Dense<T>{out, k, true, true},
+        cta_gemm_fit<T>(rt, ro, k, Dense<T>{Rt, k, false, false}, Dense<T>{out, k, true, true},
                     [=](int i, int j, cx<T> v) {
                         *accp += abs2(v);
                         Kb[(int64_t)i * ro + j] = v;
@@ -350,7 +389,7 @@ __global__ void k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows
     } else {
         const T sc_ = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
         // out[i][nu] = sum_mu R_t[i][mu] S[mu][nu] / |G_b|
-        cta_gemm<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+        cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
                     [&](int mu, int nu) { return S(mu, nu); },
                     [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = sc_ * v; });
     }
@@ -539,11 +578,11 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
     const int n = tk.rows, rz = tk.rz;
     const cx<T>* Zt = Z + tk.z;
     // A = V Z^*  (n x rz), working precision (a perturbation of A at the square-root level)
-    cta_gemm<T>(n, rz, k, V, [&](int nu, int j) { return conj(Zt[(int64_t)j * k + nu]); },
+    cta_gemm_fit<T>(n, rz, k, V, [&](int nu, int j) { return conj(Zt[(int64_t)j * k + nu]); },
                 [&](int i, int j, cx<T> v) { Ascr[(int64_t)i * rz + j] = v; });
     __syncthreads();
     // M = A A^*  (n x n), FP64: its eigenvalues are the squared singular values
-    cta_gemm<double>(n, n, rz, DenseCvt<double, T>{Ascr, rz, false, false}, DenseCvt<double, T>{Ascr, rz, true, true},
+    cta_gemm_fit<double>(n, n, rz, DenseCvt<double, T>{Ascr, rz, false, false}, DenseCvt<double, T>{Ascr, rz, true, true},
                      [&](int i, int j, cx<double> v) { M[(int64_t)i * n + j] = v; });
     __syncthreads();
     eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err);
@@ -575,7 +614,7 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
         Q[tk.q + (int64_t)i * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
     }
     // C = Q^* V  (kt x k)
-    cta_gemm<T>(kt, k, n,
+    cta_gemm_fit<T>(kt, k, n,
                 [&](int r, int i) {
                     const cx<double> u = U[(int64_t)i * n + s_order[r]];
                     return cx<T>{T(u.x), T(-u.y)};
@@ -619,7 +658,7 @@ __global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, const cx<
     const int n = tk.n, rt = tk.rt;
     EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.scr);
     const cx<T>* Vt = V + tk.v;
-    cta_gemm<double>(n, n, k, DenseCvt<double, T>{Vt, k, false, false}, DenseCvt<double, T>{Vt, k, true, true},
+    cta_gemm_fit<double>(n, n, k, DenseCvt<double, T>{Vt, k, false, false}, DenseCvt<double, T>{Vt, k, true, true},
                      [&](int i, int j, cx<double> v) { e.M[(int64_t)i * n + j] = v; });
     __syncthreads();
     eig_desc<T>(n, e.M, e.U, e.rot, red, e.lam, e.order, err);
@@ -628,7 +667,7 @@ __global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, const cx<
         const cx<double> u = e.U[(int64_t)i * n + e.order[j]];
         P[tk.p + idx] = cx<T>{T(u.x), T(u.y)};
     }
-    cta_gemm<T>(rt, k, n,
+    cta_gemm_fit<T>(rt, k, n,
                 [&](int j, int i) {
                     const cx<double> u = e.U[(int64_t)i * n + e.order[j]];
                     return cx<T>{T(u.x), T(-u.y)};
@@ -658,7 +697,7 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
     EigSpace e = eig_space(rt, smem_n, smraw, gscr + tk.scr);
     const cx<T>* Zt = Z + tk.z;
     // M' = Z'^* Z'  (rt x rt)
-    cta_gemm<double>(rt, rt, rz,
+    cta_gemm_fit<double>(rt, rt, rz,
                      [&](int i, int j) {
                          cx<T> z = Zt[(int64_t)j * rt + i];
                          return cx<double>{double(z.x), -double(z.y)};
@@ -695,14 +734,14 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
         Up[tk.up + (int64_t)j * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
     }
     // Q = P U'[:, :kt]  (n x kt)
-    cta_gemm<T>(n, kt, rt, Dense<T>{P + tk.p, rt, false, false},
+    cta_gemm_fit<T>(n, kt, rt, Dense<T>{P + tk.p, rt, false, false},
                 [&](int j, int r) {
                     const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
                     return cx<T>{T(u.x), T(u.y)};
                 },
                 [&](int i, int r, cx<T> v) { Q[tk.q + (int64_t)i * tk.qld + r] = v; });
     // C = U'[:, :kt]^* R  (kt x k)
-    cta_gemm<T>(kt, k, rt,
+    cta_gemm_fit<T>(kt, k, rt,
                 [&](int r, int j) {
                     const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
                     return cx<T>{T(u.x), T(-u.y)};
@@ -769,7 +808,7 @@ struct ProjTask {
 };
 
 template <class T>
-__global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
+__global__ void __launch_bounds__(256, 2) k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
                           const int32_t* __restrict__ adm_t, const int32_t* __restrict__ adm_s,
                           const int32_t* __restrict__ adm_c, const int32_t* __restrict__ tc_level,
                           const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
@@ -778,8 +817,6 @@ __global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
                           const cx<T>* __restrict__ Kst, const cx<T>* __restrict__ Upr,
                           const cx<T>* __restrict__ Upc, cx<T>* scratch, cx<T>* Stilde) {
     extern __shared__ unsigned char smraw[];
-    T* D = reinterpret_cast<T*>(smraw);
-    T* P = D + 3 * m * m;
     const int k = m * m * m;
     cx<T>* T1 = scratch + (int64_t)blockIdx.x * k * k;
     for (int64_t w = blockIdx.x; w < ntasks; w += gridDim.x) {
@@ -788,13 +825,13 @@ __global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
         if (tk.leafpair) {
             // S~ = C_t S_b C_s^* with C = U'^* R for leaves: U'_t^* (R_t S_b R_s^*) U'_s
             __syncthreads();
-            cta_gemm<T>(tk.kt, tk.rs, tk.rt, [&](int i, int j) { return conj(Upr[tk.upt + (int64_t)j * tk.ldt + i]); },
+            cta_gemm_fit<T>(tk.kt, tk.rs, tk.rt, [&](int i, int j) { return conj(Upr[tk.upt + (int64_t)j * tk.ldt + i]); },
                         Dense<T>{Kst + tk.koff, tk.rs, false, false},
                         [&](int i, int j, cx<T> v) { T1[(int64_t)i * k + j] = v; });
             __syncthreads();
             cx<T>* out = Stilde + tk.dst;
             const int ks = tk.ks;
-            cta_gemm<T>(tk.kt, ks, tk.rs, Dense<T>{T1, k, false, false}, Dense<T>{Upc + tk.ups, tk.lds, false, false},
+            cta_gemm_fit<T>(tk.kt, ks, tk.rs, Dense<T>{T1, k, false, false}, Dense<T>{Upc + tk.ups, tk.lds, false, false},
                         [&](int i, int j, cx<T> v) { out[(int64_t)i * ks + j] = v; });
             __syncthreads();
             continue;
@@ -802,17 +839,16 @@ __global__ void k_project(const ProjTask* __restrict__ tasks, int64_t ntasks,
         const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
         const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
         __syncthreads();
-        load_sgen_tables<T>(t, s, cd, nodes, m, D, P);
-        SGen<T> S{D, P, m, (T)kappa};
+        const SGen<T> S = load_sgen_tables<T>(t, s, cd, nodes, m, kappa, smraw);
         // T1 = C_t S_b  (kt x k)
-        cta_gemm<T>(tk.kt, k, k, Dense<T>{Crow + tk.crow, k, false, false},
+        cta_gemm_fit<T>(tk.kt, k, k, Dense<T>{Crow + tk.crow, k, false, false},
                     [&](int mu, int nu) { return S(mu, nu); },
                     [&](int i, int nu, cx<T> v) { T1[(int64_t)i * k + nu] = v; });
         __syncthreads();
         // S~ = T1 C_s^*  (kt x ks)
         cx<T>* out = Stilde + tk.dst;
         const int ks = tk.ks;
-        cta_gemm<T>(tk.kt, ks, k, Dense<T>{T1, k, false, false}, Dense<T>{Ccol + tk.ccol, k, true, true},
+        cta_gemm_fit<T>(tk.kt, ks, k, Dense<T>{T1, k, false, false}, Dense<T>{Ccol + tk.ccol, k, true, true},
                     [&](int i, int j, cx<T> v) { out[(int64_t)i * ks + j] = v; });
         __syncthreads();
     }
@@ -1118,7 +1154,7 @@ struct StageTimer {
 
 const char* const kKernelNames[K_COUNT] = {
     "nearfield", "leaf_basis", "transfer", "kron", "stack_blocks", "tsqr", "truncate", "project",
-    "mv_gather", "mv_forward", "mv_coupling", "mv_backward", "mv_leaf_out"};
+    "mv_gather", "mv_forward", "mv_coupling", "mv_backward", "mv_leaf_out", "tsqr_narrow", "leaf_orth"};
 
 namespace {
 // CUDA-event pairs around individual launches, summed per kernel id on collect().
@@ -1206,7 +1242,7 @@ public:
     void export_ranks(int32_t* rr, int32_t* rc, cudaStream_t s) override;
     void set_timing(bool on) override {
         timing_on_ = on;
-        for (int i = K_MV_GATHER; i < K_COUNT; ++i) {
+        for (int i = K_MV_GATHER; i <= K_MV_LEAF_OUT; ++i) {
             info.kernel_ms[i] = 0;
             info.kernel_launches[i] = 0;
         }
@@ -1543,26 +1579,35 @@ void Num<T>::nearfield(cudaStream_t s) {
 
 // ----------------------------------------------------------------------------- TSQR dispatch
 
+// One launch per column class: stacks of at most 32 or 64 columns run with that pitch,
+// so that their shared memory and R scratch are sized for the class instead of for k.
 template <class TSrc, class TQ, class TDst, int RPL>
-void launch_tsqr(const std::vector<QRTask>& tasks, int k, const cx<TSrc>* src, cx<TDst>* dst,
+void launch_tsqr(const std::vector<QRTask>& all, int k, const cx<TSrc>* src, cx<TDst>* dst,
                  DBuf<cx<TQ>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err) {
-    if (tasks.empty()) return;
-    const size_t smem = tsqr_smem_bytes<TQ, RPL>(k);
+    std::vector<QRTask> cls[3];
+    const int pitch[3] = {std::min(k, 32), std::min(k, 64), k};
+    for (const QRTask& t : all) cls[t.ncols <= pitch[0] ? 0 : t.ncols <= pitch[1] ? 1 : 2].push_back(t);
     auto kern = k_tsqr<TSrc, TQ, TDst, RPL>;
-    DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int64_t per = (int64_t)k * k;
-    const int64_t max_tasks = std::max<int64_t>(1, (int64_t(1) << 31) / (per * (int64_t)sizeof(cx<TQ>)));
-    for (size_t b0 = 0; b0 < tasks.size(); b0 += (size_t)max_tasks) {
-        size_t cnt = std::min<size_t>((size_t)max_tasks, tasks.size() - b0);
-        std::vector<QRTask> part(tasks.begin() + b0, tasks.begin() + b0 + cnt);
-        DBuf<QRTask> d;
-        upload_vec(d, part, s);
-        scratch.reserve(cnt * per);
-        ev.begin(K_TSQR, s);
-        kern<<<(unsigned)cnt, kThreads, smem, s>>>(d.p, k, src, scratch.p, dst, err);
-        ev.end(s);
-        DH2_CHECK_LAUNCH("k_tsqr");
-        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    for (int c = 0; c < 3; ++c) {
+        const std::vector<QRTask>& tasks = cls[c];
+        if (tasks.empty()) continue;
+        const int kl = pitch[c];
+        const size_t smem = tsqr_smem_bytes<TQ, RPL>(kl);
+        DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int64_t per = (int64_t)kl * kl;
+        const int64_t max_tasks = std::max<int64_t>(1, (int64_t(1) << 31) / (per * (int64_t)sizeof(cx<TQ>)));
+        for (size_t b0 = 0; b0 < tasks.size(); b0 += (size_t)max_tasks) {
+            size_t cnt = std::min<size_t>((size_t)max_tasks, tasks.size() - b0);
+            std::vector<QRTask> part(tasks.begin() + b0, tasks.begin() + b0 + cnt);
+            DBuf<QRTask> d;
+            upload_vec(d, part, s);
+            scratch.reserve(cnt * per);
+            ev.begin(c == 0 ? K_TSQR_NARROW : K_TSQR, s);
+            kern<<<(unsigned)cnt, kThreads, smem, s>>>(d.p, kl, src, scratch.p, dst, err);
+            ev.end(s);
+            DH2_CHECK_LAUNCH("k_tsqr");
+            DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        }
     }
 }
 
@@ -1571,10 +1616,10 @@ void launch_tsqr(const std::vector<QRTask>& tasks, int k, const cx<TSrc>* src, c
 template <class T, class TQ, int RPL>
 void tsqr_grouped(const std::vector<QRTask>& tasks, int k, int group, const cx<T>* src, cx<T>* dst,
                   cudaStream_t s, EventLog& ev, unsigned* err) {
-    const int32_t kQRGroup = group;
     std::vector<QRTask> direct, groups, merges;
     int64_t mel = 0;   // elements of the merge buffer used so far (group R factors, compact rows)
     for (const QRTask& t : tasks) {
+        const int32_t kQRGroup = group > 0 ? group : 1024;
         if (t.nrows <= kQRGroup) {
             direct.push_back(t);
             continue;
@@ -1638,7 +1683,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
                 OrthTask o{offV_[a], offP_[a], offR_[a], gel, rows_[a], rR_[a]};
                 if (rows_[a] > smem_n) gel += eig_global_elems(rows_[a]);
                 leafo.push_back(o);
-                work_[K_TRUNCATE] += 8.0 * rows_[a] * rows_[a] * kk + 8.0 * rR_[a] * kk * rows_[a];
+                work_[K_LEAF_ORTH] += 8.0 * rows_[a] * rows_[a] * kk + 8.0 * rR_[a] * kk * rows_[a];
             } else {
                 int32_t s0 = sons_[0][a], s1 = sons_[1][a];
                 kron.push_back(KronTask{offR_[s0], offE_[a], srow * kk, rR_[s0], 0});
@@ -1656,7 +1701,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
             const size_t smem = eig_smem_bytes(smem_n);
             auto kern = k_leaf_orth<T>;
             DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            ev_.begin(K_TRUNCATE, s);
+            ev_.begin(K_LEAF_ORTH, s);
             kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, V_.p, gscr.p, smem_n, P_.p, R_.p, err_.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_leaf_orth");
@@ -1741,13 +1786,13 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                     srow += rZ_[pass][ap];
                 }
                 qtasks.push_back(QRTask{r0 * kk, offZ_[pass][a], (int32_t)(srow - r0), rZ_[pass][a], zc, kk});
-                work_[K_TSQR] += 8.0 * (srow - r0) * zc * zc;
+                work_[zc <= 32 ? K_TSQR_NARROW : K_TSQR] += 8.0 * (srow - r0) * zc * zc;
             }
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             if (!btasks.empty()) {
                 DBuf<BlockRowTask> d;
                 upload_vec(d, btasks, s);
-                size_t smem = 2 * 3 * (size_t)m_ * m_ * sizeof(T);
+                const size_t smem = sgen_smem_bytes<T>(m_);
                 ev_.begin(K_STACK_BLOCKS, s);
                 k_stack_blocks<T><<<(unsigned)btasks.size(), kThreads, smem, s>>>(
                     d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p, st_.dir_off_d.p,
@@ -1976,7 +2021,7 @@ void Num<T>::project(cudaStream_t s) {
         Crow = reinterpret_cast<const cx<T>*>(Cd_[0].p);
         Ccol = reinterpret_cast<const cx<T>*>(Cd_[1].p);
     }
-    size_t smem = 2 * 3 * (size_t)m_ * m_ * sizeof(T);
+    const size_t smem = sgen_smem_bytes<T>(m_);
     ev_.begin(K_PROJECT, s);
     k_project<T><<<(unsigned)grid, kThreads, smem, s>>>(d.p, nb, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
                                                         tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
@@ -2187,6 +2232,8 @@ void Num<T>::build(cudaStream_t s) {
     info.kernel_work_kind[K_STACK_BLOCKS] = w32;
     info.kernel_work_kind[K_TSQR] = wqr;
     info.kernel_work_kind[K_TRUNCATE] = W_FLOP64;
+    info.kernel_work_kind[K_LEAF_ORTH] = W_FLOP64;
+    info.kernel_work_kind[K_TSQR_NARROW] = info.kernel_work_kind[K_TSQR];
     info.kernel_work_kind[K_PROJECT] = w32;
     // matvec leaf kernel: nearfield panels + leaf row bases streamed once, x and y once
     int64_t qleaf = 0;

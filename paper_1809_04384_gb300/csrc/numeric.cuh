@@ -35,7 +35,7 @@ struct BuildParams {
 
 enum KernelId {
     K_NEARFIELD = 0, K_LEAF_BASIS, K_TRANSFER, K_KRON, K_STACK_BLOCKS, K_TSQR, K_TRUNCATE, K_PROJECT,
-    K_MV_GATHER, K_MV_FORWARD, K_MV_COUPLING, K_MV_BACKWARD, K_MV_LEAF_OUT, K_COUNT
+    K_MV_GATHER, K_MV_FORWARD, K_MV_COUPLING, K_MV_BACKWARD, K_MV_LEAF_OUT, K_TSQR_NARROW, K_LEAF_ORTH, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
