@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form")
     ap.add_argument("--error-rows", type=int, default=256)
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched build")
+    ap.add_argument("--batch-meshes", type=int, default=64)
     return ap.parse_args()
 
 
@@ -245,6 +247,82 @@ def sampled_dense_error(mat, torch, v, f, cfg, x, rows_count, seed):
     return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
 
 
+BATCH_SEED = 1809_0003
+
+
+def batch_measure(pkg, torch, count, stream):
+    """The batched workload: `count` spheres/ellipsoids of 1280-20480 triangles
+    (synth.batch_meshes), kappa U[4, 16], leaf 32, eta1 10, eta2 1, m 5, eps 1e-4.
+    Builds are blocking host calls that fan out over several streams, so they are
+    timed with the host clock around the call (trees included, built beforehand
+    for the build-only figures); the products with CUDA events on `stream`, which
+    joins the internal streams."""
+    import synth
+
+    meshes = synth.batch_meshes(count, BATCH_SEED)
+    m, eta2, eta1, eps, leaf = 5, 1.0, 10.0, 1e-4, 32
+    kappas = [k for _, _, k in meshes]
+    ntri = int(sum(len(f) for _, f, _ in meshes))
+    trees = [pkg.Tree(v, f, leaf_max=leaf) for v, f, _ in meshes]
+
+    def batch_build(nstreams):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mats = pkg.build_batch(trees, kappas, m, eta2, eps, eta1=eta1, nstreams=nstreams)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0, mats
+
+    _, warm = batch_build(8)             # warm-up: kernels loaded, pool sized
+    for mt in warm:
+        mt.close()
+    t1, mats1 = batch_build(1)
+    for mt in mats1:
+        mt.close()
+    t8, mats = batch_build(8)
+    xs = [torch.from_numpy(synth.random_vector(len(f), BATCH_SEED + i)).to(torch.complex64).cuda()
+          for i, (_, f, _) in enumerate(meshes)]
+    ys = [torch.empty_like(x) for x in xs]
+
+    def products(batched):
+        if batched:
+            pkg.matvec_batch(mats, xs, ys, stream)
+        else:
+            for mt, x, y in zip(mats, xs, ys):
+                mt.matvec(x, y, stream)
+
+    def mv_ms(batched, reps=5):
+        for _ in range(2):
+            products(batched)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            products(batched)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    mv_batch, mv_serial = mv_ms(True), mv_ms(False)
+    mv_bytes = int(sum(mt.get_info().matvec_bytes for mt in mats))
+    # end to end: host meshes in, trees + batched build
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    trees2 = [pkg.Tree(v, f, leaf_max=leaf) for v, f, _ in meshes]
+    mats2 = pkg.build_batch(trees2, kappas, m, eta2, eps, eta1=eta1, nstreams=8)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    for obj in mats + mats2 + trees + trees2:
+        obj.close()
+    return {"workload": f"batch{count}: spheres/ellipsoids (icosphere L3-L5, semi-axes U[0.5,2]^3 for half), "
+                        f"kappa U[4,16], seed {BATCH_SEED}, leaf {leaf}, eta1 {eta1}, eta2 {eta2}, m {m}, eps {eps}",
+            "meshes": count, "triangles": ntri,
+            "build_s_8_streams": t8, "build_s_1_stream": t1, "build_speedup_streams": t1 / t8,
+            "build_s_e2e_with_trees": t_e2e,
+            "matvec_ms_batched": mv_batch, "matvec_ms_serial": mv_serial,
+            "matvec_gbs_batched": mv_bytes / (mv_batch * 1e-3) / 1e9, "timing": "build: host clock around the "
+            "blocking call; matvec: CUDA events on the joining stream"}
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -373,6 +451,10 @@ def main():
         for m_ in mats64:
             m_.close()
 
+    batch = None
+    if not args.no_batch:
+        batch = batch_measure(pkg, torch, args.batch_meshes, stream)
+
     baseline = None
     if rank == 0 and not args.no_baseline:
         try:
@@ -402,6 +484,7 @@ def main():
             "roofline": roof,
             "matvec_roofline": mv_roof,
             "plain_fp64": fp64,
+            "batch": batch,
             "cpu_baseline": baseline,
             "e2e": {"value": float(np.mean(e2e)), "unit": "s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},

@@ -16,6 +16,9 @@
  *     reference to nothing but its own copies: the tree may be freed first.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Device pointers must be valid on the current CUDA device.
+ *   - Device memory of the library comes from the device's default memory
+ *     pool, allocated and freed in stream order on the call's stream; memory
+ *     freed inside a build is kept in the pool until the build ends.
  *   - Invalid arguments are rejected with DH2_EINVAL before any GPU work.
  *   - Complex vectors are interleaved (re, im) pairs: DH2_C64 = 2 x float,
  *     DH2_C128 = 2 x double.
@@ -58,8 +61,8 @@ typedef struct {
                                DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted */
     int32_t qr_fp64;        /* DH2_MIXED only: 1 = run the weight QRs (R, Z-hat) in FP64 */
     int32_t qr_group_rows;  /* stacks taller than this are factored in row groups whose R
-                               factors are merged by a second QR (0 = 1024 rows, 8192 for
-                               stacks of at most 32 columns) */
+                               factors are stacked and factored again (0 = 1024 rows; never
+                               below twice the stack's columns) */
     int64_t workspace_bytes;/* cap on the stacked weight workspace per level (0 = 16 GiB) */
 } dh2_options;
 
@@ -129,6 +132,25 @@ dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, dou
                          const dh2_options* opt, void* stream, dh2_matrix* out);
 
 /*
+ * Batched build (the paper has no counterpart; it builds one matrix at a time):
+ * out[i] = dh2_build_dh2(trees[i], kappas[i], m, eta, eps, opt) for i < count.
+ * The builds run concurrently: `nstreams` host worker threads (0 = min(count, 8)),
+ * each with its own non-blocking CUDA stream on the calling thread's current
+ * device, take the meshes largest first from a shared queue, so the kernels of
+ * small meshes fill the SMs that the small launches of other meshes leave idle.
+ * Each matrix is identical to the one dh2_build_dh2 gives for the same arguments
+ * (up to floating-point summation order).  Blocks until all are built.  trees,
+ * kappas, out: host arrays of `count` entries; the trees stay owned by the caller.
+ * Errors: every argument is checked first (as for dh2_build_dh2, plus count < 0,
+ * nstreams < 0, NULL arrays: DH2_EINVAL before any GPU work).  If any build fails,
+ * every matrix of the batch is freed, out[] is all NULL and the first failure's
+ * status is returned.
+ */
+dh2_status dh2_build_dh2_batch(const dh2_tree* trees, int32_t count, const double* kappas, int32_t m,
+                               double eta, double eps, const dh2_options* opt, int32_t nstreams,
+                               dh2_matrix* out);
+
+/*
  * y = G~ x with the recompressed DH^2 matrix: forward transform with the
  * column basis, couplings, backward transform with the row basis, nearfield
  * (derived from Eq. nested and Eq. vsw).  x, y: DEVICE buffers of n complex
@@ -138,6 +160,19 @@ dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, dou
  * different streams race.  Errors: DH2_EINVAL (bad dtype, NULL), DH2_ECUDA.
  */
 dh2_status dh2_matvec(dh2_matrix mat, const void* x, void* y, int32_t dtype, void* stream);
+
+/*
+ * Batched product (no counterpart in the paper): y[i] = G~_i x[i] for count
+ * distinct matrices, with x[i], y[i] device buffers as in dh2_matvec.  The
+ * products are issued on up to eight internal non-blocking streams that wait
+ * for `stream` and that `stream` then waits for, so they overlap on the GPU and
+ * the call is asynchronous on `stream` like dh2_matvec.  mats, x, y: host arrays
+ * of `count` entries.  Errors: DH2_EINVAL for NULL entries, aliased x[i]/y[i],
+ * a bad dtype or a matrix that appears twice (its work buffers would be shared);
+ * DH2_ECUDA.
+ */
+dh2_status dh2_matvec_batch(const dh2_matrix* mats, int32_t count, const void* const* x, void* const* y,
+                            int32_t dtype, void* stream);
 
 /*
  * Allocation-free variant of dh2_matvec (the paper has no counterpart; this is
@@ -233,6 +268,9 @@ const char* dh2_stage_name(int32_t i);
 /* Name of kernel i for dh2_matrix_info.kernel_ms (NULL past the end). */
 const char* dh2_kernel_name(int32_t i);
 
+/* Release a handle (NULL is ignored).  Both wait for the device first, since
+ * work queued on any stream may still read the object, then return the freed
+ * memory of the library's pool to the device. */
 void dh2_free_tree(dh2_tree tree);
 void dh2_free_matrix(dh2_matrix mat);
 const char* dh2_last_error(void);

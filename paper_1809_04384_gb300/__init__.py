@@ -65,7 +65,10 @@ _SIGS = {
     "dh2_build_tree": (C.c_int, [_P, C.c_int64, _P, C.c_int64, C.POINTER(dh2_options), _P, C.POINTER(_P)]),
     "dh2_build_dh2": (C.c_int, [_P, C.c_double, C.c_int32, C.c_double, C.c_double, C.POINTER(dh2_options), _P,
                                 C.POINTER(_P)]),
+    "dh2_build_dh2_batch": (C.c_int, [_P, C.c_int32, _P, C.c_int32, C.c_double, C.c_double,
+                                      C.POINTER(dh2_options), C.c_int32, _P]),
     "dh2_matvec": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
+    "dh2_matvec_batch": (C.c_int, [_P, C.c_int32, _P, _P, C.c_int32, _P]),
     "dh2_matvec_noalloc": (C.c_int, [_P, _P, _P, C.c_int32, _P]),
     "dh2_matvec_host": (C.c_int, [_P, _P, _P, _P]),
     "dh2_set_timing": (C.c_int, [_P, C.c_int32]),
@@ -146,6 +149,49 @@ def dh2_build_dh2(tree, kappa, m, eta, eps, opts=None, stream=None):
     _check(lib().dh2_build_dh2(tree, float(kappa), int(m), float(eta), float(eps), C.byref(opts or options()),
                                _stream(stream), C.byref(h)))
     return h
+
+
+def dh2_build_dh2_batch(trees, kappas, m, eta, eps, opts=None, nstreams=0):
+    """Concurrent builds of len(trees) matrices; returns their handles in order."""
+    count = len(trees)
+    th = (C.c_void_p * max(count, 1))(*[t for t in trees])
+    ka = np.ascontiguousarray(kappas, dtype=np.float64)
+    if len(ka) != count:
+        raise ValueError("one kappa per tree")
+    out = (C.c_void_p * max(count, 1))()
+    _check(lib().dh2_build_dh2_batch(C.cast(th, C.c_void_p), count, _ptr(ka), int(m), float(eta), float(eps),
+                                     C.byref(opts or options()), int(nstreams), C.cast(out, C.c_void_p)))
+    return [C.c_void_p(out[i]) for i in range(count)]
+
+
+def _vec_dtype(xs, ys):
+    import torch
+    dts = {x.dtype for x in xs} | {y.dtype for y in ys}
+    if len(dts) != 1 or next(iter(dts)) not in (torch.complex64, torch.complex128):
+        raise TypeError("all vectors must share one dtype, complex64 or complex128")
+    for v in list(xs) + list(ys):
+        if not (v.is_cuda and v.is_contiguous()):
+            raise TypeError("vectors must be contiguous CUDA tensors")
+    return DH2_C64 if next(iter(dts)) == torch.complex64 else DH2_C128
+
+
+def dh2_matvec_batch(mats, xs, ys, stream=None):
+    """ys[i] = G~_i xs[i] for distinct matrices (CUDA tensors, one dtype)."""
+    import torch
+    count = len(mats)
+    if len(xs) != count or len(ys) != count:
+        raise ValueError("one x and one y per matrix")
+    if count == 0:
+        return ys
+    dtype = _vec_dtype(xs, ys)
+    if stream is None:
+        stream = torch.cuda.current_stream(xs[0].device)
+    mh = (C.c_void_p * count)(*[m for m in mats])
+    xp = (C.c_void_p * count)(*[x.data_ptr() for x in xs])
+    yp = (C.c_void_p * count)(*[y.data_ptr() for y in ys])
+    _check(lib().dh2_matvec_batch(C.cast(mh, C.c_void_p), count, C.cast(xp, C.c_void_p), C.cast(yp, C.c_void_p),
+                                  dtype, _stream(stream)))
+    return ys
 
 
 def dh2_matvec(mat, x, y, stream=None):
@@ -241,6 +287,16 @@ class Matrix:
         self.info = self.get_info()
         self.n = self.info.n
 
+    @classmethod
+    def from_handle(cls, handle, precision):
+        """Takes ownership of a dh2_matrix handle (e.g. one of dh2_build_dh2_batch)."""
+        self = cls.__new__(cls)
+        self.precision = precision
+        self.handle = handle
+        self.info = self.get_info()
+        self.n = self.info.n
+        return self
+
     def get_info(self):
         info = dh2_matrix_info()
         _check(lib().dh2_matrix_get_info(self.handle, C.byref(info)))
@@ -334,3 +390,19 @@ class Matrix:
             self.close()
         except Exception:
             pass
+
+
+def build_batch(trees, kappas, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
+                nstreams=0):
+    """Concurrent builds (dh2_build_dh2_batch) wrapped as Matrix objects, in order."""
+    opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule)
+    handles = dh2_build_dh2_batch([t.handle for t in trees], kappas, m, eta, eps, opts, nstreams)
+    return [Matrix.from_handle(h, precision) for h in handles]
+
+
+def matvec_batch(mats, xs, ys=None, stream=None):
+    """Overlapped products ys[i] = mats[i] xs[i] (dh2_matvec_batch)."""
+    import torch
+    if ys is None:
+        ys = [torch.empty_like(x) for x in xs]
+    return dh2_matvec_batch([m.handle for m in mats], xs, ys, stream)

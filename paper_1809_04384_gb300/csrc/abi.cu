@@ -1,8 +1,13 @@
 // extern "C" entry points of libdh2 (declared in include/dh2.h).
+#include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <numeric>
 #include <string>
+#include <thread>
 
 #include "numeric.cuh"
 #include "structure.cuh"
@@ -78,12 +83,126 @@ void clone_tree(Tree& dst, const Tree& src, cudaStream_t s) {
     copy_dbuf(dst.x7, src.x7, s);
 }
 
+void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double eps, const dh2_options& o,
+                      const char* fn) {
+    const std::string f(fn);
+    if (tree == nullptr) throw Error{DH2_EINVAL, f + ": tree is NULL"};
+    if (tree->tr.point_mode) throw Error{DH2_EINVAL, f + ": a point-mode tree has no Galerkin elements"};
+    if (!(std::isfinite(kappa) && kappa >= 0.0)) throw Error{DH2_EINVAL, f + ": kappa must be >= 0"};
+    if (!(m >= 1 && m <= 8)) throw Error{DH2_EINVAL, f + ": m must be in [1, 8]"};
+    if (!(std::isfinite(eta) && eta > 0.0)) throw Error{DH2_EINVAL, f + ": eta must be > 0"};
+    if (!(std::isfinite(eps) && eps > 0.0)) throw Error{DH2_EINVAL, f + ": eps must be > 0"};
+    if (!(std::isfinite(o.eta1) && o.eta1 > 0.0)) throw Error{DH2_EINVAL, f + ": eta1 must be > 0"};
+    if (!(o.precision == DH2_FP64 || o.precision == DH2_MIXED)) throw Error{DH2_EINVAL, f + ": bad precision"};
+    if (!(o.rank_rule == DH2_RANK_BLOCKREL || o.rank_rule == DH2_RANK_GLOBAL))
+        throw Error{DH2_EINVAL, f + ": bad rank rule"};
+    if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
+}
+
+// The whole build of one matrix on stream s (arguments already checked); blocks until done.
+dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, double eps, const dh2_options& o,
+                        cudaStream_t s) {
+    auto mat = std::make_unique<dh2_matrix_s>();
+    cudaEvent_t e0, e1;
+    DH2_CHECK_CUDA(cudaEventCreate(&e0));
+    DH2_CHECK_CUDA(cudaEventCreate(&e1));
+    DH2_CHECK_CUDA(cudaEventRecord(e0, s));
+    clone_tree(mat->tr, tree->tr, s);
+    build_structure(mat->tr, mat->st, kappa, o.eta1, eta, s);
+    DH2_CHECK_CUDA(cudaEventRecord(e1, s));
+    download_structure(mat->tr, mat->st, mat->hs, s);
+    float ms = 0;
+    DH2_CHECK_CUDA(cudaEventSynchronize(e1));
+    DH2_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    mat->structure_ms = ms;
+    mat->depth = mat->tr.depth;
+    mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
+                          o.workspace_bytes};
+    mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
+    mat->num->build(s);
+    mat->num->info.stage_ms[ST_STRUCTURE] += ms;
+    DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    return mat.release();
+}
+
+// A few non-blocking streams per device for the batched products (created on first use,
+// kept for the life of the process).
+constexpr int kBatchStreams = 8;
+cudaStream_t batch_stream(int i) {
+    static std::mutex mu;
+    static std::vector<std::vector<cudaStream_t>> per_dev;
+    int dev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
+    auto& v = per_dev[dev];
+    if (v.empty()) {
+        v.resize(kBatchStreams);
+        for (auto& st : v) DH2_CHECK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    }
+    return v[i % kBatchStreams];
+}
+
 const char* kStageNames[] = {"structure",      "nearfield",          "analytic",        "basis_weights",
                              "total_weights_row", "total_weights_col", "truncate_row",   "truncate_col",
                              "project",        "matvec_plan"};
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+// ----------------------------------------------------------------------------- device memory
+
+namespace {
+std::mutex g_pool_mu;
+bool g_pool_ready[64] = {};
+}  // namespace
+
+void* dev_alloc(size_t bytes) {
+    int dev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&dev));
+    thread_local uint64_t seen = 0;   // devices (< 64) whose pool is known to be configured
+    if (dev >= 64 || !((seen >> dev) & 1)) {
+        std::lock_guard<std::mutex> lk(g_pool_mu);
+        if (dev >= 64 || !g_pool_ready[dev]) {
+            // keep freed memory in the pool between the many short-lived buffers of a build
+            cudaMemPool_t pool;
+            DH2_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+            uint64_t keep = UINT64_MAX;
+            DH2_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+            if (dev < 64) g_pool_ready[dev] = true;
+        }
+        if (dev < 64) seen |= uint64_t(1) << dev;
+    }
+    void* p = nullptr;
+    DH2_CHECK_CUDA(cudaMallocAsync(&p, bytes, alloc_stream()));
+    return p;
+}
+
+void ensure_smem(const void* fn, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> cur;
+    int dev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& c = cur[{dev, fn}];
+    if (bytes > c) {
+        DH2_CHECK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        c = bytes;
+    }
+}
+
+void dev_free(void* p) {
+    if (p) cudaFreeAsync(p, alloc_stream());
+}
+
+void trim_pool() {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
+        cudaMemPoolTrimTo(pool, 0);
+}
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -144,6 +263,7 @@ dh2_status dh2_build_tree(const double* vertices, int64_t nv, const int32_t* tri
             for (int64_t i = 0; i < 3 * nt; ++i)
                 DH2_REQUIRE(triangles[i] >= 0 && triangles[i] < nv, "dh2_build_tree: vertex id out of range");
         cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
         auto h = std::make_unique<dh2_tree_s>();
         Tree& tr = h->tr;
         tr.n = n;
@@ -168,43 +288,88 @@ dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, dou
     return guarded([&] {
         DH2_REQUIRE(out != nullptr, "dh2_build_dh2: out is NULL");
         *out = nullptr;
-        DH2_REQUIRE(tree != nullptr, "dh2_build_dh2: tree is NULL");
-        DH2_REQUIRE(!tree->tr.point_mode, "dh2_build_dh2: a point-mode tree has no Galerkin elements");
-        DH2_REQUIRE(std::isfinite(kappa) && kappa >= 0.0, "dh2_build_dh2: kappa must be >= 0");
-        DH2_REQUIRE(m >= 1 && m <= 8, "dh2_build_dh2: m must be in [1, 8]");
-        DH2_REQUIRE(std::isfinite(eta) && eta > 0.0, "dh2_build_dh2: eta must be > 0");
-        DH2_REQUIRE(std::isfinite(eps) && eps > 0.0, "dh2_build_dh2: eps must be > 0");
         dh2_options o;
         if (opt) o = *opt; else dh2_options_default(&o);
-        DH2_REQUIRE(std::isfinite(o.eta1) && o.eta1 > 0.0, "dh2_build_dh2: eta1 must be > 0");
-        DH2_REQUIRE(o.precision == DH2_FP64 || o.precision == DH2_MIXED, "dh2_build_dh2: bad precision");
-        DH2_REQUIRE(o.rank_rule == DH2_RANK_BLOCKREL || o.rank_rule == DH2_RANK_GLOBAL,
-                    "dh2_build_dh2: bad rank rule");
+        check_build_args(tree, kappa, m, eta, eps, o, "dh2_build_dh2");
         cudaStream_t s = as_stream(stream);
-        auto mat = std::make_unique<dh2_matrix_s>();
-        cudaEvent_t e0, e1;
-        DH2_CHECK_CUDA(cudaEventCreate(&e0));
-        DH2_CHECK_CUDA(cudaEventCreate(&e1));
-        DH2_CHECK_CUDA(cudaEventRecord(e0, s));
-        clone_tree(mat->tr, tree->tr, s);
-        build_structure(mat->tr, mat->st, kappa, o.eta1, eta, s);
-        DH2_CHECK_CUDA(cudaEventRecord(e1, s));
-        download_structure(mat->tr, mat->st, mat->hs, s);
-        float ms = 0;
-        DH2_CHECK_CUDA(cudaEventSynchronize(e1));
-        DH2_CHECK_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        mat->structure_ms = ms;
-        mat->depth = mat->tr.depth;
-        DH2_REQUIRE(o.qr_group_rows >= 0, "dh2_build_dh2: qr_group_rows must be >= 0");
-        mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
-                              o.workspace_bytes};
-        mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
-        mat->num->build(s);
-        mat->num->info.stage_ms[ST_STRUCTURE] += ms;
-        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
-        *out = mat.release();
+        {
+            AllocScope scope(s);
+            *out = build_matrix(tree, kappa, m, eta, eps, o, s);
+        }
+        trim_pool();
+    });
+}
+
+dh2_status dh2_build_dh2_batch(const dh2_tree* trees, int32_t count, const double* kappas, int32_t m,
+                               double eta, double eps, const dh2_options* opt, int32_t nstreams,
+                               dh2_matrix* out) {
+    return guarded([&] {
+        DH2_REQUIRE(count >= 0, "dh2_build_dh2_batch: count must be >= 0");
+        DH2_REQUIRE(count == 0 || (trees != nullptr && kappas != nullptr && out != nullptr),
+                    "dh2_build_dh2_batch: NULL array");
+        DH2_REQUIRE(nstreams >= 0, "dh2_build_dh2_batch: nstreams must be >= 0");
+        for (int32_t i = 0; i < count; ++i) out[i] = nullptr;
+        dh2_options o;
+        if (opt) o = *opt; else dh2_options_default(&o);
+        for (int32_t i = 0; i < count; ++i) check_build_args(trees[i], kappas[i], m, eta, eps, o, "dh2_build_dh2_batch");
+        if (count == 0) return;
+        // largest meshes first, so that the small ones fill in at the end
+        std::vector<int32_t> order(count);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return trees[a]->tr.n > trees[b]->tr.n; });
+        const int nw = std::min<int>(count, nstreams > 0 ? nstreams : 8);
+        int dev = 0;
+        DH2_CHECK_CUDA(cudaGetDevice(&dev));
+        std::atomic<int32_t> next{0};
+        std::atomic<bool> failed{false};
+        std::mutex mu;
+        dh2_status first = DH2_OK;
+        std::string first_msg;
+        auto fail = [&](dh2_status st, const std::string& msg) {
+            std::lock_guard<std::mutex> lk(mu);
+            if (first == DH2_OK) {
+                first = st;
+                first_msg = msg;
+            }
+            failed = true;
+        };
+        auto worker = [&] {
+            cudaStream_t s = nullptr;
+            try {
+                DH2_CHECK_CUDA(cudaSetDevice(dev));
+                DH2_CHECK_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+                AllocScope scope(s);
+                for (;;) {
+                    const int32_t j = next.fetch_add(1);
+                    if (j >= count || failed) break;
+                    const int32_t i = order[j];
+                    out[i] = build_matrix(trees[i], kappas[i], m, eta, eps, o, s);
+                }
+            } catch (const Error& e) {
+                fail(e.status, e.msg);
+            } catch (const std::bad_alloc&) {
+                fail(DH2_ENOMEM, "host allocation failed");
+            } catch (const std::exception& e) {
+                fail(DH2_ECUDA, e.what());
+            }
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        };
+        std::vector<std::thread> pool;
+        for (int w = 0; w < nw; ++w) pool.emplace_back(worker);
+        for (auto& t : pool) t.join();
+        if (failed) {
+            cudaDeviceSynchronize();
+            for (int32_t i = 0; i < count; ++i) {
+                delete out[i];
+                out[i] = nullptr;
+            }
+        }
+        trim_pool();
+        if (failed) throw Error{first, "dh2_build_dh2_batch: " + first_msg};
     });
 }
 
@@ -228,11 +393,47 @@ dh2_status dh2_matvec_noalloc(dh2_matrix mat, const void* x, void* y, int32_t dt
     });
 }
 
+dh2_status dh2_matvec_batch(const dh2_matrix* mats, int32_t count, const void* const* x, void* const* y,
+                            int32_t dtype, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(count >= 0, "dh2_matvec_batch: count must be >= 0");
+        DH2_REQUIRE(count == 0 || (mats != nullptr && x != nullptr && y != nullptr), "dh2_matvec_batch: NULL array");
+        DH2_REQUIRE(dtype == DH2_C64 || dtype == DH2_C128, "dh2_matvec_batch: dtype must be DH2_C64 or DH2_C128");
+        for (int32_t i = 0; i < count; ++i) {
+            DH2_REQUIRE(mats[i] != nullptr && mats[i]->num, "dh2_matvec_batch: matrix is NULL");
+            DH2_REQUIRE(x[i] != nullptr && y[i] != nullptr, "dh2_matvec_batch: NULL vector");
+            DH2_REQUIRE(x[i] != y[i], "dh2_matvec_batch: x and y must not alias");
+        }
+        std::vector<dh2_matrix> sorted(mats, mats + count);
+        std::sort(sorted.begin(), sorted.end());
+        DH2_REQUIRE(std::adjacent_find(sorted.begin(), sorted.end()) == sorted.end(),
+                    "dh2_matvec_batch: a matrix appears twice (its work buffers would be shared)");
+        if (count == 0) return;
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        const int ns = std::min<int>(count, kBatchStreams);
+        cudaEvent_t fork;
+        DH2_CHECK_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        DH2_CHECK_CUDA(cudaEventRecord(fork, s));
+        for (int i = 0; i < ns; ++i) DH2_CHECK_CUDA(cudaStreamWaitEvent(batch_stream(i), fork, 0));
+        cudaEventDestroy(fork);
+        for (int32_t i = 0; i < count; ++i) mats[i]->num->matvec(x[i], y[i], dtype, batch_stream(i % ns));
+        for (int i = 0; i < ns; ++i) {
+            cudaEvent_t join;
+            DH2_CHECK_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+            DH2_CHECK_CUDA(cudaEventRecord(join, batch_stream(i)));
+            DH2_CHECK_CUDA(cudaStreamWaitEvent(s, join, 0));
+            cudaEventDestroy(join);
+        }
+    });
+}
+
 dh2_status dh2_matvec_host(dh2_matrix mat, const double* x_host, double* y_host, void* stream) {
     return guarded([&] {
         DH2_REQUIRE(mat != nullptr && mat->num, "dh2_matvec_host: matrix is NULL");
         DH2_REQUIRE(x_host != nullptr && y_host != nullptr, "dh2_matvec_host: NULL vector");
         cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
         const int64_t n = mat->tr.n;
         DBuf<double> xd(2 * n), yd(2 * n);
         DH2_CHECK_CUDA(cudaMemcpyAsync(xd.p, x_host, 2 * n * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -371,7 +572,19 @@ dh2_status dh2_export_ranks(dh2_matrix mat, int32_t* rank_row, int32_t* rank_col
     });
 }
 
-void dh2_free_tree(dh2_tree tree) { delete tree; }
-void dh2_free_matrix(dh2_matrix mat) { delete mat; }
+// Work on any stream may still read the object: wait for the device before its memory
+// goes back to the pool.
+void dh2_free_tree(dh2_tree tree) {
+    if (!tree) return;
+    cudaDeviceSynchronize();
+    delete tree;
+    trim_pool();
+}
+void dh2_free_matrix(dh2_matrix mat) {
+    if (!mat) return;
+    cudaDeviceSynchronize();
+    delete mat;
+    trim_pool();
+}
 
 }  // extern "C"

@@ -34,17 +34,47 @@ void count_launch();
 #define DH2_CHECK_LAUNCH(name)                                                        \
     do {                                                                              \
         ::dh2::count_launch();                                                        \
-        DH2_CHECK_CUDA(cudaGetLastError());                                           \
+        cudaError_t e_ = cudaGetLastError();                                          \
+        if (e_ != cudaSuccess)                                                        \
+            throw ::dh2::Error{e_ == cudaErrorMemoryAllocation ? DH2_ENOMEM : DH2_ECUDA, \
+                               std::string("launch of ") + (name) + ": " + cudaGetErrorString(e_)}; \
     } while (0)
+
+// Raises the dynamic shared memory limit of kernel `fn` on the current device to at
+// least `bytes`.  It never lowers it: the limit belongs to the kernel, not to a launch,
+// and builds running concurrently on other threads rely on the limit they set.
+void ensure_smem(const void* fn, size_t bytes);
 
 #define DH2_REQUIRE(cond, msg)                                                        \
     do {                                                                              \
         if (!(cond)) throw ::dh2::Error{DH2_EINVAL, msg};                             \
     } while (0)
 
-// ----------------------------------------------------------------------------- device buffers
+// ----------------------------------------------------------------------------- device memory
 
-// Owning device allocation (cudaMalloc); moves only.
+// Device memory comes from the device's default memory pool in stream order
+// (cudaMallocAsync / cudaFreeAsync) on the stream of the entry point that is running,
+// which every entry point sets with AllocScope for its duration (the legacy default
+// stream otherwise).  Freeing then never waits for the whole device, so builds on
+// different streams overlap.  The pool keeps freed memory for reuse until trim_pool().
+inline cudaStream_t& alloc_stream() {
+    thread_local cudaStream_t s = nullptr;
+    return s;
+}
+
+struct AllocScope {
+    cudaStream_t prev;
+    explicit AllocScope(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+    ~AllocScope() { alloc_stream() = prev; }
+    AllocScope(const AllocScope&) = delete;
+    AllocScope& operator=(const AllocScope&) = delete;
+};
+
+void* dev_alloc(size_t bytes);   // throws Error (DH2_ENOMEM / DH2_ECUDA)
+void dev_free(void* p);          // errors are ignored (used from destructors)
+void trim_pool();                // return the pool's unused memory to the device
+
+// Owning device allocation (see above); moves only.
 template <class T>
 struct DBuf {
     T* p = nullptr;
@@ -62,12 +92,12 @@ struct DBuf {
     void alloc(size_t count) {
         release();
         n = count;
-        if (count) DH2_CHECK_CUDA(cudaMalloc(&p, count * sizeof(T)));
+        if (count) p = static_cast<T*>(dev_alloc(count * sizeof(T)));
     }
     // grow-only reallocation (contents are not kept)
     void reserve(size_t count) { if (count > n) alloc(count); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) dev_free(p);
         p = nullptr;
         n = 0;
     }

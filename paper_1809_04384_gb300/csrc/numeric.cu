@@ -1593,7 +1593,7 @@ void launch_tsqr(const std::vector<QRTask>& all, int k, const cx<TSrc>* src, cx<
         if (tasks.empty()) continue;
         const int kl = pitch[c];
         const size_t smem = tsqr_smem_bytes<TQ, RPL>(kl);
-        DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        ensure_smem(reinterpret_cast<const void*>(kern), smem);
         const int64_t per = (int64_t)kl * kl;
         const int64_t max_tasks = std::max<int64_t>(1, (int64_t(1) << 31) / (per * (int64_t)sizeof(cx<TQ>)));
         for (size_t b0 = 0; b0 < tasks.size(); b0 += (size_t)max_tasks) {
@@ -1611,23 +1611,29 @@ void launch_tsqr(const std::vector<QRTask>& all, int k, const cx<TSrc>* src, cx<
     }
 }
 
-// Stacks taller than `group` rows are split into row groups: the R factors of the groups
-// (pass 1) are stacked and factored again (pass 2).  This gives every level enough CTAs.
-template <class T, class TQ, int RPL>
-void tsqr_grouped(const std::vector<QRTask>& tasks, int k, int group, const cx<T>* src, cx<T>* dst,
-                  cudaStream_t s, EventLog& ev, unsigned* err) {
+// Stacks taller than their group size are split into row groups; the R factors of the
+// groups are stacked and factored again (the R factor of a stack is the R factor of the
+// stacked R factors of its parts).  Group size: `group` if positive, else 1024 rows;
+// never below twice the column count.  (Smaller groups sized to fill every SM, and
+// further merge levels for tall merges, both measured slower at 20480 triangles: the
+// extra merges cost more than the parallelism they add.)
+template <class TS, class TQ, class TD, int RPL>
+void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>* src, cx<TD>* dst,
+               cudaStream_t s, EventLog& ev, unsigned* err) {
+    const int32_t gauto = 1024;
     std::vector<QRTask> direct, groups, merges;
     int64_t mel = 0;   // elements of the merge buffer used so far (group R factors, compact rows)
     for (const QRTask& t : tasks) {
-        const int32_t kQRGroup = group > 0 ? group : 1024;
-        if (t.nrows <= kQRGroup) {
+        int32_t g = std::max(group > 0 ? group : gauto, 2 * t.ncols);
+        g = (g + 31) / 32 * 32;
+        if (t.nrows <= g) {
             direct.push_back(t);
             continue;
         }
         const int64_t m0 = mel;
         int32_t mrows = 0;
-        for (int32_t r0 = 0; r0 < t.nrows; r0 += kQRGroup) {
-            const int32_t h = std::min(kQRGroup, t.nrows - r0);
+        for (int32_t r0 = 0; r0 < t.nrows; r0 += g) {
+            const int32_t h = std::min(g, t.nrows - r0);
             const int32_t ro = std::min(h, t.ncols);
             groups.push_back(QRTask{t.src + (int64_t)r0 * t.ld, mel, h, ro, t.ncols, t.ld});
             mel += (int64_t)ro * t.ncols;
@@ -1636,11 +1642,11 @@ void tsqr_grouped(const std::vector<QRTask>& tasks, int k, int group, const cx<T
         merges.push_back(QRTask{m0, t.dst, mrows, t.rout, t.ncols, t.ncols});
     }
     DBuf<cx<TQ>> scratch, merge;
-    launch_tsqr<T, TQ, T, RPL>(direct, k, src, dst, scratch, s, ev, err);
+    launch_tsqr<TS, TQ, TD, RPL>(direct, k, src, dst, scratch, s, ev, err);
     if (!groups.empty()) {
         merge.alloc((size_t)mel);
-        launch_tsqr<T, TQ, TQ, RPL>(groups, k, src, merge.p, scratch, s, ev, err);
-        launch_tsqr<TQ, TQ, T, RPL>(merges, k, merge.p, dst, scratch, s, ev, err);
+        launch_tsqr<TS, TQ, TQ, RPL>(groups, k, src, merge.p, scratch, s, ev, err);
+        launch_tsqr<TQ, TQ, TD, RPL>(merges, k, merge.p, dst, scratch, s, ev, err);
     }
 }
 
@@ -1652,11 +1658,11 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
     if (fp64) {
         if (tsqr_smem_bytes<double, 1>(k_) > 200 * 1024)
             throw Error{DH2_EUNSUPPORTED, "FP64 weight QR supports m <= 6"};
-        tsqr_grouped<T, double, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+        tsqr_tree<T, double, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
     } else if (tsqr_smem_bytes<float, 2>(k_) <= 100 * 1024) {
-        tsqr_grouped<T, float, 2>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+        tsqr_tree<T, float, T, 2>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
     } else {
-        tsqr_grouped<T, float, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+        tsqr_tree<T, float, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
     }
     check_err(s, where);
 }
@@ -1700,7 +1706,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
             upload_vec(d, leafo, s);
             const size_t smem = eig_smem_bytes(smem_n);
             auto kern = k_leaf_orth<T>;
-            DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_LEAF_ORTH, s);
             kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, V_.p, gscr.p, smem_n, P_.p, R_.p, err_.p);
             ev_.end(s);
@@ -1917,7 +1923,7 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
             upload_vec(d, lt, s);
             const size_t smem = eig_smem_bytes(smem_l);
             auto kern = k_trunc_leaf<T>;
-            DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_TRUNCATE, s);
             kern<<<(unsigned)lt.size(), kThreads, smem, s>>>(d.p, kk, Z_[pass].p, P_.p, R_.p, lscr.p, smem_l,
                                                               bp_.eps, bp_.rank_rule, Q_[pass].p, Cd_[pass].p, Ct,
@@ -1939,7 +1945,7 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
             upload_vec(d, tt, s);
             size_t smem = eig_smem_bytes(smem_n);
             auto kern = k_truncate<T>;
-            DH2_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_TRUNCATE, s);
             kern<<<(unsigned)tt.size(), kThreads, smem, s>>>(d.p, kk, vhat.p, Z_[pass].p, ascr.p, gscr.p, smem_n,
                                                               bp_.eps, bp_.rank_rule, Q_[pass].p, Cd_[pass].p, Ct,

@@ -13,6 +13,8 @@
 //   dist      = the same norm of the per-axis gaps max(max(lo_t-hi_s, lo_s-hi_t), 0)
 //   m_l       = ceil(((sqrt2 * kappa) * d_l) / eta1)
 //   nearest   = argmin ((a0-b0)^2 + (a1-b1)^2) + (a2-b2)^2, ties to the lowest index
+#include <mutex>
+
 #include "structure.cuh"
 
 namespace dh2 {
@@ -650,8 +652,14 @@ void build_tree_gpu(Tree& tr, cudaStream_t s) {
 }
 
 void prepare_quadrature(Tree& tr, cudaStream_t s) {
-    static bool init = false;
-    if (!init) {
+    // the rules' barycentric coordinates go to constant memory once per device
+    static std::mutex mu;
+    static bool ready[64] = {};
+    int dev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&dev));
+    DH2_REQUIRE(dev < 64, "prepare_quadrature: device ordinal >= 64");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ready[dev]) {
         const double b3[3][3] = {{2.0 / 3.0, 1.0 / 6.0, 1.0 / 6.0},
                                  {1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0},
                                  {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0}};
@@ -662,7 +670,7 @@ void prepare_quadrature(Tree& tr, cudaStream_t s) {
                                  {a1, a1, b1}, {b2, a2, a2}, {a2, b2, a2}, {a2, a2, b2}};
         DH2_CHECK_CUDA(cudaMemcpyToSymbol(c_bary3, b3, sizeof(b3)));
         DH2_CHECK_CUDA(cudaMemcpyToSymbol(c_bary7, b7, sizeof(b7)));
-        init = true;
+        ready[dev] = true;
     }
     const int64_t n = tr.n;
     tr.area.alloc(n);

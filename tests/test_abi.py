@@ -65,3 +65,30 @@ def test_invalid_arguments_rejected_before_gpu_work(libpath):
     with pytest.raises(pkg.DH2Error) as e:
         pkg.dh2_build_dh2(None, 1.0, 4, 1.0, 1e-4)
     assert e.value.status == pkg.DH2_EINVAL
+
+
+def test_batch_arguments_rejected_before_gpu_work(libpath):
+    import ctypes as C
+
+    import paper_1809_04384_gb300 as pkg
+
+    L = pkg.lib()
+    assert L.dh2_build_dh2_batch(None, -1, None, 5, 1.0, 1e-4, None, 0, None) == pkg.DH2_EINVAL
+    assert L.dh2_build_dh2_batch(None, 2, None, 5, 1.0, 1e-4, None, 0, None) == pkg.DH2_EINVAL
+    # a NULL tree inside the batch: every output slot is cleared, nothing is built
+    trees = (C.c_void_p * 2)(None, None)
+    kappas = (C.c_double * 2)(1.0, 2.0)
+    out = (C.c_void_p * 2)(1, 1)
+    st = L.dh2_build_dh2_batch(C.cast(trees, C.c_void_p), 2, C.cast(kappas, C.c_void_p), 5, 1.0, 1e-4, None, 0,
+                               C.cast(out, C.c_void_p))
+    assert st == pkg.DH2_EINVAL and out[0] is None and out[1] is None
+    assert b"tree is NULL" in L.dh2_last_error()
+    assert L.dh2_build_dh2_batch(None, 0, None, 5, 1.0, 1e-4, None, -1, None) == pkg.DH2_EINVAL
+    assert L.dh2_build_dh2_batch(None, 0, None, 5, 1.0, 1e-4, None, 0, None) == pkg.DH2_OK
+    assert L.dh2_matvec_batch(None, 1, None, None, pkg.DH2_C64, None) == pkg.DH2_EINVAL
+    mats = (C.c_void_p * 1)(None)
+    xs = (C.c_void_p * 1)(None)
+    assert L.dh2_matvec_batch(C.cast(mats, C.c_void_p), 1, C.cast(xs, C.c_void_p), C.cast(xs, C.c_void_p),
+                              pkg.DH2_C64, None) == pkg.DH2_EINVAL
+    assert L.dh2_matvec_batch(None, 0, None, None, 7, None) == pkg.DH2_EINVAL
+    assert L.dh2_matvec_batch(None, 0, None, None, pkg.DH2_C64, None) == pkg.DH2_OK

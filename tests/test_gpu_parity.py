@@ -184,8 +184,9 @@ def test_matvec_dtypes_agree(precision):
 @pytest.mark.parametrize("name", ["mixed1280", "lowfreq1280"])
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_grouped_weight_qr_matches_oracle(name, precision):
-    """Stacks split into row groups (forced to 40 rows) whose R factors are merged by a
-    second QR give the same total weights and matvec as the oracle."""
+    """Stacks split into small row groups (40 rows requested; raised to twice the columns)
+    whose R factors are merged by a second QR give the same total weights and matvec as
+    the oracle."""
     import torch
 
     import paper_1809_04384_gb300 as dh2
