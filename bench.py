@@ -37,11 +37,22 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
-    # name: (icosphere level, kappa, leaf, eta1, eta2, m, eps)
-    "sphere20480": (5, 16.0, 32, 10.0, 1.0, 5, 1e-4),
-    "sphere1280": (3, 4.0, 32, 10.0, 1.0, 4, 1e-4),
-    "sphere5120": (4, 8.0, 32, 10.0, 1.0, 5, 1e-4),     # same kappa h, for profiling captures
+    # name: (mesh, kappa, leaf, eta1, eta2, m, eps); mesh ("icosphere", L) has 20 * 4^L
+    # triangles, ("cube", q) is the surface of [-1/2, 1/2]^3 with 12 q^2 triangles
+    "sphere20480": (("icosphere", 5), 16.0, 32, 10.0, 1.0, 5, 1e-4),
+    "sphere1280": (("icosphere", 3), 4.0, 32, 10.0, 1.0, 4, 1e-4),
+    "sphere5120": (("icosphere", 4), 8.0, 32, 10.0, 1.0, 5, 1e-4),     # same kappa h, for profiling captures
+    "sphere81920": (("icosphere", 6), 32.0, 32, 10.0, 1.0, 5, 1e-4),
+    "sphere327680": (("icosphere", 7), 64.0, 64, 10.0, 1.0, 5, 1e-4),
+    "cube196608": (("cube", 128), 48.0, 64, 10.0, 1.0, 5, 1e-4),
 }
+
+
+def workload_mesh(name):
+    import synth
+
+    kind, size = WORKLOADS[name][0]
+    return synth.icosphere(size) if kind == "icosphere" else synth.cube(size)
 METRIC = "DH2 build s + matvec GB/s at rel.err≤1e-4 vs dense; vs plain FP64 GPU form"
 
 
@@ -62,9 +73,13 @@ def parse():
 
 
 def workload_config(name):
-    lvl, kappa, leaf, eta1, eta2, m, eps = WORKLOADS[name]
-    return dict(workload=f"icosphere{20 * 4 ** lvl}", mesh="unit sphere, icosahedral refinement",
-                triangles=20 * 4 ** lvl, kappa=kappa, leaf=leaf, eta1=eta1, eta2=eta2, m=m, k=m ** 3, eps=eps)
+    (kind, size), kappa, leaf, eta1, eta2, m, eps = WORKLOADS[name]
+    if kind == "icosphere":
+        ntri, mesh = 20 * 4 ** size, "unit sphere, icosahedral refinement"
+    else:
+        ntri, mesh = 12 * size ** 2, f"surface of the cube [-1/2,1/2]^3, {size} x {size} squares per face"
+    return dict(workload=f"{kind}{ntri}", mesh=mesh, triangles=ntri, kappa=kappa, leaf=leaf, eta1=eta1,
+                eta2=eta2, m=m, k=m ** 3, eps=eps)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -135,8 +150,8 @@ def oracle_sample_seconds(name, out_queue=None):
     from oracle.recompress import Recompression
     from oracle.structure import build_block_tree, build_cluster_tree, build_directions
 
-    lvl, kappa, leaf, eta1, eta2, m, eps = WORKLOADS[name]
-    v, f = synth.icosphere(lvl)
+    _, kappa, leaf, eta1, eta2, m, eps = WORKLOADS[name]
+    v, f = workload_mesh(name)
     t0 = time.perf_counter()
     tr = build_cluster_tree(v, f, leaf)
     dirs = build_directions(tr, kappa, eta1)
@@ -361,8 +376,7 @@ def main():
         dist.init_process_group("nccl")
     pkg.lib()
     precision = pkg.DH2_MIXED if args.precision == "mixed" else pkg.DH2_FP64
-    lvl = WORKLOADS[args.workload][0]
-    v, f = synth.icosphere(lvl)
+    v, f = workload_mesh(args.workload)
     n = len(f)
     x = synth.random_vector(n, 1809_0002)
     xdt = torch.complex64 if precision == pkg.DH2_MIXED else torch.complex128

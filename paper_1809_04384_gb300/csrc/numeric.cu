@@ -484,6 +484,153 @@ __global__ void __launch_bounds__(256) k_tsqr(const QRTask* __restrict__ tasks, 
     }
 }
 
+// R-factor of the stacked rows for FP32 stacks of at most 256 / TPC columns, column
+// parallel: the TPC consecutive threads of column l hold rows sub*RT + i (i < RT) of the
+// current chunk of H = TPC*RT rows in registers.  Column j's owners build its reflector
+// (xLARFG convention, scaled column as in tsqr_chunk) and post it in shared memory; after
+// one block barrier every later column applies it with a dot product inside its threads
+// and a log2(TPC)-step shuffle.  Row j of R (global scratch, pitch ncols) only meets
+// column l's owners, so R needs no further synchronisation; the next row is fetched one
+// step ahead.
+// Reductions over the TPC lanes of one column.  They run inside branches that only that
+// column's lanes take, so the shuffle mask names exactly those lanes (all of which
+// execute the same shuffles), never the whole warp.
+template <int TPC>
+__device__ __forceinline__ unsigned group_mask() {
+    const unsigned lane = threadIdx.x & 31u;
+    return (TPC == 32 ? 0xffffffffu : ((1u << TPC) - 1u)) << (lane & ~(unsigned)(TPC - 1));
+}
+template <int TPC>
+__device__ __forceinline__ float group_max(float v) {
+    const unsigned mask = group_mask<TPC>();
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o));
+    return v;
+}
+template <int TPC>
+__device__ __forceinline__ float group_sum_r(float v) {
+    const unsigned mask = group_mask<TPC>();
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+template <int TPC>
+__device__ __forceinline__ cx<float> group_sum(cx<float> v) {
+    const unsigned mask = group_mask<TPC>();
+#pragma unroll
+    for (int o = 1; o < TPC; o <<= 1) v = cx<float>{v.x + __shfl_xor_sync(mask, v.x, o), v.y + __shfl_xor_sync(mask, v.y, o)};
+    return v;
+}
+
+template <int TPC, int RT, class TSrc, class TDst>
+__global__ void __launch_bounds__(256, 3) k_tsqr_cols(const QRTask* __restrict__ tasks, int kl,
+                                                      const cx<TSrc>* __restrict__ src, cx<float>* scratch,
+                                                      cx<TDst>* dst, unsigned* err) {
+    static_assert(RT % 4 == 0, "rows per thread");
+    constexpr int H = TPC * RT;
+    constexpr int SL = RT + 2;   // slice pitch: one spare 16-byte word staggers the banks
+    __shared__ __align__(16) cx<float> vbuf[2][TPC * SL];
+    __shared__ cx<float> taub[2];
+    const QRTask tk = tasks[blockIdx.x];
+    const int nc = tk.ncols;
+    const int col = threadIdx.x / TPC, sub = threadIdx.x % TPC;
+    const bool mine = col < nc;
+    cx<float>* R = scratch + (int64_t)blockIdx.x * kl * kl;
+    for (int idx = threadIdx.x; idx < nc * nc; idx += blockDim.x) R[idx] = zero<float>();
+    __syncthreads();
+    const cx<TSrc>* S = src + tk.src;
+    bool bad = false;
+    cx<float> w[RT];   // rows sub*RT + i of this column
+    for (int r0 = 0; r0 < tk.nrows; r0 += H) {
+        const int h = min(H, tk.nrows - r0);
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            const int row = sub * RT + i;
+            cx<float> v = zero<float>();
+            if (mine && row < h) {
+                const cx<TSrc> u = S[(int64_t)(r0 + row) * tk.ld + col];
+                bad |= !isfinite(u.x) || !isfinite(u.y);
+                v = cx<float>{float(u.x), float(u.y)};
+            }
+            w[i] = v;
+        }
+        cx<float> rj = mine ? R[col] : zero<float>();   // R[j][col] for j = 0
+        for (int j = 0; j < nc; ++j) {
+            const int b = j & 1;
+            const cx<float> rnext = (mine && j + 1 < nc) ? R[(j + 1) * nc + col] : zero<float>();
+            float4* vq = reinterpret_cast<float4*>(&vbuf[b][sub * SL]);
+            if (col == j) {
+                // reflector of column j; uniform over the TPC owners.  Four partial
+                // maxima / sums keep the dependency chains short.
+                float m4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                for (int i = 0; i < RT; ++i) m4[i & 3] = fmaxf(m4[i & 3], fmaxf(fabsf(w[i].x), fabsf(w[i].y)));
+                const float xmax = group_max<TPC>(fmaxf(fmaxf(m4[0], m4[1]), fmaxf(m4[2], m4[3])));
+                if (xmax >= 1.17549435e-38f) {
+                    const float amax = fmaxf(xmax, fmaxf(fabsf(rj.x), fabsf(rj.y)));
+                    const float inv = 1.0f / amax;
+                    float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int i = 0; i < RT; ++i) s4[i & 3] += abs2(inv * w[i]);
+                    const float xn2 = group_sum_r<TPC>((s4[0] + s4[1]) + (s4[2] + s4[3]));
+                    const cx<float> als = inv * rj;
+                    const float betas = -copysignf(sqrtf(abs2(als) + xn2), als.x);   // beta / amax
+                    const float rb = 1.0f / betas;
+                    const cx<float> tauc = mk<float>((betas - als.x) * rb, als.y * rb);
+                    const cx<float> d = mk<float>(als.x - betas, als.y);
+                    const float dn = inv / abs2(d);
+                    const cx<float> sc = mk<float>(d.x * dn, -d.y * dn);   // 1 / (alpha - beta)
+#pragma unroll
+                    for (int i = 0; i < RT; i += 2) {
+                        const cx<float> a0 = w[i] * sc, a1 = w[i + 1] * sc;
+                        vq[i / 2] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                    }
+                    if (sub == 0) {
+                        R[j * nc + j] = mk<float>(betas * amax, 0.0f);
+                        taub[b] = tauc;
+                    }
+                } else {   // numerically zero column: identity reflector
+#pragma unroll
+                    for (int i = 0; i < RT; i += 2) vq[i / 2] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    if (sub == 0) taub[b] = zero<float>();
+                }
+            }
+            __syncthreads();
+            if (mine && col > j) {
+                const cx<float> tauc = taub[b];
+                cx<float> d4[4] = {zero<float>(), zero<float>(), zero<float>(), zero<float>()};
+#pragma unroll
+                for (int i = 0; i < RT; i += 2) {
+                    const float4 q = vq[i / 2];
+                    fma_cjx(d4[i & 3], cx<float>{q.x, q.y}, w[i]);
+                    fma_cjx(d4[(i + 1) & 3], cx<float>{q.z, q.w}, w[i + 1]);
+                }
+                const cx<float> sdot = group_sum<TPC>((d4[0] + d4[1]) + (d4[2] + d4[3]));
+                const cx<float> tw = tauc * (rj + sdot);
+                // read the reflector again rather than keep RT more values in registers
+                asm volatile("" ::: "memory");
+#pragma unroll
+                for (int i = 0; i < RT; i += 2) {
+                    const float4 q = vq[i / 2];
+                    w[i] = w[i] - cx<float>{q.x, q.y} * tw;
+                    w[i + 1] = w[i + 1] - cx<float>{q.z, q.w} * tw;
+                }
+                if (sub == 0) R[j * nc + col] = rj - tw;
+            }
+            rj = rnext;
+        }
+        __syncthreads();   // the next chunk's first reflector reuses vbuf[0]
+    }
+    if (bad) raise_err(err, ERR_TSQR_INPUT);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < tk.rout * nc; idx += blockDim.x) {
+        const int i = idx / nc, l = idx - i * nc;
+        const cx<float> v = l >= i ? R[idx] : zero<float>();
+        if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_TSQR_NONFINITE);
+        dst[tk.dst + idx] = cx<TDst>{TDst(v.x), TDst(v.y)};
+    }
+}
+
 template <class TQ, int RPL>
 size_t tsqr_smem_bytes(int k) {
     return ((size_t)k * (32 * RPL + 1) + (size_t)kQRNB * k + 2 * kQRNB * kQRNB + kQRNB) * sizeof(cx<TQ>) +
@@ -1581,9 +1728,46 @@ void Num<T>::nearfield(cudaStream_t s) {
 
 // One launch per column class: stacks of at most 32 or 64 columns run with that pitch,
 // so that their shared memory and R scratch are sized for the class instead of for k.
+template <int TPC, class TSrc, class TDst>
+void launch_tsqr_cols(const std::vector<QRTask>& tasks, int kl, const cx<TSrc>* src, cx<TDst>* dst,
+                      DBuf<cx<float>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err, int id) {
+    if (tasks.empty()) return;
+    const int64_t per = (int64_t)kl * kl;
+    const int64_t max_tasks = std::max<int64_t>(1, (int64_t(1) << 31) / (per * (int64_t)sizeof(cx<float>)));
+    for (size_t b0 = 0; b0 < tasks.size(); b0 += (size_t)max_tasks) {
+        size_t cnt = std::min<size_t>((size_t)max_tasks, tasks.size() - b0);
+        std::vector<QRTask> part(tasks.begin() + b0, tasks.begin() + b0 + cnt);
+        DBuf<QRTask> d;
+        upload_vec(d, part, s);
+        scratch.reserve(cnt * per);
+        ev.begin(id, s);
+        k_tsqr_cols<TPC, 16, TSrc, TDst><<<(unsigned)cnt, 256, 0, s>>>(d.p, kl, src, scratch.p, dst, err);
+        ev.end(s);
+        DH2_CHECK_LAUNCH("k_tsqr_cols");
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    }
+}
+
 template <class TSrc, class TQ, class TDst, int RPL>
-void launch_tsqr(const std::vector<QRTask>& all, int k, const cx<TSrc>* src, cx<TDst>* dst,
+void launch_tsqr(const std::vector<QRTask>& all_in, int k, const cx<TSrc>* src, cx<TDst>* dst,
                  DBuf<cx<TQ>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err) {
+    const std::vector<QRTask>* pall = &all_in;
+    std::vector<QRTask> rest;
+    if constexpr (std::is_same<TQ, float>::value) {
+        // at most 128 columns: column-parallel kernel (2, 4 or 8 threads per column)
+        std::vector<QRTask> c2, c4, c8;
+        for (const QRTask& t : all_in) {
+            if (t.ncols <= 32) c8.push_back(t);
+            else if (t.ncols <= 64) c4.push_back(t);
+            else if (t.ncols <= 128) c2.push_back(t);
+            else rest.push_back(t);
+        }
+        launch_tsqr_cols<8>(c8, 32, src, dst, scratch, s, ev, err, K_TSQR_NARROW);
+        launch_tsqr_cols<4>(c4, 64, src, dst, scratch, s, ev, err, K_TSQR);
+        launch_tsqr_cols<2>(c2, 128, src, dst, scratch, s, ev, err, K_TSQR);
+        pall = &rest;
+    }
+    const std::vector<QRTask>& all = *pall;
     std::vector<QRTask> cls[3];
     const int pitch[3] = {std::min(k, 32), std::min(k, 64), k};
     for (const QRTask& t : all) cls[t.ncols <= pitch[0] ? 0 : t.ncols <= pitch[1] ? 1 : 2].push_back(t);
