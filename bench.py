@@ -429,9 +429,11 @@ def main():
     peaks = load_peaks()
     build_kernels = {k: v_ for k, v_ in ktimes.items() if not k.startswith("mv_") and v_[1] > 0}
     dom = max(build_kernels, key=lambda k: build_kernels[k][0])
-    roof = roofline_obj(dom, build_kernels[dom], work, peaks, len(mats))
+    roof = roofline_obj(dom, build_kernels[dom], work, peaks, len(mats),
+                        measured_traffic(cfg["workload"], dom, args.precision))
     leaf_ms, leaf_cnt = mv_kernels.get("mv_leaf_out", (0.0, 0))
-    mv_roof = roofline_obj("mv_leaf_out", (leaf_ms, leaf_cnt), work, peaks, 10)
+    mv_roof = roofline_obj("mv_leaf_out", (leaf_ms, leaf_cnt), work, peaks, 10,
+                           measured_traffic(cfg["workload"], "mv_leaf_out", args.precision))
 
     # e2e: host mesh in, host vector in/out, through the C ABI
     xh = np.ascontiguousarray(x.astype(np.complex128))
@@ -529,7 +531,31 @@ def kernel_work(mat, info, cfg):
     return mat.kernel_work()
 
 
-def roofline_obj(name, timing, work, peaks, nsteps):
+KERNEL_SOURCES = ["paper_1809_04384_gb300/csrc/numeric.cu", "paper_1809_04384_gb300/csrc/linalg.cuh",
+                  "paper_1809_04384_gb300/csrc/common.cuh"]
+
+
+def measured_traffic(workload, name, precision):
+    """DRAM bytes per launch of kernel id `name` from the committed ncu summary of this
+    workload, or None when there is none or the kernel sources changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"dram_per_launch_{workload}_{precision}.txt")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read().split("\n")
+    want = next((ln.split()[1] for ln in text if ln.startswith("sources_sha256_16:")), None)
+    have = hashlib.sha256(b"".join(open(os.path.join(ROOT, p), "rb").read() for p in KERNEL_SOURCES)).hexdigest()[:16]
+    if want != have:
+        return None
+    for ln in text:
+        f = ln.split()
+        if len(f) == 4 and f[0] == "traffic" and f[1] == workload and f[2] == name:
+            return float(f[3])
+    return None
+
+
+def roofline_obj(name, timing, work, peaks, nsteps, traffic=None):
     ms, launches = timing
     if launches == 0 or ms <= 0:
         return None
@@ -544,14 +570,14 @@ def roofline_obj(name, timing, work, peaks, nsteps):
         achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peaks["source"] + " copy bandwidth",
+                "frac": achieved / peak, "traffic": traffic, "peak_source": peaks["source"] + " copy bandwidth",
                 "algorithmic_bytes_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
     # FP32 / FP64 SIMT arithmetic: peak from unit counts and the maximum SM clock
     lanes = {"flop32": 128, "flop64": 2}[kind]
     peak = 152 * lanes * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
     achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "peak_source": f"derived: 152 SMs x {lanes} {'FP32' if lanes == 128 else 'FP64'} FMA lanes x 2 x "
                            f"{peaks['sm_max_mhz']:.0f} MHz",
             "algorithmic_flop_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
