@@ -7,6 +7,7 @@
 //   * tsqr_chunk      Householder update of an upper-triangular R (global) by
 //                     a block of extra rows held in shared memory
 //   * herm_jacobi     parallel cyclic Jacobi eigensolver for Hermitian matrices
+//   * rowjac_f32      one-sided Jacobi SVD (FP32) on the rows of a complex matrix
 #pragma once
 
 #include <cuda_runtime.h>
@@ -407,6 +408,112 @@ __device__ void tsqr_chunk(int k, cx<T>* R, cx<T>* W, cx<T>* s_tau, int* s_skip,
         }
         __syncthreads();
     }
+}
+
+// --------------------------------------------------------------------------- one-sided Jacobi (FP32)
+
+// One-sided (Hestenes) Jacobi on the rows of W (n x m, row pitch ldw, FP32 complex, global
+// or shared memory): builds a unitary J (n x n) such that the rows of J^H W_in = W_out are
+// mutually orthogonal, so W_in = J W_out is an SVD with the left singular vectors as the
+// columns of J and the singular values as the row norms of W_out.  Jt receives J^T (row i
+// of Jt is column i of J, contiguous).  Rows p, q with Gram [[a, g], [conj(g), b]],
+// g = sum_j w_p[j] conj(w_q[j]) = |g| e^{i phi}, are rotated by G = diag(1, e^{-i phi}) R with
+// the real Jacobi rotation R = [[c, s], [-s, c]] of [[a, |g|], [|g|, b]]:
+//   zeta = (b - a) / (2|g|),  t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),  c = 1/sqrt(1 + t^2),
+//   s = c t;  w_p <- c w_p - s e^{i phi} w_q,  w_q <- s w_p + c e^{i phi} w_q  (W <- G^H W),
+//   j_p <- c j_p - s e^{-i phi} j_q,  j_q <- s j_p + c e^{-i phi} j_q  (J <- J G).
+// Pairs follow the round-robin (circle) schedule, one warp per pair, a block barrier per
+// round; sweeps stop when no pair has |g| > tol sqrt(a b) (pairs with |g| < 1e-30 are not
+// rotated), after at most max_sweeps.  On
+// return lam[i] = |w_i|^2 (FP64 sums) and order[] lists the rows by descending lam.
+// Returns the number of sweeps.  All threads of the block must call it.
+__device__ inline int rowjac_f32(int n, int m, cx<float>* W, int ldw, cx<float>* Jt, double* lam, int* order,
+                                 int* s_flag, int max_sweeps, float tol) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, j = idx - i * n;
+        Jt[idx] = cx<float>{i == j ? 1.0f : 0.0f, 0.0f};
+    }
+    const int np = n + (n & 1);
+    int sweep = 0;
+    for (; sweep < max_sweeps && n > 1; ++sweep) {
+        if (threadIdx.x == 0) *s_flag = 0;
+        __syncthreads();
+        for (int r = 0; r < np - 1; ++r) {
+            for (int i = warp; i < np / 2; i += nwarps) {
+                // circle method: position 0 fixed, the others rotate by one per round
+                const int pa = i == 0 ? 0 : 1 + (i - 1 + r) % (np - 1);
+                const int pb = 1 + (np - 2 - i + r) % (np - 1);
+                const int p = min(pa, pb), q = max(pa, pb);
+                if (q >= n) continue;   // the padding row of an odd n
+                cx<float>* wp = W + (int64_t)p * ldw;
+                cx<float>* wq = W + (int64_t)q * ldw;
+                float a = 0.0f, b = 0.0f, gr = 0.0f, gi = 0.0f;
+                for (int j = lane; j < m; j += 32) {
+                    const cx<float> x = wp[j], y = wq[j];
+                    a += abs2(x);
+                    b += abs2(y);
+                    gr += x.x * y.x + x.y * y.y;   // x conj(y)
+                    gi += x.y * y.x - x.x * y.y;
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    a += __shfl_xor_sync(0xffffffffu, a, o);
+                    b += __shfl_xor_sync(0xffffffffu, b, o);
+                    gr += __shfl_xor_sync(0xffffffffu, gr, o);
+                    gi += __shfl_xor_sync(0xffffffffu, gi, o);
+                }
+                // |g| without underflow (rows of a tall W shrink towards zero, and the phase
+                // g / |g| must keep unit modulus for the rotation to stay unitary); couplings
+                // below 1e-30 are left alone
+                const float ag = hypotf(gr, gi);
+                if (!(ag > tol * sqrtf(a) * sqrtf(b)) || !(ag >= 1e-30f)) continue;   // warp-uniform
+                if (lane == 0) *s_flag = 1;
+                const float zeta = (b - a) / (2.0f * ag);
+                float t;
+                if (fabsf(zeta) > 1e18f) t = 0.5f / zeta;
+                else t = copysignf(1.0f, zeta) / (fabsf(zeta) + sqrtf(1.0f + zeta * zeta));
+                const float c = 1.0f / sqrtf(1.0f + t * t), sn = c * t;
+                const cx<float> e = mk<float>(gr / ag, gi / ag);        // e^{i phi}
+                const cx<float> se = mk<float>(sn * e.x, sn * e.y);     // s e^{i phi}
+                const cx<float> sec = mk<float>(sn * e.x, -sn * e.y);   // s e^{-i phi}
+                const cx<float> ce = mk<float>(c * e.x, c * e.y);       // c e^{i phi}
+                const cx<float> cec = mk<float>(c * e.x, -c * e.y);     // c e^{-i phi}
+                for (int j = lane; j < m; j += 32) {
+                    const cx<float> x = wp[j], y = wq[j];
+                    wp[j] = c * x - se * y;
+                    wq[j] = sn * x + ce * y;
+                }
+                cx<float>* jp = Jt + (int64_t)p * n;
+                cx<float>* jq = Jt + (int64_t)q * n;
+                for (int j = lane; j < n; j += 32) {
+                    const cx<float> x = jp[j], y = jq[j];
+                    jp[j] = c * x - sec * y;
+                    jq[j] = sn * x + cec * y;
+                }
+            }
+            __syncthreads();
+        }
+        const int more = *s_flag;
+        __syncthreads();
+        if (!more) break;
+    }
+    for (int i = warp; i < n; i += nwarps) {
+        double acc = 0.0;
+        for (int j = lane; j < m; j += 32) acc += (double)abs2(W[(int64_t)i * ldw + j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) lam[i] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double li = lam[i];
+        int rk = 0;
+        for (int j = 0; j < n; ++j) rk += (lam[j] > li || (lam[j] == li && j < i)) ? 1 : 0;
+        order[rk] = i;
+    }
+    __syncthreads();
+    return sweep;
 }
 
 // --------------------------------------------------------------------------- Hermitian Jacobi

@@ -441,6 +441,11 @@ struct QRTask {
 
 constexpr int kQRNB = 8;   // panel width of the blocked Householder update
 
+// FP32 one-sided Jacobi of the mixed form: stop when every pair has |g| <= tol sqrt(a b)
+// (a few units of FP32 rounding over rows of ~100 entries), at most this many sweeps.
+constexpr float kJacobiTolF32 = 4e-6f;
+constexpr int kJacobiSweepsF32 = 16;
+
 // R-factor of the stacked rows: R scratch (k x k, TQ) per CTA, chunks of 32*RPL rows.
 // Reads TSrc, writes the rout leading rows of R as TDst.
 template <class TSrc, class TQ, class TDst, int RPL>
@@ -724,15 +729,34 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
     __shared__ int s_rank;
     const int n = tk.rows, rz = tk.rz;
     const cx<T>* Zt = Z + tk.z;
-    // A = V Z^*  (n x rz), working precision (a perturbation of A at the square-root level)
+    // A = V Z^*  (n x rz), working precision
     cta_gemm_fit<T>(n, rz, k, V, [&](int nu, int j) { return conj(Zt[(int64_t)j * k + nu]); },
                 [&](int i, int j, cx<T> v) { Ascr[(int64_t)i * rz + j] = v; });
     __syncthreads();
-    // M = A A^*  (n x n), FP64: its eigenvalues are the squared singular values
-    cta_gemm_fit<double>(n, n, rz, DenseCvt<double, T>{Ascr, rz, false, false}, DenseCvt<double, T>{Ascr, rz, true, true},
-                     [&](int i, int j, cx<double> v) { M[(int64_t)i * n + j] = v; });
-    __syncthreads();
-    eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err);
+    // left singular vectors of A: FP32 one-sided Jacobi on the rows of A (mixed form), or the
+    // FP64 Gram A A^* and a Hermitian Jacobi eigensolver (FP64 form); u(i, r) is entry i of
+    // the r-th vector by descending singular value, s_lam[s_order[r]] its squared value
+    cx<float>* Jt = reinterpret_cast<cx<float>*>(M);
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ int s_flag;
+        rowjac_f32(n, rz, Ascr, rz, Jt, s_lam, s_order, &s_flag, kJacobiSweepsF32, kJacobiTolF32);
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (!isfinite(s_lam[i])) raise_err(err, ERR_TRUNC_NONFINITE);
+    } else {
+        cta_gemm_fit<double>(n, n, rz, DenseCvt<double, T>{Ascr, rz, false, false},
+                             DenseCvt<double, T>{Ascr, rz, true, true},
+                             [&](int i, int j, cx<double> v) { M[(int64_t)i * n + j] = v; });
+        __syncthreads();
+        eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err);
+    }
+    auto u = [&](int i, int r) -> cx<T> {
+        if constexpr (std::is_same<T, float>::value) {
+            return Jt[(int64_t)s_order[r] * n + i];
+        } else {
+            const cx<double> v = U[(int64_t)i * n + s_order[r]];
+            return cx<T>{T(v.x), T(v.y)};
+        }
+    };
     const int nsig = min(n, rz);
     if (threadIdx.x == 0) {
         double total = 0;
@@ -757,16 +781,10 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
     const int kt = s_rank;
     for (int idx = threadIdx.x; idx < n * kt; idx += blockDim.x) {
         int i = idx / kt, r = idx % kt;
-        cx<double> u = U[(int64_t)i * n + s_order[r]];
-        Q[tk.q + (int64_t)i * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
+        Q[tk.q + (int64_t)i * tk.qld + r] = u(i, r);
     }
     // C = Q^* V  (kt x k)
-    cta_gemm_fit<T>(kt, k, n,
-                [&](int r, int i) {
-                    const cx<double> u = U[(int64_t)i * n + s_order[r]];
-                    return cx<T>{T(u.x), T(-u.y)};
-                },
-                V,
+    cta_gemm_fit<T>(kt, k, n, [&](int r, int i) { return conj(u(i, r)); }, V,
                 [&](int r, int nu, cx<T> v) {
                     Cd[tk.c + (int64_t)r * k + nu] = cx<double>{double(v.x), double(v.y)};
                     Ct[tk.c + (int64_t)r * k + nu] = v;
@@ -797,14 +815,32 @@ struct OrthTask {
 // Gram, Hermitian Jacobi); P = U[:, :rt] (descending eigenvalues), R = P^* V, so V = P R
 // and R^* R = V^* V (Eq. basis_weights_def up to a unitary left factor).
 template <class T>
-__global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, const cx<T>* __restrict__ V,
+__global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, cx<T>* V,
                             cx<double>* gscr, int smem_n, cx<T>* P, cx<T>* R, unsigned* err) {
     extern __shared__ unsigned char smraw[];
     __shared__ double red[32];
     const OrthTask tk = tasks[blockIdx.x];
     const int n = tk.n, rt = tk.rt;
     EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.scr);
-    const cx<T>* Vt = V + tk.v;
+    cx<T>* Vt = V + tk.v;
+    if constexpr (std::is_same<T, float>::value) {
+        // FP32 one-sided Jacobi on the rows of V (rotated in place, V is not used later):
+        // V = J W with orthogonal rows w_i, so P = J[:, order], R = W[order, :]
+        __shared__ int s_flag;
+        cx<float>* Jt = reinterpret_cast<cx<float>*>(e.M);
+        rowjac_f32(n, k, Vt, k, Jt, e.lam, e.order, &s_flag, kJacobiSweepsF32, kJacobiTolF32);
+        for (int i = threadIdx.x; i < n; i += blockDim.x)
+            if (!isfinite(e.lam[i])) raise_err(err, ERR_TRUNC_NONFINITE);
+        for (int idx = threadIdx.x; idx < n * rt; idx += blockDim.x) {
+            const int i = idx / rt, j = idx - i * rt;
+            P[tk.p + idx] = Jt[(int64_t)e.order[j] * n + i];
+        }
+        for (int idx = threadIdx.x; idx < rt * k; idx += blockDim.x) {
+            const int j = idx / k, nu = idx - j * k;
+            R[tk.r + idx] = Vt[(int64_t)e.order[j] * k + nu];
+        }
+        return;
+    }
     cta_gemm_fit<double>(n, n, k, DenseCvt<double, T>{Vt, k, false, false}, DenseCvt<double, T>{Vt, k, true, true},
                      [&](int i, int j, cx<double> v) { e.M[(int64_t)i * n + j] = v; });
     __syncthreads();
@@ -843,16 +879,40 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
     const int rt = tk.rt, rz = tk.rz, n = tk.n;
     EigSpace e = eig_space(rt, smem_n, smraw, gscr + tk.scr);
     const cx<T>* Zt = Z + tk.z;
-    // M' = Z'^* Z'  (rt x rt)
-    cta_gemm_fit<double>(rt, rt, rz,
-                     [&](int i, int j) {
-                         cx<T> z = Zt[(int64_t)j * rt + i];
-                         return cx<double>{double(z.x), -double(z.y)};
-                     },
-                     DenseCvt<double, T>{Zt, rt, false, false},
-                     [&](int i, int j, cx<double> v) { e.M[(int64_t)i * rt + j] = v; });
-    __syncthreads();
-    eig_desc<T>(rt, e.M, e.U, e.rot, red, e.lam, e.order, err);
+    cx<float>* Jt = reinterpret_cast<cx<float>*>(e.M);
+    if constexpr (std::is_same<T, float>::value) {
+        // W = Z'^* (rt x rz, rz <= rt) in the U area; FP32 one-sided Jacobi on its rows
+        __shared__ int s_flag;
+        cx<float>* Wl = reinterpret_cast<cx<float>*>(e.U);
+        for (int idx = threadIdx.x; idx < rt * rz; idx += blockDim.x) {
+            const int i = idx / rz, j = idx - i * rz;
+            Wl[idx] = conj(Zt[(int64_t)j * rt + i]);
+        }
+        __syncthreads();
+        rowjac_f32(rt, rz, Wl, rz, Jt, e.lam, e.order, &s_flag, kJacobiSweepsF32, kJacobiTolF32);
+        for (int i = threadIdx.x; i < rt; i += blockDim.x)
+            if (!isfinite(e.lam[i])) raise_err(err, ERR_TRUNC_NONFINITE);
+    } else {
+        // M' = Z'^* Z'  (rt x rt), FP64 Hermitian Jacobi
+        cta_gemm_fit<double>(rt, rt, rz,
+                             [&](int i, int j) {
+                                 cx<T> z = Zt[(int64_t)j * rt + i];
+                                 return cx<double>{double(z.x), -double(z.y)};
+                             },
+                             DenseCvt<double, T>{Zt, rt, false, false},
+                             [&](int i, int j, cx<double> v) { e.M[(int64_t)i * rt + j] = v; });
+        __syncthreads();
+        eig_desc<T>(rt, e.M, e.U, e.rot, red, e.lam, e.order, err);
+    }
+    // entry j of the r-th left singular vector of Z'^* (descending)
+    auto u = [&](int j, int r) -> cx<T> {
+        if constexpr (std::is_same<T, float>::value) {
+            return Jt[(int64_t)e.order[r] * rt + j];
+        } else {
+            const cx<double> v = e.U[(int64_t)j * rt + e.order[r]];
+            return cx<T>{T(v.x), T(v.y)};
+        }
+    };
     const int nsig = min(rt, rz);
     if (threadIdx.x == 0) {
         double total = 0;
@@ -877,22 +937,13 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
     const int kt = s_rank;
     for (int idx = threadIdx.x; idx < rt * kt; idx += blockDim.x) {
         const int j = idx / kt, r = idx - j * kt;
-        const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
-        Up[tk.up + (int64_t)j * tk.qld + r] = cx<T>{T(u.x), T(u.y)};
+        Up[tk.up + (int64_t)j * tk.qld + r] = u(j, r);
     }
     // Q = P U'[:, :kt]  (n x kt)
-    cta_gemm_fit<T>(n, kt, rt, Dense<T>{P + tk.p, rt, false, false},
-                [&](int j, int r) {
-                    const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
-                    return cx<T>{T(u.x), T(u.y)};
-                },
+    cta_gemm_fit<T>(n, kt, rt, Dense<T>{P + tk.p, rt, false, false}, [&](int j, int r) { return u(j, r); },
                 [&](int i, int r, cx<T> v) { Q[tk.q + (int64_t)i * tk.qld + r] = v; });
     // C = U'[:, :kt]^* R  (kt x k)
-    cta_gemm_fit<T>(kt, k, rt,
-                [&](int r, int j) {
-                    const cx<double> u = e.U[(int64_t)j * rt + e.order[r]];
-                    return cx<T>{T(u.x), T(-u.y)};
-                },
+    cta_gemm_fit<T>(kt, k, rt, [&](int r, int j) { return conj(u(j, r)); },
                 Dense<T>{R + tk.r, k, false, false},
                 [&](int r, int nu, cx<T> v) {
                     Cd[tk.c + (int64_t)r * k + nu] = cx<double>{double(v.x), double(v.y)};
