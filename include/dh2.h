@@ -17,8 +17,9 @@
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Device pointers must be valid on the current CUDA device.
  *   - Device memory of the library comes from the device's default memory
- *     pool, allocated and freed in stream order on the call's stream; memory
- *     freed inside a build is kept in the pool until the build ends.
+ *     pool, allocated and freed in stream order on the call's stream.  The
+ *     library sets the pool's release threshold to a quarter of the device's
+ *     memory: up to that much freed memory stays mapped for reuse.
  *   - Invalid arguments are rejected with DH2_EINVAL before any GPU work.
  *   - Complex vectors are interleaved (re, im) pairs: DH2_C64 = 2 x float,
  *     DH2_C128 = 2 x double.
@@ -269,8 +270,8 @@ const char* dh2_stage_name(int32_t i);
 const char* dh2_kernel_name(int32_t i);
 
 /* Release a handle (NULL is ignored).  Both wait for the device first, since
- * work queued on any stream may still read the object, then return the freed
- * memory of the library's pool to the device. */
+ * work queued on any stream may still read the object; the memory returns to
+ * the device's default pool. */
 void dh2_free_tree(dh2_tree tree);
 void dh2_free_matrix(dh2_matrix mat);
 const char* dh2_last_error(void);

@@ -166,10 +166,14 @@ void* dev_alloc(size_t bytes) {
     if (dev >= 64 || !((seen >> dev) & 1)) {
         std::lock_guard<std::mutex> lk(g_pool_mu);
         if (dev >= 64 || !g_pool_ready[dev]) {
-            // keep freed memory in the pool between the many short-lived buffers of a build
+            // keep up to a quarter of the device's memory of freed blocks in the pool, so
+            // that the many short-lived buffers of a build, and the next build, reuse
+            // mapped memory instead of going back to the driver
             cudaMemPool_t pool;
             DH2_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
-            uint64_t keep = UINT64_MAX;
+            size_t free_b = 0, total_b = 0;
+            DH2_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            uint64_t keep = total_b / 4;
             DH2_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
             if (dev < 64) g_pool_ready[dev] = true;
         }
@@ -197,12 +201,6 @@ void dev_free(void* p) {
     if (p) cudaFreeAsync(p, alloc_stream());
 }
 
-void trim_pool() {
-    int dev = 0;
-    cudaMemPool_t pool;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess)
-        cudaMemPoolTrimTo(pool, 0);
-}
 
 static std::atomic<int64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -292,11 +290,8 @@ dh2_status dh2_build_dh2(dh2_tree tree, double kappa, int32_t m, double eta, dou
         if (opt) o = *opt; else dh2_options_default(&o);
         check_build_args(tree, kappa, m, eta, eps, o, "dh2_build_dh2");
         cudaStream_t s = as_stream(stream);
-        {
-            AllocScope scope(s);
-            *out = build_matrix(tree, kappa, m, eta, eps, o, s);
-        }
-        trim_pool();
+        AllocScope scope(s);
+        *out = build_matrix(tree, kappa, m, eta, eps, o, s);
     });
 }
 
@@ -368,7 +363,6 @@ dh2_status dh2_build_dh2_batch(const dh2_tree* trees, int32_t count, const doubl
                 out[i] = nullptr;
             }
         }
-        trim_pool();
         if (failed) throw Error{first, "dh2_build_dh2_batch: " + first_msg};
     });
 }
@@ -578,13 +572,11 @@ void dh2_free_tree(dh2_tree tree) {
     if (!tree) return;
     cudaDeviceSynchronize();
     delete tree;
-    trim_pool();
 }
 void dh2_free_matrix(dh2_matrix mat) {
     if (!mat) return;
     cudaDeviceSynchronize();
     delete mat;
-    trim_pool();
 }
 
 }  // extern "C"

@@ -56,7 +56,8 @@ void ensure_smem(const void* fn, size_t bytes);
 // (cudaMallocAsync / cudaFreeAsync) on the stream of the entry point that is running,
 // which every entry point sets with AllocScope for its duration (the legacy default
 // stream otherwise).  Freeing then never waits for the whole device, so builds on
-// different streams overlap.  The pool keeps freed memory for reuse until trim_pool().
+// different streams overlap.  The pool keeps up to a quarter of the device's memory of
+// freed blocks for reuse (its release threshold).
 inline cudaStream_t& alloc_stream() {
     thread_local cudaStream_t s = nullptr;
     return s;
@@ -72,7 +73,6 @@ struct AllocScope {
 
 void* dev_alloc(size_t bytes);   // throws Error (DH2_ENOMEM / DH2_ECUDA)
 void dev_free(void* p);          // errors are ignored (used from destructors)
-void trim_pool();                // return the pool's unused memory to the device
 
 // Owning device allocation (see above); moves only.
 template <class T>

@@ -146,6 +146,7 @@ struct NearSeg {
     int32_t ld;                       // panel width of the row leaf
     int32_t pad;
     int64_t poff;                     // panel offset of (row 0, first column of this segment)
+    int64_t cpos;                     // where the segment's column indices go in the panel's list
 };
 
 // split of an FP64 coordinate into float hi + lo (for differences in FP32)
@@ -196,9 +197,11 @@ template <class T>
 __global__ void k_nearfield(const NearSeg* __restrict__ segs, QuadRows<T> qr,
                             const int32_t* __restrict__ perm, const double* __restrict__ area,
                             const double* __restrict__ x3, const double* __restrict__ x7, double kappa,
-                            cx<T>* P) {
+                            cx<T>* P, int32_t* colidx) {
     const NearSeg sg = segs[blockIdx.x];
     const T kap = (T)kappa;
+    // the panel's column -> x~ index list, read by the matvec
+    for (int j = threadIdx.x; j < sg.cols; j += blockDim.x) colidx[sg.cpos + j] = sg.coff + j;
     for (int idx = threadIdx.x; idx < sg.rows * sg.cols; idx += blockDim.x) {
         int i = idx / sg.cols, j = idx % sg.cols;
         int64_t r = sg.roff + i, c = sg.coff + j;
@@ -1711,8 +1714,7 @@ void Num<T>::nearfield(cudaStream_t s) {
     // one dense row panel per leaf: its segments side by side, sorted by column offset; the
     // width is padded to even (zero column) so that every row starts on 16 bytes
     std::vector<NearSeg> all;
-    std::vector<int32_t> colidx;
-    int64_t poff = 0, real = 0;
+    int64_t poff = 0, real = 0, ncol = 0;
     leaf_poff_.assign(leaf_order_.size(), 0);
     leaf_coff_.assign(leaf_order_.size(), 0);
     leaf_ld_.assign(leaf_order_.size(), 0);
@@ -1723,24 +1725,25 @@ void Num<T>::nearfield(cudaStream_t s) {
         for (auto& sg : v) width += sg.cols;
         const int32_t ld = width + (width & 1);
         leaf_poff_[i] = poff;
-        leaf_coff_[i] = (int64_t)colidx.size();
+        leaf_coff_[i] = ncol;
         leaf_ld_[i] = ld;
         int32_t col = 0;
         for (auto& sg : v) {
             sg.ld = ld;
             sg.poff = poff + col;
+            sg.cpos = ncol + col;
             col += sg.cols;
             all.push_back(sg);
-            for (int32_t j = 0; j < sg.cols; ++j) colidx.push_back(sg.coff + j);
         }
-        if (ld > width) colidx.push_back(0);
+        ncol += ld;   // a padding column keeps index 0 (its panel entries are zero)
         poff += (int64_t)h.size[leaf_order_[i]] * ld;
         real += (int64_t)h.size[leaf_order_[i]] * width;
     }
     info.near_entries = real;
     near_.alloc(std::max<int64_t>(poff, 1));
     near_.zero(s);
-    upload_vec(colidx_, colidx, s);
+    colidx_.alloc(std::max<int64_t>(ncol, 1));
+    colidx_.zero(s);
     const double s15 = std::sqrt(15.0);
     const double w7[7] = {9.0 / 40.0,           (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0,
                           (155.0 - s15) / 1200.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0,
@@ -1768,10 +1771,9 @@ void Num<T>::nearfield(cudaStream_t s) {
         upload_vec(d, part, s);
         ev_.begin(K_NEARFIELD, s);
         k_nearfield<T><<<(unsigned)cnt, kThreads, 0, s>>>(d.p, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
-                                                          tr_.x7.p, bp_.kappa, near_.p);
+                                                          tr_.x7.p, bp_.kappa, near_.p, colidx_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_nearfield");
-        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
     }
 }
 
@@ -1795,7 +1797,6 @@ void launch_tsqr_cols(const std::vector<QRTask>& tasks, int kl, const cx<TSrc>* 
         k_tsqr_cols<TPC, 16, TSrc, TDst><<<(unsigned)cnt, 256, 0, s>>>(d.p, kl, src, scratch.p, dst, err);
         ev.end(s);
         DH2_CHECK_LAUNCH("k_tsqr_cols");
-        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
     }
 }
 
@@ -1841,7 +1842,6 @@ void launch_tsqr(const std::vector<QRTask>& all_in, int k, const cx<TSrc>* src, 
             kern<<<(unsigned)cnt, kThreads, smem, s>>>(d.p, kl, src, scratch.p, dst, err);
             ev.end(s);
             DH2_CHECK_LAUNCH("k_tsqr");
-            DH2_CHECK_CUDA(cudaStreamSynchronize(s));
         }
     }
 }
