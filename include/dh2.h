@@ -65,6 +65,10 @@ typedef struct {
                                factors are stacked and factored again (0 = 1024 rows; never
                                below twice the stack's columns) */
     int64_t workspace_bytes;/* cap on the stacked weight workspace per level (0 = 16 GiB) */
+    int32_t tensor_cores;   /* DH2_MIXED with m <= 5: 1 (default) = coupling products of the
+                               total weights on the tcgen05 tensor cores in 3xTF32 (FP32-level
+                               accuracy); 0 = FP32 CUDA-core products */
+    int32_t reserved;       /* set to 0 */
 } dh2_options;
 
 typedef struct {

@@ -97,6 +97,7 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (!(o.rank_rule == DH2_RANK_BLOCKREL || o.rank_rule == DH2_RANK_GLOBAL))
         throw Error{DH2_EINVAL, f + ": bad rank rule"};
     if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
+    if (o.tensor_cores != 0 && o.tensor_cores != 1) throw Error{DH2_EINVAL, f + ": tensor_cores must be 0 or 1"};
 }
 
 // The whole build of one matrix on stream s (arguments already checked); blocks until done.
@@ -119,7 +120,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->structure_ms = ms;
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
-                          o.workspace_bytes};
+                          o.workspace_bytes, o.tensor_cores};
     mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
     mat->num->build(s);
     mat->num->info.stage_ms[ST_STRUCTURE] += ms;
@@ -238,6 +239,8 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->qr_fp64 = 0;
     opt->qr_group_rows = 0;
     opt->workspace_bytes = 0;
+    opt->tensor_cores = 1;
+    opt->reserved = 0;
     return DH2_OK;
 }
 

@@ -19,6 +19,7 @@
 #include <string>
 
 #include "numeric.cuh"
+#include "tcgen05.cuh"
 
 namespace dh2 {
 
@@ -31,7 +32,7 @@ constexpr int kThreads = 256;
 // the host reads the word after each stage and returns DH2_ENUMERIC.
 enum : unsigned {
     ERR_TSQR_NONFINITE = 1u, ERR_TRUNC_NONFINITE = 2u, ERR_TSQR_INPUT = 4u, ERR_STACK_NONFINITE = 8u,
-    ERR_KRON_NONFINITE = 16u
+    ERR_KRON_NONFINITE = 16u, ERR_TC_TIMEOUT = 32u
 };
 __device__ __forceinline__ void raise_err(unsigned* err, unsigned bit) { atomicOr(err, bit); }
 
@@ -331,9 +332,133 @@ struct BlockRowTask {
     int64_t koff;      // rows pass: where K_b = R_t S_b R_s^* is stored
 };
 
+// Coupling product on the tensor cores (k <= 128, FP32 data, 3xTF32):
+//   rows pass  out[i][nu] = scale * sum_mu R[i][mu] conj(S[nu][mu]),
+//   cols pass  out[i][nu] = scale * sum_mu R[i][mu] S[mu][nu],      i < ro <= NT/2, nu < k.
+// The MMA computes D[nu][col] (M = 128 rows nu, N = NT columns) as two real products into
+// one TMEM tile: D = A1 B1 + A2 B2 with A1 = Re S', A2 = Im S' (S' = S, or S^T in the cols
+// pass) and, for row i of R (RP = NT/2): B1[i] = Re R_i, B1[i+RP] = Im R_i, and
+// B2[i] = Im R_i, B2[i+RP] = -Re R_i (rows pass) or B2[i] = -Im R_i, B2[i+RP] = Re R_i (cols
+// pass), so that D[nu][i] and D[nu][i+RP] are the real and imaginary parts of the result.
+// Every operand is split into TF32 hi + lo and each real product is hi*hi + hi*lo + lo*hi.
+// K (mu) runs in chunks of KC; the operands of a chunk are generated into shared memory
+// (K-major core-matrix layout, see tcgen05.cuh) while the previous chunk is complete.
+// All threads of the block (256) must call it.  Returns false after an mbarrier timeout
+// (error bit set, TMEM released).
+template <int NT>
+struct TcTile {
+    static constexpr int KC = NT <= 128 ? 32 : 16;
+    static constexpr int RP = NT / 2;
+    static constexpr size_t kOperandBytes = (size_t)4 * (128 + NT) * KC * sizeof(float);
+};
+
+constexpr int kTcWaitPolls = 1 << 22;
+
+template <int NT>
+__device__ bool tc_coupling_product(const SGen<float>& S, bool rows_pass, const cx<float>* __restrict__ Rm, int ro,
+                                    int k, cx<float>* out, float scale, float* buf, uint64_t* mbar,
+                                    uint32_t* tmem_slot, unsigned* err) {
+    using Tile = TcTile<NT>;
+    constexpr int KC = Tile::KC, RP = Tile::RP;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float* A1h = buf;
+    float* A1l = A1h + 128 * KC;
+    float* A2h = A1l + 128 * KC;
+    float* A2l = A2h + 128 * KC;
+    float* B1h = A2l + 128 * KC;
+    float* B1l = B1h + NT * KC;
+    float* B2h = B1l + NT * KC;
+    float* B2l = B2h + NT * KC;
+    if (warp == 0) tc::tmem_alloc(tmem_slot, NT);
+    if (tid == 0) tc::mbar_init(mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tmem_slot;
+    const float b2s = rows_pass ? 1.0f : -1.0f;   // sign of B2[i] = +-Im R_i
+    const int nchunks = (k + KC - 1) / KC;
+    bool ok = true;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        if (ch > 0) {   // the tensor cores are done with the previous chunk's operands
+            ok = __syncthreads_and(tc::mbar_wait(mbar, (ch - 1) & 1, kTcWaitPolls));
+            if (!ok) break;
+        }
+        const int mu0 = ch * KC;
+        // A: 128 x KC; thread idx writes float offset idx (core matrices in order)
+        for (int idx = tid; idx < 128 * KC; idx += blockDim.x) {
+            const int core = idx >> 5, w = idx & 31;
+            const int nu = (core & 15) * 8 + (w >> 2), kk = (core >> 4) * 4 + (w & 3);
+            const int mu = mu0 + kk;
+            cx<float> v = zero<float>();
+            if (nu < k && mu < k) v = rows_pass ? S(nu, mu) : S(mu, nu);
+            tc::split_tf32(v.x, A1h[idx], A1l[idx]);
+            tc::split_tf32(v.y, A2h[idx], A2l[idx]);
+        }
+        // B: rows i < RP and i + RP of the NT x KC operands
+        for (int idx = tid; idx < RP * KC; idx += blockDim.x) {
+            const int core = idx >> 5, w = idx & 31;
+            const int i = (core % (RP / 8)) * 8 + (w >> 2), kk = (core / (RP / 8)) * 4 + (w & 3);
+            const int mu = mu0 + kk;
+            const cx<float> r = (i < ro && mu < k) ? Rm[(int64_t)i * k + mu] : zero<float>();
+            const int o0 = tc::kmaj_off(i, kk, NT), o1 = tc::kmaj_off(i + RP, kk, NT);
+            tc::split_tf32(r.x, B1h[o0], B1l[o0]);
+            tc::split_tf32(r.y, B1h[o1], B1l[o1]);
+            tc::split_tf32(b2s * r.y, B2h[o0], B2l[o0]);
+            tc::split_tf32(-b2s * r.x, B2h[o1], B2l[o1]);
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (NT / 8) * 128, sbo = 128;
+            const uint32_t idesc = tc::idesc_tf32(128, NT);
+            const float* As[6] = {A1h, A1h, A1l, A2h, A2h, A2l};
+            const float* Bs[6] = {B1h, B1l, B1h, B2h, B2l, B2h};
+#pragma unroll 1
+            for (int st = 0; st < KC / 8; ++st)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const uint64_t da = tc::sdesc(tc::smem_u32(As[q]) + st * 2 * lboA, lboA, sbo);
+                    const uint64_t db = tc::sdesc(tc::smem_u32(Bs[q]) + st * 2 * lboB, lboB, sbo);
+                    tc::mma_tf32(tmem, da, db, idesc, ch > 0 || st > 0 || q > 0);
+                }
+            tc::commit(mbar);
+        }
+    }
+    if (ok) ok = __syncthreads_and(tc::mbar_wait(mbar, (nchunks - 1) & 1, kTcWaitPolls));
+    if (!ok) {
+        if (tid == 0) raise_err(err, ERR_TC_TIMEOUT);
+        // let products still in flight finish before the TMEM is released (bounded)
+        tc::mbar_wait(mbar, (nchunks - 1) & 1, kTcWaitPolls);
+    }
+    tc::fence_after_sync();
+    if (ok) {
+        // warp w reads TMEM lanes 32 (w & 3) + lane (rows nu) and half (w >> 2) of the columns
+        const int q = warp & 3, h = warp >> 2;
+        const int nu = 32 * q + lane;
+        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+        for (int c0 = h * (RP / 2); c0 < (h + 1) * (RP / 2); c0 += 16) {
+            if (c0 >= ro) break;   // warp-uniform
+            float re[16], im[16];
+            tc::tmem_ld16(trow + (uint32_t)c0, re);
+            tc::tmem_ld16(trow + (uint32_t)(c0 + RP), im);
+            if (nu < k) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < ro) out[(int64_t)(c0 + j) * k + nu] = cx<float>{scale * re[j], scale * im[j]};
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, NT);
+    return ok;
+}
+
 // rows pass: R_sc S_b^*, then |G_b|_F = |R_tc S_b R_sc^*|_F, rows scaled by 1/|G_b|.
 // cols pass: R_tc S_b / |G_b|.
-template <class T>
+template <class T, int NT>
 __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __restrict__ tasks, bool rows_pass,
                                const int32_t* __restrict__ adm_t, const int32_t* __restrict__ adm_s,
                                const int32_t* __restrict__ adm_c, const int32_t* __restrict__ tc_level,
@@ -352,11 +477,20 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
     const int ro = rrows[tk.other];
     const cx<T>* Ro = R + roff[tk.other];
     cx<T>* out = stack + tk.dst;
+    // tensor-core operands after the generator tables, on a 128-byte boundary
+    [[maybe_unused]] float* tcbuf = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(smraw + sgen_smem_bytes<T>(m)) + 127) & ~uintptr_t(127));
+    __shared__ __align__(8) uint64_t tc_mbar;
+    __shared__ uint32_t tc_tmem;
     if (rows_pass) {
         // out[i][nu] = sum_mu R_s[i][mu] conj(S[nu][mu])
-        cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
-                    [&](int mu, int nu) { return conj(S(nu, mu)); },
-                    [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
+        if constexpr (NT > 0) {
+            if (!tc_coupling_product<NT>(S, true, Ro, ro, k, out, 1.0f, tcbuf, &tc_mbar, &tc_tmem, err)) return;
+        } else {
+            cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+                        [&](int mu, int nu) { return conj(S(nu, mu)); },
+                        [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
+        }
         __syncthreads();
         // K_b = R_t S R_s^* = R_t Y with Y[nu][i] = conj(out[i][nu]); |G_b|_F = |K_b|_F
         const int rt = rrows[tk.own];
@@ -392,9 +526,13 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
     } else {
         const T sc_ = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
         // out[i][nu] = sum_mu R_t[i][mu] S[mu][nu] / |G_b|
-        cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
-                    [&](int mu, int nu) { return S(mu, nu); },
-                    [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = sc_ * v; });
+        if constexpr (NT > 0) {
+            tc_coupling_product<NT>(S, false, Ro, ro, k, out, sc_, tcbuf, &tc_mbar, &tc_tmem, err);
+        } else {
+            cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+                        [&](int mu, int nu) { return S(mu, nu); },
+                        [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = sc_ * v; });
+        }
     }
 }
 
@@ -1525,6 +1663,8 @@ private:
     void nearfield(cudaStream_t s);
     void basis_weights(cudaStream_t s);
     void total_weights(int pass, cudaStream_t s);
+    template <int NT>
+    void launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pass, cx<T>* stack, cudaStream_t s);
     void truncate(int pass, cudaStream_t s);
     void project(cudaStream_t s);
     void plan_matvec(cudaStream_t s);
@@ -1968,6 +2108,29 @@ void Num<T>::basis_weights(cudaStream_t s) {
 // ----------------------------------------------------------------------------- total weights
 
 template <class T>
+template <int NT>
+void Num<T>::launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pass, cx<T>* stack, cudaStream_t s) {
+    if (tasks.empty()) return;
+    if constexpr (NT > 0 && !std::is_same<T, float>::value) {
+        throw Error{DH2_EUNSUPPORTED, "tensor-core coupling products need FP32 data"};
+    } else {
+        DBuf<BlockRowTask> d;
+        upload_vec(d, tasks, s);
+        size_t smem = sgen_smem_bytes<T>(m_);
+        if constexpr (NT > 0) smem += 128 + TcTile<NT>::kOperandBytes;   // 128: alignment slack
+        auto kern = k_stack_blocks<T, NT>;
+        ensure_smem(reinterpret_cast<const void*>(kern), smem);
+        ev_.begin(K_STACK_BLOCKS, s);
+        kern<<<(unsigned)tasks.size(), kThreads, smem, s>>>(d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
+                                                          tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
+                                                          bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack, K_.p,
+                                                          err_.p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_stack_blocks");
+    }
+}
+
+template <class T>
 void Num<T>::total_weights(int pass, cudaStream_t s) {
     const auto& h = hs_;
     const auto& ptr = pass == 0 ? h.row_ptr : h.col_ptr;
@@ -2031,16 +2194,21 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
             }
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             if (!btasks.empty()) {
-                DBuf<BlockRowTask> d;
-                upload_vec(d, btasks, s);
-                const size_t smem = sgen_smem_bytes<T>(m_);
-                ev_.begin(K_STACK_BLOCKS, s);
-                k_stack_blocks<T><<<(unsigned)btasks.size(), kThreads, smem, s>>>(
-                    d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p, st_.dir_off_d.p,
-                    st_.dirs.p, nodes_.p, m_, bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack.p, K_.p,
-                    err_.p);
-                ev_.end(s);
-                DH2_CHECK_LAUNCH("k_stack_blocks");
+                bool tcore = false;
+                if constexpr (std::is_same<T, float>::value) tcore = bp_.tensor_cores && kk <= 128;
+                if (tcore) {
+                    // tensor-core tiles by the rank of the R factor: N = 2 x (32 | 64 | 128)
+                    std::vector<BlockRowTask> cls[3];
+                    for (const BlockRowTask& b : btasks) {
+                        const int32_t ro = rR_[b.other];
+                        cls[ro <= 32 ? 0 : ro <= 64 ? 1 : 2].push_back(b);
+                    }
+                    launch_stack_blocks<64>(cls[0], pass, stack.p, s);
+                    launch_stack_blocks<128>(cls[1], pass, stack.p, s);
+                    launch_stack_blocks<256>(cls[2], pass, stack.p, s);
+                } else {
+                    launch_stack_blocks<0>(btasks, pass, stack.p, s);
+                }
             }
             if (!ktasks.empty()) {
                 DBuf<KRowTask> d;

@@ -205,3 +205,31 @@ def test_grouped_weight_qr_matches_oracle(name, precision):
     dt = torch.complex128 if precision == "fp64" else torch.complex64
     y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
     assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision == "mixed" else 0)
+
+
+@pytest.mark.parametrize("name", ["mixed1280", "dir1280"])
+def test_tensor_core_and_cuda_core_products_agree(name):
+    """The coupling products of the total weights on the tcgen05 tensor cores (3xTF32) and
+    on the CUDA cores (FP32) give the same ranks and, within the mixed tolerance, the same
+    product; both match the oracle's recompressed matvec."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    rc = oracle_recompression(name)
+    v, f, p, *_ = oracle_structure(name)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    mats = [dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], precision=dh2.DH2_MIXED, eta1=p["eta1"],
+                       tensor_cores=tc) for tc in (1, 0)]
+    x = x_vector(rc.tree.n)
+    ys = [m.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+          for m in mats]
+    r1, c1 = mats[0].ranks()
+    r0, c0 = mats[1].ranks()
+    slack = TOL["mixed"]["rank_slack"]
+    assert np.mean(r1 != r0) <= slack and np.mean(c1 != c0) <= slack
+    tol = max(TOL["mixed"]["matvec_same_ranks"], 2 * rc.eps)
+    assert rel(ys[0], ys[1]) <= tol
+    yo = rc.matvec(x)
+    for y in ys:
+        assert rel(y, yo) <= tol
