@@ -332,19 +332,17 @@ struct BlockRowTask {
     int64_t koff;      // rows pass: where K_b = R_t S_b R_s^* is stored
 };
 
-// Coupling product on the tensor cores (k <= 128, FP32 data, 3xTF32):
-//   rows pass  out[i][nu] = scale * sum_mu R[i][mu] conj(S[nu][mu]),
-//   cols pass  out[i][nu] = scale * sum_mu R[i][mu] S[mu][nu],      i < ro <= NT/2, nu < k.
-// The MMA computes D[nu][col] (M = 128 rows nu, N = NT columns) as two real products into
-// one TMEM tile: D = A1 B1 + A2 B2 with A1 = Re S', A2 = Im S' (S' = S, or S^T in the cols
-// pass) and, for row i of R (RP = NT/2): B1[i] = Re R_i, B1[i+RP] = Im R_i, and
-// B2[i] = Im R_i, B2[i+RP] = -Re R_i (rows pass) or B2[i] = -Im R_i, B2[i+RP] = Re R_i (cols
-// pass), so that D[nu][i] and D[nu][i+RP] are the real and imaginary parts of the result.
+// ----------------------------------------------------------------------------- tensor-core products
+
+// Products on the tcgen05 tensor cores in 3xTF32 (k <= 128, FP32 data).  A complex product
+// D = X Y (M = 128 rows, N = NT columns holding the real parts in [0, RP) and the imaginary
+// parts in [RP, NT), RP = NT/2) is formed as two real products into one TMEM tile,
+// D = A1 B1 + A2 B2, with A1 / A2 the real / imaginary part of X and B1, B2 arranged from
+// Y so that the sums land on the real and imaginary columns (see the generators below).
 // Every operand is split into TF32 hi + lo and each real product is hi*hi + hi*lo + lo*hi.
-// K (mu) runs in chunks of KC; the operands of a chunk are generated into shared memory
-// (K-major core-matrix layout, see tcgen05.cuh) while the previous chunk is complete.
-// All threads of the block (256) must call it.  Returns false after an mbarrier timeout
-// (error bit set, TMEM released).
+// K runs in chunks of KC: the operands of a chunk are generated into shared memory
+// (K-major core-matrix layout, see tcgen05.cuh) once the tensor cores are done with the
+// previous chunk; one thread issues the chunk's MMAs and commits them to an mbarrier.
 template <int NT>
 struct TcTile {
     static constexpr int KC = NT <= 128 ? 32 : 16;
@@ -354,48 +352,141 @@ struct TcTile {
 
 constexpr int kTcWaitPolls = 1 << 22;
 
+struct TcState {
+    float* buf;          // operand buffer (TcTile<NT>::kOperandBytes)
+    uint64_t* mbar;      // completion barrier of the chunks
+    uint32_t tmem;       // TMEM base (2 NT columns)
+    uint32_t phase;      // chunks committed so far
+    bool ok;             // no wait has timed out
+};
+
 template <int NT>
-__device__ bool tc_coupling_product(const SGen<float>& S, bool rows_pass, const cx<float>* __restrict__ Rm, int ro,
-                                    int k, cx<float>* out, float scale, float* buf, uint64_t* mbar,
-                                    uint32_t* tmem_slot, unsigned* err) {
-    using Tile = TcTile<NT>;
-    constexpr int KC = Tile::KC, RP = Tile::RP;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    float* A1h = buf;
-    float* A1l = A1h + 128 * KC;
-    float* A2h = A1l + 128 * KC;
-    float* A2l = A2h + 128 * KC;
-    float* B1h = A2l + 128 * KC;
-    float* B1l = B1h + NT * KC;
-    float* B2h = B1l + NT * KC;
-    float* B2l = B2h + NT * KC;
-    if (warp == 0) tc::tmem_alloc(tmem_slot, NT);
-    if (tid == 0) tc::mbar_init(mbar, 1);
+__device__ __forceinline__ void tc_operands(float* buf, float*& A1h, float*& A1l, float*& A2h, float*& A2l,
+                                            float*& B1h, float*& B1l, float*& B2h, float*& B2l) {
+    constexpr int KC = TcTile<NT>::KC;
+    A1h = buf;
+    A1l = A1h + 128 * KC;
+    A2h = A1l + 128 * KC;
+    A2l = A2h + 128 * KC;
+    B1h = A2l + 128 * KC;
+    B1l = B1h + NT * KC;
+    B2h = B1l + NT * KC;
+    B2l = B2h + NT * KC;
+}
+
+// D (TMEM columns [col0, col0 + NT)) = sum over K chunks of the generated operands.
+// genA(mu0, A1h, A1l, A2h, A2l) and genB(mu0, B1h, B1l, B2h, B2l) fill one chunk; they are
+// called by every thread of the block.  All threads of the block must call this.
+template <int NT, class GA, class GB>
+__device__ void tc_product(TcState& st, uint32_t col0, int K, const GA& genA, const GB& genB) {
+    constexpr int KC = TcTile<NT>::KC;
+    float *A1h, *A1l, *A2h, *A2l, *B1h, *B1l, *B2h, *B2l;
+    tc_operands<NT>(st.buf, A1h, A1l, A2h, A2l, B1h, B1l, B2h, B2l);
+    const int nchunks = (K + KC - 1) / KC;
+    for (int ch = 0; ch < nchunks && st.ok; ++ch) {
+        if (st.phase > 0) {   // the tensor cores are done with the previous operands
+            st.ok = __syncthreads_and(tc::mbar_wait(st.mbar, (st.phase - 1) & 1, kTcWaitPolls));
+            if (!st.ok) break;
+        }
+        genA(ch * KC, A1h, A1l, A2h, A2l);
+        genB(ch * KC, B1h, B1l, B2h, B2l);
+        tc::fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::fence_after_sync();
+            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (NT / 8) * 128, sbo = 128;
+            const uint32_t idesc = tc::idesc_tf32(128, NT);
+            const float* As[6] = {A1h, A1h, A1l, A2h, A2h, A2l};
+            const float* Bs[6] = {B1h, B1l, B1h, B2h, B2l, B2h};
+#pragma unroll 1
+            for (int s8 = 0; s8 < KC / 8; ++s8)
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const uint64_t da = tc::sdesc(tc::smem_u32(As[q]) + s8 * 2 * lboA, lboA, sbo);
+                    const uint64_t db = tc::sdesc(tc::smem_u32(Bs[q]) + s8 * 2 * lboB, lboB, sbo);
+                    tc::mma_tf32(st.tmem + col0, da, db, idesc, ch > 0 || s8 > 0 || q > 0);
+                }
+            tc::commit(st.mbar);
+        }
+        ++st.phase;
+    }
+    // the product is complete before anyone reads it
+    if (st.ok && st.phase > 0) st.ok = __syncthreads_and(tc::mbar_wait(st.mbar, (st.phase - 1) & 1, kTcWaitPolls));
+    tc::fence_after_sync();
+}
+
+template <int NT>
+__device__ void tc_begin(TcState& st, float* buf, uint64_t* mbar, uint32_t* tmem_slot) {
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(tmem_slot, 2 * NT);
+    if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tmem = *tmem_slot;
-    const float b2s = rows_pass ? 1.0f : -1.0f;   // sign of B2[i] = +-Im R_i
-    const int nchunks = (k + KC - 1) / KC;
-    bool ok = true;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        if (ch > 0) {   // the tensor cores are done with the previous chunk's operands
-            ok = __syncthreads_and(tc::mbar_wait(mbar, (ch - 1) & 1, kTcWaitPolls));
-            if (!ok) break;
-        }
-        const int mu0 = ch * KC;
-        // A: 128 x KC; thread idx writes float offset idx (core matrices in order)
-        for (int idx = tid; idx < 128 * KC; idx += blockDim.x) {
+    st = TcState{buf, mbar, *tmem_slot, 0u, true};
+}
+
+// releases the TMEM; after a timeout, first lets committed products finish (bounded)
+template <int NT>
+__device__ void tc_end(TcState& st, unsigned* err) {
+    if (!st.ok) {
+        if (threadIdx.x == 0) raise_err(err, ERR_TC_TIMEOUT);
+        if (st.phase > 0) tc::mbar_wait(st.mbar, (st.phase - 1) & 1, kTcWaitPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(st.tmem, 2 * NT);
+}
+
+// Operand generators.  A chunk of an M = 128 operand is written at float offset idx
+// (core matrices in order); the two halves of an N = NT operand at kmaj_off(i, kk, NT) and
+// kmaj_off(i + RP, kk, NT).
+
+// A[nu][mu] = S(nu, mu) (or S(mu, nu) when transposed), split into real / imaginary parts
+template <int NT>
+struct GenS {
+    const SGen<float>& S;
+    int k;
+    bool transposed;
+    __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
+        constexpr int KC = TcTile<NT>::KC;
+        for (int idx = threadIdx.x; idx < 128 * KC; idx += blockDim.x) {
             const int core = idx >> 5, w = idx & 31;
-            const int nu = (core & 15) * 8 + (w >> 2), kk = (core >> 4) * 4 + (w & 3);
-            const int mu = mu0 + kk;
+            const int nu = (core & 15) * 8 + (w >> 2), mu = mu0 + (core >> 4) * 4 + (w & 3);
             cx<float> v = zero<float>();
-            if (nu < k && mu < k) v = rows_pass ? S(nu, mu) : S(mu, nu);
+            if (nu < k && mu < k) v = transposed ? S(mu, nu) : S(nu, mu);
             tc::split_tf32(v.x, A1h[idx], A1l[idx]);
             tc::split_tf32(v.y, A2h[idx], A2l[idx]);
         }
-        // B: rows i < RP and i + RP of the NT x KC operands
-        for (int idx = tid; idx < RP * KC; idx += blockDim.x) {
+    }
+};
+
+// A[a][mu] = X[a][mu] for rows a < rows of a row-major matrix X (pitch ld), else 0
+template <int NT>
+struct GenRowsA {
+    const cx<float>* X;
+    int rows, ld, kmax;
+    __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
+        constexpr int KC = TcTile<NT>::KC;
+        for (int idx = threadIdx.x; idx < 128 * KC; idx += blockDim.x) {
+            const int core = idx >> 5, w = idx & 31;
+            const int a = (core & 15) * 8 + (w >> 2), mu = mu0 + (core >> 4) * 4 + (w & 3);
+            const cx<float> v = (a < rows && mu < kmax) ? X[(int64_t)a * ld + mu] : zero<float>();
+            tc::split_tf32(v.x, A1h[idx], A1l[idx]);
+            tc::split_tf32(v.y, A2h[idx], A2l[idx]);
+        }
+    }
+};
+
+// B from the rows of R (row-major, pitch k): B1[i] = Re R_i, B1[i+RP] = Im R_i,
+// B2[i] = s Im R_i, B2[i+RP] = -s Re R_i with s = +1 (for conj(S) R^T) or -1 (for S^T R^T)
+template <int NT>
+struct GenRowsB {
+    const cx<float>* Rm;
+    int ro, k;
+    float s;
+    __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
+        constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
+        for (int idx = threadIdx.x; idx < RP * KC; idx += blockDim.x) {
             const int core = idx >> 5, w = idx & 31;
             const int i = (core % (RP / 8)) * 8 + (w >> 2), kk = (core / (RP / 8)) * 4 + (w & 3);
             const int mu = mu0 + kk;
@@ -403,57 +494,140 @@ __device__ bool tc_coupling_product(const SGen<float>& S, bool rows_pass, const 
             const int o0 = tc::kmaj_off(i, kk, NT), o1 = tc::kmaj_off(i + RP, kk, NT);
             tc::split_tf32(r.x, B1h[o0], B1l[o0]);
             tc::split_tf32(r.y, B1h[o1], B1l[o1]);
-            tc::split_tf32(b2s * r.y, B2h[o0], B2l[o0]);
-            tc::split_tf32(-b2s * r.x, B2h[o1], B2l[o1]);
-        }
-        tc::fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (NT / 8) * 128, sbo = 128;
-            const uint32_t idesc = tc::idesc_tf32(128, NT);
-            const float* As[6] = {A1h, A1h, A1l, A2h, A2h, A2l};
-            const float* Bs[6] = {B1h, B1l, B1h, B2h, B2l, B2h};
-#pragma unroll 1
-            for (int st = 0; st < KC / 8; ++st)
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    const uint64_t da = tc::sdesc(tc::smem_u32(As[q]) + st * 2 * lboA, lboA, sbo);
-                    const uint64_t db = tc::sdesc(tc::smem_u32(Bs[q]) + st * 2 * lboB, lboB, sbo);
-                    tc::mma_tf32(tmem, da, db, idesc, ch > 0 || st > 0 || q > 0);
-                }
-            tc::commit(mbar);
+            tc::split_tf32(s * r.y, B2h[o0], B2l[o0]);
+            tc::split_tf32(-s * r.x, B2h[o1], B2l[o1]);
         }
     }
-    if (ok) ok = __syncthreads_and(tc::mbar_wait(mbar, (nchunks - 1) & 1, kTcWaitPolls));
-    if (!ok) {
-        if (tid == 0) raise_err(err, ERR_TC_TIMEOUT);
-        // let products still in flight finish before the TMEM is released (bounded)
-        tc::mbar_wait(mbar, (nchunks - 1) & 1, kTcWaitPolls);
-    }
-    tc::fence_after_sync();
-    if (ok) {
-        // warp w reads TMEM lanes 32 (w & 3) + lane (rows nu) and half (w >> 2) of the columns
-        const int q = warp & 3, h = warp >> 2;
-        const int nu = 32 * q + lane;
-        const uint32_t trow = tmem + ((uint32_t)(32 * q) << 16);
-#pragma unroll 1
-        for (int c0 = h * (RP / 2); c0 < (h + 1) * (RP / 2); c0 += 16) {
-            if (c0 >= ro) break;   // warp-uniform
+};
+
+// B from the TMEM tile D1 (rows nu, real parts in columns [0, RP), imaginary in [RP, NT))
+// of the rows-pass product, for K[a][j] = sum_nu R_t[a][nu] conj(D1[nu][j]):
+// B1[j] = Re D1[.][j], B1[j+RP] = -Im D1[.][j], B2[j] = Im D1[.][j], B2[j+RP] = Re D1[.][j].
+// The rows nu of a chunk live in TMEM lanes that only warps (chunk quarter) and
+// (quarter + 4) may read; each of the two reads half of the columns j.
+template <int NT>
+struct GenFromTmem {
+    uint32_t d1;   // TMEM address of D1 (lane 0, first column)
+    int ro;
+    __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
+        constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int q = mu0 >> 5;                 // TMEM lane quarter of this chunk (KC <= 32)
+        if ((warp & 3) != q) return;
+        const int sub = lane - (mu0 & 31);      // row of the chunk held by this lane
+        const uint32_t trow = d1 + ((uint32_t)(32 * q) << 16);
+        const int half = warp >> 2;
+        for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2); c0 += 16) {
             float re[16], im[16];
             tc::tmem_ld16(trow + (uint32_t)c0, re);
             tc::tmem_ld16(trow + (uint32_t)(c0 + RP), im);
-            if (nu < k) {
+            if (sub < 0 || sub >= KC) continue;   // lanes of the quarter outside this chunk
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j < ro) out[(int64_t)(c0 + j) * k + nu] = cx<float>{scale * re[j], scale * im[j]};
+            for (int jj = 0; jj < 16; ++jj) {
+                const int j = c0 + jj;
+                const float dr = j < ro ? re[jj] : 0.0f, di = j < ro ? im[jj] : 0.0f;
+                const int o0 = tc::kmaj_off(j, sub, NT), o1 = tc::kmaj_off(j + RP, sub, NT);
+                tc::split_tf32(dr, B1h[o0], B1l[o0]);
+                tc::split_tf32(-di, B1h[o1], B1l[o1]);
+                tc::split_tf32(di, B2h[o0], B2l[o0]);
+                tc::split_tf32(dr, B2h[o1], B2l[o1]);
             }
         }
     }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, NT);
-    return ok;
+};
+
+// Tensor-core form of one block task (both passes; see the comment of k_stack_blocks).
+// Rows pass: D1 = (R_s S_b^*)^T (TMEM columns [0, NT)), then K_b = R_t conj(D1)
+// (columns [NT, 2 NT)); |G_b|_F = |K_b|_F; the stack rows are written once, scaled:
+// w K_b^* for a leaf row cluster, w R_s S_b^* otherwise.  Cols pass: (R_t S_b)^T, scaled.
+template <int NT>
+__device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const SGen<float>& S, int k,
+                                const cx<float>* Ro, int ro, const cx<float>* __restrict__ R,
+                                const int64_t* __restrict__ roff, const int32_t* __restrict__ rrows, double* bnorm,
+                                cx<float>* out, cx<float>* Kst, float* tcbuf, uint64_t* mbar, uint32_t* tmem_slot,
+                                float* red, unsigned* err) {
+    constexpr int RP = TcTile<NT>::RP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, half = warp >> 2;
+    const int row = 32 * q + lane;   // TMEM lane (D row) read by this thread
+    TcState st;
+    tc_begin<NT>(st, tcbuf, mbar, tmem_slot);
+    const uint32_t trow = st.tmem + ((uint32_t)(32 * q) << 16);
+    if (!rows_pass) {
+        const float sc_ = bnorm[tk.b] > 0.0 ? float(1.0 / bnorm[tk.b]) : 0.0f;
+        tc_product<NT>(st, 0, k, GenS<NT>{S, k, true}, GenRowsB<NT>{Ro, ro, k, -1.0f});
+        if (st.ok) {
+            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(trow + (uint32_t)c0, re);
+                tc::tmem_ld16(trow + (uint32_t)(c0 + RP), im);
+                if (row < k)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < ro) out[(int64_t)(c0 + j) * k + row] = cx<float>{sc_ * re[j], sc_ * im[j]};
+            }
+        }
+        tc_end<NT>(st, err);
+        return;
+    }
+    tc_product<NT>(st, 0, k, GenS<NT>{S, k, false}, GenRowsB<NT>{Ro, ro, k, 1.0f});
+    const int rt = rrows[tk.own];
+    const cx<float>* Rt = R + roff[tk.own];
+    cx<float>* Kb = Kst + tk.koff;
+    tc_product<NT>(st, NT, k, GenRowsA<NT>{Rt, rt, k, k}, GenFromTmem<NT>{st.tmem, ro});
+    // K_b (rows a = TMEM lanes, columns j < ro) and |K_b|_F
+    float acc = 0.0f;
+    if (st.ok) {
+        for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+            float re[16], im[16];
+            tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
+            tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
+            if (row < rt)
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < ro) {
+                        Kb[(int64_t)row * ro + c0 + j] = cx<float>{re[j], im[j]};
+                        acc += re[j] * re[j] + im[j] * im[j];
+                    }
+        }
+    }
+    const float nrm = sqrtf(block_sum(acc, red));
+    if (threadIdx.x == 0) bnorm[tk.b] = (double)nrm;
+    const float sc_ = nrm > 0.0f ? 1.0f / nrm : 0.0f;
+    if (st.ok) {
+        if (tk.own_leaf) {
+            // w K_b^*: stack row j (< ro), column a (< rt), pitch k
+            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
+                tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
+                if (row < rt)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < ro) {
+                            const cx<float> v{sc_ * re[j], -sc_ * im[j]};
+                            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                            out[(int64_t)(c0 + j) * k + row] = v;
+                        }
+            }
+        } else {
+            // w R_s S_b^*: stack row i (< ro), column nu (< k)
+            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(trow + (uint32_t)c0, re);
+                tc::tmem_ld16(trow + (uint32_t)(c0 + RP), im);
+                if (row < k)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < ro) {
+                            const cx<float> v{sc_ * re[j], sc_ * im[j]};
+                            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                            out[(int64_t)(c0 + j) * k + row] = v;
+                        }
+            }
+        }
+    }
+    tc_end<NT>(st, err);
 }
 
 // rows pass: R_sc S_b^*, then |G_b|_F = |R_tc S_b R_sc^*|_F, rows scaled by 1/|G_b|.
@@ -482,15 +656,16 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
         (reinterpret_cast<uintptr_t>(smraw + sgen_smem_bytes<T>(m)) + 127) & ~uintptr_t(127));
     __shared__ __align__(8) uint64_t tc_mbar;
     __shared__ uint32_t tc_tmem;
+    if constexpr (NT > 0) {
+        stack_blocks_tc<NT>(tk, rows_pass, S, k, Ro, ro, R, roff, rrows, bnorm, out, Kst, tcbuf, &tc_mbar, &tc_tmem,
+                            red, err);
+        return;
+    }
     if (rows_pass) {
         // out[i][nu] = sum_mu R_s[i][mu] conj(S[nu][mu])
-        if constexpr (NT > 0) {
-            if (!tc_coupling_product<NT>(S, true, Ro, ro, k, out, 1.0f, tcbuf, &tc_mbar, &tc_tmem, err)) return;
-        } else {
-            cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
-                        [&](int mu, int nu) { return conj(S(nu, mu)); },
-                        [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
-        }
+        cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+                    [&](int mu, int nu) { return conj(S(nu, mu)); },
+                    [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = v; });
         __syncthreads();
         // K_b = R_t S R_s^* = R_t Y with Y[nu][i] = conj(out[i][nu]); |G_b|_F = |K_b|_F
         const int rt = rrows[tk.own];
@@ -526,13 +701,9 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
     } else {
         const T sc_ = bnorm[tk.b] > 0.0 ? T(1.0 / bnorm[tk.b]) : T(0);
         // out[i][nu] = sum_mu R_t[i][mu] S[mu][nu] / |G_b|
-        if constexpr (NT > 0) {
-            tc_coupling_product<NT>(S, false, Ro, ro, k, out, sc_, tcbuf, &tc_mbar, &tc_tmem, err);
-        } else {
-            cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
-                        [&](int mu, int nu) { return S(mu, nu); },
-                        [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = sc_ * v; });
-        }
+        cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
+                    [&](int mu, int nu) { return S(mu, nu); },
+                    [&](int i, int nu, cx<T> v) { out[(int64_t)i * k + nu] = sc_ * v; });
     }
 }
 

@@ -100,14 +100,13 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// x = hi + lo with hi, lo representable in TF32 (round to nearest, ties away); the
-// products hi*hi + hi*lo + lo*hi carry about 21 bits of each operand ("3xTF32")
+// x = hi + lo for the 3xTF32 products hi*hi + hi*lo + lo*hi: hi is x with the 13 low
+// mantissa bits cleared (exactly representable in TF32), lo = x - hi is exact in FP32;
+// the kind::tf32 MMA reads only the top 10 mantissa bits of lo, which leaves an error of
+// about 2^-21 |x| per operand.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-    uint32_t h, l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-    hi = __uint_as_float(h);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hi));
-    lo = __uint_as_float(l);
+    hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+    lo = x - hi;
 }
 
 }  // namespace tc
