@@ -441,24 +441,85 @@ __device__ void tc_end(TcState& st, unsigned* err) {
 // (core matrices in order); the two halves of an N = NT operand at kmaj_off(i, kk, NT) and
 // kmaj_off(i + RP, kk, NT).
 
-// A[nu][mu] = S(nu, mu) (or S(mu, nu) when transposed), split into real / imaginary parts
+// Coupling operand A[nu][mu] = S(nu, mu) (rows pass) or S(mu, nu) (cols pass) from two
+// node tables in shared memory: P[nu] holds the node on the row side of A, Q[mu] the node on
+// the column side, both as (x, y, z, w) FP32 differences from one reference node (taken in
+// FP64, so that x_P - x_Q keeps full relative accuracy), and w = +-<node - ref, c> such that
+// <xi_t - xi_s, c> = P.w - Q.w.  Each thread keeps one row nu and writes four consecutive
+// mu with one 16-byte store per operand array.
+__device__ __forceinline__ cx<float> coupling_value(float4 p, float4 q, float kappa) {
+    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
+    constexpr double k2pi = 2.0 * kPi;
+    constexpr float hi = (float)k2pi;
+    constexpr float lo = (float)(k2pi - (double)hi);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ri = rsqrtf(r2);
+    const float ph = kappa * (r2 * ri - (p.w - q.w));
+    const float j = rintf(ph * (float)(1.0 / k2pi));
+    float red = fmaf(-j, hi, ph);
+    red = fmaf(-j, lo, red);
+    float sn, cs;
+    __sincosf(red, &sn, &cs);
+    const float f = ri * (float)(1.0 / (4.0 * kPi));
+    return cx<float>{cs * f, sn * f};
+}
+
 template <int NT>
 struct GenS {
-    const SGen<float>& S;
+    const float4* P;   // 128 entries (row side), zero-padded past k
+    const float4* Q;   // k entries (column side)
     int k;
-    bool transposed;
+    float kappa;
     __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
         constexpr int KC = TcTile<NT>::KC;
-        for (int idx = threadIdx.x; idx < 128 * KC; idx += blockDim.x) {
-            const int core = idx >> 5, w = idx & 31;
-            const int nu = (core & 15) * 8 + (w >> 2), mu = mu0 + (core >> 4) * 4 + (w & 3);
-            cx<float> v = zero<float>();
-            if (nu < k && mu < k) v = transposed ? S(mu, nu) : S(nu, mu);
-            tc::split_tf32(v.x, A1h[idx], A1l[idx]);
-            tc::split_tf32(v.y, A2h[idx], A2l[idx]);
+        constexpr int GROUPS = KC / 4;                          // 4-wide groups of a chunk
+        for (int w = threadIdx.x; w < 128 * GROUPS; w += blockDim.x) {
+            const int nu = w & 127, g = w >> 7;
+            const float4 p = P[nu];
+            float4 h1, l1, h2, l2;
+            float* ph1 = &h1.x; float* pl1 = &l1.x; float* ph2 = &h2.x; float* pl2 = &l2.x;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int mu = mu0 + 4 * g + e;
+                cx<float> v = zero<float>();
+                if (nu < k && mu < k) v = coupling_value(p, Q[mu], kappa);
+                tc::split_tf32(v.x, ph1[e], pl1[e]);
+                tc::split_tf32(v.y, ph2[e], pl2[e]);
+            }
+            const int off = tc::kmaj_off(nu, 4 * g, 128);
+            *reinterpret_cast<float4*>(A1h + off) = h1;
+            *reinterpret_cast<float4*>(A1l + off) = l1;
+            *reinterpret_cast<float4*>(A2h + off) = h2;
+            *reinterpret_cast<float4*>(A2l + off) = l2;
         }
     }
 };
+
+// node tables of GenS for block (t, s) with direction c: rows pass P = xi_t, Q = xi_s;
+// cols pass P = xi_s, Q = xi_t (w negated); reference = the first node of the Q cluster
+__device__ void load_node_tables(int32_t t, int32_t s, const double* __restrict__ cd,
+                                 const double* __restrict__ nodes, int m, bool rows_pass, float4* P, float4* Q) {
+    const int mm = m * m, k = mm * m;
+    const int32_t cp = rows_pass ? t : s, cq = rows_pass ? s : t;
+    const double sg = rows_pass ? 1.0 : -1.0;
+    const double* np_ = nodes + (int64_t)cp * 3 * m;
+    const double* nq_ = nodes + (int64_t)cq * 3 * m;
+    const double rx = nq_[0], ry = nq_[m], rz = nq_[2 * m];
+    for (int idx = threadIdx.x; idx < 128 + k; idx += blockDim.x) {
+        const bool isp = idx < 128;
+        const int nu = isp ? idx : idx - 128;
+        const double* nn = isp ? np_ : nq_;
+        float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (nu < k) {
+            const int ix = nu % m, iy = (nu / m) % m, iz = nu / mm;
+            const double x = nn[ix] - rx, y = nn[m + iy] - ry, z = nn[2 * m + iz] - rz;
+            v = make_float4((float)x, (float)y, (float)z, (float)(sg * ((x * cd[0] + y * cd[1]) + z * cd[2])));
+        }
+        if (isp) P[nu] = v;
+        else Q[nu] = v;
+    }
+    __syncthreads();
+}
 
 // A[a][mu] = X[a][mu] for rows a < rows of a row-major matrix X (pitch ld), else 0
 template <int NT>
@@ -541,7 +602,8 @@ struct GenFromTmem {
 // (columns [NT, 2 NT)); |G_b|_F = |K_b|_F; the stack rows are written once, scaled:
 // w K_b^* for a leaf row cluster, w R_s S_b^* otherwise.  Cols pass: (R_t S_b)^T, scaled.
 template <int NT>
-__device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const SGen<float>& S, int k,
+__device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const float4* Ptab, const float4* Qtab,
+                                float kappa, int k,
                                 const cx<float>* Ro, int ro, const cx<float>* __restrict__ R,
                                 const int64_t* __restrict__ roff, const int32_t* __restrict__ rrows, double* bnorm,
                                 cx<float>* out, cx<float>* Kst, float* tcbuf, uint64_t* mbar, uint32_t* tmem_slot,
@@ -555,7 +617,7 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const SG
     const uint32_t trow = st.tmem + ((uint32_t)(32 * q) << 16);
     if (!rows_pass) {
         const float sc_ = bnorm[tk.b] > 0.0 ? float(1.0 / bnorm[tk.b]) : 0.0f;
-        tc_product<NT>(st, 0, k, GenS<NT>{S, k, true}, GenRowsB<NT>{Ro, ro, k, -1.0f});
+        tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, kappa}, GenRowsB<NT>{Ro, ro, k, -1.0f});
         if (st.ok) {
             for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
                 float re[16], im[16];
@@ -570,7 +632,7 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const SG
         tc_end<NT>(st, err);
         return;
     }
-    tc_product<NT>(st, 0, k, GenS<NT>{S, k, false}, GenRowsB<NT>{Ro, ro, k, 1.0f});
+    tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, kappa}, GenRowsB<NT>{Ro, ro, k, 1.0f});
     const int rt = rrows[tk.own];
     const cx<float>* Rt = R + roff[tk.own];
     cx<float>* Kb = Kst + tk.koff;
@@ -647,20 +709,23 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
     const int k = m * m * m;
     const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
     const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
-    const SGen<T> S = load_sgen_tables<T>(t, s, cd, nodes, m, kappa, smraw);
     const int ro = rrows[tk.other];
     const cx<T>* Ro = R + roff[tk.other];
     cx<T>* out = stack + tk.dst;
-    // tensor-core operands after the generator tables, on a 128-byte boundary
-    [[maybe_unused]] float* tcbuf = reinterpret_cast<float*>(
-        (reinterpret_cast<uintptr_t>(smraw + sgen_smem_bytes<T>(m)) + 127) & ~uintptr_t(127));
-    __shared__ __align__(8) uint64_t tc_mbar;
-    __shared__ uint32_t tc_tmem;
     if constexpr (NT > 0) {
-        stack_blocks_tc<NT>(tk, rows_pass, S, k, Ro, ro, R, roff, rrows, bnorm, out, Kst, tcbuf, &tc_mbar, &tc_tmem,
-                            red, err);
+        // node tables (2 x 128 float4), then the tensor-core operands on a 128-byte boundary
+        __shared__ __align__(8) uint64_t tc_mbar;
+        __shared__ uint32_t tc_tmem;
+        float4* Ptab = reinterpret_cast<float4*>(
+            (reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+        float4* Qtab = Ptab + 128;
+        float* tcbuf = reinterpret_cast<float*>(Qtab + 128);
+        load_node_tables(t, s, cd, nodes, m, rows_pass, Ptab, Qtab);
+        stack_blocks_tc<NT>(tk, rows_pass, Ptab, Qtab, (float)kappa, k, Ro, ro, R, roff, rrows, bnorm, out, Kst,
+                            tcbuf, &tc_mbar, &tc_tmem, red, err);
         return;
     }
+    const SGen<T> S = load_sgen_tables<T>(t, s, cd, nodes, m, kappa, smraw);
     if (rows_pass) {
         // out[i][nu] = sum_mu R_s[i][mu] conj(S[nu][mu])
         cta_gemm_fit<T>(ro, k, k, Dense<T>{Ro, k, false, false},
@@ -2288,7 +2353,7 @@ void Num<T>::launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pas
         DBuf<BlockRowTask> d;
         upload_vec(d, tasks, s);
         size_t smem = sgen_smem_bytes<T>(m_);
-        if constexpr (NT > 0) smem += 128 + TcTile<NT>::kOperandBytes;   // 128: alignment slack
+        if constexpr (NT > 0) smem = 128 + 2 * 128 * sizeof(float4) + TcTile<NT>::kOperandBytes;   // 128: alignment
         auto kern = k_stack_blocks<T, NT>;
         ensure_smem(reinterpret_cast<const void*>(kern), smem);
         ev_.begin(K_STACK_BLOCKS, s);
