@@ -46,7 +46,7 @@ typedef enum {
 
 enum { DH2_FP64 = 0, DH2_MIXED = 1 };                 /* dh2_options.precision */
 enum { DH2_C64 = 1, DH2_C128 = 2 };                   /* vector dtypes */
-enum { DH2_RANK_BLOCKREL = 0, DH2_RANK_GLOBAL = 1 };  /* dh2_options.rank_rule */
+enum { DH2_RANK_BLOCKREL = 0, DH2_RANK_GLOBAL = 1, DH2_RANK_SPECTRAL = 2 };  /* dh2_options.rank_rule */
 
 typedef struct dh2_tree_s* dh2_tree;
 typedef struct dh2_matrix_s* dh2_matrix;
@@ -59,7 +59,10 @@ typedef struct {
                                SVD truncation (Gram + Jacobi) and basis-change matrices */
     int32_t rank_rule;      /* DH2_RANK_BLOCKREL: sum_{i>k} sigma_i^2 <= eps^2 with every block
                                weighted by 1/|G_b|_F (blockwise relative Frobenius, Section 5);
-                               DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted */
+                               DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted;
+                               DH2_RANK_SPECTRAL: sigma_{k+1} <= eps with the block weights
+                               of DH2_RANK_BLOCKREL (error control in the spectral norm,
+                               Section 5) */
     int32_t qr_fp64;        /* DH2_MIXED only: 1 = run the weight QRs (R, Z-hat) in FP64 */
     int32_t qr_group_rows;  /* stacks taller than this are factored in row groups whose R
                                factors are stacked and factored again (0 = 1024 rows; never

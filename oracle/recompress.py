@@ -20,7 +20,9 @@ Steps, in the paper's order (all pairs (t,c) of the active set, W = V):
    A = V-hat Z-hat^* with V-hat = [C_{t1c1} E_{t1c}; C_{t2c2} E_{t2c}]; SVD of A;
    rank k_tc = smallest k with sum_{i>k} sigma_i^2 <= eps^2 (blockwise
    relative: every block carries norm 1), or <= eps^2 sum sigma^2 ("global"
-   reading); Q = first k_tc left singular vectors (leaf) or
+   reading), or, for error control in the spectral norm (Section 5, Table
+   "spectral norm"; the best rank-k error in the spectral norm is sigma_{k+1}),
+   the smallest k with sigma_{k+1} <= eps on the same weighted matrix; Q = first k_tc left singular vectors (leaf) or
    Q-hat = [F_{t1c}; F_{t2c}] (non-leaf); C_tc = Q^* V (or Q-hat^* V-hat)
    (Eq. C_tc).
 5. projection S~_b = C_tc S_b C^W_sc^*  (Lemma "Projections").
@@ -45,6 +47,7 @@ from .interp import InterpolatedDH2
 
 RANK_BLOCKREL = 0
 RANK_GLOBAL = 1
+RANK_SPECTRAL = 2
 
 
 def qr_r(a, k):
@@ -55,7 +58,10 @@ def qr_r(a, k):
 
 
 def choose_rank(sigma, eps, rule=RANK_BLOCKREL):
-    """Smallest k with sum_{i>k} sigma_i^2 <= bound (Section 3.1, Frobenius)."""
+    """Smallest k with sum_{i>k} sigma_i^2 <= bound (Section 3.1, Frobenius), or with
+    sigma_{k+1} <= eps (spectral norm; sigma sorted descending)."""
+    if rule == RANK_SPECTRAL:
+        return int(np.count_nonzero(np.asarray(sigma, dtype=np.float64) > eps))
     s2 = sigma.astype(np.float64) ** 2
     tail = np.concatenate([np.cumsum(s2[::-1])[::-1], [0.0]])   # tail[k] = sum_{i>=k}
     bound = eps * eps if rule == RANK_BLOCKREL else eps * eps * float(s2.sum())

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libdh2.so")
 DH2_OK, DH2_EINVAL, DH2_ENOMEM, DH2_ECUDA, DH2_ETIMEOUT, DH2_ENUMERIC, DH2_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 DH2_FP64, DH2_MIXED = 0, 1
 DH2_C64, DH2_C128 = 1, 2
-DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL = 0, 1
+DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL, DH2_RANK_SPECTRAL = 0, 1, 2
 (DH2_X_R, DH2_X_ZROW, DH2_X_ZCOL, DH2_X_SROW, DH2_X_SCOL, DH2_X_QROW, DH2_X_QCOL,
  DH2_X_CROW, DH2_X_CCOL, DH2_X_P) = range(10)
 

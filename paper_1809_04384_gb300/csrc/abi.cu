@@ -94,7 +94,7 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (!(std::isfinite(eps) && eps > 0.0)) throw Error{DH2_EINVAL, f + ": eps must be > 0"};
     if (!(std::isfinite(o.eta1) && o.eta1 > 0.0)) throw Error{DH2_EINVAL, f + ": eta1 must be > 0"};
     if (!(o.precision == DH2_FP64 || o.precision == DH2_MIXED)) throw Error{DH2_EINVAL, f + ": bad precision"};
-    if (!(o.rank_rule == DH2_RANK_BLOCKREL || o.rank_rule == DH2_RANK_GLOBAL))
+    if (!(o.rank_rule == DH2_RANK_BLOCKREL || o.rank_rule == DH2_RANK_GLOBAL || o.rank_rule == DH2_RANK_SPECTRAL))
         throw Error{DH2_EINVAL, f + ": bad rank rule"};
     if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
     if (o.tensor_cores != 0 && o.tensor_cores != 1) throw Error{DH2_EINVAL, f + ": tensor_cores must be 0 or 1"};

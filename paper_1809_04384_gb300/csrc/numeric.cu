@@ -1150,6 +1150,10 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
                 break;
             }
         }
+        if (rule == DH2_RANK_SPECTRAL) {   // smallest k with sigma_{k+1} <= eps
+            kk = nsig;
+            while (kk > 0 && s_lam[s_order[kk - 1]] <= eps * eps) --kk;
+        }
         s_rank = kk;
         rank[tk.a] = kk;
     }
@@ -1305,6 +1309,10 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
             } else {
                 break;
             }
+        }
+        if (rule == DH2_RANK_SPECTRAL) {   // smallest k with sigma_{k+1} <= eps
+            kk = nsig;
+            while (kk > 0 && e.lam[e.order[kk - 1]] <= eps * eps) --kk;
         }
         s_rank = kk;
         rank[tk.a] = kk;

@@ -233,3 +233,32 @@ def test_tensor_core_and_cuda_core_products_agree(name):
     yo = rc.matvec(x)
     for y in ys:
         assert rel(y, yo) <= tol
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_spectral_rank_rule_matches_oracle(precision):
+    """Error control in the spectral norm: ranks and matvec as the oracle's."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+    from oracle.geometry import Discretisation
+    from oracle.interp import InterpolatedDH2
+    from oracle.recompress import RANK_SPECTRAL, Recompression
+
+    v, f, p, tr, dirs, bt = oracle_structure("mixed1280")
+    rc = Recompression(InterpolatedDH2(Discretisation(v, f), tr, dirs, bt, p["kappa"], p["m"]), p["eps"],
+                       RANK_SPECTRAL)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    prec = dh2.DH2_FP64 if precision == "fp64" else dh2.DH2_MIXED
+    mat = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], precision=prec, eta1=p["eta1"],
+                     rank_rule=dh2.DH2_RANK_SPECTRAL)
+    tol = TOL[precision]
+    rr, rcol = mat.ranks()
+    act = np.nonzero(rc.pairs.active)[0]
+    ro = np.array([rc.row["rank"][tc] for tc in act])
+    co = np.array([rc.col["rank"][tc] for tc in act])
+    assert np.mean(rr[act] != ro) <= tol["rank_slack"] and np.mean(rcol[act] != co) <= tol["rank_slack"]
+    x = x_vector(rc.tree.n)
+    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
+    assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision == "mixed" else 0)

@@ -9,7 +9,7 @@ import synth
 from oracle.dense_compress import ancestors, dense_singular_values, explicit_Gtc
 from oracle.geometry import Discretisation
 from oracle.interp import InterpolatedDH2
-from oracle.recompress import RANK_BLOCKREL, RANK_GLOBAL, Recompression, choose_rank
+from oracle.recompress import RANK_BLOCKREL, RANK_GLOBAL, RANK_SPECTRAL, Recompression, choose_rank
 from oracle.structure import build_block_tree, build_cluster_tree, build_directions
 from tests.cases import mesh, params
 
@@ -101,6 +101,40 @@ def test_choose_rank_rules():
     assert choose_rank(s, 1e-2, RANK_GLOBAL) == 2
     assert choose_rank(10 * s, 1e-4, RANK_GLOBAL) == 3
     assert choose_rank(np.zeros(0), 1e-4) == 0
+    # spectral norm: the best rank-k error is sigma_{k+1}, so k = #{sigma_i > eps}
+    assert choose_rank(s, 1e-4, RANK_SPECTRAL) == 3
+    assert choose_rank(s, 1e-2, RANK_SPECTRAL) == 2
+    assert choose_rank(s, 0.1, RANK_SPECTRAL) == 1      # sigma_2 = eps is allowed to go
+    assert choose_rank(s, 2.0, RANK_SPECTRAL) == 0
+    assert choose_rank(np.zeros(0), 1e-4, RANK_SPECTRAL) == 0
+
+
+@pytest.mark.parametrize("name", ["dir320", "mixed1280"])
+def test_spectral_rule_leaf_projection_error(name):
+    """Spectral-norm error control: on every leaf pair the new basis Q leaves
+    |G_tc - Q Q^* G_tc|_2 <= eps for the explicitly assembled weighted G_tc (numpy 2-norm,
+    independent of the oracle's SVD path), and one column fewer would not; the ranks never
+    exceed those of the Frobenius rule (sigma_{k+1} <= (sum_{i>k} sigma_i^2)^(1/2))."""
+    rs = _rc(name, rule=RANK_SPECTRAL)
+    rf = _rc(name)
+    checked = 0
+    for t, c, tc in _active(rs):
+        assert rs.row["rank"][tc] <= rf.row["rank"][tc]
+        assert rs.col["rank"][tc] <= rf.col["rank"][tc]
+        if not rs.tree.is_leaf(t):
+            continue
+        G = explicit_Gtc(rs, t, c, True)
+        if G.shape[1] == 0:
+            continue
+        Q = rs.row["Q"][tc]
+        k = Q.shape[1]
+        err = np.linalg.norm(G - Q @ (Q.conj().T @ G), 2)
+        assert err <= rs.eps * (1 + 1e-8) + 1e-14
+        if k > 0:
+            Qm = Q[:, : k - 1]
+            assert np.linalg.norm(G - Qm @ (Qm.conj().T @ G), 2) > rs.eps
+        checked += 1
+    assert checked > 0
 
 
 @pytest.mark.parametrize("name", CASES)
