@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form")
     ap.add_argument("--error-rows", type=int, default=256)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched build")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the host-buffer end-to-end builds (a second matrix may not fit beside the first)")
     ap.add_argument("--batch-meshes", type=int, default=64)
     return ap.parse_args()
 
@@ -407,6 +409,8 @@ def main():
         build_s, step_ms = float(t[0]), float(t[1])
     mat = mats[-1]
     info = mat.get_info()
+    free_b, total_b = torch.cuda.mem_get_info()
+    device_used_gb = (total_b - free_b) / 1e9
 
     # matvec throughput: algorithmic bytes / device time, repeated launches
     mv_rep_ms = matvec_repeat_ms(torch, mat, x_dev, 20, stream)
@@ -438,7 +442,7 @@ def main():
     # e2e: host mesh in, host vector in/out, through the C ABI
     xh = np.ascontiguousarray(x.astype(np.complex128))
     e2e = []
-    for i in range(1 + min(args.steps, 3)):
+    for i in range(0 if args.no_e2e else 1 + min(args.steps, 3)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         m2 = gpu_build(pkg, v, f, cfg, precision, None)
@@ -502,8 +506,9 @@ def main():
             "plain_fp64": fp64,
             "batch": batch,
             "cpu_baseline": baseline,
-            "e2e": {"value": float(np.mean(e2e)), "unit": "s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+            "e2e": ({"value": float(np.mean(e2e)), "unit": "s", "h2d_bytes_per_step": int(h2d),
+                     "d2h_bytes_per_step": int(d2h)} if e2e else None),
+            "device_memory_used_gb": device_used_gb,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(),
             "wall_s_timed_region": t_wall,
