@@ -347,7 +347,9 @@ template <int NT>
 struct TcTile {
     static constexpr int KC = NT <= 128 ? 32 : 16;
     static constexpr int RP = NT / 2;
-    static constexpr size_t kOperandBytes = (size_t)4 * (128 + NT) * KC * sizeof(float);
+    // B operands use the padded layout (kmaj_off_pad): (NT/8)*32 + 4 floats per K group
+    static constexpr int BSZ = (KC / 4) * ((NT / 8) * 32 + 4);
+    static constexpr size_t kOperandBytes = ((size_t)4 * 128 * KC + (size_t)4 * BSZ) * sizeof(float);
 };
 
 constexpr int kTcWaitPolls = 1 << 22;
@@ -363,15 +365,15 @@ struct TcState {
 template <int NT>
 __device__ __forceinline__ void tc_operands(float* buf, float*& A1h, float*& A1l, float*& A2h, float*& A2l,
                                             float*& B1h, float*& B1l, float*& B2h, float*& B2l) {
-    constexpr int KC = TcTile<NT>::KC;
+    constexpr int KC = TcTile<NT>::KC, BSZ = TcTile<NT>::BSZ;
     A1h = buf;
     A1l = A1h + 128 * KC;
     A2h = A1l + 128 * KC;
     A2l = A2h + 128 * KC;
     B1h = A2l + 128 * KC;
-    B1l = B1h + NT * KC;
-    B2h = B1l + NT * KC;
-    B2l = B2h + NT * KC;
+    B1l = B1h + BSZ;
+    B2h = B1l + BSZ;
+    B2l = B2h + BSZ;
 }
 
 // D (TMEM columns [col0, col0 + NT)) = sum over K chunks of the generated operands.
@@ -394,7 +396,7 @@ __device__ void tc_product(TcState& st, uint32_t col0, int K, const GA& genA, co
         __syncthreads();
         if (threadIdx.x == 0) {
             tc::fence_after_sync();
-            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (NT / 8) * 128, sbo = 128;
+            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (NT / 8) * 128 + 16, sbo = 128;
             const uint32_t idesc = tc::idesc_tf32(128, NT);
             const float* As[6] = {A1h, A1h, A1l, A2h, A2h, A2l};
             const float* Bs[6] = {B1h, B1l, B1h, B2h, B2l, B2h};
@@ -438,8 +440,8 @@ __device__ void tc_end(TcState& st, unsigned* err) {
 }
 
 // Operand generators.  A chunk of an M = 128 operand is written at float offset idx
-// (core matrices in order); the two halves of an N = NT operand at kmaj_off(i, kk, NT) and
-// kmaj_off(i + RP, kk, NT).
+// (core matrices in order); the two halves of an N = NT operand at kmaj_off_pad(i, kk, NT)
+// and kmaj_off_pad(i + RP, kk, NT) (padded layout, leading byte offset (NT/8) * 128 + 16).
 
 // Coupling operand A[nu][mu] = S(nu, mu) (rows pass) or S(mu, nu) (cols pass) from two
 // node tables in shared memory: P[nu] holds the node on the row side of A, Q[mu] the node on
@@ -552,7 +554,7 @@ struct GenRowsB {
             const int i = (core % (RP / 8)) * 8 + (w >> 2), kk = (core / (RP / 8)) * 4 + (w & 3);
             const int mu = mu0 + kk;
             const cx<float> r = (i < ro && mu < k) ? Rm[(int64_t)i * k + mu] : zero<float>();
-            const int o0 = tc::kmaj_off(i, kk, NT), o1 = tc::kmaj_off(i + RP, kk, NT);
+            const int o0 = tc::kmaj_off_pad(i, kk, NT), o1 = tc::kmaj_off_pad(i + RP, kk, NT);
             tc::split_tf32(r.x, B1h[o0], B1l[o0]);
             tc::split_tf32(r.y, B1h[o1], B1l[o1]);
             tc::split_tf32(s * r.y, B2h[o0], B2l[o0]);
@@ -587,7 +589,7 @@ struct GenFromTmem {
             for (int jj = 0; jj < 16; ++jj) {
                 const int j = c0 + jj;
                 const float dr = j < ro ? re[jj] : 0.0f, di = j < ro ? im[jj] : 0.0f;
-                const int o0 = tc::kmaj_off(j, sub, NT), o1 = tc::kmaj_off(j + RP, sub, NT);
+                const int o0 = tc::kmaj_off_pad(j, sub, NT), o1 = tc::kmaj_off_pad(j + RP, sub, NT);
                 tc::split_tf32(dr, B1h[o0], B1l[o0]);
                 tc::split_tf32(-di, B1h[o1], B1l[o1]);
                 tc::split_tf32(di, B2h[o0], B2l[o0]);

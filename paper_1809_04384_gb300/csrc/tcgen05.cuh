@@ -25,6 +25,13 @@ __host__ __device__ __forceinline__ int kmaj_off(int r, int k, int R) {
     return ((k >> 2) * (R >> 3) + (r >> 3)) * 32 + (r & 7) * 4 + (k & 3);
 }
 
+// The same layout with 4 spare floats (16 B) after every K-direction group of core
+// matrices: leading byte offset (R/8) * 128 + 16.  Stores whose K index runs across the
+// lanes of a warp then fall into different banks.
+__host__ __device__ __forceinline__ int kmaj_off_pad(int r, int k, int R) {
+    return (k >> 2) * ((R >> 3) * 32 + 4) + (r >> 3) * 32 + (r & 7) * 4 + (k & 3);
+}
+
 // shared-memory matrix descriptor: start address, leading / stride byte offsets (16-byte
 // units), descriptor version 1, base offset 0, no swizzle
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
