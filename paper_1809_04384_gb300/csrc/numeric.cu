@@ -475,7 +475,10 @@ struct GenS {
     __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
         constexpr int KC = TcTile<NT>::KC;
         constexpr int GROUPS = KC / 4;                          // 4-wide groups of a chunk
-        for (int w = threadIdx.x; w < 128 * GROUPS; w += blockDim.x) {
+        constexpr int IT = 128 * GROUPS / kThreads;             // the block has kThreads threads
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int w = threadIdx.x + it * kThreads;
             const int nu = w & 127, g = w >> 7;
             const float4 p = P[nu];
             float4 h1, l1, h2, l2;
@@ -530,12 +533,19 @@ struct GenRowsA {
     int rows, ld, kmax;
     __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
         constexpr int KC = TcTile<NT>::KC;
-        for (int idx = threadIdx.x; idx < 128 * KC; idx += blockDim.x) {
-            const int core = idx >> 5, w = idx & 31;
+        constexpr int IT = 128 * KC / kThreads;
+        cx<float> v[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {   // all loads of the chunk in flight together
+            const int idx = threadIdx.x + it * kThreads, core = idx >> 5, w = idx & 31;
             const int a = (core & 15) * 8 + (w >> 2), mu = mu0 + (core >> 4) * 4 + (w & 3);
-            const cx<float> v = (a < rows && mu < kmax) ? X[(int64_t)a * ld + mu] : zero<float>();
-            tc::split_tf32(v.x, A1h[idx], A1l[idx]);
-            tc::split_tf32(v.y, A2h[idx], A2l[idx]);
+            v[it] = (a < rows && mu < kmax) ? X[(int64_t)a * ld + mu] : zero<float>();
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int idx = threadIdx.x + it * kThreads;
+            tc::split_tf32(v[it].x, A1h[idx], A1l[idx]);
+            tc::split_tf32(v[it].y, A2h[idx], A2l[idx]);
         }
     }
 };
@@ -549,11 +559,19 @@ struct GenRowsB {
     float s;
     __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
         constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
-        for (int idx = threadIdx.x; idx < RP * KC; idx += blockDim.x) {
-            const int core = idx >> 5, w = idx & 31;
+        constexpr int IT = RP * KC / kThreads;
+        cx<float> rv[IT];
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {   // all loads of the chunk in flight together
+            const int idx = threadIdx.x + it * kThreads, core = idx >> 5, w = idx & 31;
+            const int i = (core % (RP / 8)) * 8 + (w >> 2), mu = mu0 + (core / (RP / 8)) * 4 + (w & 3);
+            rv[it] = (i < ro && mu < k) ? Rm[(int64_t)i * k + mu] : zero<float>();
+        }
+#pragma unroll
+        for (int it = 0; it < IT; ++it) {
+            const int idx = threadIdx.x + it * kThreads, core = idx >> 5, w = idx & 31;
             const int i = (core % (RP / 8)) * 8 + (w >> 2), kk = (core / (RP / 8)) * 4 + (w & 3);
-            const int mu = mu0 + kk;
-            const cx<float> r = (i < ro && mu < k) ? Rm[(int64_t)i * k + mu] : zero<float>();
+            const cx<float> r = rv[it];
             const int o0 = tc::kmaj_off_pad(i, kk, NT), o1 = tc::kmaj_off_pad(i + RP, kk, NT);
             tc::split_tf32(r.x, B1h[o0], B1l[o0]);
             tc::split_tf32(r.y, B1h[o1], B1l[o1]);
