@@ -2292,7 +2292,7 @@ void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>*
 template <class T>
 void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s,
                   const char* where) {
-    check_err(s, where);   // inputs of this QR
+    (void)where;   // the device error word is sticky: the stage that ran this QR reads it once
     const bool fp64 = std::is_same<T, double>::value || bp_.qr_fp64;
     if (fp64) {
         if (tsqr_smem_bytes<double, 1>(k_) > 200 * 1024)
@@ -2303,7 +2303,6 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
     } else {
         tsqr_tree<T, float, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
     }
-    check_err(s, where);
 }
 
 // ----------------------------------------------------------------------------- basis weights
@@ -2367,6 +2366,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
     std::vector<int32_t> rr(rR_.begin(), rR_.end());
     upload_vec(rR_d_, rr, s);
     upload_vec(offR_d_, offR_, s);
+    check_err(s, "basis weights");
 }
 
 // ----------------------------------------------------------------------------- total weights
@@ -2500,6 +2500,7 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
             tsqr(qtasks, stack.p, Z_[pass].p, s, pass == 0 ? "total weights (rows)" : "total weights (columns)");
         }
     }
+    check_err(s, pass == 0 ? "total weights (rows)" : "total weights (columns)");
 }
 
 // ----------------------------------------------------------------------------- truncation
