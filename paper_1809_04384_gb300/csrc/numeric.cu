@@ -936,6 +936,7 @@ __global__ void __launch_bounds__(256, 3) k_tsqr_cols(const QRTask* __restrict__
     const QRTask tk = tasks[blockIdx.x];
     const int nc = tk.ncols;
     const int col = threadIdx.x / TPC, sub = threadIdx.x % TPC;
+    const int warp = threadIdx.x >> 5;
     const bool mine = col < nc;
     cx<float>* R = scratch + (int64_t)blockIdx.x * kl * kl;
     for (int idx = threadIdx.x; idx < nc * nc; idx += blockDim.x) R[idx] = zero<float>();
@@ -957,7 +958,13 @@ __global__ void __launch_bounds__(256, 3) k_tsqr_cols(const QRTask* __restrict__
             w[i] = v;
         }
         cx<float> rj = mine ? R[col] : zero<float>();   // R[j][col] for j = 0
-        for (int j = 0; j < nc; ++j) {
+        // Step j involves the warps that hold a column >= j: [fa, nwv) with fa the warp of
+        // column j.  A warp whose columns are all < j is done with this chunk and leaves the
+        // loop; the others meet at named barrier 1 with exactly that many threads.
+        const int nwv = (nc * TPC + 31) / 32;
+        for (int j = 0; j < nc && warp < nwv; ++j) {
+            const int fa = (j * TPC) / 32;
+            if (warp < fa) break;
             const int b = j & 1;
             const cx<float> rnext = (mine && j + 1 < nc) ? R[(j + 1) * nc + col] : zero<float>();
             float4* vq = reinterpret_cast<float4*>(&vbuf[b][sub * SL]);
@@ -997,7 +1004,7 @@ __global__ void __launch_bounds__(256, 3) k_tsqr_cols(const QRTask* __restrict__
                     if (sub == 0) taub[b] = zero<float>();
                 }
             }
-            __syncthreads();
+            asm volatile("bar.sync 1, %0;" :: "r"(32 * (nwv - fa)) : "memory");
             if (mine && col > j) {
                 const cx<float> tauc = taub[b];
                 cx<float> d4[4] = {zero<float>(), zero<float>(), zero<float>(), zero<float>()};
@@ -2148,11 +2155,23 @@ void Num<T>::nearfield(cudaStream_t s) {
     near_.zero(s);
     colidx_.alloc(std::max<int64_t>(ncol, 1));
     colidx_.zero(s);
-    const double s15 = std::sqrt(15.0);
-    const double w7[7] = {9.0 / 40.0,           (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0,
-                          (155.0 - s15) / 1200.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0,
-                          (155.0 + s15) / 1200.0};
-    DH2_CHECK_CUDA(cudaMemcpyToSymbol(c_w7, w7, sizeof(w7)));
+    {
+        // weights of the 7-point rule, to constant memory once per device
+        static std::mutex mu;
+        static bool ready[64] = {};
+        int dev = 0;
+        DH2_CHECK_CUDA(cudaGetDevice(&dev));
+        DH2_REQUIRE(dev < 64, "nearfield: device ordinal >= 64");
+        std::lock_guard<std::mutex> lk(mu);
+        if (!ready[dev]) {
+            const double s15 = std::sqrt(15.0);
+            const double w7[7] = {9.0 / 40.0,           (155.0 - s15) / 1200.0, (155.0 - s15) / 1200.0,
+                                  (155.0 - s15) / 1200.0, (155.0 + s15) / 1200.0, (155.0 + s15) / 1200.0,
+                                  (155.0 + s15) / 1200.0};
+            DH2_CHECK_CUDA(cudaMemcpyToSymbol(c_w7, w7, sizeof(w7)));
+            ready[dev] = true;
+        }
+    }
     QuadRows<T> qr{};
     if constexpr (std::is_same<T, float>::value) {
         qh_.alloc(9 * n_);
@@ -2167,14 +2186,13 @@ void Num<T>::nearfield(cudaStream_t s) {
         DH2_CHECK_LAUNCH("k_cluster_quad");
         qr.x = x3c_.p;
     }
-    const int64_t chunk = 1 << 22;
+    DBuf<NearSeg> dseg;
+    upload_vec(dseg, all, s);
+    const int64_t chunk = 1 << 22;   // segments (CTAs) per launch
     for (int64_t b0 = 0; b0 < (int64_t)all.size(); b0 += chunk) {
         int64_t cnt = std::min<int64_t>(chunk, (int64_t)all.size() - b0);
-        std::vector<NearSeg> part(all.begin() + b0, all.begin() + b0 + cnt);
-        DBuf<NearSeg> d;
-        upload_vec(d, part, s);
         ev_.begin(K_NEARFIELD, s);
-        k_nearfield<T><<<(unsigned)cnt, kThreads, 0, s>>>(d.p, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
+        k_nearfield<T><<<(unsigned)cnt, kThreads, 0, s>>>(dseg.p + b0, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
                                                           tr_.x7.p, bp_.kappa, near_.p, colidx_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_nearfield");
