@@ -581,15 +581,18 @@ struct GenRowsB {
     }
 };
 
-// B from the TMEM tile D1 (rows nu, real parts in columns [0, RP), imaginary in [RP, NT))
-// of the rows-pass product, for K[a][j] = sum_nu R_t[a][nu] conj(D1[nu][j]):
-// B1[j] = Re D1[.][j], B1[j+RP] = -Im D1[.][j], B2[j] = Im D1[.][j], B2[j+RP] = Re D1[.][j].
+// B from the TMEM tile D1 (rows nu, real parts in columns [0, RP), imaginary in [RP, NT)):
+//   conj_d = true  (X conj(D1), X = A1 + i A2):
+//     B1[j] = Re D1[.][j], B1[j+RP] = -Im D1[.][j], B2[j] = Im D1[.][j], B2[j+RP] = Re D1[.][j];
+//   conj_d = false (conj(X) D1):
+//     B1[j] = Re D1[.][j], B1[j+RP] =  Im D1[.][j], B2[j] = Im D1[.][j], B2[j+RP] = -Re D1[.][j].
 // The rows nu of a chunk live in TMEM lanes that only warps (chunk quarter) and
 // (quarter + 4) may read; each of the two reads half of the columns j.
 template <int NT>
 struct GenFromTmem {
     uint32_t d1;   // TMEM address of D1 (lane 0, first column)
     int ro;
+    bool conj_d;
     __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
         constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -609,9 +612,9 @@ struct GenFromTmem {
                 const float dr = j < ro ? re[jj] : 0.0f, di = j < ro ? im[jj] : 0.0f;
                 const int o0 = tc::kmaj_off_pad(j, sub, NT), o1 = tc::kmaj_off_pad(j + RP, sub, NT);
                 tc::split_tf32(dr, B1h[o0], B1l[o0]);
-                tc::split_tf32(-di, B1h[o1], B1l[o1]);
+                tc::split_tf32(conj_d ? -di : di, B1h[o1], B1l[o1]);
                 tc::split_tf32(di, B2h[o0], B2l[o0]);
-                tc::split_tf32(dr, B2h[o1], B2l[o1]);
+                tc::split_tf32(conj_d ? dr : -dr, B2h[o1], B2l[o1]);
             }
         }
     }
@@ -656,7 +659,7 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const fl
     const int rt = rrows[tk.own];
     const cx<float>* Rt = R + roff[tk.own];
     cx<float>* Kb = Kst + tk.koff;
-    tc_product<NT>(st, NT, k, GenRowsA<NT>{Rt, rt, k, k}, GenFromTmem<NT>{st.tmem, ro});
+    tc_product<NT>(st, NT, k, GenRowsA<NT>{Rt, rt, k, k}, GenFromTmem<NT>{st.tmem, ro, true});
     // K_b (rows a = TMEM lanes, columns j < ro) and |K_b|_F
     float acc = 0.0f;
     if (st.ok) {
@@ -1464,6 +1467,57 @@ __global__ void __launch_bounds__(256, 2) k_project(const ProjTask* __restrict__
     }
 }
 
+// Projection of a block whose clusters are not both leaves on the tensor cores (k <= 128,
+// FP32 data): D1 = (C_t S_b)^T (TMEM columns [0, NT)), then D2 = conj(C_s) D1 (columns
+// [NT, 2 NT)), so that S~_b = C_t S_b C_s^* has S~[i][j] = D2[j][i].  One task per CTA.
+template <int NT>
+__global__ void __launch_bounds__(256, 2) k_project_tc(const ProjTask* __restrict__ tasks,
+                                                       const int32_t* __restrict__ adm_t,
+                                                       const int32_t* __restrict__ adm_s,
+                                                       const int32_t* __restrict__ adm_c,
+                                                       const int32_t* __restrict__ tc_level,
+                                                       const int32_t* __restrict__ dir_off,
+                                                       const double* __restrict__ dirs,
+                                                       const double* __restrict__ nodes, int m, double kappa,
+                                                       const cx<float>* __restrict__ Crow,
+                                                       const cx<float>* __restrict__ Ccol, cx<float>* Stilde,
+                                                       unsigned* err) {
+    extern __shared__ unsigned char smraw[];
+    __shared__ __align__(8) uint64_t tc_mbar;
+    __shared__ uint32_t tc_tmem;
+    constexpr int RP = TcTile<NT>::RP;
+    const ProjTask tk = tasks[blockIdx.x];
+    const int k = m * m * m;
+    const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
+    const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
+    float4* Ptab = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
+    float4* Qtab = Ptab + 128;
+    float* tcbuf = reinterpret_cast<float*>(Qtab + 128);
+    load_node_tables(t, s, cd, nodes, m, false, Ptab, Qtab);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, half = warp >> 2;
+    const int row = 32 * q + lane;
+    const int kt = tk.kt, ks = tk.ks;
+    TcState st;
+    tc_begin<NT>(st, tcbuf, &tc_mbar, &tc_tmem);
+    tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, (float)kappa}, GenRowsB<NT>{Crow + tk.crow, kt, k, -1.0f});
+    tc_product<NT>(st, NT, k, GenRowsA<NT>{Ccol + tk.ccol, ks, k, k}, GenFromTmem<NT>{st.tmem, kt, false});
+    if (st.ok) {
+        const uint32_t trow = st.tmem + ((uint32_t)(32 * q) << 16);
+        cx<float>* out = Stilde + tk.dst;
+        for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < kt; c0 += 16) {
+            float re[16], im[16];
+            tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
+            tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
+            if (row < ks)
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    if (c0 + i < kt) out[(int64_t)(c0 + i) * ks + row] = cx<float>{re[i], im[i]};
+        }
+    }
+    tc_end<NT>(st, err);
+}
+
 // ----------------------------------------------------------------------------- matvec kernels
 
 template <class T, class TX>
@@ -1936,6 +1990,8 @@ private:
     void total_weights(int pass, cudaStream_t s);
     template <int NT>
     void launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pass, cx<T>* stack, cudaStream_t s);
+    template <int NT>
+    void launch_project_tc(const std::vector<ProjTask>& tasks, cudaStream_t s);
     void truncate(int pass, cudaStream_t s);
     void project(cudaStream_t s);
     void plan_matvec(cudaStream_t s);
@@ -2651,6 +2707,23 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
 // ----------------------------------------------------------------------------- projection
 
 template <class T>
+template <int NT>
+void Num<T>::launch_project_tc(const std::vector<ProjTask>& tasks, cudaStream_t s) {
+    if (tasks.empty()) return;
+    if constexpr (std::is_same<T, float>::value) {
+        DBuf<ProjTask> d;
+        upload_vec(d, tasks, s);
+        const size_t smem = 128 + 2 * 128 * sizeof(float4) + TcTile<NT>::kOperandBytes;
+        auto kern = k_project_tc<NT>;
+        ensure_smem(reinterpret_cast<const void*>(kern), smem);
+        kern<<<(unsigned)tasks.size(), kThreads, smem, s>>>(d.p, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p,
+                                                          st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_, bp_.kappa,
+                                                          Ct_[0].p, Ct_[1].p, St_.p, err_.p);
+        DH2_CHECK_LAUNCH("k_project_tc");
+    }
+}
+
+template <class T>
 void Num<T>::project(cudaStream_t s) {
     const auto& h = hs_;
     const int64_t nb = (int64_t)h.adm_t.size();
@@ -2700,9 +2773,30 @@ void Num<T>::project(cudaStream_t s) {
     info.coupling_entries = off;
     St_.alloc(std::max<int64_t>(off, 1));
     if (nb == 0) return;
+    if constexpr (std::is_same<T, float>::value) {
+        if (bp_.tensor_cores && k_ <= 128) {
+            // blocks whose clusters are not both leaves: tensor-core tiles by k_t
+            std::vector<ProjTask> rest, cls[3];
+            for (const ProjTask& p : pt) {
+                if (p.leafpair || p.kt == 0 || p.ks == 0) rest.push_back(p);
+                else cls[p.kt <= 32 ? 0 : p.kt <= 64 ? 1 : 2].push_back(p);
+            }
+            ev_.begin(K_PROJECT, s);
+            launch_project_tc<64>(cls[0], s);
+            launch_project_tc<128>(cls[1], s);
+            launch_project_tc<256>(cls[2], s);
+            ev_.end(s);
+            pt.swap(rest);
+        }
+    }
+    const int64_t np_ = (int64_t)pt.size();
+    if (np_ == 0) {
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        return;
+    }
     DBuf<ProjTask> d;
     upload_vec(d, pt, s);
-    const int64_t grid = std::min<int64_t>(nb, 152 * 8);
+    const int64_t grid = std::min<int64_t>(np_, 152 * 8);
     DBuf<cx<T>> scratch((size_t)grid * k_ * k_);
     const cx<T>* Crow;
     const cx<T>* Ccol;
@@ -2715,7 +2809,7 @@ void Num<T>::project(cudaStream_t s) {
     }
     const size_t smem = sgen_smem_bytes<T>(m_);
     ev_.begin(K_PROJECT, s);
-    k_project<T><<<(unsigned)grid, kThreads, smem, s>>>(d.p, nb, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
+    k_project<T><<<(unsigned)grid, kThreads, smem, s>>>(d.p, np_, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
                                                         tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
                                                         bp_.kappa, Crow, Ccol, K_.p, Up_[0].p, Up_[1].p, scratch.p,
                                                         St_.p);
