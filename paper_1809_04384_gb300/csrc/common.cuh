@@ -29,8 +29,11 @@ struct Error {
                                std::string(#call) + ": " + cudaGetErrorString(e_)};   \
     } while (0)
 
-// every kernel launch of the library is followed by DH2_CHECK_LAUNCH, which also counts it
+// every kernel launch of the library is followed by DH2_CHECK_LAUNCH, which also counts it;
+// graph replays add their kernels, graph captures take theirs back
 void count_launch();
+void count_launches(int64_t n);
+void uncount_launches(int64_t n);
 #define DH2_CHECK_LAUNCH(name)                                                        \
     do {                                                                              \
         ::dh2::count_launch();                                                        \

@@ -1720,7 +1720,9 @@ struct LeafOut2 {
 // y[perm[r]] = sum_c Q_tc y^_tc + nearfield row panel: one CTA per leaf.  The x~ values of a
 // chunk of panel columns are gathered into shared memory once; each warp then streams its rows
 // with 16-byte loads (lane-partial sums kept in registers for up to 8 rows per warp).
-template <class T, class TY>
+// MODE 0: both parts; MODE 1: the nearfield part only (y = panel x~); MODE 2: the leaf-basis
+// part only, added to y (y += Q y^), so that the nearfield can run beside the transforms.
+template <class T, class TY, int MODE>
 __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ leaves,
                                                    const LeafQ* __restrict__ qitems,
                                                    const int32_t* __restrict__ colidx,
@@ -1736,7 +1738,7 @@ __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ 
         cx<T> acc[RW];
 #pragma unroll
         for (int q = 0; q < RW; ++q) acc[q] = zero<T>();
-        for (int c0 = 0; c0 < lf.ld; c0 += CH) {
+        for (int c0 = 0; c0 < (MODE == 2 ? 0 : lf.ld); c0 += CH) {
             const int w = min(CH, lf.ld - c0);
             for (int j = threadIdx.x; j < w; j += blockDim.x) xg[j] = xt[colidx[lf.coff + c0 + j]];
             __syncthreads();
@@ -1769,13 +1771,19 @@ __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ 
             const int i = r0 + warp + 8 * q;
             if (i >= lf.rows) break;
             cx<T> a = acc[q];
-            for (int e = lf.qbeg; e < lf.qend; ++e) {
-                const LeafQ it = qitems[e];
-                const cx<T>* row = Q + it.q + (int64_t)i * it.ld;
-                for (int r = lane; r < it.k; r += 32) fma_cx(a, row[r], yh[it.yh + r]);
+            if (MODE != 1) {
+                for (int e = lf.qbeg; e < lf.qend; ++e) {
+                    const LeafQ it = qitems[e];
+                    const cx<T>* row = Q + it.q + (int64_t)i * it.ld;
+                    for (int r = lane; r < it.k; r += 32) fma_cx(a, row[r], yh[it.yh + r]);
+                }
             }
             a = warp_sum(a);
-            if (lane == 0) y[perm[lf.off + i]] = cx<TY>{TY(a.x), TY(a.y)};
+            if (lane == 0) {
+                cx<TY>& yo = y[perm[lf.off + i]];
+                if (MODE == 2) yo = cx<TY>{yo.x + TY(a.x), yo.y + TY(a.y)};
+                else yo = cx<TY>{TY(a.x), TY(a.y)};
+            }
         }
     }
 }
@@ -1900,6 +1908,14 @@ public:
 
     void build(cudaStream_t s) override;
     void matvec(const void* x, void* y, int dtype, cudaStream_t s) override;
+    ~Num() override {
+        for (auto& g : graph_)
+            if (g.exec) cudaGraphExecDestroy(g.exec);
+        if (capture_stream_) cudaStreamDestroy(capture_stream_);
+        if (side_stream_) cudaStreamDestroy(side_stream_);
+        if (fork_ev_) cudaEventDestroy(fork_ev_);
+        if (join_ev_) cudaEventDestroy(join_ev_);
+    }
     void matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) override;
     void export_pair(int which, int64_t tc, double* out, int64_t cap, int32_t* rows, int32_t* cols,
                      cudaStream_t s) override;
@@ -1992,6 +2008,15 @@ private:
     void launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pass, cx<T>* stack, cudaStream_t s);
     template <int NT>
     void launch_project_tc(const std::vector<ProjTask>& tasks, cudaStream_t s);
+    void launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bool split = false);
+    struct MatvecGraph {
+        cudaGraphExec_t exec = nullptr;
+        DBuf<unsigned char> x, y;   // the graph's input and output vectors
+        int64_t nodes = 0;          // kernels per replay
+    };
+    MatvecGraph graph_[2];          // complex64, complex128 vectors
+    cudaStream_t capture_stream_ = nullptr, side_stream_ = nullptr;
+    cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
     void truncate(int pass, cudaStream_t s);
     void project(cudaStream_t s);
     void plan_matvec(cudaStream_t s);
@@ -3031,8 +3056,56 @@ void Num<T>::build(cudaStream_t s) {
 
 // ----------------------------------------------------------------------------- matvec
 
+// y = G~ x.  Without per-kernel timing the product runs as a CUDA graph: its ~40 launches
+// (one per tree level for the transforms) are captured once per precision, on an internal
+// stream, against internal copies of x and y, and replayed on the caller's stream between
+// two device copies of n values; the graph's parameters never change.
 template <class T>
 void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
+    if (timing_on_) {
+        launch_matvec(x, y, dtype, s);
+        return;
+    }
+    const int di = dtype == DH2_C64 ? 0 : 1;
+    const size_t bytes = (size_t)n_ * (dtype == DH2_C64 ? sizeof(cx<float>) : sizeof(cx<double>));
+    MatvecGraph& mg = graph_[di];
+    if (!mg.exec) {
+        mg.x.alloc(bytes);
+        mg.y.alloc(bytes);
+        if (!capture_stream_) DH2_CHECK_CUDA(cudaStreamCreateWithFlags(&capture_stream_, cudaStreamNonBlocking));
+        if (!side_stream_) {
+            DH2_CHECK_CUDA(cudaStreamCreateWithFlags(&side_stream_, cudaStreamNonBlocking));
+            DH2_CHECK_CUDA(cudaEventCreateWithFlags(&fork_ev_, cudaEventDisableTiming));
+            DH2_CHECK_CUDA(cudaEventCreateWithFlags(&join_ev_, cudaEventDisableTiming));
+        }
+        cudaGraph_t graph = nullptr;
+        DH2_CHECK_CUDA(cudaStreamBeginCapture(capture_stream_, cudaStreamCaptureModeThreadLocal));
+        try {
+            launch_matvec(mg.x.p, mg.y.p, dtype, capture_stream_, true);
+        } catch (...) {
+            cudaStreamEndCapture(capture_stream_, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        DH2_CHECK_CUDA(cudaStreamEndCapture(capture_stream_, &graph));
+        size_t nodes = 0;   // every node is one captured kernel launch
+        cudaGraphGetNodes(graph, nullptr, &nodes);
+        mg.nodes = (int64_t)nodes;
+        uncount_launches(mg.nodes);   // counted when captured, not launched
+        const cudaError_t e = cudaGraphInstantiate(&mg.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        DH2_CHECK_CUDA(e);
+    }
+    DH2_CHECK_CUDA(cudaMemcpyAsync(mg.x.p, x, bytes, cudaMemcpyDeviceToDevice, s));
+    DH2_CHECK_CUDA(cudaGraphLaunch(mg.exec, s));
+    DH2_CHECK_CUDA(cudaMemcpyAsync(y, mg.y.p, bytes, cudaMemcpyDeviceToDevice, s));
+    count_launches(mg.nodes);
+}
+
+// split = true (graph capture only): the nearfield part of the output runs on a side branch
+// that forks after the gather and joins before the leaf-basis part, which adds into y.
+template <class T>
+void Num<T>::launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bool split) {
     const unsigned g = grid_for(n_, kThreads);
     if (dtype == DH2_C64) {
         if (timing_on_) ev_.begin(K_MV_GATHER, s);
@@ -3045,6 +3118,18 @@ void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
         if (timing_on_) ev_.end(s);
     }
     DH2_CHECK_LAUNCH("k_gather");
+    if (split && n_leaves_) {
+        DH2_CHECK_CUDA(cudaEventRecord(fork_ev_, s));
+        DH2_CHECK_CUDA(cudaStreamWaitEvent(side_stream_, fork_ev_, 0));
+        if (dtype == DH2_C64)
+            k_leaf_out2<T, float, 1><<<(unsigned)n_leaves_, 256, 0, side_stream_>>>(
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
+        else
+            k_leaf_out2<T, double, 1><<<(unsigned)n_leaves_, 256, 0, side_stream_>>>(
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
+        DH2_CHECK_LAUNCH("k_leaf_out2 (nearfield)");
+        DH2_CHECK_CUDA(cudaEventRecord(join_ev_, side_stream_));
+    }
     constexpr int WPB = 8;   // warps per CTA of the transform kernels
     if (n_fwd_leaf_) {
         if (timing_on_) ev_.begin(K_MV_FORWARD, s);
@@ -3082,16 +3167,25 @@ void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
         }
         off += cnt;
     }
-    if (n_leaves_) {
+    if (split && n_leaves_) {
+        DH2_CHECK_CUDA(cudaStreamWaitEvent(s, join_ev_, 0));
+        if (dtype == DH2_C64)
+            k_leaf_out2<T, float, 2><<<(unsigned)n_leaves_, 256, 0, s>>>(
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
+        else
+            k_leaf_out2<T, double, 2><<<(unsigned)n_leaves_, 256, 0, s>>>(
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
+        DH2_CHECK_LAUNCH("k_leaf_out2 (leaf bases)");
+    } else if (n_leaves_) {
         if (dtype == DH2_C64) {
             if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);
-            k_leaf_out2<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
+            k_leaf_out2<T, float, 0><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                     yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
             if (timing_on_) ev_.end(s);
         }
         else {
             if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);
-            k_leaf_out2<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
+            k_leaf_out2<T, double, 0><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                      yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
             if (timing_on_) ev_.end(s);
         }
@@ -3193,10 +3287,10 @@ void Num<T>::matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) {
     }
     if (n_leaves_) {
         if (dtype == DH2_C64)
-            k_leaf_out2<T, float><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
+            k_leaf_out2<T, float, 0><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                     yh, near_.p, xt, tr_.perm.p, (cx<float>*)y);
         else
-            k_leaf_out2<T, double><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
+            k_leaf_out2<T, double, 0><<<(unsigned)n_leaves_, 256, 0, s>>>(leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p,
                                                                      yh, near_.p, xt, tr_.perm.p, (cx<double>*)y);
         DH2_CHECK_LAUNCH("k_leaf_out");
     }
