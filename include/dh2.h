@@ -71,7 +71,10 @@ typedef struct {
     int32_t tensor_cores;   /* DH2_MIXED with m <= 5: 1 (default) = coupling products of the
                                total weights on the tcgen05 tensor cores in 3xTF32 (FP32-level
                                accuracy); 0 = FP32 CUDA-core products */
-    int32_t reserved;       /* set to 0 */
+    int32_t kb_store;       /* with the tensor-core path: 0 (default) = keep the block products
+                               K_b = R_t S_b R_s^* for the column pass and the projection of leaf
+                               pairs when they take at most a quarter of the free device memory,
+                               recompute them otherwise; 1 = always keep; 2 = always recompute */
 } dh2_options;
 
 typedef struct {

@@ -33,7 +33,7 @@ _STATUS = {DH2_EINVAL: "EINVAL", DH2_ENOMEM: "ENOMEM", DH2_ECUDA: "ECUDA", DH2_E
 class dh2_options(C.Structure):
     _fields_ = [("eta1", C.c_double), ("leaf_max", C.c_int32), ("precision", C.c_int32),
                 ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("qr_group_rows", C.c_int32),
-                ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("reserved", C.c_int32)]
+                ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32)]
 
 
 class dh2_tree_info(C.Structure):
@@ -278,9 +278,10 @@ class Matrix:
     """Recompressed DH^2 matrix on the GPU (owning handle)."""
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, stream=None):
+                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
-                       qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes, tensor_cores=tensor_cores)
+                       qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes, tensor_cores=tensor_cores,
+                       kb_store=kb_store)
         self.precision = precision
         self.handle = dh2_build_dh2(tree.handle, kappa, m, eta, eps, opts, stream)
         self.info = self.get_info()

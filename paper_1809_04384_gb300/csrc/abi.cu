@@ -98,6 +98,7 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
         throw Error{DH2_EINVAL, f + ": bad rank rule"};
     if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
     if (o.tensor_cores != 0 && o.tensor_cores != 1) throw Error{DH2_EINVAL, f + ": tensor_cores must be 0 or 1"};
+    if (o.kb_store < 0 || o.kb_store > 2) throw Error{DH2_EINVAL, f + ": kb_store must be 0, 1 or 2"};
 }
 
 // The whole build of one matrix on stream s (arguments already checked); blocks until done.
@@ -120,7 +121,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->structure_ms = ms;
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
-                          o.workspace_bytes, o.tensor_cores};
+                          o.workspace_bytes, o.tensor_cores, o.kb_store};
     mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
     mat->num->build(s);
     mat->num->info.stage_ms[ST_STRUCTURE] += ms;
@@ -242,7 +243,7 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->qr_group_rows = 0;
     opt->workspace_bytes = 0;
     opt->tensor_cores = 1;
-    opt->reserved = 0;
+    opt->kb_store = 0;
     return DH2_OK;
 }
 

@@ -327,7 +327,9 @@ struct BlockRowTask {
     int32_t b;         // admissible block id
     int32_t other;     // active pair whose weight R multiplies S (rows pass: s, cols pass: t)
     int32_t own;       // active pair of the other side (rows pass: t; for |G_b|)
-    int32_t own_leaf;  // rows pass: the row cluster is a leaf (rows projected onto its basis)
+    int32_t own_leaf;  // rows pass: the row cluster is a leaf (rows projected onto its basis);
+                       // cols pass, 2: the column cluster is a leaf and K_b is not stored:
+                       // rows w K_b recomputed here (other = the s pair, own = the t pair)
     int64_t dst;       // element offset of the first row in the stack
     int64_t koff;      // rows pass: where K_b = R_t S_b R_s^* is stored
 };
@@ -638,7 +640,8 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const fl
     TcState st;
     tc_begin<NT>(st, tcbuf, mbar, tmem_slot);
     const uint32_t trow = st.tmem + ((uint32_t)(32 * q) << 16);
-    if (!rows_pass) {
+    const bool kmode = !rows_pass && tk.own_leaf == 2;   // column stack rows w K_b, recomputed
+    if (!rows_pass && !kmode) {
         const float sc_ = bnorm[tk.b] > 0.0 ? float(1.0 / bnorm[tk.b]) : 0.0f;
         tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, kappa}, GenRowsB<NT>{Ro, ro, k, -1.0f});
         if (st.ok) {
@@ -658,7 +661,7 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const fl
     tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, kappa}, GenRowsB<NT>{Ro, ro, k, 1.0f});
     const int rt = rrows[tk.own];
     const cx<float>* Rt = R + roff[tk.own];
-    cx<float>* Kb = Kst + tk.koff;
+    cx<float>* Kb = (Kst && !kmode) ? Kst + tk.koff : nullptr;   // stored only if there is a store
     tc_product<NT>(st, NT, k, GenRowsA<NT>{Rt, rt, k, k}, GenFromTmem<NT>{st.tmem, ro, true});
     // K_b (rows a = TMEM lanes, columns j < ro) and |K_b|_F
     float acc = 0.0f;
@@ -671,16 +674,31 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const fl
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                     if (c0 + j < ro) {
-                        Kb[(int64_t)row * ro + c0 + j] = cx<float>{re[j], im[j]};
+                        if (Kb) Kb[(int64_t)row * ro + c0 + j] = cx<float>{re[j], im[j]};
                         acc += re[j] * re[j] + im[j] * im[j];
                     }
         }
     }
     const float nrm = sqrtf(block_sum(acc, red));
-    if (threadIdx.x == 0) bnorm[tk.b] = (double)nrm;
+    if (threadIdx.x == 0 && !kmode) bnorm[tk.b] = (double)nrm;
     const float sc_ = nrm > 0.0f ? 1.0f / nrm : 0.0f;
     if (st.ok) {
-        if (tk.own_leaf) {
+        if (kmode) {
+            // w K_b: column-stack row a (< rt), column j (< ro), pitch k
+            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
+                tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
+                if (row < rt)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < ro) {
+                            const cx<float> v{sc_ * re[j], sc_ * im[j]};
+                            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                            out[(int64_t)row * k + c0 + j] = v;
+                        }
+            }
+        } else if (tk.own_leaf) {
             // w K_b^*: stack row j (< ro), column a (< rt), pitch k
             for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
                 float re[16], im[16];
@@ -743,7 +761,7 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
             (reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
         float4* Qtab = Ptab + 128;
         float* tcbuf = reinterpret_cast<float*>(Qtab + 128);
-        load_node_tables(t, s, cd, nodes, m, rows_pass, Ptab, Qtab);
+        load_node_tables(t, s, cd, nodes, m, rows_pass || tk.own_leaf == 2, Ptab, Qtab);
         stack_blocks_tc<NT>(tk, rows_pass, Ptab, Qtab, (float)kappa, k, Ro, ro, R, roff, rrows, bnorm, out, Kst,
                             tcbuf, &tc_mbar, &tc_tmem, red, err);
         return;
@@ -2016,6 +2034,7 @@ private:
     };
     MatvecGraph graph_[2];          // complex64, complex128 vectors
     cudaStream_t capture_stream_ = nullptr, side_stream_ = nullptr;
+    bool kstore_ = true;            // K_b kept for the column pass / leaf-pair projection
     cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
     void truncate(int pass, cudaStream_t s);
     void project(cudaStream_t s);
@@ -2486,8 +2505,8 @@ void Num<T>::launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pas
         ev_.begin(K_STACK_BLOCKS, s);
         kern<<<(unsigned)tasks.size(), kThreads, smem, s>>>(d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
                                                           tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
-                                                          bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack, K_.p,
-                                                          err_.p);
+                                                          bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack,
+                                                          kstore_ ? K_.p : nullptr, err_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_stack_blocks");
     }
@@ -2501,7 +2520,19 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
     Z_[pass].alloc(std::max<int64_t>(offZ_[pass][na_], 1));
     if (pass == 0) {
         bnorm_.alloc(std::max<int64_t>((int64_t)h.adm_t.size(), 1));
-        K_.alloc(std::max<int64_t>(offK_.back(), 1));
+        // K_b = R_t S_b R_s^* is kept for the column pass of leaf columns and the projection of
+        // leaf pairs; where the store would not fit (or on request) the tensor-core path
+        // recomputes it instead
+        kstore_ = true;
+        bool can_recompute = false;
+        if constexpr (std::is_same<T, float>::value) can_recompute = bp_.tensor_cores && k_ <= 128;
+        if (can_recompute && bp_.kb_store != 1) {
+            size_t free_b = 0, total_b = 0;
+            DH2_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+            const double bytes = (double)offK_.back() * sizeof(cx<T>);
+            kstore_ = !(bp_.kb_store == 2 || bytes > 0.25 * (double)free_b);
+        }
+        K_.alloc(kstore_ ? std::max<int64_t>(offK_.back(), 1) : 1);
     }
     const int kk = k_;
     const int64_t cap_rows = std::max<int64_t>(
@@ -2532,9 +2563,14 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                     const int32_t b = idx[e];
                     const int32_t other = pass == 0 ? h.adm_s[b] : h.adm_t[b];
                     const int32_t ao = h.pair_of(other, c);
-                    if (pass == 1 && leaf_[a]) {
+                    if (pass == 1 && leaf_[a] && kstore_) {
                         // rows w K_b (r_t x r_s) from the row pass, no coupling evaluation
                         ktasks.push_back(KRowTask{offK_[b], srow * kk, b, rR_[ao], rR_[a], 0});
+                    } else if (pass == 1 && leaf_[a]) {
+                        // the same rows, K_b recomputed on the tensor cores (other = s, own = t)
+                        btasks.push_back(BlockRowTask{b, (int32_t)a, ao, 2, srow * kk, 0});
+                        work_[K_STACK_BLOCKS] += kEvalFlops * kk * kk + 8.0 * rR_[a] * kk * kk +
+                                                 8.0 * rR_[ao] * kk * rR_[a];
                     } else {
                         btasks.push_back(BlockRowTask{b, ao, (int32_t)a, pass == 0 ? (int32_t)leaf_[a] : 0,
                                                       srow * kk, pass == 0 ? offK_[b] : 0});
@@ -2779,7 +2815,7 @@ void Num<T>::project(cudaStream_t s) {
         p.crow = offC_[0][at];
         p.ccol = offC_[1][as];
         p.dst = st_off_[b];
-        p.leafpair = leaf_[at] && leaf_[as];
+        p.leafpair = leaf_[at] && leaf_[as] && kstore_;
         if (p.leafpair) {
             p.koff = offK_[b];
             p.upt = offUp_[0][at];

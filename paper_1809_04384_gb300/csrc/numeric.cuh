@@ -31,7 +31,7 @@ struct BuildParams {
     double kappa, eta, eps;
     int32_t m, precision, rank_rule, qr_fp64, qr_group_rows;
     int64_t workspace_bytes;
-    int32_t tensor_cores;
+    int32_t tensor_cores, kb_store;
 };
 
 enum KernelId {

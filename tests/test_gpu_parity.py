@@ -262,3 +262,29 @@ def test_spectral_rank_rule_matches_oracle(precision):
     dt = torch.complex128 if precision == "fp64" else torch.complex64
     y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
     assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision == "mixed" else 0)
+
+
+@pytest.mark.parametrize("name", ["mixed1280", "dir1280"])
+def test_recomputed_block_products_match_stored(name):
+    """K_b = R_t S_b R_s^* recomputed on the tensor cores (column pass of leaf columns,
+    leaf-pair projection through C_t S_b C_s^*) instead of kept: same ranks, same product,
+    and both match the oracle."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    rc = oracle_recompression(name)
+    v, f, p, *_ = oracle_structure(name)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    mats = [dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], precision=dh2.DH2_MIXED, eta1=p["eta1"],
+                       kb_store=mode) for mode in (1, 2)]
+    x = x_vector(rc.tree.n)
+    ys = [m.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+          for m in mats]
+    r1, c1 = mats[0].ranks()
+    r2, c2 = mats[1].ranks()
+    slack = TOL["mixed"]["rank_slack"]
+    assert np.mean(r1 != r2) <= slack and np.mean(c1 != c2) <= slack
+    tol = max(TOL["mixed"]["matvec_same_ranks"], 2 * rc.eps)
+    assert rel(ys[1], ys[0]) <= tol
+    assert rel(ys[1], rc.matvec(x)) <= tol
