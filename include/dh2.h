@@ -50,6 +50,7 @@ enum { DH2_RANK_BLOCKREL = 0, DH2_RANK_GLOBAL = 1, DH2_RANK_SPECTRAL = 2 };  /* 
 
 typedef struct dh2_tree_s* dh2_tree;
 typedef struct dh2_matrix_s* dh2_matrix;
+typedef struct dh2_model_s* dh2_model;   /* learned order/rank model, see below */
 
 typedef struct {
     double eta1;            /* direction parameter eta_1 of Eq. (3a)/(4); paper: 10 (Section 5) */
@@ -75,6 +76,12 @@ typedef struct {
                                K_b = R_t S_b R_s^* for the column pass and the projection of leaf
                                pairs when they take at most a quarter of the free device memory,
                                recompute them otherwise; 1 = always keep; 2 = always recompute */
+    int32_t learned;        /* 1 = choose the interpolation order and cap the truncation ranks
+                               with `model` (see "Learned order and rank" below); the m argument
+                               of the build is then ignored.  0 (default) = the plain fixed-order
+                               method */
+    int32_t reserved0;      /* must be 0 */
+    dh2_model model;        /* the model used when learned = 1 (not owned) */
 } dh2_options;
 
 typedef struct {
@@ -104,6 +111,10 @@ typedef struct {
     double kernel_work[16]; /* algorithmic work of each kernel in one build (build kernels) or
                                one matvec (matvec kernels), in the unit of kernel_work_kind */
     int32_t kernel_work_kind[16]; /* 0 none, 1 FP32 flop, 2 FP64 flop, 3 bytes moved */
+    int32_t learned_m;      /* the order the learned model chose (0 for a plain build) */
+    int32_t rank_cap_retries; /* truncation passes redone because a rank exceeded its learned cap */
+    int64_t truncation_bytes; /* device bytes of the truncated bases of both passes as allocated
+                               (Q / F, C, U', singular values), which the learned rank caps size */
 } dh2_matrix_info;
 
 /* Fills *opt with the paper's parameters: eta1 = 10, leaf_max = 32, DH2_MIXED,
@@ -225,6 +236,73 @@ int64_t dh2_kernel_launches(void);
 
 /* Waits for `stream` and reports deferred device errors. */
 dh2_status dh2_sync(void* stream);
+
+/* ---- Learned order and rank (no counterpart in the paper) ----
+ *
+ * The paper uses one interpolation order m for the whole matrix (Section 5) and
+ * finds every rank k_tc by SVD truncation (Section 3.2).  A dh2_model is a small
+ * MLP, 8 -> 128 -> 128 -> 2 with ReLU hidden layers and a linear output, BF16
+ * weights and FP32 biases, accumulation in FP32, that maps 8 geometric features of
+ * a pair (t, c) to (m_tc / 8, k_tc / 64): the order its interpolation needs and its
+ * truncation rank.  A build with opt->learned = 1 computes the features of every
+ * pair from the block structure, evaluates the model, builds with the largest
+ * predicted order over the active pairs (the transfer matrices E of Eq. nested tie
+ * the orders of a cluster and its sons, so one order serves the matrix) and sizes
+ * the truncated bases by the predicted ranks (1.25 x + 4 columns per pair).  The
+ * SVD truncation still decides every rank: a pass in which one exceeds its cap is
+ * redone with the structural bounds (dh2_matrix_info.rank_cap_retries).
+ *
+ * Features per pair (t, c), t on level l (FP32, [npairs][8]):
+ *   f0 = kappa diam(B_t) / eta1; f1 = atan(sqrt(2) / m_l) / pi, 1 when D_l = {0};
+ *   f2 = l / depth; f3 >= f4 >= f5 = extents of B_t / diam(B_t);
+ *   f6 = log2(#t) / 16; f7 = max over the admissible blocks (t, s, c) of
+ *   diam(B_t) / dist(B_t, B_s) (0 without blocks).
+ * Labels come from the method itself: dh2_learned_probe gives the interpolation
+ * error of each pair at m = 3..8 (the order label is the smallest m whose error is
+ * <= eps / 2), and dh2_export_ranks of a plain build gives the ranks.
+ *
+ * Parameters are packed FP32: W1 [128][8], b1 [128], W2 [128][128], b2 [128],
+ * W3 [2][128], b3 [2] (DH2_MLP_NPARAMS values).  All device arrays are row-major.
+ */
+enum { DH2_MLP_IN = 8, DH2_MLP_HIDDEN = 128, DH2_MLP_OUT = 2, DH2_MLP_NPARAMS = 17922, DH2_PROBE_ORDERS = 6 };
+
+/* Creates a model on the current device from HOST parameters (copied).  Errors:
+ * DH2_EINVAL for NULL pointers or non-finite parameters; DH2_ENOMEM; DH2_ECUDA. */
+dh2_status dh2_model_create(const float* params, void* stream, dh2_model* out);
+/* Copies the FP32 master parameters to HOST memory (DH2_MLP_NPARAMS floats). */
+dh2_status dh2_model_get_params(dh2_model model, float* params);
+/* Y = MLP(X): X DEVICE FP32 [n][8], Y DEVICE FP32 [n][2]; asynchronous on `stream`.
+ * n = 0 does nothing.  Errors: DH2_EINVAL (NULL, n < 0), DH2_ECUDA. */
+dh2_status dh2_model_forward(dh2_model model, const float* X, int64_t n, float* Y, void* stream);
+/* Loss L = sum_{s,o} (y_so - t_so)^2 / (2n) and its gradient with respect to the
+ * parameters (the BF16 weights' gradient is taken as the master weights'), into
+ * DEVICE buffers grad [DH2_MLP_NPARAMS] and loss [1].  X, T: DEVICE FP32 [n][8] and
+ * [n][2].  Asynchronous.  Errors: DH2_EINVAL (NULL, n <= 0), DH2_ECUDA. */
+dh2_status dh2_model_grad(dh2_model model, const float* X, const float* T, int64_t n, float* grad, float* loss,
+                          void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the loss of
+ * the batch X, T (as dh2_model_grad); loss (DEVICE, may be NULL) receives the batch
+ * loss before the step.  Asynchronous.  Errors: as dh2_model_grad, and lr <= 0. */
+dh2_status dh2_model_train_step(dh2_model model, const float* X, const float* T, int64_t n, float lr, float* loss,
+                                void* stream);
+void dh2_free_model(dh2_model model);
+
+/* Features of every pair (t, c) of the block structure for (tree, kappa, eta,
+ * opt->eta1), in pair order tc: features DEVICE FP32 [cap][8]; *npairs receives the
+ * number of pairs; with features == NULL only *npairs is computed.  active (HOST
+ * int8 [cap], may be NULL) marks the pairs the recompression visits.  Blocks until
+ * done.  Errors: as dh2_build_dh2 for the arguments; DH2_EINVAL when cap < npairs
+ * (nothing is written then but *npairs). */
+dh2_status dh2_learned_features(dh2_tree tree, double kappa, double eta, const dh2_options* opt, void* stream,
+                                float* features, int64_t cap, int64_t* npairs, int8_t* active);
+/* Interpolation error of every pair at m = 3..8 (HOST FP64 [cap][6], pair order; NULL
+ * computes only *npairs; cap < npairs is DH2_EINVAL): for the first 8
+ * admissible blocks (t, s, c) of row(t, c), the Chebyshev interpolant of g_c(., y)
+ * on the padded box of t (Section 2) against g_c at the 3-point quadrature nodes of
+ * up to 8 elements of t and of s; the largest error over the samples divided by the
+ * largest |g_c|, maximised over the blocks; 0 for pairs without blocks.  Blocks. */
+dh2_status dh2_learned_probe(dh2_tree tree, double kappa, double eta, const dh2_options* opt, void* stream,
+                             double* err, int64_t cap, int64_t* npairs);
 
 /* ---- inspection and parity exports (host copies; caller-allocated buffers) ---- */
 

@@ -25,6 +25,9 @@ DH2_C64, DH2_C128 = 1, 2
 DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL, DH2_RANK_SPECTRAL = 0, 1, 2
 (DH2_X_R, DH2_X_ZROW, DH2_X_ZCOL, DH2_X_SROW, DH2_X_SCOL, DH2_X_QROW, DH2_X_QCOL,
  DH2_X_CROW, DH2_X_CCOL, DH2_X_P) = range(10)
+DH2_MLP_IN, DH2_MLP_HIDDEN, DH2_MLP_OUT, DH2_MLP_NPARAMS, DH2_PROBE_ORDERS = 8, 128, 2, 17922, 6
+# the trained weights of the learned order/rank model (FP32, little endian, packed order of dh2.h)
+LEARNED_WEIGHTS = os.path.join(HERE, "learned_order_rank.f32")
 
 _STATUS = {DH2_EINVAL: "EINVAL", DH2_ENOMEM: "ENOMEM", DH2_ECUDA: "ECUDA", DH2_ETIMEOUT: "ETIMEOUT",
            DH2_ENUMERIC: "ENUMERIC", DH2_EUNSUPPORTED: "EUNSUPPORTED"}
@@ -33,7 +36,8 @@ _STATUS = {DH2_EINVAL: "EINVAL", DH2_ENOMEM: "ENOMEM", DH2_ECUDA: "ECUDA", DH2_E
 class dh2_options(C.Structure):
     _fields_ = [("eta1", C.c_double), ("leaf_max", C.c_int32), ("precision", C.c_int32),
                 ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("qr_group_rows", C.c_int32),
-                ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32)]
+                ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32),
+                ("learned", C.c_int32), ("reserved0", C.c_int32), ("model", C.c_void_p)]
 
 
 class dh2_tree_info(C.Structure):
@@ -48,7 +52,8 @@ class dh2_matrix_info(C.Structure):
                 ("mean_rank_row", C.c_double), ("mean_rank_col", C.c_double),
                 ("stage_ms", C.c_double * 16), ("kernel_ms", C.c_double * 16),
                 ("kernel_launches", C.c_int64 * 16), ("kernel_work", C.c_double * 16),
-                ("kernel_work_kind", C.c_int32 * 16)]
+                ("kernel_work_kind", C.c_int32 * 16), ("learned_m", C.c_int32), ("rank_cap_retries", C.c_int32),
+                ("truncation_bytes", C.c_int64)]
 
 
 class DH2Error(RuntimeError):
@@ -86,6 +91,16 @@ _SIGS = {
     "dh2_free_matrix": (None, [_P]),
     "dh2_last_error": (C.c_char_p, []),
     "dh2_kernel_launches": (C.c_int64, []),
+    "dh2_model_create": (C.c_int, [_P, _P, C.POINTER(_P)]),
+    "dh2_model_get_params": (C.c_int, [_P, _P]),
+    "dh2_model_forward": (C.c_int, [_P, _P, C.c_int64, _P, _P]),
+    "dh2_model_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
+    "dh2_model_train_step": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
+    "dh2_free_model": (None, [_P]),
+    "dh2_learned_features": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
+                                       C.POINTER(C.c_int64), _P]),
+    "dh2_learned_probe": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
+                                    C.POINTER(C.c_int64)]),
 }
 
 
@@ -275,13 +290,17 @@ class Tree:
 
 
 class Matrix:
-    """Recompressed DH^2 matrix on the GPU (owning handle)."""
+    """Recompressed DH^2 matrix on the GPU (owning handle).  With ``model`` (a ``Model``) the
+    build chooses the order and sizes the truncation by the learned model (m is ignored)."""
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, stream=None):
+                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None, stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
                        qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes, tensor_cores=tensor_cores,
                        kb_store=kb_store)
+        if model is not None:
+            opts.learned = 1
+            opts.model = model.handle
         self.precision = precision
         self.handle = dh2_build_dh2(tree.handle, kappa, m, eta, eps, opts, stream)
         self.info = self.get_info()
@@ -393,9 +412,12 @@ class Matrix:
 
 
 def build_batch(trees, kappas, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                nstreams=0):
+                nstreams=0, model=None):
     """Concurrent builds (dh2_build_dh2_batch) wrapped as Matrix objects, in order."""
     opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule)
+    if model is not None:
+        opts.learned = 1
+        opts.model = model.handle
     handles = dh2_build_dh2_batch([t.handle for t in trees], kappas, m, eta, eps, opts, nstreams)
     return [Matrix.from_handle(h, precision) for h in handles]
 
@@ -406,3 +428,104 @@ def matvec_batch(mats, xs, ys=None, stream=None):
     if ys is None:
         ys = [torch.empty_like(x) for x in xs]
     return dh2_matvec_batch([m.handle for m in mats], xs, ys, stream)
+
+
+# ----------------------------------------------------------------------------- learned order and rank
+
+def _f32_cuda(a, cols):
+    import torch
+    if not (isinstance(a, torch.Tensor) and a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()
+            and a.dim() == 2 and a.shape[1] == cols):
+        raise TypeError(f"expected a contiguous CUDA float32 tensor of shape (n, {cols})")
+    return a
+
+
+class Model:
+    """The learned order/rank MLP on the current GPU (owning handle, dh2_model_*)."""
+
+    def __init__(self, params, stream=None):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (DH2_MLP_NPARAMS,):
+            raise ValueError(f"expected {DH2_MLP_NPARAMS} parameters")
+        self.handle = C.c_void_p()
+        _check(lib().dh2_model_create(_ptr(p), _stream(stream), C.byref(self.handle)))
+
+    @classmethod
+    def load(cls, path=None, stream=None):
+        """The trained model shipped with the package (or the FP32 file at ``path``)."""
+        return cls(np.fromfile(path or LEARNED_WEIGHTS, dtype="<f4"), stream)
+
+    def params(self):
+        out = np.empty(DH2_MLP_NPARAMS, dtype=np.float32)
+        _check(lib().dh2_model_get_params(self.handle, _ptr(out)))
+        return out
+
+    def save(self, path):
+        self.params().astype("<f4").tofile(path)
+
+    def forward(self, X, stream=None):
+        import torch
+        X = _f32_cuda(X, DH2_MLP_IN)
+        Y = torch.empty((X.shape[0], DH2_MLP_OUT), dtype=torch.float32, device=X.device)
+        s = stream or torch.cuda.current_stream(X.device)
+        _check(lib().dh2_model_forward(self.handle, C.c_void_p(X.data_ptr()), X.shape[0], C.c_void_p(Y.data_ptr()),
+                                       _stream(s)))
+        return Y
+
+    def grad(self, X, T, stream=None):
+        """(gradient [NPARAMS], loss [1]) as CUDA tensors."""
+        import torch
+        X, T = _f32_cuda(X, DH2_MLP_IN), _f32_cuda(T, DH2_MLP_OUT)
+        g = torch.empty(DH2_MLP_NPARAMS, dtype=torch.float32, device=X.device)
+        L = torch.empty(1, dtype=torch.float32, device=X.device)
+        s = stream or torch.cuda.current_stream(X.device)
+        _check(lib().dh2_model_grad(self.handle, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()), X.shape[0],
+                                    C.c_void_p(g.data_ptr()), C.c_void_p(L.data_ptr()), _stream(s)))
+        return g, L
+
+    def train_step(self, X, T, lr, loss=None, stream=None):
+        """One Adam step on the batch; the batch loss (before the step) goes to ``loss`` if given."""
+        import torch
+        X, T = _f32_cuda(X, DH2_MLP_IN), _f32_cuda(T, DH2_MLP_OUT)
+        s = stream or torch.cuda.current_stream(X.device)
+        _check(lib().dh2_model_train_step(self.handle, C.c_void_p(X.data_ptr()), C.c_void_p(T.data_ptr()),
+                                          X.shape[0], float(lr), None if loss is None else C.c_void_p(loss.data_ptr()),
+                                          _stream(s)))
+        return loss
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dh2_free_model(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def learned_features(tree: Tree, kappa, eta, eta1=10.0, stream=None):
+    """(features [npairs, 8] CUDA float32 tensor, active [npairs] bool) for the block structure."""
+    import torch
+    opts = options(eta1=eta1)
+    n = C.c_int64()
+    _check(lib().dh2_learned_features(tree.handle, float(kappa), float(eta), C.byref(opts), _stream(stream), None, 0,
+                                      C.byref(n), None))
+    F = torch.empty((max(n.value, 1), DH2_MLP_IN), dtype=torch.float32, device="cuda")
+    act = np.zeros(max(n.value, 1), dtype=np.int8)
+    _check(lib().dh2_learned_features(tree.handle, float(kappa), float(eta), C.byref(opts), _stream(stream),
+                                      C.c_void_p(F.data_ptr()), F.shape[0], C.byref(n), _ptr(act)))
+    return F[: n.value], act[: n.value].astype(bool)
+
+
+def learned_probe(tree: Tree, kappa, eta, eta1=10.0, stream=None):
+    """Interpolation error [npairs, 6] of every pair at m = 3..8 (dh2_learned_probe)."""
+    opts = options(eta1=eta1)
+    n = C.c_int64()
+    _check(lib().dh2_learned_probe(tree.handle, float(kappa), float(eta), C.byref(opts), _stream(stream), None, 0,
+                                   C.byref(n)))
+    err = np.zeros((max(n.value, 1), DH2_PROBE_ORDERS))
+    _check(lib().dh2_learned_probe(tree.handle, float(kappa), float(eta), C.byref(opts), _stream(stream), _ptr(err),
+                                   err.shape[0], C.byref(n)))
+    return err[: n.value]

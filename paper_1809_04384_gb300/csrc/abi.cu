@@ -9,6 +9,7 @@
 #include <string>
 #include <thread>
 
+#include "learned.cuh"
 #include "numeric.cuh"
 #include "structure.cuh"
 
@@ -23,7 +24,12 @@ struct dh2_matrix_s {
     dh2::BuildParams bp;
     std::unique_ptr<dh2::NumBase> num;
     int32_t depth = 0;
+    int32_t learned_m = 0;
     double structure_ms = 0;
+};
+
+struct dh2_model_s {
+    dh2::learned::Model md;
 };
 
 namespace dh2 {
@@ -99,6 +105,13 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
     if (o.tensor_cores != 0 && o.tensor_cores != 1) throw Error{DH2_EINVAL, f + ": tensor_cores must be 0 or 1"};
     if (o.kb_store < 0 || o.kb_store > 2) throw Error{DH2_EINVAL, f + ": kb_store must be 0, 1 or 2"};
+    if (o.learned != 0 && o.learned != 1) throw Error{DH2_EINVAL, f + ": learned must be 0 or 1"};
+    if (o.learned && o.model == nullptr) throw Error{DH2_EINVAL, f + ": learned = 1 needs a model"};
+    if (o.learned) {
+        int dev = 0;
+        DH2_CHECK_CUDA(cudaGetDevice(&dev));
+        if (o.model->md.dev != dev) throw Error{DH2_EINVAL, f + ": the model lives on another device"};
+    }
 }
 
 // The whole build of one matrix on stream s (arguments already checked); blocks until done.
@@ -121,7 +134,13 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->structure_ms = ms;
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
-                          o.workspace_bytes, o.tensor_cores, o.kb_store};
+                          o.workspace_bytes, o.tensor_cores, o.kb_store, {}};
+    if (o.learned) {
+        int32_t ml = m;
+        learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);
+        mat->bp.m = ml;
+        mat->learned_m = ml;
+    }
     mat->num = make_numeric(mat->tr, mat->st, mat->hs, mat->bp);
     mat->num->build(s);
     mat->num->info.stage_ms[ST_STRUCTURE] += ms;
@@ -244,6 +263,8 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->workspace_bytes = 0;
     opt->tensor_cores = 1;
     opt->kb_store = 0;
+    opt->learned = 0;
+    opt->model = nullptr;
     return DH2_OK;
 }
 
@@ -514,6 +535,133 @@ dh2_status dh2_matrix_get_info(dh2_matrix mat, dh2_matrix_info* out) {
             out->kernel_work[i] = in.kernel_work[i];
             out->kernel_work_kind[i] = in.kernel_work_kind[i];
         }
+        out->learned_m = mat->learned_m;
+        out->rank_cap_retries = in.rank_cap_retries;
+        out->truncation_bytes = in.truncation_bytes;
+    });
+}
+
+// ----------------------------------------------------------------------------- learned model
+
+dh2_status dh2_model_create(const float* params, void* stream, dh2_model* out) {
+    return guarded([&] {
+        DH2_REQUIRE(out != nullptr, "dh2_model_create: out is NULL");
+        *out = nullptr;
+        DH2_REQUIRE(params != nullptr, "dh2_model_create: params is NULL");
+        for (int i = 0; i < learned::kParams; ++i)
+            DH2_REQUIRE(std::isfinite(params[i]), "dh2_model_create: non-finite parameter");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        auto h = std::make_unique<dh2_model_s>();
+        learned::model_init(h->md, params, s);
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        *out = h.release();
+    });
+}
+
+dh2_status dh2_model_get_params(dh2_model model, float* params) {
+    return guarded([&] {
+        DH2_REQUIRE(model != nullptr && params != nullptr, "dh2_model_get_params: NULL");
+        model->md.master.download(params, learned::kParams, 0);
+        DH2_CHECK_CUDA(cudaStreamSynchronize(0));
+    });
+}
+
+dh2_status dh2_model_forward(dh2_model model, const float* X, int64_t n, float* Y, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(model != nullptr && n >= 0, "dh2_model_forward: NULL model or n < 0");
+        if (n == 0) return;
+        DH2_REQUIRE(X != nullptr && Y != nullptr, "dh2_model_forward: NULL");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        learned::model_forward(model->md, X, n, Y, s);
+    });
+}
+
+dh2_status dh2_model_grad(dh2_model model, const float* X, const float* T, int64_t n, float* grad, float* loss,
+                          void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(model != nullptr && X != nullptr && T != nullptr && grad != nullptr && loss != nullptr,
+                    "dh2_model_grad: NULL");
+        DH2_REQUIRE(n > 0, "dh2_model_grad: n must be > 0");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        learned::model_grad(model->md, X, T, n, false, 0.f, s);
+        DH2_CHECK_CUDA(cudaMemcpyAsync(grad, model->md.grad.p, learned::kParams * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, s));
+        DH2_CHECK_CUDA(cudaMemcpyAsync(loss, model->md.loss.p, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    });
+}
+
+dh2_status dh2_model_train_step(dh2_model model, const float* X, const float* T, int64_t n, float lr, float* loss,
+                                void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(model != nullptr && X != nullptr && T != nullptr, "dh2_model_train_step: NULL");
+        DH2_REQUIRE(n > 0, "dh2_model_train_step: n must be > 0");
+        DH2_REQUIRE(std::isfinite(lr) && lr > 0.f, "dh2_model_train_step: lr must be > 0");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        learned::model_grad(model->md, X, T, n, true, lr, s);
+        if (loss)
+            DH2_CHECK_CUDA(cudaMemcpyAsync(loss, model->md.loss.p, sizeof(float), cudaMemcpyDeviceToDevice, s));
+    });
+}
+
+void dh2_free_model(dh2_model model) {
+    if (!model) return;
+    cudaDeviceSynchronize();
+    delete model;
+}
+
+namespace {
+// the block structure of (tree, kappa, eta) for the learned-model helpers
+struct ProbeStructure {
+    Structure st;
+    HostStructure hs;
+};
+void learned_structure(dh2_tree tree, double kappa, double eta, const dh2_options* opt, cudaStream_t s,
+                       const char* fn, ProbeStructure& ps) {
+    dh2_options o;
+    if (opt) o = *opt; else dh2_options_default(&o);
+    o.learned = 0;
+    check_build_args(tree, kappa, 1, eta, 1.0, o, fn);
+    build_structure(tree->tr, ps.st, kappa, o.eta1, eta, s);
+    download_structure(tree->tr, ps.st, ps.hs, s);
+}
+}  // namespace
+
+dh2_status dh2_learned_features(dh2_tree tree, double kappa, double eta, const dh2_options* opt, void* stream,
+                                float* features, int64_t cap, int64_t* npairs, int8_t* active) {
+    return guarded([&] {
+        DH2_REQUIRE(npairs != nullptr, "dh2_learned_features: npairs is NULL");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        ProbeStructure ps;
+        learned_structure(tree, kappa, eta, opt, s, "dh2_learned_features", ps);
+        *npairs = ps.st.ntc;
+        if (!features) return;
+        DH2_REQUIRE(cap >= ps.st.ntc, "dh2_learned_features: cap < number of pairs");
+        learned::features(tree->tr, ps.st, features, s);
+        if (active)
+            for (int64_t tc = 0; tc < ps.st.ntc; ++tc) active[tc] = ps.hs.aidx[tc] >= 0 ? 1 : 0;
+    });
+}
+
+dh2_status dh2_learned_probe(dh2_tree tree, double kappa, double eta, const dh2_options* opt, void* stream,
+                             double* err, int64_t cap, int64_t* npairs) {
+    return guarded([&] {
+        DH2_REQUIRE(npairs != nullptr, "dh2_learned_probe: npairs is NULL");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        ProbeStructure ps;
+        learned_structure(tree, kappa, eta, opt, s, "dh2_learned_probe", ps);
+        *npairs = ps.st.ntc;
+        if (!err) return;
+        DH2_REQUIRE(cap >= ps.st.ntc, "dh2_learned_probe: cap < number of pairs");
+        DBuf<double> d((size_t)std::max<int64_t>(ps.st.ntc, 1) * learned::kOrders);
+        learned::probe(tree->tr, ps.st, ps.hs, d.p, s);
+        d.download(err, (size_t)ps.st.ntc * learned::kOrders, s);
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
     });
 }
 

@@ -32,7 +32,8 @@ constexpr int kThreads = 256;
 // the host reads the word after each stage and returns DH2_ENUMERIC.
 enum : unsigned {
     ERR_TSQR_NONFINITE = 1u, ERR_TRUNC_NONFINITE = 2u, ERR_TSQR_INPUT = 4u, ERR_STACK_NONFINITE = 8u,
-    ERR_KRON_NONFINITE = 16u, ERR_TC_TIMEOUT = 32u
+    ERR_KRON_NONFINITE = 16u, ERR_TC_TIMEOUT = 32u,
+    ERR_RANK_CAP = 64u   // not an error: a truncation rank exceeded its learned cap (the pass is redone)
 };
 __device__ __forceinline__ void raise_err(unsigned* err, unsigned bit) { atomicOr(err, bit); }
 
@@ -1202,6 +1203,10 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
             kk = nsig;
             while (kk > 0 && s_lam[s_order[kk - 1]] <= eps * eps) --kk;
         }
+        if (kk > tk.qld) {                 // over the learned cap: the host redoes the pass
+            raise_err(err, ERR_RANK_CAP);
+            kk = tk.qld;
+        }
         s_rank = kk;
         rank[tk.a] = kk;
     }
@@ -1361,6 +1366,10 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
         if (rule == DH2_RANK_SPECTRAL) {   // smallest k with sigma_{k+1} <= eps
             kk = nsig;
             while (kk > 0 && e.lam[e.order[kk - 1]] <= eps * eps) --kk;
+        }
+        if (kk > tk.qld) {                 // over the learned cap: the host redoes the pass
+            raise_err(err, ERR_RANK_CAP);
+            kk = tk.qld;
         }
         s_rank = kk;
         rank[tk.a] = kk;
@@ -2018,6 +2027,8 @@ private:
     }
 
     void layout();
+    void layout_trunc(int pass);
+    bool capped_[2] = {false, false};
     void analytic(cudaStream_t s);
     void nearfield(cudaStream_t s);
     void basis_weights(cudaStream_t s);
@@ -2037,6 +2048,7 @@ private:
     bool kstore_ = true;            // K_b kept for the column pass / leaf-pair projection
     cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
     void truncate(int pass, cudaStream_t s);
+    bool truncate_once(int pass, cudaStream_t s);
     void project(cudaStream_t s);
     void plan_matvec(cudaStream_t s);
     void tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s, const char* where);
@@ -2100,11 +2112,6 @@ void Num<T>::layout() {
             // basis (zcols = r_t columns), the others in the interpolation basis (k columns)
             rZ_[pass][a] = (int32_t)std::min<int64_t>(rows, zcols(a));
         }
-        ub_[pass].assign(na_, 0);
-        for (int64_t a = na_ - 1; a >= 0; --a) {
-            int32_t rows = leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
-            ub_[pass][a] = std::min(rows, rZ_[pass][a]);
-        }
     }
     // offsets
     auto scan = [&](std::vector<int64_t>& off, auto sizef) {
@@ -2130,19 +2137,46 @@ void Num<T>::layout() {
     }
     for (int pass = 0; pass < 2; ++pass) {
         scan(offZ_[pass], [&](int64_t a) -> int64_t { return (int64_t)rZ_[pass][a] * zcols(a); });
-        ldQ_[pass].resize(na_);
-        for (int64_t a = 0; a < na_; ++a) ldQ_[pass][a] = std::max(ub_[pass][a], 1);
-        scan(offQ_[pass], [&](int64_t a) -> int64_t {
-            int64_t rows = leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
-            return rows * ldQ_[pass][a];
-        });
-        scan(offC_[pass], [&](int64_t a) -> int64_t { return (int64_t)ub_[pass][a] * k_; });
-        scan(offUp_[pass], [&](int64_t a) -> int64_t { return leaf_[a] ? (int64_t)rR_[a] * ldQ_[pass][a] : 0; });
-        scan(offSig_[pass], [&](int64_t a) -> int64_t {
-            return leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
-        });
-        rank_[pass].assign(na_, 0);
+        capped_[pass] = !bp_.rank_cap.empty();
+        layout_trunc(pass);
     }
+}
+
+// Column bounds of the truncated bases of one pass and the offsets of Q, C, U' and the
+// singular values.  The bound ub is min(rows, rank of Z-hat), rows being #t at a leaf and
+// the sum of the sons' bounds above; a learned cap, while the pass uses it, lowers it
+// further.
+template <class T>
+void Num<T>::layout_trunc(int pass) {
+    if (capped_[pass] && (int64_t)bp_.rank_cap.size() != na_)
+        throw Error{DH2_EINVAL, "rank caps: one entry per active pair expected"};
+    ub_[pass].assign(na_, 0);
+    for (int64_t a = na_ - 1; a >= 0; --a) {
+        int32_t rows = leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
+        ub_[pass][a] = std::min(rows, rZ_[pass][a]);
+        if (capped_[pass]) ub_[pass][a] = std::min(ub_[pass][a], std::max(bp_.rank_cap[a], 1));
+    }
+    auto scan = [&](std::vector<int64_t>& off, auto sizef) {
+        off.resize(na_ + 1);
+        int64_t acc = 0;
+        for (int64_t a = 0; a < na_; ++a) {
+            off[a] = acc;
+            acc += sizef(a);
+        }
+        off[na_] = acc;
+    };
+    ldQ_[pass].resize(na_);
+    for (int64_t a = 0; a < na_; ++a) ldQ_[pass][a] = std::max(ub_[pass][a], 1);
+    scan(offQ_[pass], [&](int64_t a) -> int64_t {
+        int64_t rows = leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
+        return rows * ldQ_[pass][a];
+    });
+    scan(offC_[pass], [&](int64_t a) -> int64_t { return (int64_t)ub_[pass][a] * k_; });
+    scan(offUp_[pass], [&](int64_t a) -> int64_t { return leaf_[a] ? (int64_t)rR_[a] * ldQ_[pass][a] : 0; });
+    scan(offSig_[pass], [&](int64_t a) -> int64_t {
+        return leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
+    });
+    rank_[pass].assign(na_, 0);
 }
 
 // ----------------------------------------------------------------------------- analytic stage
@@ -2642,6 +2676,21 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
 
 template <class T>
 void Num<T>::truncate(int pass, cudaStream_t s) {
+    while (!truncate_once(pass, s)) {
+        // a rank exceeded its learned cap: redo the pass with the structural bounds
+        err_.zero(s);
+        capped_[pass] = false;
+        layout_trunc(pass);
+        ++info.rank_cap_retries;
+    }
+    const int64_t cb = std::is_same<T, float>::value ? (int64_t)sizeof(cx<float>) : 0;
+    info.truncation_bytes += offQ_[pass][na_] * (int64_t)sizeof(cx<T>) + offUp_[pass][na_] * (int64_t)sizeof(cx<T>) +
+                             offC_[pass][na_] * ((int64_t)sizeof(cx<double>) + cb) + offSig_[pass][na_] * 8;
+}
+
+// One truncation pass, level by level bottom-up; false when a rank exceeded its cap.
+template <class T>
+bool Num<T>::truncate_once(int pass, cudaStream_t s) {
     const auto& h = hs_;
     const int kk = k_;
     Q_[pass].alloc(std::max<int64_t>(offQ_[pass][na_], 1));
@@ -2761,8 +2810,12 @@ void Num<T>::truncate(int pass, cudaStream_t s) {
                                        cudaMemcpyDeviceToHost, s));
         DH2_CHECK_CUDA(cudaStreamSynchronize(s));
         for (int64_t a = a0; a < a1; ++a) rank_[pass][a] = rk[a - a0];
-        check_err(s, "truncation");
+        const unsigned e = read_scalar(err_.p, s);
+        if (e & ~ERR_RANK_CAP)
+            throw Error{DH2_ENUMERIC, "non-finite value in truncation (code " + std::to_string(e) + ")"};
+        if (e & ERR_RANK_CAP) return false;
     }
+    return true;
 }
 
 // ----------------------------------------------------------------------------- projection

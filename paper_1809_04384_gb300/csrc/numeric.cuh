@@ -32,6 +32,10 @@ struct BuildParams {
     int32_t m, precision, rank_rule, qr_fp64, qr_group_rows;
     int64_t workspace_bytes;
     int32_t tensor_cores, kb_store;
+    // per active pair: the most columns its truncated bases may need (a learned estimate);
+    // empty = the structural bound min(rows, k).  A pair whose truncation rank exceeds its
+    // cap sends the whole pass back to the structural bound.
+    std::vector<int32_t> rank_cap;
 };
 
 enum KernelId {
@@ -49,6 +53,8 @@ struct MatrixInfoAcc {
     int64_t kernel_launches[16] = {0};
     double kernel_work[16] = {0};
     int32_t kernel_work_kind[16] = {0};
+    int32_t rank_cap_retries = 0;
+    int64_t truncation_bytes = 0;
 };
 enum WorkKind { W_NONE = 0, W_FLOP32 = 1, W_FLOP64 = 2, W_BYTES = 3 };
 

@@ -92,3 +92,52 @@ def test_batch_arguments_rejected_before_gpu_work(libpath):
                               pkg.DH2_C64, None) == pkg.DH2_EINVAL
     assert L.dh2_matvec_batch(None, 0, None, None, 7, None) == pkg.DH2_EINVAL
     assert L.dh2_matvec_batch(None, 0, None, None, pkg.DH2_C64, None) == pkg.DH2_OK
+
+
+def test_struct_layouts_match_header(libpath, tmp_path):
+    """The ctypes mirrors of dh2_options / dh2_matrix_info have the C sizes and offsets."""
+    import ctypes as C
+
+    import paper_1809_04384_gb300 as pkg
+
+    src = tmp_path / "sz.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "dh2.h"\n'
+        "int main(void) {\n"
+        '  printf("%zu %zu %zu %zu %zu\\n", sizeof(dh2_options), offsetof(dh2_options, model),\n'
+        "         sizeof(dh2_matrix_info), offsetof(dh2_matrix_info, learned_m),\n"
+        "         offsetof(dh2_matrix_info, truncation_bytes));\n  return 0;\n}\n")
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    want = [C.sizeof(pkg.dh2_options), pkg.dh2_options.model.offset, C.sizeof(pkg.dh2_matrix_info),
+            pkg.dh2_matrix_info.learned_m.offset, pkg.dh2_matrix_info.truncation_bytes.offset]
+    assert got == want
+
+
+def test_learned_arguments_rejected_before_gpu_work(libpath):
+    import ctypes as C
+
+    import numpy as np
+
+    import paper_1809_04384_gb300 as pkg
+
+    L = pkg.lib()
+    o = pkg.options()
+    assert o.learned == 0 and not o.model
+    h = C.c_void_p()
+    assert L.dh2_model_create(None, None, C.byref(h)) == pkg.DH2_EINVAL and not h.value
+    p = np.zeros(pkg.DH2_MLP_NPARAMS, dtype=np.float32)
+    p[17] = np.nan
+    assert L.dh2_model_create(C.c_void_p(p.ctypes.data), None, C.byref(h)) == pkg.DH2_EINVAL
+    assert b"non-finite" in L.dh2_last_error()
+    assert L.dh2_model_forward(None, None, 4, None, None) == pkg.DH2_EINVAL
+    assert L.dh2_model_grad(None, None, None, 4, None, None, None) == pkg.DH2_EINVAL
+    assert L.dh2_model_train_step(None, None, None, 4, 1e-3, None, None) == pkg.DH2_EINVAL
+    n = C.c_int64(-1)
+    assert L.dh2_learned_features(None, 1.0, 1.0, None, None, None, 0, C.byref(n), None) == pkg.DH2_EINVAL
+    assert L.dh2_learned_probe(None, 1.0, 1.0, None, None, None, 0, C.byref(n)) == pkg.DH2_EINVAL
+    assert L.dh2_learned_features(None, 1.0, 1.0, None, None, None, 0, None, None) == pkg.DH2_EINVAL
+    # a learned build without a model
+    o.learned = 1
+    assert L.dh2_build_dh2(None, 1.0, 5, 1.0, 1e-4, C.byref(o), None, C.byref(h)) == pkg.DH2_EINVAL
