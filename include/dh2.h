@@ -224,6 +224,16 @@ dh2_status dh2_matvec_noalloc(dh2_matrix mat, const void* x, void* y, int32_t dt
  */
 dh2_status dh2_matvec_host(dh2_matrix mat, const double* x_host, double* y_host, void* stream);
 
+/* Reference rows of the Galerkin matrix (Eq. 2) times x, in FP64 on the GPU, for the
+ * error of the compressed product on sampled rows: out[i] = sum_j g_{rows[i], j} x_j
+ * with the entries of the nearfield (3 x 3 interior Gauss points off the diagonal, the
+ * 7-point degree-5 rule against the 3-point rule on it), every column evaluated.
+ * rows: HOST int32 [count], original element ids; x: DEVICE complex128 [n], original
+ * order; out: HOST complex128 [count].  Blocks until done.  Errors: DH2_EINVAL for NULL
+ * pointers, count < 0, a point-mode tree, a row out of range or kappa < 0; DH2_ECUDA. */
+dh2_status dh2_dense_rows(dh2_tree tree, double kappa, const int32_t* rows, int32_t count, const double* x,
+                          double* out, void* stream);
+
 /* Turns per-launch CUDA-event timing of the matvec kernels on (1) or off (0);
  * the sums are reported in dh2_matrix_info.kernel_ms / kernel_launches (matvec
  * entries are reset by this call).  Timing synchronises the stream per launch. */

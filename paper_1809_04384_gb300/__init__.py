@@ -97,6 +97,7 @@ _SIGS = {
     "dh2_model_grad": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, _P]),
     "dh2_model_train_step": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
     "dh2_free_model": (None, [_P]),
+    "dh2_dense_rows": (C.c_int, [_P, C.c_double, _P, C.c_int32, _P, _P, _P]),
     "dh2_learned_features": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
                                        C.POINTER(C.c_int64), _P]),
     "dh2_learned_probe": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
@@ -244,6 +245,21 @@ def dh2_matvec_host(mat, x, stream=None):
     y = np.empty_like(x)
     _check(lib().dh2_matvec_host(mat, _ptr(x), _ptr(y), _stream(stream)))
     return y
+
+
+def dh2_dense_rows(tree, kappa, rows, x, stream=None):
+    """(G x)[rows] in FP64 on the GPU (reference rows for the product's error); x: complex128
+    CUDA tensor in original element order, rows: original element ids."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.complex128 and x.is_contiguous()):
+        raise TypeError("x must be a contiguous complex128 CUDA tensor")
+    r = np.ascontiguousarray(rows, dtype=np.int32)
+    out = np.empty(len(r), dtype=np.complex128)
+    if stream is None:
+        stream = torch.cuda.current_stream(x.device)
+    _check(lib().dh2_dense_rows(tree, float(kappa), _ptr(r), len(r), C.c_void_p(x.data_ptr()), _ptr(out),
+                                _stream(stream)))
+    return out
 
 
 def dh2_free_tree(tree):

@@ -475,6 +475,22 @@ dh2_status dh2_sync(void* stream) {
     return guarded([&] { DH2_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream))); });
 }
 
+dh2_status dh2_dense_rows(dh2_tree tree, double kappa, const int32_t* rows, int32_t count, const double* x,
+                          double* out, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(tree != nullptr && count >= 0, "dh2_dense_rows: NULL tree or count < 0");
+        DH2_REQUIRE(!tree->tr.point_mode, "dh2_dense_rows: a point-mode tree has no Galerkin elements");
+        DH2_REQUIRE(std::isfinite(kappa) && kappa >= 0.0, "dh2_dense_rows: kappa must be >= 0");
+        if (count == 0) return;
+        DH2_REQUIRE(rows != nullptr && x != nullptr && out != nullptr, "dh2_dense_rows: NULL");
+        for (int32_t i = 0; i < count; ++i)
+            DH2_REQUIRE(rows[i] >= 0 && rows[i] < tree->tr.n, "dh2_dense_rows: row out of range");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        dense_rows(tree->tr, kappa, rows, count, x, out, s);
+    });
+}
+
 dh2_status dh2_tree_get_info(dh2_tree tree, dh2_tree_info* out) {
     return guarded([&] {
         DH2_REQUIRE(tree != nullptr && out != nullptr, "dh2_tree_get_info: NULL");

@@ -170,5 +170,8 @@ struct Tree {
 
 void build_tree_gpu(Tree& tr, cudaStream_t s);
 void prepare_quadrature(Tree& tr, cudaStream_t s);
+// out_host[i] = (G x)[rows_host[i]] in FP64 (dense.cu); x_dev complex128, original order
+void dense_rows(const Tree& tr, double kappa, const int32_t* rows_host, int32_t count, const double* x_dev,
+                double* out_host, cudaStream_t s);
 
 }  // namespace dh2
