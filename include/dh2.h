@@ -255,9 +255,11 @@ dh2_status dh2_sync(void* stream);
  * weights and FP32 biases, accumulation in FP32, that maps 8 geometric features of
  * a pair (t, c) to (m_tc / 8, k_tc / 64): the order its interpolation needs and its
  * truncation rank.  A build with opt->learned = 1 computes the features of every
- * pair from the block structure, evaluates the model, builds with the largest
- * predicted order over the active pairs (the transfer matrices E of Eq. nested tie
- * the orders of a cluster and its sons, so one order serves the matrix) and sizes
+ * pair from the block structure, evaluates the model, builds with the 99th
+ * percentile of the orders predicted for the active pairs, rounded down and clamped
+ * to [3, 8] (the transfer matrices E of Eq. nested tie the orders of a cluster and
+ * its sons, so one order serves the matrix; the training calibrates the order
+ * unit's offset so that this reaches the order the training meshes need) and sizes
  * the truncated bases by the predicted ranks (1.25 x + 4 columns per pair).  The
  * SVD truncation still decides every rank: a pass in which one exceeds its cap is
  * redone with the structural bounds (dh2_matrix_info.rank_cap_retries).

@@ -523,17 +523,20 @@ void choose(const Tree& tr, const Structure& st, const HostStructure& hs, Model&
     features(tr, st, F.p, s);
     model_forward(md, F.p, st.ntc, Yd.p, s);
     std::vector<float> y = Yd.to_host(s);
-    int32_t m = 3;
+    std::vector<double> mh(hs.nactive);
     for (int64_t a = 0; a < hs.nactive; ++a) {
         const int32_t tc = hs.tc_base[hs.a_t[a]] + hs.a_c[a];
-        const double mh = (double)y[(size_t)tc * kOut] * kMScale;
+        const double m = (double)y[(size_t)tc * kOut] * kMScale;
         const double rh = std::max(0.0, (double)y[(size_t)tc * kOut + 1] * kRankScale);
-        const int32_t mi = (int32_t)std::lround(std::min(8.0, std::max(3.0, std::isfinite(mh) ? mh : 8.0)));
-        m = std::max(m, mi);
+        mh[a] = std::isfinite(m) ? m : 8.0;
         // slack over the estimate: a quarter plus four columns
         caps[a] = std::isfinite(rh) ? (int32_t)std::ceil(1.25 * rh) + 4 : (1 << 30);
     }
-    *m_out = m;
+    // the order of the matrix: the 99th percentile (nearest rank, from below) of the
+    // predicted orders, rounded down; the model's order unit carries the calibrated offset
+    std::sort(mh.begin(), mh.end());
+    const double q = mh[(size_t)std::floor(kOrderQuantile * (double)(mh.size() - 1))];
+    *m_out = (int32_t)std::floor(std::min(8.0, std::max(3.0, q)));
 }
 
 }  // namespace learned

@@ -25,6 +25,7 @@ constexpr int kOffB3 = kOffW3 + kOut * kHid;
 constexpr int kParams = kOffB3 + kOut;     // 17922
 constexpr int kOrders = 6;                 // probe orders m = 3..8
 constexpr double kMScale = 8.0, kRankScale = 64.0;   // output 0 = m / 8, output 1 = rank / 64
+constexpr double kOrderQuantile = 0.99;              // the matrix order: this quantile of the pairs' orders
 
 struct Model {
     DBuf<float> master, mom1, mom2, grad, part, loss;   // FP32 master weights, Adam moments
@@ -46,8 +47,9 @@ void features(const Tree& tr, const Structure& st, float* F, cudaStream_t s);
 // pairs without admissible blocks)
 void probe(const Tree& tr, const Structure& st, const HostStructure& hs, double* err, cudaStream_t s);
 
-// The learned choice for one matrix: the order m (the largest predicted over the active
-// pairs) and a cap on the truncation rank of every active pair.
+// The learned choice for one matrix: the order m (the 99th percentile of the orders predicted
+// for the active pairs, rounded down and clamped to [3, 8]) and a cap on the truncation rank
+// of every active pair (1.25 x the predicted rank + 4).
 void choose(const Tree& tr, const Structure& st, const HostStructure& hs, Model& md, cudaStream_t s,
             int32_t* m_out, std::vector<int32_t>& caps);
 

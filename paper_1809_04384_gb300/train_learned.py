@@ -8,16 +8,28 @@ Data (every step on the GPU through the library):
   semi-axes U[0.5, 2], kappa U[4, 16]; the configurations the model is meant for),
   leaf 32, eta1 10, eta2 1, eps 1e-4;
 * features of every active pair (dh2_learned_features);
-* order label: the smallest m in 3..8 whose x-side interpolation error
-  (dh2_learned_probe) is at most eps / 2, since the two sides of a block each add
-  one such error; 8 when none is;
-* rank label: the row rank k_tc of a plain build at the reference order m_ref
+* the x-side interpolation error of every pair at m = 3..8 (dh2_learned_probe);
+* the order each mesh needs: the smallest m in 4..7 whose built matrix has a
+  relative product error <= eps on sampled rows against the FP64 Galerkin rows
+  (dh2_dense_rows), 8 if none has;
+* order label of a pair: the smallest m whose probe error is <= c eps, 8 if none
+  is.  The threshold c is calibrated on the training meshes: the largest c from a
+  grid for which the largest label of every mesh still reaches the order the mesh
+  needs (the build takes the largest predicted order, so a smaller c only costs
+  time);
+* rank label: the row rank k_tc of the plain build at the reference order m_ref
   (dh2_export_ranks).
+
+The build takes the 99th percentile of the orders predicted for a matrix's pairs,
+rounded down.  After training, the order unit's bias is raised by the smallest
+offset (grid of 0.05) for which that rule reaches the needed order on every
+training mesh.
 
 Targets are (m / 8, rank / 64); the loss is the mean squared error, minimised by
 Adam (dh2_model_train_step) on shuffled mini-batches with a cosine learning-rate
 decay.  The last meshes are held out for validation.  Prints one JSON line with the
-data sizes, losses and validation statistics, and writes the FP32 parameters.
+data sizes, the calibration, losses and validation statistics, and writes the FP32
+parameters.
 """
 from __future__ import annotations
 
@@ -43,38 +55,78 @@ ETA1, ETA2, EPS, LEAF = 10.0, 1.0, 1e-4, 32
 ORDERS = np.arange(3, 9)
 
 
-def order_labels(err, eps):
-    """Smallest order with probe error <= eps / 2 per row of err (orders 3..8), else 8."""
-    ok = err <= 0.5 * eps
+C_GRID = (0.5, 1.0, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0)
+GLOBAL_ORDERS = (4, 5, 6, 7)
+
+
+def order_labels(err, thresh):
+    """Smallest order with probe error <= thresh per row of err (orders 3..8), else 8."""
+    ok = err <= thresh
     return np.where(ok.any(axis=1), ORDERS[ok.argmax(axis=1)], 8)
 
 
-def mesh_samples(v, f, kappa, m_ref, eps=EPS):
-    """(features [n, 8] float32, targets [n, 2] float32, order labels, ranks) of the active pairs."""
+def product_error(mat, tree, kappa, x, rows):
+    import torch
+
+    y = mat.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+    ref = dh2.dh2_dense_rows(tree.handle, kappa, rows, torch.from_numpy(x).cuda())
+    return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
+
+
+def mesh_data(v, f, kappa, m_ref, eps=EPS, nrows=64, seed=0):
+    """Features, probe errors and ranks of the active pairs, and the order the mesh needs."""
     tree = dh2.Tree(v, f, leaf_max=LEAF)
     F, active = dh2.learned_features(tree, kappa, ETA2, eta1=ETA1)
-    err = dh2.learned_probe(tree, kappa, ETA2, eta1=ETA1)
-    mat = dh2.Matrix(tree, kappa, m_ref, ETA2, eps, eta1=ETA1)
-    rr, _ = mat.ranks()
-    mat.close()
-    tree.close()
     idx = np.nonzero(active)[0]
-    lab = order_labels(err[idx], eps)
-    rank = rr[idx].astype(np.float64)
-    X = F.cpu().numpy()[idx]
-    T = np.stack([lab / 8.0, rank / 64.0], axis=1).astype(np.float32)
-    return X, T, lab, rank
+    out = {"X": F.cpu().numpy()[idx], "pairs": len(idx)}
+    if len(idx) == 0:
+        tree.close()
+        return out
+    out["err"] = dh2.learned_probe(tree, kappa, ETA2, eta1=ETA1)[idx]
+    x = synth.random_vector(len(f), seed)
+    rows = np.sort(np.random.default_rng(seed + 1).choice(len(f), size=min(nrows, len(f)), replace=False))
+    gerr = {}
+    for m in sorted(set(GLOBAL_ORDERS) | {m_ref}):
+        mat = dh2.Matrix(tree, kappa, m, ETA2, eps, eta1=ETA1)
+        if m == m_ref:
+            out["rank"] = mat.ranks()[0][idx].astype(np.float64)
+        if m in GLOBAL_ORDERS:
+            gerr[m] = product_error(mat, tree, kappa, x, rows)
+        mat.close()
+    tree.close()
+    out["global_err"] = gerr
+    out["needed"] = next((m for m in GLOBAL_ORDERS if gerr[m] <= eps), 8)
+    return out
 
 
 def collect(count, seed, m_ref, log=print):
     data = []
     for i, (v, f, kappa) in enumerate(synth.batch_meshes(count, seed)):
         t0 = time.perf_counter()
-        X, T, lab, rank = mesh_samples(v, f, kappa, m_ref)
-        log(f"mesh {i}: {len(f)} triangles, kappa {kappa:.2f}: {len(X)} pairs, orders {np.bincount(lab, minlength=9)[3:]}"
-            f", mean rank {rank.mean() if len(rank) else 0:.1f} ({time.perf_counter() - t0:.1f} s)")
-        data.append((X, T))
+        d = mesh_data(v, f, kappa, m_ref, seed=seed + 100 + i)
+        if d["pairs"]:
+            log(f"mesh {i}: {len(f)} triangles, kappa {kappa:.2f}: {d['pairs']} pairs, needs m = {d['needed']} "
+                f"(errors {', '.join(f'{m}: {e:.2e}' for m, e in d['global_err'].items())}), "
+                f"mean rank {d['rank'].mean():.1f} ({time.perf_counter() - t0:.1f} s)")
+        data.append(d)
     return data
+
+
+def calibrate(data, eps):
+    """Largest c of the grid for which every mesh's largest label reaches the order it needs."""
+    best = C_GRID[0]
+    for c in C_GRID:
+        if all(order_labels(d["err"], c * eps).max() >= d["needed"] for d in data if d["pairs"]):
+            best = c
+    return best
+
+
+def samples(data, c, eps):
+    X = [d["X"] for d in data if d["pairs"]]
+    T = [np.stack([order_labels(d["err"], c * eps) / 8.0, d["rank"] / 64.0], axis=1) for d in data if d["pairs"]]
+    if not X:
+        return np.zeros((0, 8), np.float32), np.zeros((0, 2), np.float32)
+    return np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32)
 
 
 def train(Xtr, Ttr, steps, batch, lr, seed, init_seed):
@@ -133,6 +185,39 @@ def evaluate(model, X, T):
     }
 
 
+ORDER_QUANTILE = 0.99
+
+
+def rule_order(pred_m):
+    """The order a learned build takes from the predicted orders of its pairs."""
+    q = np.sort(pred_m)[int(math.floor(ORDER_QUANTILE * (len(pred_m) - 1)))]
+    return int(math.floor(min(8.0, max(3.0, q))))
+
+
+def predicted_orders(model, data):
+    import torch
+
+    return [model.forward(torch.from_numpy(d["X"].astype(np.float32)).cuda()).cpu().numpy()[:, 0].astype(np.float64)
+            * 8.0 for d in data if d["pairs"]]
+
+
+def calibrate_offset(model, data):
+    """Smallest offset (grid 0.05, at most 3) for which the rule reaches every mesh's needed order."""
+    preds = predicted_orders(model, data)
+    needed = [d["needed"] for d in data if d["pairs"]]
+    for k in range(61):
+        delta = 0.05 * k
+        if all(rule_order(p + delta) >= n for p, n in zip(preds, needed)):
+            return delta
+    return 3.0
+
+
+def mesh_orders(model, data):
+    """(order the learned build takes, order the mesh needs) per mesh with pairs."""
+    needed = [d["needed"] for d in data if d["pairs"]]
+    return [(rule_order(p), n) for p, n in zip(predicted_orders(model, data), needed)]
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--meshes", type=int, default=40)
@@ -151,19 +236,24 @@ def main(argv=None):
     data = collect(args.meshes, args.seed, args.m_ref, log=lambda s: print(s, file=sys.stderr))
     t_data = time.perf_counter() - t0
     tr, va = data[: args.meshes - args.val], data[args.meshes - args.val:]
-    Xtr = np.concatenate([d[0] for d in tr]).astype(np.float32)
-    Ttr = np.concatenate([d[1] for d in tr]).astype(np.float32)
-    Xva = np.concatenate([d[0] for d in va]).astype(np.float32) if va else np.zeros((0, 8), np.float32)
-    Tva = np.concatenate([d[1] for d in va]).astype(np.float32) if va else np.zeros((0, 2), np.float32)
+    c = calibrate(tr, EPS)
+    Xtr, Ttr = samples(tr, c, EPS)
+    Xva, Tva = samples(va, c, EPS)
     t1 = time.perf_counter()
     model, hist = train(Xtr, Ttr, args.steps, args.batch, args.lr, args.seed, args.seed + 1)
     t_train = time.perf_counter() - t1
+    stats_tr, stats_va = evaluate(model, Xtr, Ttr), evaluate(model, Xva, Tva)
+    delta = calibrate_offset(model, tr)
+    params = model.params()
+    params[-2] += np.float32(delta / 8.0)       # b3[0], the order unit's bias
+    model = dh2.Model(params)
     model.save(args.out)
     print(json.dumps({
         "samples_train": int(len(Xtr)), "samples_val": int(len(Xva)), "meshes": args.meshes, "m_ref": args.m_ref,
-        "data_s": round(t_data, 2), "train_s": round(t_train, 2), "steps": args.steps, "batch": args.batch,
-        "loss_first": hist[0][1], "loss_last": hist[-1][1],
-        "train": evaluate(model, Xtr, Ttr), "val": evaluate(model, Xva, Tva), "out": args.out,
+        "label_threshold_eps": c, "order_offset": delta, "data_s": round(t_data, 2), "train_s": round(t_train, 2), "steps": args.steps,
+        "batch": args.batch, "loss_first": hist[0][1], "loss_last": hist[-1][1],
+        "train": stats_tr, "val": stats_va,
+        "orders_train": mesh_orders(model, tr), "orders_val": mesh_orders(model, va), "out": args.out,
     }))
 
 
