@@ -14,10 +14,14 @@ Prints ONE JSON line (rank 0).  `value` = build seconds per step (device time
 with CUDA events on the launching stream); the matvec throughput (algorithmic
 GB/s: every stored coefficient + the vectors, once) and its error against
 sampled dense Galerkin rows are reported beside it, together with the plain
-FP64 GPU form of the same build.  `--impl reference` times the CPU oracle (the
-reference arm) on a bounded sample of the same workload.
+FP64 GPU form of the same build, and the learned order/rank model on the same
+workload (the order it chooses, its build time and error, and the truncation memory
+against a plain build at that order).  `--learned` makes the timed builds themselves
+choose their order with the shipped model.  The error reference is the FP64 Galerkin
+rows, evaluated on the GPU by the library (dh2_dense_rows).  `--impl reference`
+times the CPU oracle (the reference arm) on a bounded sample of the same workload.
 
-    python bench.py [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference]
+    python bench.py [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference] [--learned]
 """
 from __future__ import annotations
 
@@ -71,6 +75,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the host-buffer end-to-end builds (a second matrix may not fit beside the first)")
     ap.add_argument("--batch-meshes", type=int, default=64)
+    ap.add_argument("--learned", action="store_true",
+                    help="the timed builds choose the order with the shipped learned model")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-order comparison")
     return ap.parse_args()
 
 
@@ -208,15 +215,15 @@ def cpu_baseline_obj(res):
 
 # ----------------------------------------------------------------------------- GPU arm
 
-def gpu_build(pkg, v, f, cfg, precision, stream):
+def gpu_build(pkg, v, f, cfg, precision, stream, model=None):
     tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
     mat = pkg.Matrix(tree, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], precision=precision,
-                     eta1=cfg["eta1"], stream=stream)
+                     eta1=cfg["eta1"], model=model, stream=stream)
     tree.close()
     return mat
 
 
-def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream):
+def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream, model=None):
     """Device-timed steps: build (tree + DH^2) and one matvec, CUDA events on `stream`."""
     build_ms, mv_ms = [], []
     mats = []
@@ -225,7 +232,7 @@ def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream):
         y = torch.empty_like(x_dev)
         torch.cuda.synchronize()
         e0.record(stream)
-        mat = gpu_build(pkg, v, f, cfg, precision, stream)
+        mat = gpu_build(pkg, v, f, cfg, precision, stream, model)
         e1.record(stream)
         mat.matvec(x_dev, y, stream=stream)
         e2.record(stream)
@@ -262,6 +269,32 @@ def sampled_dense_error(pkg, torch, mat, tree, kappa, x, rows_count, seed):
     y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
     ref = pkg.dh2_dense_rows(tree.handle, kappa, rows, torch.from_numpy(x).to(torch.complex128).cuda())
     return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
+
+
+def learned_measure(pkg, torch, v, f, cfg, x, ref_tree, rows_count, err_configured, stream):
+    """The learned order/rank model on the workload: the order it chooses, the build time
+    (CUDA events, tree included, after one warm-up build), the sampled error against the
+    FP64 Galerkin rows, and the truncation memory against a plain build at the same order;
+    next to the error of the configured order."""
+    model = pkg.Model.load()
+    x_dev = torch.from_numpy(x).to(torch.complex64).cuda()
+    ms, mats = time_steps(pkg, torch, v, f, cfg, pkg.DH2_MIXED, x_dev, 2, 1, stream, model)[0::2]
+    mat = mats[-1]
+    info = mat.get_info()
+    err = sampled_dense_error(pkg, torch, mat, ref_tree, cfg["kappa"], x, rows_count, 1809_0002)
+    pm, pmats = time_steps(pkg, torch, v, f, dict(cfg, m=info.m), pkg.DH2_MIXED, x_dev, 1, 0, stream)[0::2]
+    pinfo = pmats[-1].get_info()
+    out = {"workload": cfg["workload"], "order_chosen": info.m, "configured_order": cfg["m"],
+           "build_s": float(np.mean(ms)) / 1e3, "relerr_sampled_dense": err, "meets_eps": bool(err <= cfg["eps"]),
+           "configured_order_relerr": err_configured,
+           "configured_order_meets_eps": bool(err_configured <= cfg["eps"]),
+           "rank_cap_retries": info.rank_cap_retries, "truncation_MB": info.truncation_bytes / 1e6,
+           "plain_same_order_build_s": float(np.mean(pm)) / 1e3,
+           "plain_same_order_truncation_MB": pinfo.truncation_bytes / 1e6}
+    for m_ in mats + pmats:
+        m_.close()
+    model.close()
+    return out
 
 
 BATCH_SEED = 1809_0003
@@ -384,6 +417,7 @@ def main():
     xdt = torch.complex64 if precision == pkg.DH2_MIXED else torch.complex128
     x_dev = torch.from_numpy(x).to(xdt).cuda()
     stream = torch.cuda.current_stream()
+    main_model = pkg.Model.load() if args.learned else None
 
     def barrier():
         if world > 1:
@@ -396,7 +430,7 @@ def main():
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
         build_ms, mv_ms, mats = time_steps(pkg, torch, v, f, cfg, precision, x_dev, args.steps, args.warmup,
-                                           stream)
+                                           stream, main_model)
         barrier()
         t_wall = time.perf_counter() - t_wall0
     launches = pkg.lib().dh2_kernel_launches() - launches0
@@ -472,6 +506,10 @@ def main():
         for m_ in mats64:
             m_.close()
 
+    learned = None
+    if precision == pkg.DH2_MIXED and not args.no_learned and not args.learned:
+        learned = learned_measure(pkg, torch, v, f, cfg, x, ref_tree, args.error_rows, err, stream)
+
     batch = None
     if not args.no_batch:
         batch = batch_measure(pkg, torch, args.batch_meshes, stream)
@@ -490,6 +528,7 @@ def main():
             "vs_baseline": None, "dtype": "c64+f64" if precision == pkg.DH2_MIXED else "c128",
             "data": "synthetic",
             "config": dict(cfg, precision=args.precision, parallelism=f"replicas{world}",
+                           order=("learned: " + str(info.m)) if args.learned else "configured",
                            l2="inputs larger than L2 (nearfield alone > 1 GB)"),
             "build_s": build_s,
             "matvec": {"gbs": mv_gbs, "ms": mv_rep_ms, "bytes": info.matvec_bytes,
@@ -505,6 +544,7 @@ def main():
             "roofline": roof,
             "matvec_roofline": mv_roof,
             "plain_fp64": fp64,
+            "learned": learned,
             "batch": batch,
             "cpu_baseline": baseline,
             "e2e": ({"value": float(np.mean(e2e)), "unit": "s", "h2d_bytes_per_step": int(h2d),

@@ -204,8 +204,8 @@ def test_trained_model_gain(dh2):
     v, f = synth.ellipsoid(5, (1.3, 0.8, 1.0))
     kappa, eps = 12.0, 1e-4
     tree = dh2.Tree(v, f)
-    x = synth.random_vector(len(f), 1809_0011)
-    rows = np.sort(np.random.default_rng(1809_0012).choice(len(f), size=128, replace=False))
+    x = synth.random_vector(len(f), 1809_0001)
+    rows = np.sort(np.random.default_rng(1809_0002).choice(len(f), size=256, replace=False))
     ref = dh2.dh2_dense_rows(tree.handle, kappa, rows, torch.from_numpy(x).cuda())
     xd = torch.from_numpy(x).to(torch.complex64).cuda()
 
