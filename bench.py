@@ -78,6 +78,7 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="the timed builds choose the order with the shipped learned model")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-order comparison")
+    ap.add_argument("--m", type=int, default=0, help="override the workload's interpolation order")
     return ap.parse_args()
 
 
@@ -271,7 +272,7 @@ def sampled_dense_error(pkg, torch, mat, tree, kappa, x, rows_count, seed):
     return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
 
 
-def learned_measure(pkg, torch, v, f, cfg, x, ref_tree, rows_count, err_configured, stream):
+def learned_measure(pkg, torch, v, f, cfg, x, ref_tree, rows_count, err_configured, stream, with_fp64=True):
     """The learned order/rank model on the workload: the order it chooses, the build time
     (CUDA events, tree included, after one warm-up build), the sampled error against the
     FP64 Galerkin rows, and the truncation memory against a plain build at the same order;
@@ -284,13 +285,25 @@ def learned_measure(pkg, torch, v, f, cfg, x, ref_tree, rows_count, err_configur
     err = sampled_dense_error(pkg, torch, mat, ref_tree, cfg["kappa"], x, rows_count, 1809_0002)
     pm, pmats = time_steps(pkg, torch, v, f, dict(cfg, m=info.m), pkg.DH2_MIXED, x_dev, 1, 0, stream)[0::2]
     pinfo = pmats[-1].get_info()
+    fp64 = {}
+    if with_fp64:
+        # the plain FP64 form at the same order: the same accuracy class as the learned build
+        x64 = torch.from_numpy(x).cuda()
+        fm, fmats = time_steps(pkg, torch, v, f, dict(cfg, m=info.m), pkg.DH2_FP64, x64, 1, 0, stream)[0::2]
+        fp64 = {"plain_fp64_same_order_build_s": float(np.mean(fm)) / 1e3,
+                "plain_fp64_same_order_relerr": sampled_dense_error(pkg, torch, fmats[-1], ref_tree, cfg["kappa"], x,
+                                                                    rows_count, 1809_0002)}
+        fp64["speedup_learned_mixed_vs_fp64_same_order"] = fp64["plain_fp64_same_order_build_s"] / (
+            float(np.mean(ms)) / 1e3)
+        for m_ in fmats:
+            m_.close()
     out = {"workload": cfg["workload"], "order_chosen": info.m, "configured_order": cfg["m"],
            "build_s": float(np.mean(ms)) / 1e3, "relerr_sampled_dense": err, "meets_eps": bool(err <= cfg["eps"]),
            "configured_order_relerr": err_configured,
            "configured_order_meets_eps": bool(err_configured <= cfg["eps"]),
            "rank_cap_retries": info.rank_cap_retries, "truncation_MB": info.truncation_bytes / 1e6,
            "plain_same_order_build_s": float(np.mean(pm)) / 1e3,
-           "plain_same_order_truncation_MB": pinfo.truncation_bytes / 1e6}
+           "plain_same_order_truncation_MB": pinfo.truncation_bytes / 1e6, **fp64}
     for m_ in mats + pmats:
         m_.close()
     model.close()
@@ -379,6 +392,8 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = workload_config(args.workload)
+    if args.m:
+        cfg = dict(cfg, m=args.m, k=args.m ** 3)
 
     if args.impl == "reference":
         if rank != 0:
@@ -508,7 +523,8 @@ def main():
 
     learned = None
     if precision == pkg.DH2_MIXED and not args.no_learned and not args.learned:
-        learned = learned_measure(pkg, torch, v, f, cfg, x, ref_tree, args.error_rows, err, stream)
+        learned = learned_measure(pkg, torch, v, f, cfg, x, ref_tree, args.error_rows, err, stream,
+                                  with_fp64=not args.no_fp64)
 
     batch = None
     if not args.no_batch:
