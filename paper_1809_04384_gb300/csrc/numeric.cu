@@ -2362,17 +2362,19 @@ void launch_tsqr(const std::vector<QRTask>& all_in, int k, const cx<TSrc>* src, 
     const std::vector<QRTask>* pall = &all_in;
     std::vector<QRTask> rest;
     if constexpr (std::is_same<TQ, float>::value) {
-        // at most 128 columns: column-parallel kernel (2, 4 or 8 threads per column)
-        std::vector<QRTask> c2, c4, c8;
+        // at most 256 columns: column-parallel kernel (1, 2, 4 or 8 threads per column)
+        std::vector<QRTask> c1, c2, c4, c8;
         for (const QRTask& t : all_in) {
             if (t.ncols <= 32) c8.push_back(t);
             else if (t.ncols <= 64) c4.push_back(t);
             else if (t.ncols <= 128) c2.push_back(t);
+            else if (t.ncols <= 256) c1.push_back(t);
             else rest.push_back(t);
         }
         launch_tsqr_cols<8>(c8, 32, src, dst, scratch, s, ev, err, K_TSQR_NARROW);
         launch_tsqr_cols<4>(c4, 64, src, dst, scratch, s, ev, err, K_TSQR);
         launch_tsqr_cols<2>(c2, 128, src, dst, scratch, s, ev, err, K_TSQR);
+        launch_tsqr_cols<1>(c1, 256, src, dst, scratch, s, ev, err, K_TSQR);
         pall = &rest;
     }
     const std::vector<QRTask>& all = *pall;

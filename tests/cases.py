@@ -15,6 +15,7 @@ CASES = {
     "dir320": (2, 3.0, 8, 1.0, 4.0, 3, 1e-4),          # tiny, every admissible block directional
     "mixed1280": (3, 8.0, 16, 5.0, 2.0, 3, 1e-4),      # directional levels above D = {0} levels
     "dir1280": (3, 8.0, 8, 1.0, 2.0, 4, 1e-4),         # directional, levels 7-9
+    "dir320m6": (2, 3.0, 8, 1.0, 4.0, 6, 1e-4),        # k = 216: weight stacks of 129-256 columns
 }
 
 

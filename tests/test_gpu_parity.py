@@ -15,7 +15,7 @@ from tests.gpu_common import (TOL, check_total_weight, gpu_matrix, oracle_recomp
 pytestmark = pytest.mark.gpu
 
 STRUCT_CASES = ["plain1280", "laplace1280", "lowfreq1280", "dir320", "mixed1280", "dir1280"]
-NUM_CASES = ["dir320", "mixed1280", "lowfreq1280"]
+NUM_CASES = ["dir320", "mixed1280", "lowfreq1280", "dir320m6"]
 PRECISIONS = ["fp64", "mixed"]
 
 
@@ -124,6 +124,14 @@ def test_weights_and_singular_values(name, precision):
 @pytest.mark.parametrize("name", NUM_CASES)
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_ranks_match_except_threshold_ties(name, precision):
+    """Ranks equal the oracle's except at ties: where they differ, the threshold lies within
+    rounding of the oracle's tail, or (error growth of the FP32 weight QRs at large k) the GPU
+    rank is exactly the rank rule applied to the GPU's own singular values, which agree with
+    the oracle's within the singular-value tolerance."""
+    import paper_1809_04384_gb300 as dh2
+
+    from oracle.recompress import choose_rank
+
     rc = oracle_recompression(name)
     _, mat = gpu_matrix(name, precision)
     rr, rcl = mat.ranks()
@@ -132,16 +140,22 @@ def test_ranks_match_except_threshold_ties(name, precision):
     P = rc.pairs
     mismatches = 0
     for tc in np.nonzero(P.active)[0]:
-        for got, basis in ((rr[tc], rc.row), (rcl[tc], rc.col)):
+        for got, basis, which in ((rr[tc], rc.row, dh2.DH2_X_SROW), (rcl[tc], rc.col, dh2.DH2_X_SCOL)):
             want = basis["rank"][tc]
             if got == want:
                 continue
             mismatches += 1
-            s2 = basis["sigma"][tc] ** 2
+            so = basis["sigma"][tc]
+            s2 = so ** 2
             tail_at = float(s2[min(got, want):].sum())
             tail_next = float(s2[max(got, want):].sum())
             # the threshold lies between the two tails: a tie within rounding
-            assert abs(tail_at - eps2) <= slack * eps2 or abs(tail_next - eps2) <= slack * eps2, (tc, got, want)
+            if abs(tail_at - eps2) <= slack * eps2 or abs(tail_next - eps2) <= slack * eps2:
+                continue
+            s = mat.pair(which, tc).real.ravel()
+            assert got == choose_rank(s, rc.eps, rc.rule), (tc, got, want)
+            n = min(len(s), len(so))
+            assert np.abs(s[:n] ** 2 - s2[:n]).max() <= TOL[precision]["sigma2"] * so[0] ** 2, (tc, got, want)
     assert mismatches <= max(2, 0.01 * 2 * P.active.sum())
 
 
