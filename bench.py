@@ -17,7 +17,9 @@ sampled dense Galerkin rows are reported beside it, together with the plain
 FP64 GPU form of the same build, and the learned order/rank model on the same
 workload (the order it chooses, its build time and error, and the truncation memory
 against a plain build at that order).  `--learned` makes the timed builds themselves
-choose their order with the shipped model.  The error reference is the FP64 Galerkin
+choose their order with the shipped model.  Before the timed region the library's
+autotuner (dh2_autotune) picks the weight-QR tile shapes on the workload itself; every
+build of the run uses them (`--no-autotune`: library defaults; `--qr-tpc a,b,c`: fixed).  The error reference is the FP64 Galerkin
 rows, evaluated on the GPU by the library (dh2_dense_rows).  `--impl reference`
 times the CPU oracle (the reference arm) on a bounded sample of the same workload.
 
@@ -79,6 +81,9 @@ def parse():
                     help="the timed builds choose the order with the shipped learned model")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-order comparison")
     ap.add_argument("--m", type=int, default=0, help="override the workload's interpolation order")
+    ap.add_argument("--no-autotune", action="store_true", help="library default tile shapes, no autotuning")
+    ap.add_argument("--qr-tpc", default="", help="fixed weight-QR threads per column 'a,b,c' (skips autotuning)")
+    ap.add_argument("--qr-group-rows", type=int, default=0, help="fixed weight-QR row-group size (with --qr-tpc)")
     return ap.parse_args()
 
 
@@ -216,12 +221,33 @@ def cpu_baseline_obj(res):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+TILES = {}   # weight-QR tile shapes chosen by the autotuner for this run (empty: library defaults)
+
+
 def gpu_build(pkg, v, f, cfg, precision, stream, model=None):
     tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
     mat = pkg.Matrix(tree, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], precision=precision,
-                     eta1=cfg["eta1"], model=model, stream=stream)
+                     eta1=cfg["eta1"], model=model, stream=stream, **TILES)
     tree.close()
     return mat
+
+
+def autotune(pkg, v, f, cfg, precision, stream):
+    """dh2_autotune on the workload itself (outside the timed region): sets TILES and returns
+    the report for the JSON line."""
+    import time as _t
+
+    tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
+    base = pkg.options(eta1=cfg["eta1"], precision=precision)
+    t0 = _t.perf_counter()
+    tuned, t_ms, b_ms = pkg.dh2_autotune(tree.handle, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], base, reps=2,
+                                         stream=stream)
+    wall = _t.perf_counter() - t0
+    tree.close()
+    TILES.update(qr_tpc=tuple(int(t) for t in tuned.qr_tpc), qr_group_rows=int(tuned.qr_group_rows))
+    return {"qr_threads_per_column": list(TILES["qr_tpc"]), "qr_group_rows": TILES["qr_group_rows"],
+            "qr_ms_per_build_tuned": t_ms, "qr_ms_per_build_default": b_ms, "tuning_s": wall,
+            "note": "0 = library default (8, 4, 2 threads per column; 1024-row groups)"}
 
 
 def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream, model=None):
@@ -331,7 +357,7 @@ def batch_measure(pkg, torch, count, stream):
     def batch_build(nstreams):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        mats = pkg.build_batch(trees, kappas, m, eta2, eps, eta1=eta1, nstreams=nstreams)
+        mats = pkg.build_batch(trees, kappas, m, eta2, eps, eta1=eta1, nstreams=nstreams, **TILES)
         torch.cuda.synchronize()
         return time.perf_counter() - t0, mats
 
@@ -438,6 +464,13 @@ def main():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+
+    if args.qr_tpc:
+        TILES.update(qr_tpc=tuple(int(t) for t in args.qr_tpc.split(",")), qr_group_rows=args.qr_group_rows)
+        tuning = {"qr_threads_per_column": list(TILES["qr_tpc"]), "qr_group_rows": args.qr_group_rows,
+                  "note": "fixed on the command line"}
+    else:
+        tuning = None if args.no_autotune else autotune(pkg, v, f, cfg, precision, stream)
 
     # warm-up and timed steps (one replica per GPU: the path is not sharded)
     launches0 = pkg.lib().dh2_kernel_launches()
@@ -560,6 +593,7 @@ def main():
             "roofline": roof,
             "matvec_roofline": mv_roof,
             "plain_fp64": fp64,
+            "autotune": tuning,
             "learned": learned,
             "batch": batch,
             "cpu_baseline": baseline,

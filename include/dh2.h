@@ -82,6 +82,12 @@ typedef struct {
                                method */
     int32_t reserved0;      /* must be 0 */
     dh2_model model;        /* the model used when learned = 1 (not owned) */
+    int32_t qr_tpc[3];      /* FP32 weight QRs of at most 32, 64 and 128 columns: threads per
+                               column of the column-parallel kernel, which sets the rows per
+                               chunk (16 x threads); 0 = the defaults 8, 4, 2; allowed
+                               1, 2, 4, 8 with threads x class width <= 256 (dh2_autotune
+                               picks them) */
+    int32_t reserved1;      /* must be 0 */
 } dh2_options;
 
 typedef struct {
@@ -246,6 +252,21 @@ int64_t dh2_kernel_launches(void);
 
 /* Waits for `stream` and reports deferred device errors. */
 dh2_status dh2_sync(void* stream);
+
+/*
+ * Autotuner (no counterpart in the paper): picks the tile shapes of the FP32 weight
+ * QRs (the dominant kernels of a build) for a workload by timing complete builds of
+ * it on `stream`.  Coordinate search starting from *base: for the column classes of
+ * at most 32, 64 and 128 columns in turn, the threads per column (qr_tpc: 16 x
+ * threads rows per chunk), then the row-group size of tall stacks (qr_group_rows in
+ * {512, 1024, 2048, 4096}); each candidate is scored by the summed CUDA-event time of
+ * the QR kernels over `reps` builds, after one warm-up build.  *tuned = *base with the
+ * chosen qr_tpc and qr_group_rows; *tuned_ms and *base_ms (may be NULL) receive the
+ * QR time per build of the choice and of *base.  The builds are discarded.  Blocks.
+ * Errors: as dh2_build_dh2, and reps < 1 or NULL tuned (DH2_EINVAL).
+ */
+dh2_status dh2_autotune(dh2_tree tree, double kappa, int32_t m, double eta, double eps, const dh2_options* base,
+                        int32_t reps, void* stream, dh2_options* tuned, double* tuned_ms, double* base_ms);
 
 /* ---- Learned order and rank (no counterpart in the paper) ----
  *

@@ -37,7 +37,8 @@ class dh2_options(C.Structure):
     _fields_ = [("eta1", C.c_double), ("leaf_max", C.c_int32), ("precision", C.c_int32),
                 ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("qr_group_rows", C.c_int32),
                 ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32),
-                ("learned", C.c_int32), ("reserved0", C.c_int32), ("model", C.c_void_p)]
+                ("learned", C.c_int32), ("reserved0", C.c_int32), ("model", C.c_void_p),
+                ("qr_tpc", C.c_int32 * 3), ("reserved1", C.c_int32)]
 
 
 class dh2_tree_info(C.Structure):
@@ -98,6 +99,8 @@ _SIGS = {
     "dh2_model_train_step": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
     "dh2_free_model": (None, [_P]),
     "dh2_dense_rows": (C.c_int, [_P, C.c_double, _P, C.c_int32, _P, _P, _P]),
+    "dh2_autotune": (C.c_int, [_P, C.c_double, C.c_int32, C.c_double, C.c_double, C.POINTER(dh2_options), C.c_int32,
+                               _P, C.POINTER(dh2_options), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dh2_learned_features": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
                                        C.POINTER(C.c_int64), _P]),
     "dh2_learned_probe": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
@@ -145,8 +148,22 @@ def options(**kw) -> dh2_options:
     o = dh2_options()
     _check(lib().dh2_options_default(C.byref(o)))
     for k, v in kw.items():
-        setattr(o, k, v)
+        if k == "qr_tpc":
+            for i, t in enumerate(v):
+                o.qr_tpc[i] = int(t)
+        else:
+            setattr(o, k, v)
     return o
+
+
+def dh2_autotune(tree, kappa, m, eta, eps, base=None, reps=2, stream=None):
+    """(tuned options, QR ms per build tuned, QR ms per build of base): the weight-QR tile
+    shapes and row-group size that build this workload fastest (timed builds)."""
+    tuned = dh2_options()
+    t_ms, b_ms = C.c_double(), C.c_double()
+    _check(lib().dh2_autotune(tree, float(kappa), int(m), float(eta), float(eps), C.byref(base or options()),
+                              int(reps), _stream(stream), C.byref(tuned), C.byref(t_ms), C.byref(b_ms)))
+    return tuned, t_ms.value, b_ms.value
 
 
 # ----------------------------------------------------------------------------- C names
@@ -310,10 +327,11 @@ class Matrix:
     build chooses the order and sizes the truncation by the learned model (m is ignored)."""
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None, stream=None):
+                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None, qr_tpc=(0, 0, 0),
+                 stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
                        qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes, tensor_cores=tensor_cores,
-                       kb_store=kb_store)
+                       kb_store=kb_store, qr_tpc=qr_tpc)
         if model is not None:
             opts.learned = 1
             opts.model = model.handle
@@ -428,9 +446,10 @@ class Matrix:
 
 
 def build_batch(trees, kappas, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                nstreams=0, model=None):
+                nstreams=0, model=None, qr_tpc=(0, 0, 0), qr_group_rows=0):
     """Concurrent builds (dh2_build_dh2_batch) wrapped as Matrix objects, in order."""
-    opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule)
+    opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_tpc=qr_tpc,
+                   qr_group_rows=qr_group_rows)
     if model is not None:
         opts.learned = 1
         opts.model = model.handle

@@ -105,6 +105,13 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
     if (o.tensor_cores != 0 && o.tensor_cores != 1) throw Error{DH2_EINVAL, f + ": tensor_cores must be 0 or 1"};
     if (o.kb_store < 0 || o.kb_store > 2) throw Error{DH2_EINVAL, f + ": kb_store must be 0, 1 or 2"};
+    static const int width[3] = {32, 64, 128};
+    for (int c = 0; c < 3; ++c) {
+        const int v = o.qr_tpc[c];
+        if (!(v == 0 || ((v == 1 || v == 2 || v == 4 || v == 8) && v * width[c] <= 256)))
+            throw Error{DH2_EINVAL, f + ": qr_tpc[" + std::to_string(c) + "] must be 0, or 1, 2, 4, 8 with "
+                                        "threads x class width <= 256"};
+    }
     if (o.learned != 0 && o.learned != 1) throw Error{DH2_EINVAL, f + ": learned must be 0 or 1"};
     if (o.learned && o.model == nullptr) throw Error{DH2_EINVAL, f + ": learned = 1 needs a model"};
     if (o.learned) {
@@ -134,7 +141,8 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->structure_ms = ms;
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
-                          o.workspace_bytes, o.tensor_cores, o.kb_store, {}};
+                          o.workspace_bytes, o.tensor_cores, o.kb_store, {o.qr_tpc[0], o.qr_tpc[1], o.qr_tpc[2]},
+                          {}};
     if (o.learned) {
         int32_t ml = m;
         learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);
@@ -265,6 +273,7 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->kb_store = 0;
     opt->learned = 0;
     opt->model = nullptr;
+    opt->qr_tpc[0] = opt->qr_tpc[1] = opt->qr_tpc[2] = 0;
     return DH2_OK;
 }
 
@@ -554,6 +563,65 @@ dh2_status dh2_matrix_get_info(dh2_matrix mat, dh2_matrix_info* out) {
         out->learned_m = mat->learned_m;
         out->rank_cap_retries = in.rank_cap_retries;
         out->truncation_bytes = in.truncation_bytes;
+    });
+}
+
+// ----------------------------------------------------------------------------- autotuner
+
+dh2_status dh2_autotune(dh2_tree tree, double kappa, int32_t m, double eta, double eps, const dh2_options* base,
+                        int32_t reps, void* stream, dh2_options* tuned, double* tuned_ms, double* base_ms) {
+    return guarded([&] {
+        DH2_REQUIRE(tuned != nullptr, "dh2_autotune: tuned is NULL");
+        DH2_REQUIRE(reps >= 1, "dh2_autotune: reps must be >= 1");
+        dh2_options o;
+        if (base) o = *base; else dh2_options_default(&o);
+        check_build_args(tree, kappa, m, eta, eps, o, "dh2_autotune");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        // QR time per build (CUDA events of the QR kernels), averaged over reps builds
+        auto score = [&](const dh2_options& c) {
+            double ms = 0;
+            for (int r = 0; r < reps; ++r) {
+                std::unique_ptr<dh2_matrix_s> mat(build_matrix(tree, kappa, m, eta, eps, c, s));
+                ms += mat->num->info.kernel_ms[K_TSQR] + mat->num->info.kernel_ms[K_TSQR_NARROW];
+            }
+            return ms / reps;
+        };
+        {   // warm-up build
+            std::unique_ptr<dh2_matrix_s> warm(build_matrix(tree, kappa, m, eta, eps, o, s));
+        }
+        dh2_options best = o;
+        const double t0 = score(best);
+        double tb = t0;
+        static const int width[3] = {32, 64, 128};
+        for (int c = 0; c < 3; ++c) {
+            for (int v : {1, 2, 4, 8}) {
+                if (v * width[c] > 256) continue;
+                dh2_options cand = best;
+                cand.qr_tpc[c] = v;
+                if (cand.qr_tpc[c] == best.qr_tpc[c] ||
+                    (best.qr_tpc[c] == 0 && v == (c == 0 ? 8 : c == 1 ? 4 : 2)))
+                    continue;   // the current choice, already scored
+                const double t = score(cand);
+                if (t < tb) {
+                    tb = t;
+                    best = cand;
+                }
+            }
+        }
+        for (int g : {512, 1024, 2048, 4096}) {
+            dh2_options cand = best;
+            cand.qr_group_rows = g;
+            if (g == (best.qr_group_rows > 0 ? best.qr_group_rows : 1024)) continue;
+            const double t = score(cand);
+            if (t < tb) {
+                tb = t;
+                best = cand;
+            }
+        }
+        *tuned = best;
+        if (tuned_ms) *tuned_ms = tb;
+        if (base_ms) *base_ms = t0;
     });
 }
 

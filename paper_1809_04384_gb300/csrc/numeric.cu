@@ -2356,13 +2356,34 @@ void launch_tsqr_cols(const std::vector<QRTask>& tasks, int kl, const cx<TSrc>* 
     }
 }
 
+// The column-parallel kernel with `tpc` threads per column (tpc * kl <= 256).
+template <class TSrc, class TDst>
+void launch_tsqr_cols_tpc(int tpc, const std::vector<QRTask>& tasks, int kl, const cx<TSrc>* src, cx<TDst>* dst,
+                          DBuf<cx<float>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err, int id) {
+    switch (tpc) {
+        case 1: launch_tsqr_cols<1>(tasks, kl, src, dst, scratch, s, ev, err, id); break;
+        case 2: launch_tsqr_cols<2>(tasks, kl, src, dst, scratch, s, ev, err, id); break;
+        case 4: launch_tsqr_cols<4>(tasks, kl, src, dst, scratch, s, ev, err, id); break;
+        default: launch_tsqr_cols<8>(tasks, kl, src, dst, scratch, s, ev, err, id); break;
+    }
+}
+
+// Threads per column of each column class: the chosen value if it fits (tpc * class width
+// <= 256), else the default (8, 4, 2 for <= 32, <= 64, <= 128 columns).
+inline int qr_class_tpc(const int32_t* tpc, int cls) {
+    static const int def[3] = {8, 4, 2}, width[3] = {32, 64, 128};
+    const int v = tpc ? tpc[cls] : 0;
+    return (v == 1 || v == 2 || v == 4 || v == 8) && v * width[cls] <= 256 ? v : def[cls];
+}
+
 template <class TSrc, class TQ, class TDst, int RPL>
 void launch_tsqr(const std::vector<QRTask>& all_in, int k, const cx<TSrc>* src, cx<TDst>* dst,
-                 DBuf<cx<TQ>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err) {
+                 DBuf<cx<TQ>>& scratch, cudaStream_t s, EventLog& ev, unsigned* err, const int32_t* tpc) {
     const std::vector<QRTask>* pall = &all_in;
     std::vector<QRTask> rest;
     if constexpr (std::is_same<TQ, float>::value) {
-        // at most 256 columns: column-parallel kernel (1, 2, 4 or 8 threads per column)
+        // at most 256 columns: column-parallel kernel (1, 2, 4 or 8 threads per column; the
+        // classes of at most 32, 64 and 128 columns take the tuned counts)
         std::vector<QRTask> c1, c2, c4, c8;
         for (const QRTask& t : all_in) {
             if (t.ncols <= 32) c8.push_back(t);
@@ -2371,9 +2392,9 @@ void launch_tsqr(const std::vector<QRTask>& all_in, int k, const cx<TSrc>* src, 
             else if (t.ncols <= 256) c1.push_back(t);
             else rest.push_back(t);
         }
-        launch_tsqr_cols<8>(c8, 32, src, dst, scratch, s, ev, err, K_TSQR_NARROW);
-        launch_tsqr_cols<4>(c4, 64, src, dst, scratch, s, ev, err, K_TSQR);
-        launch_tsqr_cols<2>(c2, 128, src, dst, scratch, s, ev, err, K_TSQR);
+        launch_tsqr_cols_tpc(qr_class_tpc(tpc, 0), c8, 32, src, dst, scratch, s, ev, err, K_TSQR_NARROW);
+        launch_tsqr_cols_tpc(qr_class_tpc(tpc, 1), c4, 64, src, dst, scratch, s, ev, err, K_TSQR);
+        launch_tsqr_cols_tpc(qr_class_tpc(tpc, 2), c2, 128, src, dst, scratch, s, ev, err, K_TSQR);
         launch_tsqr_cols<1>(c1, 256, src, dst, scratch, s, ev, err, K_TSQR);
         pall = &rest;
     }
@@ -2412,7 +2433,7 @@ void launch_tsqr(const std::vector<QRTask>& all_in, int k, const cx<TSrc>* src, 
 // extra merges cost more than the parallelism they add.)
 template <class TS, class TQ, class TD, int RPL>
 void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>* src, cx<TD>* dst,
-               cudaStream_t s, EventLog& ev, unsigned* err) {
+               cudaStream_t s, EventLog& ev, unsigned* err, const int32_t* tpc) {
     const int32_t gauto = 1024;
     std::vector<QRTask> direct, groups, merges;
     int64_t mel = 0;   // elements of the merge buffer used so far (group R factors, compact rows)
@@ -2435,11 +2456,11 @@ void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>*
         merges.push_back(QRTask{m0, t.dst, mrows, t.rout, t.ncols, t.ncols});
     }
     DBuf<cx<TQ>> scratch, merge;
-    launch_tsqr<TS, TQ, TD, RPL>(direct, k, src, dst, scratch, s, ev, err);
+    launch_tsqr<TS, TQ, TD, RPL>(direct, k, src, dst, scratch, s, ev, err, tpc);
     if (!groups.empty()) {
         merge.alloc((size_t)mel);
-        launch_tsqr<TS, TQ, TQ, RPL>(groups, k, src, merge.p, scratch, s, ev, err);
-        launch_tsqr<TQ, TQ, TD, RPL>(merges, k, merge.p, dst, scratch, s, ev, err);
+        launch_tsqr<TS, TQ, TQ, RPL>(groups, k, src, merge.p, scratch, s, ev, err, tpc);
+        launch_tsqr<TQ, TQ, TD, RPL>(merges, k, merge.p, dst, scratch, s, ev, err, tpc);
     }
 }
 
@@ -2451,11 +2472,11 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
     if (fp64) {
         if (tsqr_smem_bytes<double, 1>(k_) > 200 * 1024)
             throw Error{DH2_EUNSUPPORTED, "FP64 weight QR supports m <= 6"};
-        tsqr_tree<T, double, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+        tsqr_tree<T, double, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
     } else if (tsqr_smem_bytes<float, 2>(k_) <= 100 * 1024) {
-        tsqr_tree<T, float, T, 2>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+        tsqr_tree<T, float, T, 2>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
     } else {
-        tsqr_tree<T, float, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p);
+        tsqr_tree<T, float, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
     }
 }
 

@@ -32,6 +32,7 @@ struct BuildParams {
     int32_t m, precision, rank_rule, qr_fp64, qr_group_rows;
     int64_t workspace_bytes;
     int32_t tensor_cores, kb_store;
+    int32_t qr_tpc[3];   // threads per column of the weight QRs of <= 32, <= 64, <= 128 columns (0 = default)
     // per active pair: the most columns its truncated bases may need (a learned estimate);
     // empty = the structural bound min(rows, k).  A pair whose truncation rank exceeds its
     // cap sends the whole pass back to the structural bound.

@@ -141,3 +141,17 @@ def test_learned_arguments_rejected_before_gpu_work(libpath):
     # a learned build without a model
     o.learned = 1
     assert L.dh2_build_dh2(None, 1.0, 5, 1.0, 1e-4, C.byref(o), None, C.byref(h)) == pkg.DH2_EINVAL
+
+
+def test_autotune_arguments_rejected_before_gpu_work(libpath):
+    import ctypes as C
+
+    import paper_1809_04384_gb300 as pkg
+
+    L = pkg.lib()
+    o = pkg.options()
+    assert list(o.qr_tpc) == [0, 0, 0]
+    t = pkg.dh2_options()
+    assert L.dh2_autotune(None, 1.0, 5, 1.0, 1e-4, C.byref(o), 1, None, C.byref(t), None, None) == pkg.DH2_EINVAL
+    assert L.dh2_autotune(None, 1.0, 5, 1.0, 1e-4, C.byref(o), 0, None, C.byref(t), None, None) == pkg.DH2_EINVAL
+    assert L.dh2_autotune(None, 1.0, 5, 1.0, 1e-4, C.byref(o), 1, None, None, None, None) == pkg.DH2_EINVAL

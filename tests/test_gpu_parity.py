@@ -302,3 +302,52 @@ def test_recomputed_block_products_match_stored(name):
     tol = max(TOL["mixed"]["matvec_same_ranks"], 2 * rc.eps)
     assert rel(ys[1], ys[0]) <= tol
     assert rel(ys[1], rc.matvec(x)) <= tol
+
+
+@pytest.mark.parametrize("name", ["dir1280", "dir320m6"])
+@pytest.mark.parametrize("tpc", [(1, 1, 1), (2, 2, 1), (4, 1, 2)])
+def test_qr_tile_shapes_match_oracle(name, tpc):
+    """Every threads-per-column choice of the column-parallel weight QR (the autotuner's
+    search space) gives the oracle's weights and product."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    rc = oracle_recompression(name)
+    v, f, p, *_ = oracle_structure(name)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    mat = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"], qr_tpc=tpc)
+    tol = TOL["mixed"]
+    for tc in np.nonzero(rc.pairs.active)[0]:
+        R = mat.pair(dh2.DH2_X_R, tc)
+        Ro = rc.R[tc]
+        assert rel(R.conj().T @ R, Ro.conj().T @ Ro) <= tol["gram"], ("R", tc)
+    x = x_vector(rc.tree.n)
+    y = mat.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy().astype(np.complex128)
+    assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps)
+
+
+def test_autotune_picks_valid_tiles():
+    import paper_1809_04384_gb300 as dh2
+
+    v, f, p, *_ = oracle_structure("dir1280")
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    base = dh2.options(eta1=p["eta1"])
+    tuned, t_ms, b_ms = dh2.dh2_autotune(tree.handle, p["kappa"], p["m"], p["eta2"], p["eps"], base, reps=1)
+    assert 0 < t_ms <= b_ms
+    width = (32, 64, 128)
+    for c in range(3):
+        assert tuned.qr_tpc[c] in (0, 1, 2, 4, 8) and tuned.qr_tpc[c] * width[c] <= 256
+    assert tuned.qr_group_rows in (0, 512, 1024, 2048, 4096)
+    assert tuned.eta1 == p["eta1"] and tuned.precision == base.precision
+    # the tuned options build the same matrix up to rounding
+    m0 = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"])
+    m1 = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"],
+                    qr_tpc=tuple(tuned.qr_tpc), qr_group_rows=tuned.qr_group_rows)
+    import torch
+
+    x = torch.from_numpy(x_vector(m0.n)).to(torch.complex64).cuda()
+    assert rel(m1.matvec(x).cpu().numpy(), m0.matvec(x).cpu().numpy()) <= 2 * p["eps"]
+    # bad tile choices are refused before any GPU work
+    with pytest.raises(dh2.DH2Error):
+        dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"], qr_tpc=(0, 8, 0))
