@@ -1741,22 +1741,77 @@ struct LeafOut2 {
     int64_t poff;            // panel offset (row 0, column 0); even
     int64_t coff;            // offset of the panel's column -> x~ index list
     int32_t off, rows, ld;   // cluster-order row offset, rows, panel width (even)
-    int32_t qbeg, qend, pad;
+    int32_t qbeg, qend;      // leaf-basis items
+    int32_t nbeg, nend;      // nearfield parts (NearPart) of this leaf
+    int32_t pad;
 };
+
+// One column chunk of a leaf's nearfield panel: rows x w entries starting at panel offset
+// poff (even), row pitch ld; its partial row sums go to pbuf[pofs + i].
+struct NearPart {
+    int64_t poff, coff, pofs;
+    int32_t rows, ld, w, pad;
+};
+constexpr int kNearChunk = 2048;   // panel columns per part (and x~ values staged per CTA)
+
+// Streams one panel row chunk: sum_j row[j] * xg[j] over this lane's columns (16-byte loads
+// for complex FP32).
+template <class T>
+__device__ __forceinline__ cx<T> near_row_dot(const cx<T>* __restrict__ row, const cx<T>* xg, int w, int lane,
+                                              cx<T> a) {
+    if constexpr (sizeof(cx<T>) == 8) {
+        const float4* r4 = reinterpret_cast<const float4*>(row);
+        const int w2 = w >> 1;
+#pragma unroll 4
+        for (int j = lane; j < w2; j += 32) {
+            float4 v = __ldg(r4 + j);
+            cx<T> x0 = xg[2 * j], x1 = xg[2 * j + 1];
+            fma_cx(a, cx<T>{(T)v.x, (T)v.y}, x0);
+            fma_cx(a, cx<T>{(T)v.z, (T)v.w}, x1);
+        }
+    } else {
+#pragma unroll 4
+        for (int j = lane; j < w; j += 32) fma_cx(a, row[j], xg[j]);
+    }
+    return a;
+}
+
+// Nearfield partial sums of one panel part (one CTA per part, many per leaf, so that the
+// panels of unequal leaves spread over several waves): x~ of the part's columns staged in
+// shared memory, each warp streams rows warp, warp + 8, ... and writes pbuf[pofs + i].
+template <class T>
+__global__ void __launch_bounds__(256) k_near_part(const NearPart* __restrict__ parts,
+                                                   const int32_t* __restrict__ colidx,
+                                                   const cx<T>* __restrict__ Pn, const cx<T>* __restrict__ xt,
+                                                   cx<T>* __restrict__ pbuf) {
+    __shared__ cx<T> xg[kNearChunk];
+    const NearPart p = parts[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = threadIdx.x; j < p.w; j += blockDim.x) xg[j] = xt[colidx[p.coff + j]];
+    __syncthreads();
+    for (int i = warp; i < p.rows; i += 8) {
+        cx<T> a = near_row_dot<T>(Pn + p.poff + (int64_t)i * p.ld, xg, p.w, lane, zero<T>());
+        a = warp_sum(a);
+        if (lane == 0) pbuf[p.pofs + i] = a;
+    }
+}
 
 // y[perm[r]] = sum_c Q_tc y^_tc + nearfield row panel: one CTA per leaf.  The x~ values of a
 // chunk of panel columns are gathered into shared memory once; each warp then streams its rows
 // with 16-byte loads (lane-partial sums kept in registers for up to 8 rows per warp).
 // MODE 0: both parts; MODE 1: the nearfield part only (y = panel x~); MODE 2: the leaf-basis
-// part only, added to y (y += Q y^), so that the nearfield can run beside the transforms.
+// part plus the nearfield partial sums of the leaf's parts (k_near_part, which runs beside
+// the transforms), summed in part order.
 template <class T, class TY, int MODE>
 __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ leaves,
                                                    const LeafQ* __restrict__ qitems,
                                                    const int32_t* __restrict__ colidx,
                                                    const cx<T>* __restrict__ Q, const cx<T>* __restrict__ yh,
                                                    const cx<T>* __restrict__ Pn, const cx<T>* __restrict__ xt,
-                                                   const int32_t* __restrict__ perm, cx<TY>* y) {
-    constexpr int CH = 2048;
+                                                   const int32_t* __restrict__ perm, cx<TY>* y,
+                                                   const NearPart* __restrict__ parts = nullptr,
+                                                   const cx<T>* __restrict__ pbuf = nullptr) {
+    constexpr int CH = kNearChunk;
     constexpr int RW = 8;                    // rows per warp per row tile
     __shared__ cx<T> xg[CH];
     const LeafOut2 lf = leaves[blockIdx.x];
@@ -1773,23 +1828,7 @@ __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ 
             for (int q = 0; q < RW; ++q) {
                 const int i = r0 + warp + 8 * q;
                 if (i >= lf.rows) break;
-                const cx<T>* row = Pn + lf.poff + (int64_t)i * lf.ld + c0;
-                cx<T> a = acc[q];
-                if constexpr (sizeof(cx<T>) == 8) {
-                    const float4* r4 = reinterpret_cast<const float4*>(row);
-                    const int w2 = w >> 1;
-#pragma unroll 4
-                    for (int j = lane; j < w2; j += 32) {
-                        float4 v = __ldg(r4 + j);
-                        cx<T> x0 = xg[2 * j], x1 = xg[2 * j + 1];
-                        fma_cx(a, cx<T>{(T)v.x, (T)v.y}, x0);
-                        fma_cx(a, cx<T>{(T)v.z, (T)v.w}, x1);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int j = lane; j < w; j += 32) fma_cx(a, row[j], xg[j]);
-                }
-                acc[q] = a;
+                acc[q] = near_row_dot<T>(Pn + lf.poff + (int64_t)i * lf.ld + c0, xg, w, lane, acc[q]);
             }
             __syncthreads();
         }
@@ -1807,9 +1846,9 @@ __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ 
             }
             a = warp_sum(a);
             if (lane == 0) {
-                cx<TY>& yo = y[perm[lf.off + i]];
-                if (MODE == 2) yo = cx<TY>{yo.x + TY(a.x), yo.y + TY(a.y)};
-                else yo = cx<TY>{TY(a.x), TY(a.y)};
+                if (MODE == 2)
+                    for (int e = lf.nbeg; e < lf.nend; ++e) a = a + pbuf[parts[e].pofs + i];
+                y[perm[lf.off + i]] = cx<TY>{TY(a.x), TY(a.y)};
             }
         }
     }
@@ -2007,6 +2046,9 @@ private:
     std::vector<int64_t> st_off_;                    // per admissible block: S~ offset (row-list order)
     DBuf<int32_t> colidx_;
     DBuf<LeafOut2> leaf_out2_;
+    DBuf<NearPart> near_parts_;   // column chunks of the nearfield panels (graph product)
+    DBuf<cx<T>> near_pbuf_;       // their partial row sums
+    int64_t n_near_parts_ = 0;
     int32_t kmax_row_ = 0;
 
     bool timing_on_ = false;
@@ -3088,6 +3130,27 @@ void Num<T>::plan_matvec(cudaStream_t s) {
         o.qend = lo[i].qend;
         lo2.push_back(o);
     }
+    // nearfield parts of the graph product: every panel cut into kNearChunk-column chunks
+    std::vector<NearPart> np;
+    int64_t pofs = 0;
+    for (auto& o : lo2) {
+        o.nbeg = (int32_t)np.size();
+        for (int32_t c0 = 0; c0 < o.ld; c0 += kNearChunk) {
+            NearPart pt{};
+            pt.poff = o.poff + c0;
+            pt.coff = o.coff + c0;
+            pt.pofs = pofs;
+            pt.rows = o.rows;
+            pt.ld = o.ld;
+            pt.w = std::min(kNearChunk, o.ld - c0);
+            np.push_back(pt);
+            pofs += o.rows;
+        }
+        o.nend = (int32_t)np.size();
+    }
+    n_near_parts_ = (int64_t)np.size();
+    upload_vec(near_parts_, np, s);
+    near_pbuf_.alloc(std::max<int64_t>(pofs, 1));
     upload_vec(leaf_out2_, lo2, s);
     kmax_row_ = 0;
     for (int64_t a = 0; a < na_; ++a) kmax_row_ = std::max(kmax_row_, rank_[0][a]);
@@ -3215,7 +3278,8 @@ void Num<T>::matvec(const void* x, void* y, int dtype, cudaStream_t s) {
 }
 
 // split = true (graph capture only): the nearfield part of the output runs on a side branch
-// that forks after the gather and joins before the leaf-basis part, which adds into y.
+// that forks after the gather (k_near_part, panel column chunks) and joins before the
+// leaf-basis part, which adds the chunks' partial sums in a fixed order and writes y.
 template <class T>
 void Num<T>::launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bool split) {
     const unsigned g = grid_for(n_, kThreads);
@@ -3233,13 +3297,11 @@ void Num<T>::launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bo
     if (split && n_leaves_) {
         DH2_CHECK_CUDA(cudaEventRecord(fork_ev_, s));
         DH2_CHECK_CUDA(cudaStreamWaitEvent(side_stream_, fork_ev_, 0));
-        if (dtype == DH2_C64)
-            k_leaf_out2<T, float, 1><<<(unsigned)n_leaves_, 256, 0, side_stream_>>>(
-                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
-        else
-            k_leaf_out2<T, double, 1><<<(unsigned)n_leaves_, 256, 0, side_stream_>>>(
-                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
-        DH2_CHECK_LAUNCH("k_leaf_out2 (nearfield)");
+        if (n_near_parts_) {
+            k_near_part<T><<<(unsigned)n_near_parts_, 256, 0, side_stream_>>>(near_parts_.p, colidx_.p, near_.p,
+                                                                           xt_.p, near_pbuf_.p);
+            DH2_CHECK_LAUNCH("k_near_part");
+        }
         DH2_CHECK_CUDA(cudaEventRecord(join_ev_, side_stream_));
     }
     constexpr int WPB = 8;   // warps per CTA of the transform kernels
@@ -3283,10 +3345,12 @@ void Num<T>::launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bo
         DH2_CHECK_CUDA(cudaStreamWaitEvent(s, join_ev_, 0));
         if (dtype == DH2_C64)
             k_leaf_out2<T, float, 2><<<(unsigned)n_leaves_, 256, 0, s>>>(
-                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y);
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y,
+                near_parts_.p, near_pbuf_.p);
         else
             k_leaf_out2<T, double, 2><<<(unsigned)n_leaves_, 256, 0, s>>>(
-                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y);
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y,
+                near_parts_.p, near_pbuf_.p);
         DH2_CHECK_LAUNCH("k_leaf_out2 (leaf bases)");
     } else if (n_leaves_) {
         if (dtype == DH2_C64) {
