@@ -412,6 +412,16 @@ def batch_measure(pkg, torch, count, stream):
             "blocking call; matvec: CUDA events on the joining stream"}
 
 
+def max_over_ranks(values, torch, world, device):
+    """Each value's maximum over the ranks (the slowest replica sets the step time); the
+    values themselves when there is one rank.  device: "cuda" under NCCL, "cpu" under gloo."""
+    if world <= 1:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -485,10 +495,7 @@ def main():
     launches_per_step = launches / (args.steps + args.warmup)
     build_s = float(np.mean(build_ms)) / 1e3
     step_ms = float(np.mean(np.array(build_ms) + np.array(mv_ms)))
-    if world > 1:
-        t = torch.tensor([build_s, step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        build_s, step_ms = float(t[0]), float(t[1])
+    build_s, step_ms = max_over_ranks([build_s, step_ms], torch, world, "cuda")
     mat = mats[-1]
     info = mat.get_info()
     free_b, total_b = torch.cuda.mem_get_info()
