@@ -41,7 +41,7 @@ typedef enum {
     DH2_ECUDA = -3,         /* a CUDA runtime call or kernel launch failed */
     DH2_ETIMEOUT = -4,      /* a bounded device-side wait gave up */
     DH2_ENUMERIC = -5,      /* NaN/Inf or a non-converged factorisation */
-    DH2_EUNSUPPORTED = -6   /* valid but not supported by this build (e.g. k too large) */
+    DH2_EUNSUPPORTED = -6   /* valid but not supported by the library (e.g. k too large) */
 } dh2_status;
 
 enum { DH2_FP64 = 0, DH2_MIXED = 1 };                 /* dh2_options.precision */
