@@ -155,3 +155,37 @@ def test_autotune_arguments_rejected_before_gpu_work(libpath):
     assert L.dh2_autotune(None, 1.0, 5, 1.0, 1e-4, C.byref(o), 1, None, C.byref(t), None, None) == pkg.DH2_EINVAL
     assert L.dh2_autotune(None, 1.0, 5, 1.0, 1e-4, C.byref(o), 0, None, C.byref(t), None, None) == pkg.DH2_EINVAL
     assert L.dh2_autotune(None, 1.0, 5, 1.0, 1e-4, C.byref(o), 1, None, None, None, None) == pkg.DH2_EINVAL
+
+
+def test_null_handles_rejected_before_gpu_work(libpath):
+    """Every entry point that takes a handle refuses a NULL one with DH2_EINVAL and a message,
+    without touching the device."""
+    import ctypes as C
+
+    import paper_1809_04384_gb300 as pkg
+
+    L = pkg.lib()
+    i32 = C.c_int32()
+    buf = (C.c_double * 16)()
+    calls = {
+        "dh2_matvec": lambda: L.dh2_matvec(None, buf, buf, pkg.DH2_C64, None),
+        "dh2_matvec_noalloc": lambda: L.dh2_matvec_noalloc(None, buf, buf, pkg.DH2_C64, None),
+        "dh2_matvec_host": lambda: L.dh2_matvec_host(None, buf, buf, None),
+        "dh2_set_timing": lambda: L.dh2_set_timing(None, 1),
+        "dh2_tree_get_info": lambda: L.dh2_tree_get_info(None, C.byref(pkg.dh2_tree_info())),
+        "dh2_tree_export": lambda: L.dh2_tree_export(None, *([None] * 9)),
+        "dh2_matrix_get_info": lambda: L.dh2_matrix_get_info(None, C.byref(pkg.dh2_matrix_info())),
+        "dh2_export_directions": lambda: L.dh2_export_directions(None, 0, C.byref(i32), None, None, None),
+        "dh2_export_blocks": lambda: L.dh2_export_blocks(None, None, None, None),
+        "dh2_export_pair": lambda: L.dh2_export_pair(None, 0, 0, buf, 16, C.byref(i32), C.byref(i32)),
+        "dh2_export_ranks": lambda: L.dh2_export_ranks(None, None, None),
+        "dh2_dense_rows": lambda: L.dh2_dense_rows(None, 1.0, None, 1, None, None, None),
+        "dh2_model_get_params": lambda: L.dh2_model_get_params(None, None),
+    }
+    for name, call in calls.items():
+        assert call() == pkg.DH2_EINVAL, name
+        assert L.dh2_last_error(), name
+    # freeing NULL handles is a no-op
+    L.dh2_free_tree(None)
+    L.dh2_free_matrix(None)
+    L.dh2_free_model(None)
