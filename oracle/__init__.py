@@ -23,6 +23,11 @@ with numpy (FP64, complex128) and ``numpy.linalg`` QR/SVD as library steps:
                       to Q/F/C, projection of couplings (Lemma "Projections"),
                       and the recompressed DH^2 matvec.
 * ``dense_compress``- Section 3.1 on an explicitly expanded matrix (tiny meshes).
+* ``learned``       - the learned order/rank model: features, interpolation-error
+                      labels, MLP forward/backward with BF16 weights, Adam.
+* ``double_layer``  - the double-layer potential (Section 5's second operator):
+                      kernel and dense Galerkin matrix, the ground truth of the next
+                      operator the GPU path takes on.
 
 Parity status per function is stated in each module header; the one value
 with no pin (the distance of the DH^2 approximation from the dense matrix,

@@ -1,0 +1,76 @@
+"""Pins of the double-layer oracle (oracle/double_layer.py): derivative by finite differences,
+Gauss's solid-angle identity, Green's representation formula, matrix invariants."""
+import numpy as np
+import pytest
+
+import synth
+from oracle.double_layer import DoubleLayer, dlp_kernel, triangle_normals
+from oracle.geometry import helmholtz
+
+
+@pytest.mark.parametrize("kappa", [0.0, 3.0, 10.0])
+def test_kernel_is_the_normal_derivative_of_g(kappa):
+    rng = np.random.default_rng(11)
+    x = rng.normal(size=(50, 3))
+    y = rng.normal(size=(50, 3))
+    n = rng.normal(size=(50, 3))
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    h = 1e-5
+    fd = (helmholtz(x, y + h * n, kappa) - helmholtz(x, y - h * n, kappa)) / (2 * h)
+    k = dlp_kernel(x, y, n, kappa)
+    assert np.max(np.abs(fd - k) / np.abs(k)) < 1e-6
+
+
+def test_icosphere_normals_point_outward():
+    v, f = synth.icosphere(3)
+    n = triangle_normals(v, f)
+    cen = v[f].mean(axis=1)
+    assert np.all(np.sum(n * cen, axis=1) > 0)
+    np.testing.assert_allclose(np.linalg.norm(n, axis=1), 1.0, rtol=1e-14)
+
+
+def test_gauss_identity_inside_and_outside():
+    """kappa = 0: the potential of the constant density is -1 inside and 0 outside the closed
+    surface, exactly for the polyhedron; the quadrature error falls under refinement."""
+    inside = np.array([[0.0, 0.0, 0.0], [0.1, -0.2, 0.3]])
+    outside = np.array([[0.0, 0.0, 3.0], [2.0, 1.0, 0.0]])
+    errs = []
+    for level in (2, 3, 4):
+        v, f = synth.icosphere(level)
+        D = DoubleLayer(v, f)
+        p_in = D.potential(inside, 0.0)
+        p_out = D.potential(outside, 0.0)
+        assert np.all(np.abs(p_out) < 1e-6)
+        errs.append(np.max(np.abs(p_in + 1.0)))
+    assert errs[0] < 1e-4 and errs[1] < errs[0] / 8 and errs[2] < errs[1] / 8, errs
+
+
+@pytest.mark.parametrize("kappa", [1.0, 3.0])
+def test_green_representation_of_a_plane_wave(kappa):
+    """u(x) = int [g du/dn - dg/dn_y u] for the plane wave u = exp(i kappa <d, y>) and x inside."""
+    v, f = synth.icosphere(4)
+    D = DoubleLayer(v, f)
+    d = D.disc
+    dirv = np.array([0.48, -0.6, 0.64])
+    n = D.normals[:, None, :]
+    u = np.exp(1j * kappa * (d.x3 @ dirv))
+    du = 1j * kappa * (n @ dirv) * u
+    for x in (np.array([0.1, -0.2, 0.3]), np.zeros(3)):
+        s = np.sum(d.w3 * (helmholtz(x[None, None, :], d.x3, kappa) * du
+                           - dlp_kernel(x[None, None, :], d.x3, n, kappa) * u))
+        assert abs(s - np.exp(1j * kappa * (x @ dirv))) < 1e-6
+
+
+def test_matrix_invariants():
+    v, f = synth.icosphere(3)
+    D = DoubleLayer(v, f)
+    K0 = D.dense(0.0)
+    assert np.all(np.diag(K0) == 0)
+    assert np.abs(K0.imag).max() == 0.0
+    # on the surface the identity gives -1/2: Galerkin row sums approach -|T_i| / 2
+    ratio = K0.sum(axis=1).real / D.disc.area
+    assert np.all(np.abs(ratio + 0.5) < 0.01)
+    # entries of a sub-grid equal those of the full matrix
+    K = D.dense(4.0)
+    rows, cols = np.array([5, 77, 300]), np.array([0, 5, 1000, 1279])
+    np.testing.assert_array_equal(D.entries(rows, cols, 4.0), K[np.ix_(rows, cols)])
