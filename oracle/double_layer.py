@@ -15,17 +15,27 @@ layer operator with the kernel differentiated along the normal of the y element,
   integrand and k_ii vanish;
 * ``potential(points)`` = int_Gamma d/dn_y g(x, y) dy (density 1) by the 3-point rule.
 
+* ``InterpolatedDLP``: its directional interpolation (rows V_tc as for the single layer,
+  columns W_sc from the normal derivative of the modified Lagrange polynomials, the same
+  transfers and couplings), stored and expanded like ``oracle.interp.InterpolatedDH2``.
+
 Pins (tests/test_oracle_double_layer.py): the kernel equals central finite differences of
 g along n_y; for kappa = 0 the potential of the constant density is -1 inside the closed
 surface and 0 outside (Gauss's solid-angle identity, exact for the closed polyhedron, so only
-quadrature error remains and it falls under refinement); k_ii = 0; kappa = 0 gives a real
-matrix.
+quadrature error remains and it falls under refinement); Green's representation formula of a
+plane wave inside the sphere; k_ii = 0; kappa = 0 gives a real matrix.  Interpolated form:
+gradients of the tensor Lagrange polynomials reproduce gradients of polynomials of degree
+<= m - 1 per axis; W applied to nodal values of a cubic equals the integral of its normal
+derivative (closed form by the 7-point rule); the blockwise product equals the expanded
+matrix by brute force; the distance to the dense matrix falls as m grows (convergence, not
+a pin).
 """
 from __future__ import annotations
 
 import numpy as np
 
 from .geometry import FOUR_PI, Discretisation
+from .interp import InterpolatedDH2
 
 
 def triangle_normals(vertices, triangles):
@@ -76,3 +86,97 @@ class DoubleLayer:
         y = d.x3[None, :, :, :]                                          # (1,n,3,3)
         ny = self.normals[None, :, None, :]
         return np.sum(d.w3[None, :, :] * dlp_kernel(x, y, ny, kappa), axis=(1, 2))
+
+
+# --------------------------------------------------------------------------- interpolated DLP
+
+
+def lagrange_1d_derivative(nodes, x):
+    """l_j'(x) for the 1-D Lagrange basis on `nodes`: (len(x), m), product form
+    l_j'(x) = sum_{k != j} 1 / (xi_j - xi_k) prod_{i != j, k} (x - xi_i) / (xi_j - xi_i)."""
+    m = len(nodes)
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros((len(x), m))
+    for j in range(m):
+        for k in range(m):
+            if k == j:
+                continue
+            term = np.full(len(x), 1.0 / (nodes[j] - nodes[k]))
+            for i in range(m):
+                if i != j and i != k:
+                    term *= (x - nodes[i]) / (nodes[j] - nodes[i])
+            out[:, j] += term
+    return out
+
+
+class InterpolatedDLP(InterpolatedDH2):
+    """The analytic DH^2 matrix of the double-layer potential: rows as for the single layer
+    (V_tc), columns with the normal derivative of the modified Lagrange polynomials,
+        w_{sc, j mu} = int phi_j d/dn_j [exp(i kappa <y, c>) L_{s,mu}(y)] dy
+                     = int phi_j exp(i kappa <y, c>) (i kappa <n_j, c> L_{s,mu}(y) + <n_j, grad L_{s,mu}(y)>) dy,
+    so that a block is V_tc S_b W_sc^* (the y factor of the expansion of g is
+    exp(-i kappa <y, c>) L_{s,mu}(y), differentiated along n_y).  The transfers are those
+    of V: the normal derivative is linear and acts after the nested expansion."""
+
+    def __init__(self, layer: DoubleLayer, tree, dirs, blocks, kappa, m):
+        super().__init__(layer.disc, tree, dirs, blocks, kappa, m)
+        self.layer = layer
+
+    def lagrange_grad(self, t, x):
+        """grad L_{t,nu}(x) for points x (p, 3): array (p, k, 3), nu = nx + m ny + m^2 nz."""
+        c = self.cheb
+        l = [c.lagrange_1d(t, a, x[:, a]) for a in range(3)]
+        d = [lagrange_1d_derivative(c.nodes[t, a], x[:, a]) for a in range(3)]
+
+        def tensor(fx, fy, fz):
+            return (fz[:, :, None, None] * fy[:, None, :, None] * fx[:, None, None, :]).reshape(len(x), -1)
+
+        return np.stack([tensor(d[0], l[1], l[2]), tensor(l[0], d[1], l[2]), tensor(l[0], l[1], d[2])], axis=2)
+
+    def leaf_col_basis(self, s, c):
+        """W_sc for a leaf s: (#s, k), rows in cluster order (3-point rule)."""
+        idx = self.tree.indices(s)
+        x = self.disc.x3[idx]
+        w = self.disc.w3[idx]
+        nrm = self.layer.normals[idx]                                  # (#s, 3)
+        cvec = self.direction(s, c)
+        pts = x.reshape(-1, 3)
+        npt = np.repeat(nrm, 3, axis=0)                                # normal of each point's element
+        lag = self.cheb.lagrange(s, pts)                               # (3#s, k)
+        grad = self.lagrange_grad(s, pts)                              # (3#s, k, 3)
+        dn = np.einsum("pka,pa->pk", grad, npt) + 1j * self.kappa * (npt @ cvec)[:, None] * lag
+        wave = np.exp(1j * self.kappa * (pts @ cvec))
+        vals = (wave[:, None] * dn).reshape(len(idx), 3, -1)
+        return np.einsum("iq,iqn->in", w, vals)
+
+    def full_col_basis(self, s, c):
+        tr = self.tree
+        if tr.is_leaf(s):
+            return self.leaf_col_basis(s, c)
+        c1 = self.son_direction(s, c)
+        return np.vstack([self.full_col_basis(ss, c1) @ self.transfer(ss, c)
+                          for ss in (tr.son0[s], tr.son1[s])])
+
+    def nearfield_block(self, t, s):
+        return self.layer.entries(self.tree.indices(t), self.tree.indices(s), self.kappa)
+
+    def to_dense(self):
+        n = self.tree.n
+        A = np.zeros((n, n), dtype=np.complex128)
+        for (t, s) in self.blocks.near:
+            A[np.ix_(self.tree.indices(t), self.tree.indices(s))] = self.nearfield_block(t, s)
+        for b, (t, s, c) in enumerate(self.blocks.adm):
+            A[np.ix_(self.tree.indices(t), self.tree.indices(s))] = (
+                self.full_basis(t, c) @ self.coupling(b) @ self.full_col_basis(s, c).conj().T)
+        return A
+
+    def matvec(self, x):
+        tr = self.tree
+        y = np.zeros(tr.n, dtype=np.complex128)
+        for (t, s) in self.blocks.near:
+            y[tr.indices(t)] += self.nearfield_block(t, s) @ x[tr.indices(s)]
+        for b, (t, s, c) in enumerate(self.blocks.adm):
+            Vt = self.full_basis(t, c)
+            Ws = self.full_col_basis(s, c)
+            y[tr.indices(t)] += Vt @ (self.coupling(b) @ (Ws.conj().T @ x[tr.indices(s)]))
+        return y

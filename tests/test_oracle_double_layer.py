@@ -74,3 +74,78 @@ def test_matrix_invariants():
     K = D.dense(4.0)
     rows, cols = np.array([5, 77, 300]), np.array([0, 5, 1000, 1279])
     np.testing.assert_array_equal(D.entries(rows, cols, 4.0), K[np.ix_(rows, cols)])
+
+
+def _dir320():
+    from oracle.structure import build_block_tree, build_cluster_tree, build_directions
+    from tests.cases import CASES
+
+    level, kappa, leaf, eta1, eta2, m, eps = CASES["dir320"]
+    v, f = synth.icosphere(level)
+    tr = build_cluster_tree(v, f, leaf)
+    dirs = build_directions(tr, kappa, eta1)
+    bt = build_block_tree(tr, dirs, kappa, eta2)
+    return v, f, tr, dirs, bt, kappa
+
+
+def test_lagrange_gradients_reproduce_polynomial_gradients():
+    from oracle.double_layer import InterpolatedDLP
+
+    v, f, tr, dirs, bt, kappa = _dir320()
+    I = InterpolatedDLP(DoubleLayer(v, f), tr, dirs, bt, kappa, 3)
+    t = 5
+    xi = I.cheb.points(t)
+    p = lambda q: q[:, 0] ** 2 * q[:, 1] - 3 * q[:, 2] ** 2 + q[:, 0] * q[:, 2] + 2.0   # degree <= 2 per axis
+    grad_p = lambda q: np.stack([2 * q[:, 0] * q[:, 1] + q[:, 2], q[:, 0] ** 2, -6 * q[:, 2] + q[:, 0]], axis=1)
+    lo, hi = tr.lo[t], tr.hi[t]
+    y = lo + (hi - lo) * np.random.default_rng(2).uniform(size=(40, 3))
+    got = np.einsum("n,pna->pa", p(xi), I.lagrange_grad(t, y))
+    np.testing.assert_allclose(got, grad_p(y), atol=1e-11 * np.abs(grad_p(y)).max())
+
+
+def test_column_basis_is_the_normal_derivative_on_polynomials():
+    """W applied to the nodal values of a polynomial p (degree <= m - 1 per axis) is the
+    3-point rule of d/dn [exp(i kappa <y, c>) p(y)], here by central finite differences."""
+    from oracle.double_layer import InterpolatedDLP
+
+    v, f, tr, dirs, bt, kappa = _dir320()
+    layer = DoubleLayer(v, f)
+    I = InterpolatedDLP(layer, tr, dirs, bt, kappa, 3)
+    p = lambda q: q[..., 0] ** 2 * q[..., 1] - 3 * q[..., 2] ** 2 + q[..., 0] * q[..., 2] + 2.0
+    leaves = [t for t in range(tr.nc) if tr.is_leaf(t)]
+    checked = 0
+    for s in leaves[:6]:
+        for c in range(dirs.count(int(tr.level[s]))):
+            cvec = I.direction(s, c)
+            W = I.leaf_col_basis(s, c)
+            got = W @ p(I.cheb.points(s))
+            idx = tr.indices(s)
+            y = layer.disc.x3[idx]                                  # (#s, 3, 3)
+            n = layer.normals[idx][:, None, :]
+            h = 1e-6
+            f_ = lambda q: np.exp(1j * kappa * (q @ cvec)) * p(q)
+            dn = (f_(y + h * n) - f_(y - h * n)) / (2 * h)
+            want = np.sum(layer.disc.w3[idx] * dn, axis=1)
+            np.testing.assert_allclose(got, want, rtol=1e-7, atol=1e-9 * np.abs(want).max())
+            checked += 1
+    assert checked >= 6
+
+
+def test_interpolated_dlp_product_and_convergence():
+    from oracle.double_layer import InterpolatedDLP
+
+    v, f, tr, dirs, bt, kappa = _dir320()
+    layer = DoubleLayer(v, f)
+    Kd = layer.dense(kappa)
+    x = synth.random_vector(len(f), 5)
+    errs = []
+    for m in (3, 4, 5):
+        I = InterpolatedDLP(layer, tr, dirs, bt, kappa, m)
+        A = I.to_dense()
+        assert np.linalg.norm(I.matvec(x) - A @ x) <= 1e-13 * np.linalg.norm(A @ x)
+        errs.append(np.linalg.norm(A - Kd) / np.linalg.norm(Kd))
+        # nearfield blocks are the dense entries themselves
+        t, s = bt.near[0]
+        np.testing.assert_array_equal(A[np.ix_(tr.indices(t), tr.indices(s))],
+                                      Kd[np.ix_(tr.indices(t), tr.indices(s))])
+    assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
