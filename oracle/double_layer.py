@@ -18,6 +18,7 @@ layer operator with the kernel differentiated along the normal of the y element,
 * ``InterpolatedDLP``: its directional interpolation (rows V_tc as for the single layer,
   columns W_sc from the normal derivative of the modified Lagrange polynomials, the same
   transfers and couplings), stored and expanded like ``oracle.interp.InterpolatedDH2``.
+* ``RecompressionDLP``: Section 3.2 with separate row and column basis weights.
 
 Pins (tests/test_oracle_double_layer.py): the kernel equals central finite differences of
 g along n_y; for kappa = 0 the potential of the constant density is -1 inside the closed
@@ -28,7 +29,9 @@ gradients of the tensor Lagrange polynomials reproduce gradients of polynomials 
 <= m - 1 per axis; W applied to nodal values of a cubic equals the integral of its normal
 derivative (closed form by the 7-point rule); the blockwise product equals the expanded
 matrix by brute force; the distance to the dense matrix falls as m grows (convergence, not
-a pin).
+a pin).  Recompression: R^* R = V^* V and R_W^* R_W = W^* W through Eq. (nested); new bases
+orthonormal; every block within eps sqrt(2 (p + 1)) of the interpolated one (the Pythagoras
+chain of Section 3.1); the product equals the expanded recompressed matrix.
 """
 from __future__ import annotations
 
@@ -36,6 +39,7 @@ import numpy as np
 
 from .geometry import FOUR_PI, Discretisation
 from .interp import InterpolatedDH2
+from .recompress import RANK_BLOCKREL, Recompression, qr_r
 
 
 def triangle_normals(vertices, triangles):
@@ -180,3 +184,80 @@ class InterpolatedDLP(InterpolatedDH2):
             Ws = self.full_col_basis(s, c)
             y[tr.indices(t)] += Vt @ (self.coupling(b) @ (Ws.conj().T @ x[tr.indices(s)]))
         return y
+
+
+# --------------------------------------------------------------------------- recompression
+
+class RecompressionDLP(Recompression):
+    """Section 3.2 for a DH^2 matrix whose column basis differs from its row basis
+    (W != V, the double-layer potential): the same steps with basis weights R from V and
+    R_W from W (Eq. basis_weights_def for each basis), block norms |R_tc S_b R_W,sc^*|_F,
+    row total weights stacking R_W,sc S_b^* and column total weights stacking R_tc S_b,
+    and the row truncation on V, the column truncation on W."""
+
+    def __init__(self, dh2: InterpolatedDLP, eps: float, rule=RANK_BLOCKREL):
+        self.dh2, self.eps, self.rule = dh2, eps, rule
+        self.tree, self.pairs, self.k = dh2.tree, dh2.pairs, dh2.k
+        self._S = {}
+        self._E = {}
+        self.R = self.weights(dh2.leaf_basis)
+        self.RW = self.weights(dh2.leaf_col_basis)
+        self.block_norms()
+        self.ZR = self.total_weights(rows=True)
+        self.ZC = self.total_weights(rows=False)
+        self.row = self.truncate_basis(self.ZR, dh2.leaf_basis)
+        self.col = self.truncate_basis(self.ZC, dh2.leaf_col_basis)
+        self.project()
+
+    def weights(self, leaf):
+        tr, P, d = self.tree, self.pairs, self.dh2
+        R = {}
+        for l in range(tr.depth, -1, -1):
+            for t, c in self.active_pairs(l):
+                if tr.is_leaf(t):
+                    a = leaf(t, c)
+                else:
+                    c1 = d.son_direction(t, c)
+                    a = np.vstack([R[P.tc(ts, c1)] @ self.E(ts, c) for ts in (tr.son0[t], tr.son1[t])])
+                R[P.tc(t, c)] = qr_r(a, self.k)
+        return R
+
+    def block_norms(self):
+        P = self.pairs
+        adm = self.dh2.blocks.adm
+        self.bnorm = np.zeros(len(adm))
+        for b, (t, s, c) in enumerate(adm):
+            self.bnorm[b] = np.linalg.norm(self.R[P.tc(t, c)] @ self.S(b) @ self.RW[P.tc(s, c)].conj().T)
+
+    def total_weights(self, rows: bool):
+        tr, P = self.tree, self.pairs
+        adm = self.dh2.blocks.adm
+        Z = {}
+        for l in range(tr.depth + 1):
+            for t, c in self.active_pairs(l):
+                tc = P.tc(t, c)
+                parts = []
+                for b in (P.row[tc] if rows else P.col[tc]):
+                    tb, sb, _ = adm[b]
+                    if rows:
+                        parts.append(self.RW[P.tc(sb, c)] @ self.S(b).conj().T / self.bnorm[b])
+                    else:
+                        parts.append(self.R[P.tc(tb, c)] @ self.S(b) / self.bnorm[b])
+                tp = tr.parent[t]
+                if tp >= 0:
+                    for cp in P.sd_inverse(tp, c):
+                        zp = Z.get(P.tc(tp, cp))
+                        if zp is not None and zp.shape[0] > 0:
+                            parts.append(zp @ self.E(t, cp).conj().T)
+                stack = np.vstack(parts) if parts else np.zeros((0, self.k), dtype=np.complex128)
+                Z[tc] = qr_r(stack, self.k)
+        return Z
+
+    def truncate_basis(self, Z, leaf):
+        """The truncation of Recompression.truncate with the leaf basis `leaf` (V or W)."""
+        saved = self.dh2.leaf_basis
+        try:
+            self.dh2.leaf_basis = leaf
+            return Recompression.truncate(self, Z)
+        finally:
+            self.dh2.leaf_basis = saved

@@ -1,5 +1,7 @@
 """Pins of the double-layer oracle (oracle/double_layer.py): derivative by finite differences,
 Gauss's solid-angle identity, Green's representation formula, matrix invariants."""
+import math
+
 import numpy as np
 import pytest
 
@@ -149,3 +151,51 @@ def test_interpolated_dlp_product_and_convergence():
         np.testing.assert_array_equal(A[np.ix_(tr.indices(t), tr.indices(s))],
                                       Kd[np.ix_(tr.indices(t), tr.indices(s))])
     assert errs[1] < errs[0] / 3 and errs[2] < errs[1] / 3, errs
+
+
+@pytest.fixture(scope="module")
+def dlp_rc():
+    from oracle.double_layer import InterpolatedDLP, RecompressionDLP
+
+    v, f, tr, dirs, bt, kappa = _dir320()
+    I = InterpolatedDLP(DoubleLayer(v, f), tr, dirs, bt, kappa, 3)
+    return RecompressionDLP(I, 1e-4)
+
+
+def test_dlp_basis_weights_gram(dlp_rc):
+    """R_W^* R_W = W^* W and R^* R = V^* V with the bases expanded through Eq. (nested)."""
+    rc = dlp_rc
+    P = rc.pairs
+    for l in range(rc.tree.depth + 1):
+        for t, c in rc.active_pairs(l):
+            tc = P.tc(t, c)
+            for R, full in ((rc.R[tc], rc.dh2.full_basis), (rc.RW[tc], rc.dh2.full_col_basis)):
+                B = full(t, c)
+                g = B.conj().T @ B
+                assert np.linalg.norm(R.conj().T @ R - g) <= 1e-11 * np.linalg.norm(g)
+
+
+def test_dlp_recompression_bound_orthonormality_product(dlp_rc):
+    rc = dlp_rc
+    d, tr = rc.dh2, rc.tree
+    # new bases orthonormal
+    for basis in (rc.row, rc.col):
+        for l in range(tr.depth + 1):
+            for t, c in rc.active_pairs(l):
+                Q = rc.full_new_basis(basis, t, c)
+                if Q.shape[1]:
+                    assert np.linalg.norm(Q.conj().T @ Q - np.eye(Q.shape[1])) < 1e-12
+    # blockwise error bound of the Pythagoras chain
+    bound = rc.eps * math.sqrt(2 * (tr.depth + 1))
+    for b, (t, s, c) in enumerate(d.blocks.adm):
+        Gb = d.full_basis(t, c) @ rc.S(b) @ d.full_col_basis(s, c).conj().T
+        Gt = rc.full_new_basis(rc.row, t, c) @ rc.Stilde[b] @ rc.full_new_basis(rc.col, s, c).conj().T
+        assert np.linalg.norm(Gb - Gt) <= bound * np.linalg.norm(Gb)
+    # the product equals the expanded recompressed matrix
+    A = rc.to_dense()
+    x = synth.random_vector(tr.n, 1809_0001)
+    assert np.linalg.norm(rc.matvec(x) - A @ x) <= 1e-13 * np.linalg.norm(A @ x)
+    # W != V: row and column ranks are not all equal
+    rows = [rc.row["rank"][tc] for tc in rc.row["rank"]]
+    cols = [rc.col["rank"][tc] for tc in rc.col["rank"]]
+    assert rows != cols
