@@ -199,3 +199,44 @@ def test_dlp_recompression_bound_orthonormality_product(dlp_rc):
     rows = [rc.row["rank"][tc] for tc in rc.row["rank"]]
     cols = [rc.col["rank"][tc] for tc in rc.col["rank"]]
     assert rows != cols
+
+
+def _case(name):
+    from oracle.structure import build_block_tree, build_cluster_tree, build_directions
+    from tests.cases import CASES
+
+    level, kappa, leaf, eta1, eta2, m, eps = CASES[name]
+    v, f = synth.icosphere(level)
+    tr = build_cluster_tree(v, f, leaf)
+    dirs = build_directions(tr, kappa, eta1)
+    bt = build_block_tree(tr, dirs, kappa, eta2)
+    return v, f, tr, dirs, bt, kappa, m
+
+
+def test_no_admissible_block_gives_the_dense_matrix():
+    from oracle.double_layer import InterpolatedDLP
+
+    v, f, tr, dirs, bt, kappa, m = _case("plain1280")
+    assert len(bt.adm) == 0
+    layer = DoubleLayer(v, f)
+    I = InterpolatedDLP(layer, tr, dirs, bt, kappa, m)
+    np.testing.assert_array_equal(I.to_dense(), layer.dense(kappa))
+
+
+def test_nested_column_basis_is_exact_without_oscillation():
+    """kappa = 0 (c = 0): the transfers reproduce the father's polynomials exactly, so the
+    column basis built through them equals the father's directly integrated normal
+    derivatives (leaf_col_basis applied to the father's own elements and nodes)."""
+    from oracle.double_layer import InterpolatedDLP
+
+    v, f, tr, dirs, bt, kappa, m = _case("laplace1280")
+    I = InterpolatedDLP(DoubleLayer(v, f), tr, dirs, bt, kappa, m)
+    checked = 0
+    for t in range(tr.nc):
+        if tr.is_leaf(t) or tr.level[t] < tr.depth - 2:
+            continue
+        nested = I.full_col_basis(t, 0)
+        direct = I.leaf_col_basis(t, 0)
+        assert np.linalg.norm(nested - direct) <= 1e-11 * np.linalg.norm(direct)
+        checked += 1
+    assert checked > 0
