@@ -8,22 +8,27 @@ dh2_build_dh2), then one DH^2 matvec (dh2_matvec).
 
 Workload (default): unit sphere, icosahedral refinement to 20480 flat
 triangles, kappa = 16 (kappa h ~ 0.5), leaf <= 32, eta1 = 10, eta2 = 1,
-Chebyshev m = 5 (k = 125), eps = 1e-4, seeded N(0,1) + i N(0,1) vectors.
+eps = 1e-4, seeded N(0,1) + i N(0,1) vectors; configured Chebyshev order m = 5
+(k = 125).  The timed builds use the mixed form (complex FP32 kernel evaluation,
+3xTF32 tensor-core products and FP32 storage; FP64 weight factorisations and
+FP64 SVD truncation) and take their order from the shipped learned model
+(`--order learned`, the default), which picks the order that meets eps on this
+workload; `--order configured` or `--order N` fix it.
 
 Prints ONE JSON line (rank 0).  `value` = build seconds per step (device time
-with CUDA events on the launching stream); the matvec throughput (algorithmic
-GB/s: every stored coefficient + the vectors, once) and its error against
-sampled dense Galerkin rows are reported beside it, together with the plain
-FP64 GPU form of the same build, and the learned order/rank model on the same
-workload (the order it chooses, its build time and error, and the truncation memory
-against a plain build at that order).  `--learned` makes the timed builds themselves
-choose their order with the shipped model.  Before the timed region the library's
-autotuner (dh2_autotune) picks the weight-QR tile shapes on the workload itself; every
-build of the run uses them (`--no-autotune`: library defaults; `--qr-tpc a,b,c`: fixed).  The error reference is the FP64 Galerkin
-rows, evaluated on the GPU by the library (dh2_dense_rows).  `--impl reference`
-times the CPU oracle (the reference arm) on a bounded sample of the same workload.
+with CUDA events on the launching stream).  Beside it: the matvec throughput
+(algorithmic GB/s: every stored coefficient + the vectors, once) and the error of
+the product on sampled rows against the FP64 Galerkin rows (dh2_dense_rows, every
+column by quadrature on the GPU); side legs, each recorded as {"error": ...} if it
+fails instead of ending the run: the configured order in the same form, the
+all-FP32 variant and the plain FP64 form at the headline's order, a plain build at
+the learned order, the 64-mesh batched build, the end-to-end time through the C ABI
+with host buffers, and the CPU oracle on a bounded sample (`cpu_baseline`).
+Only the last matrix of a leg stays on the device.  `--impl reference` times the
+CPU oracle (the reference arm) on a bounded sample of the workload per step.
 
-    python bench.py [--steps K] [--warmup W] [--precision mixed|fp64] [--impl ours|reference] [--learned]
+    python bench.py [--steps K] [--warmup W] [--form mixed|mixed32|fp64] [--order learned|configured|N]
+                    [--impl ours|reference]
 """
 from __future__ import annotations
 
@@ -68,21 +73,24 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--form", default="mixed", choices=["mixed", "mixed32", "fp64"],
+                    help="mixed: FP32 products/storage with FP64 weight factorisations and SVD; "
+                         "mixed32: all FP32; fp64: all FP64")
+    ap.add_argument("--order", default="learned",
+                    help="interpolation order of the timed builds: 'learned' (the shipped model chooses), "
+                         "'configured' (the workload's m) or a number")
     ap.add_argument("--workload", default="sphere20480", choices=list(WORKLOADS))
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU form")
+    ap.add_argument("--no-fp32", action="store_true", help="skip the all-FP32 variant")
     ap.add_argument("--error-rows", type=int, default=256)
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-mesh batched build")
-    ap.add_argument("--no-e2e", action="store_true",
-                    help="skip the host-buffer end-to-end builds (a second matrix may not fit beside the first)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end builds")
     ap.add_argument("--batch-meshes", type=int, default=64)
-    ap.add_argument("--learned", action="store_true",
-                    help="the timed builds choose the order with the shipped learned model")
-    ap.add_argument("--no-learned", action="store_true", help="skip the learned-order comparison")
-    ap.add_argument("--m", type=int, default=0, help="override the workload's interpolation order")
+    ap.add_argument("--no-learned", action="store_true", help="skip the plain build at the learned order")
+    ap.add_argument("--m", type=int, default=0, help="override the workload's configured order")
     ap.add_argument("--no-autotune", action="store_true", help="library default tile shapes, no autotuning")
-    ap.add_argument("--qr-tpc", default="", help="fixed weight-QR threads per column 'a,b,c' (skips autotuning)")
+    ap.add_argument("--qr-tpc", default="", help="fixed FP32 weight-QR threads per column 'a,b,c' (skips autotuning)")
     ap.add_argument("--qr-group-rows", type=int, default=0, help="fixed weight-QR row-group size (with --qr-tpc)")
     return ap.parse_args()
 
@@ -150,14 +158,17 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
 
+PATCH_LEVEL = 3   # the sampled patch: the triangles under one cluster of this tree level
+
+
 def oracle_sample_seconds(name, out_queue=None):
     """Times the oracle on a bounded sample of the workload (runs in a child process).
 
     Sample: the full structure phase (cluster tree, directions, block tree) of the
     workload, plus the complete build (nearfield + interpolation + recompression) of
-    the mesh patch under one level-3 cluster (~1/8 of the triangles, same mesh
-    density, kappa, leaf, m, eps).  The patch costs are scaled to the full workload by
-    its admissible-block and nearfield-entry counts.
+    the mesh patch under one cluster of level PATCH_LEVEL (same mesh density, kappa,
+    leaf, m, eps).  `sample_seconds` is what the oracle ran; `estimate_s` scales the
+    patch costs to the full workload by its admissible-block and nearfield-entry counts.
     """
     import synth
     from oracle.geometry import Discretisation
@@ -174,7 +185,7 @@ def oracle_sample_seconds(name, out_queue=None):
     t_struct = time.perf_counter() - t0
     near_full = int(sum(tr.size[t] * tr.size[s] for t, s in bt.near))
     nadm_full = len(bt.adm)
-    plevel = min(3, tr.depth)
+    plevel = min(PATCH_LEVEL, tr.depth)
     t = tr.level_start[plevel]
     idx = np.sort(tr.indices(t))
     used, inv = np.unique(f[idx], return_inverse=True)
@@ -185,7 +196,7 @@ def oracle_sample_seconds(name, out_queue=None):
     b2 = build_block_tree(tr2, d2, kappa, eta2)
     dh = InterpolatedDH2(Discretisation(vs, fs), tr2, d2, b2, kappa, m)
     t1 = time.perf_counter()
-    rc = Recompression(dh, eps)
+    Recompression(dh, eps)
     t2 = time.perf_counter()
     for (a, b) in b2.near:
         dh.nearfield_block(a, b)
@@ -194,72 +205,119 @@ def oracle_sample_seconds(name, out_queue=None):
     t_recomp = t2 - t1
     t_near = t3 - t2
     est = t_struct + t_recomp * nadm_full / max(len(b2.adm), 1) + t_near * near_full / max(near_s, 1)
-    res = dict(value=est, sample_seconds=t_struct + (t3 - t0), patch_triangles=len(fs),
-               patch_adm=len(b2.adm), patch_near_entries=near_s, full_adm=nadm_full, full_near_entries=near_full,
-               t_struct=t_struct, t_recomp=t_recomp, t_near=t_near)
-    return res
+    return dict(estimate_s=est, sample_seconds=t_struct + (t3 - t0), patch_triangles=len(fs), patch_level=plevel,
+                patch_adm=len(b2.adm), patch_near_entries=near_s, full_adm=nadm_full, full_near_entries=near_full,
+                t_struct=t_struct, t_recomp=t_recomp, t_near=t_near)
 
 
-def run_oracle_child(name):
+def oracle_full_small_seconds():
+    """The complete oracle (structure, nearfield, interpolation, recompression, one matvec)
+    on the 1280-triangle sphere with the paper's parameters (kappa 4, leaf 32, m 4)."""
+    import synth
+    from oracle.geometry import Discretisation
+    from oracle.interp import InterpolatedDH2
+    from oracle.recompress import Recompression
+    from oracle.structure import build_block_tree, build_cluster_tree, build_directions
+
+    (_, lev), kappa, leaf, eta1, eta2, m, eps = WORKLOADS["sphere1280"]
+    v, f = synth.icosphere(lev)
+    x = synth.random_vector(len(f), 1809_0001)
+    t0 = time.perf_counter()
+    tr = build_cluster_tree(v, f, leaf)
+    dirs = build_directions(tr, kappa, eta1)
+    bt = build_block_tree(tr, dirs, kappa, eta2)
+    dh = InterpolatedDH2(Discretisation(v, f), tr, dirs, bt, kappa, m)
+    rc = Recompression(dh, eps)
+    t1 = time.perf_counter()
+    rc.matvec(x)
+    t2 = time.perf_counter()
+    return dict(workload="icosphere1280 (kappa 4, leaf 32, m 4; no admissible block: the nearfield is all of G)",
+                build_s=t1 - t0, build_includes="structure, interpolation, recompression",
+                matvec_s=t2 - t1, matvec_includes="the oracle's product, which evaluates the nearfield blocks",
+                triangles=len(f))
+
+
+def run_oracle_child(func, *args):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.oracle_sample_seconds(%r)))" % (ROOT, name))
+            "print(json.dumps(bench.%s(*%r)))" % (ROOT, func, tuple(args)))
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def sample_text(res):
+    return (f"oracle structure phase on the full mesh + complete oracle build (nearfield, interpolation, "
+            f"recompression) of a {res['patch_triangles']}-triangle patch (one level-{res['patch_level']} "
+            f"cluster) of the same mesh, single-threaded")
+
+
+def estimate_text(res):
+    return (f"structure + recompression x (admissible blocks {res['full_adm']} / {res['patch_adm']}) + nearfield x "
+            f"(entries {res['full_near_entries']} / {res['patch_near_entries']})")
+
+
 def cpu_baseline_obj(res):
-    return {"value": res["value"], "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"oracle structure phase on the full mesh + full oracle build of a "
-                       f"{res['patch_triangles']}-triangle patch (one level-3 cluster) of the same sphere; "
-                       f"recompression scaled by admissible blocks ({res['patch_adm']} -> {res['full_adm']}), "
-                       f"nearfield by entries ({res['patch_near_entries']} -> {res['full_near_entries']}); "
-                       f"{res['sample_seconds']:.1f} s of single-threaded CPU work")}
+    """The oracle's full-workload build time is an estimate from a measured sample."""
+    return {"value": res["estimate_s"], "unit": "s", "cores": 1, "kind": "oracle", "estimate": True,
+            "estimate_formula": estimate_text(res), "sample": sample_text(res),
+            "sample_seconds_measured": res["sample_seconds"]}
 
 
 # ----------------------------------------------------------------------------- GPU arm
 
-TILES = {}   # weight-QR tile shapes chosen by the autotuner for this run (empty: library defaults)
+TILES = {}   # FP32 weight-QR tile shapes chosen by the autotuner for this run (empty: library defaults)
 
 
-def gpu_build(pkg, v, f, cfg, precision, stream, model=None):
+def gpu_build(pkg, v, f, cfg, form, stream, model=None):
+    """Tree + DH^2 build of one workload.  form: 'mixed' (FP32 products and storage, FP64
+    weight factorisations and SVD), 'mixed32' (all FP32) or 'fp64'."""
     tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
-    mat = pkg.Matrix(tree, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], precision=precision,
-                     eta1=cfg["eta1"], model=model, stream=stream, **TILES)
+    prec = pkg.DH2_FP64 if form == "fp64" else pkg.DH2_MIXED
+    f64 = 0 if form == "mixed32" else 1
+    mat = pkg.Matrix(tree, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], precision=prec, eta1=cfg["eta1"],
+                     qr_fp64=f64, svd_fp64=f64, model=model, stream=stream, **(TILES if form == "mixed32" else {}))
     tree.close()
     return mat
 
 
-def autotune(pkg, v, f, cfg, precision, stream):
-    """dh2_autotune on the workload itself (outside the timed region): sets TILES and returns
-    the report for the JSON line."""
-    import time as _t
+def release(pkg, torch):
+    """Returns cached device memory of both allocators between the legs."""
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    pkg.dh2_release_cached()
 
+
+def autotune(pkg, v, f, cfg, stream):
+    """dh2_autotune of the FP32 weight-QR tiles on the workload itself (outside the timed region);
+    the all-FP32 builds of the run use them."""
     tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
-    base = pkg.options(eta1=cfg["eta1"], precision=precision)
-    t0 = _t.perf_counter()
+    base = pkg.options(eta1=cfg["eta1"], precision=pkg.DH2_MIXED, qr_fp64=0, svd_fp64=0)
+    t0 = time.perf_counter()
     tuned, t_ms, b_ms = pkg.dh2_autotune(tree.handle, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], base, reps=2,
                                          stream=stream)
-    wall = _t.perf_counter() - t0
+    wall = time.perf_counter() - t0
     tree.close()
     TILES.update(qr_tpc=tuple(int(t) for t in tuned.qr_tpc), qr_group_rows=int(tuned.qr_group_rows))
     return {"qr_threads_per_column": list(TILES["qr_tpc"]), "qr_group_rows": TILES["qr_group_rows"],
-            "qr_ms_per_build_tuned": t_ms, "qr_ms_per_build_default": b_ms, "tuning_s": wall,
+            "qr_ms_per_build_tuned": t_ms, "qr_ms_per_build_default": b_ms, "tuning_s": wall, "applies_to": "mixed32",
             "note": "0 = library default (8, 4, 2 threads per column; 1024-row groups)"}
 
 
-def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream, model=None):
-    """Device-timed steps: build (tree + DH^2) and one matvec, CUDA events on `stream`."""
+def time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, warmup, stream, model=None):
+    """Device-timed steps: build (tree + DH^2) and one matvec, CUDA events on `stream`.
+    Only the last matrix is kept (returned open); the per-kernel and per-stage device
+    times of the timed builds are summed as they go."""
     build_ms, mv_ms = [], []
-    mats = []
+    ktot, stot = {}, {}
+    last = None
     for i in range(warmup + steps):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         y = torch.empty_like(x_dev)
         torch.cuda.synchronize()
         e0.record(stream)
-        mat = gpu_build(pkg, v, f, cfg, precision, stream, model)
+        mat = gpu_build(pkg, v, f, cfg, form, stream, model)
         e1.record(stream)
         mat.matvec(x_dev, y, stream=stream)
         e2.record(stream)
@@ -267,10 +325,15 @@ def time_steps(pkg, torch, v, f, cfg, precision, x_dev, steps, warmup, stream, m
         if i >= warmup:
             build_ms.append(e0.elapsed_time(e1))
             mv_ms.append(e1.elapsed_time(e2))
-            mats.append(mat)
-        else:
-            mat.close()
-    return build_ms, mv_ms, mats
+            for name, (ms, cnt) in mat.kernel_times().items():
+                a, b = ktot.get(name, (0.0, 0))
+                ktot[name] = (a + ms, b + cnt)
+            for name, ms in mat.stage_ms().items():
+                stot[name] = stot.get(name, 0.0) + ms
+        if last is not None:
+            last.close()
+        last = mat
+    return build_ms, mv_ms, ktot, stot, last
 
 
 def matvec_repeat_ms(torch, mat, x_dev, reps, stream):
@@ -287,87 +350,75 @@ def matvec_repeat_ms(torch, mat, x_dev, reps, stream):
     return e0.elapsed_time(e1) / reps
 
 
-def sampled_dense_error(pkg, torch, mat, tree, kappa, x, rows_count, seed):
-    """Relative 2-norm error of the product on sampled rows against the FP64 Galerkin rows,
-    which the library evaluates on the GPU (dh2_dense_rows, every column by quadrature)."""
+ERROR_SEED = 1809_0002
+
+
+def error_rows(n, count, seed=ERROR_SEED):
     rng = np.random.default_rng(seed)
-    rows = np.sort(rng.choice(mat.n, size=min(rows_count, mat.n), replace=False))
-    dt = torch.complex64 if mat.precision == 1 else torch.complex128
+    return np.sort(rng.choice(n, size=min(count, n), replace=False))
+
+
+def sampled_dense_error(pkg, torch, mat, ref, rows, x):
+    """Relative 2-norm error of the product on sampled rows against the FP64 Galerkin rows
+    `ref` (dh2_dense_rows: every column by quadrature, on the GPU)."""
+    dt = torch.complex64 if mat.precision == pkg.DH2_MIXED else torch.complex128
     y = mat.matvec(torch.from_numpy(x).to(dt).cuda()).cpu().numpy().astype(np.complex128)
-    ref = pkg.dh2_dense_rows(tree.handle, kappa, rows, torch.from_numpy(x).to(torch.complex128).cuda())
     return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
 
 
-def learned_measure(pkg, torch, v, f, cfg, x, ref_tree, rows_count, err_configured, stream, with_fp64=True):
-    """The learned order/rank model on the workload: the order it chooses, the build time
-    (CUDA events, tree included, after one warm-up build), the sampled error against the
-    FP64 Galerkin rows, and the truncation memory against a plain build at the same order;
-    next to the error of the configured order."""
-    model = pkg.Model.load()
-    x_dev = torch.from_numpy(x).to(torch.complex64).cuda()
-    ms, mats = time_steps(pkg, torch, v, f, cfg, pkg.DH2_MIXED, x_dev, 2, 1, stream, model)[0::2]
-    mat = mats[-1]
+def side_build(pkg, torch, v, f, cfg, form, x, ref, rows, stream, model=None, steps=2):
+    """One warm-up and `steps` timed builds of a variant; its product error and sizes."""
+    x_dev = torch.from_numpy(x).to(torch.complex128 if form == "fp64" else torch.complex64).cuda()
+    b, mv, kt, _, mat = time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, 1, stream, model)
     info = mat.get_info()
-    err = sampled_dense_error(pkg, torch, mat, ref_tree, cfg["kappa"], x, rows_count, 1809_0002)
-    pm, pmats = time_steps(pkg, torch, v, f, dict(cfg, m=info.m), pkg.DH2_MIXED, x_dev, 1, 0, stream)[0::2]
-    pinfo = pmats[-1].get_info()
-    fp64 = {}
-    if with_fp64:
-        # the plain FP64 form at the same order: the same accuracy class as the learned build
-        x64 = torch.from_numpy(x).cuda()
-        fm, fmats = time_steps(pkg, torch, v, f, dict(cfg, m=info.m), pkg.DH2_FP64, x64, 1, 0, stream)[0::2]
-        fp64 = {"plain_fp64_same_order_build_s": float(np.mean(fm)) / 1e3,
-                "plain_fp64_same_order_relerr": sampled_dense_error(pkg, torch, fmats[-1], ref_tree, cfg["kappa"], x,
-                                                                    rows_count, 1809_0002)}
-        fp64["speedup_learned_mixed_vs_fp64_same_order"] = fp64["plain_fp64_same_order_build_s"] / (
-            float(np.mean(ms)) / 1e3)
-        for m_ in fmats:
-            m_.close()
-    out = {"workload": cfg["workload"], "order_chosen": info.m, "configured_order": cfg["m"],
-           "build_s": float(np.mean(ms)) / 1e3, "relerr_sampled_dense": err, "meets_eps": bool(err <= cfg["eps"]),
-           "configured_order_relerr": err_configured,
-           "configured_order_meets_eps": bool(err_configured <= cfg["eps"]),
-           "rank_cap_retries": info.rank_cap_retries, "truncation_MB": info.truncation_bytes / 1e6,
-           "plain_same_order_build_s": float(np.mean(pm)) / 1e3,
-           "plain_same_order_truncation_MB": pinfo.truncation_bytes / 1e6, **fp64}
-    for m_ in mats + pmats:
-        m_.close()
-    model.close()
+    mv_ms = matvec_repeat_ms(torch, mat, x_dev, 10, stream)
+    out = {"form": form, "m": info.m, "build_s": float(np.mean(b)) / 1e3,
+           "relerr_sampled_dense": sampled_dense_error(pkg, torch, mat, ref, rows, x),
+           "matvec_ms": mv_ms, "matvec_gbs": info.matvec_bytes / (mv_ms * 1e-3) / 1e9,
+           "truncation_MB": info.truncation_bytes / 1e6, "rank_cap_retries": info.rank_cap_retries,
+           "kernel_ms_per_build": {k: round(a / steps, 2) for k, (a, c) in kt.items() if c}}
+    out["meets_eps"] = bool(out["relerr_sampled_dense"] <= cfg["eps"])
+    mat.close()
     return out
 
 
 BATCH_SEED = 1809_0003
 
 
-def batch_measure(pkg, torch, count, stream):
+def batch_measure(pkg, torch, count, stream, form="mixed"):
     """The batched workload: `count` spheres/ellipsoids of 1280-20480 triangles
     (synth.batch_meshes), kappa U[4, 16], leaf 32, eta1 10, eta2 1, m 5, eps 1e-4.
     Builds are blocking host calls that fan out over several streams, so they are
-    timed with the host clock around the call (trees included, built beforehand
-    for the build-only figures); the products with CUDA events on `stream`, which
-    joins the internal streams."""
+    timed with the host clock around the call (trees built beforehand for the
+    build-only figures); the products with CUDA events on `stream`, which joins the
+    internal streams.  Every batch of matrices is freed before the next is built."""
     import synth
 
     meshes = synth.batch_meshes(count, BATCH_SEED)
     m, eta2, eta1, eps, leaf = 5, 1.0, 10.0, 1e-4, 32
+    f64 = 0 if form == "mixed32" else 1
     kappas = [k for _, _, k in meshes]
     ntri = int(sum(len(f) for _, f, _ in meshes))
     trees = [pkg.Tree(v, f, leaf_max=leaf) for v, f, _ in meshes]
+    tiles = TILES if form == "mixed32" else {}
 
-    def batch_build(nstreams):
+    def batch_build(nstreams, trs):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        mats = pkg.build_batch(trees, kappas, m, eta2, eps, eta1=eta1, nstreams=nstreams, **TILES)
+        mats = pkg.build_batch(trs, kappas, m, eta2, eps, eta1=eta1, nstreams=nstreams, qr_fp64=f64, svd_fp64=f64,
+                               **tiles)
         torch.cuda.synchronize()
         return time.perf_counter() - t0, mats
 
-    _, warm = batch_build(8)             # warm-up: kernels loaded, pool sized
-    for mt in warm:
-        mt.close()
-    t1, mats1 = batch_build(1)
-    for mt in mats1:
-        mt.close()
-    t8, mats = batch_build(8)
+    def close_all(objs):
+        for o in objs:
+            o.close()
+
+    _, warm = batch_build(8, trees)      # warm-up: kernels loaded, pool sized
+    close_all(warm)
+    t1, mats1 = batch_build(1, trees)
+    close_all(mats1)
+    t8, mats = batch_build(8, trees)
     xs = [torch.from_numpy(synth.random_vector(len(f), BATCH_SEED + i)).to(torch.complex64).cuda()
           for i, (_, f, _) in enumerate(meshes)]
     ys = [torch.empty_like(x) for x in xs]
@@ -393,18 +444,21 @@ def batch_measure(pkg, torch, count, stream):
 
     mv_batch, mv_serial = mv_ms(True), mv_ms(False)
     mv_bytes = int(sum(mt.get_info().matvec_bytes for mt in mats))
+    close_all(mats)
+    close_all(trees)
+    del xs, ys
+    release(pkg, torch)
     # end to end: host meshes in, trees + batched build
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     trees2 = [pkg.Tree(v, f, leaf_max=leaf) for v, f, _ in meshes]
-    mats2 = pkg.build_batch(trees2, kappas, m, eta2, eps, eta1=eta1, nstreams=8)
-    torch.cuda.synchronize()
+    _, mats2 = batch_build(8, trees2)
     t_e2e = time.perf_counter() - t0
-    for obj in mats + mats2 + trees + trees2:
-        obj.close()
+    close_all(mats2)
+    close_all(trees2)
     return {"workload": f"batch{count}: spheres/ellipsoids (icosphere L3-L5, semi-axes U[0.5,2]^3 for half), "
                         f"kappa U[4,16], seed {BATCH_SEED}, leaf {leaf}, eta1 {eta1}, eta2 {eta2}, m {m}, eps {eps}",
-            "meshes": count, "triangles": ntri,
+            "form": form, "meshes": count, "triangles": ntri,
             "build_s_8_streams": t8, "build_s_1_stream": t1, "build_speedup_streams": t1 / t8,
             "build_s_e2e_with_trees": t_e2e,
             "matvec_ms_batched": mv_batch, "matvec_ms_serial": mv_serial,
@@ -422,6 +476,49 @@ def max_over_ranks(values, torch, world, device):
     return [float(v) for v in t.tolist()]
 
 
+def leg(results, name, fn):
+    """Runs one side measurement; a failure is recorded in the line instead of ending the run."""
+    t0 = time.perf_counter()
+    try:
+        results[name] = fn()
+    except Exception as e:   # recorded, never silently replaced
+        results[name] = {"error": f"{type(e).__name__}: {e}"[:500]}
+    if isinstance(results[name], dict):
+        results[name]["leg_wall_s"] = round(time.perf_counter() - t0, 2)
+
+
+FORMS = {"mixed": "c64+f64 (complex FP32 kernel evaluation, 3xTF32 tensor-core products and storage; "
+                  "FP64 weight factorisations and SVD truncation)",
+         "mixed32": "c64 (complex FP32 everywhere: products, weight QRs, SVD truncation)",
+         "fp64": "c128 (complex FP64 everywhere)"}
+DTYPES = {"mixed": "c64+f64", "mixed32": "c64", "fp64": "c128"}
+
+
+def reference_arm(args, cfg):
+    """The CPU oracle on a bounded sample of the workload per step (rank 0 only)."""
+    samples = []
+    res = None
+    for i in range(args.warmup + args.steps):
+        res = run_oracle_child("oracle_sample_seconds", args.workload)
+        if i >= args.warmup:
+            samples.append(res)
+    value = float(np.mean([r["sample_seconds"] for r in samples]))
+    est = float(np.mean([r["estimate_s"] for r in samples]))
+    try:
+        small = run_oracle_child("oracle_full_small_seconds")
+    except Exception as e:
+        small = {"error": str(e)[:500]}
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(cfg, l2="inputs larger than L2", sample=sample_text(res)), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle", "sample": sample_text(res)},
+            "full_workload_estimate_s": est, "full_workload_estimate_formula": estimate_text(res),
+            "oracle_full_icosphere1280": small,
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -432,22 +529,8 @@ def main():
         cfg = dict(cfg, m=args.m, k=args.m ** 3)
 
     if args.impl == "reference":
-        if rank != 0:
-            return
-        vals = []
-        res = None
-        for i in range(args.warmup + args.steps):
-            res = run_oracle_child(args.workload)
-            if i >= args.warmup:
-                vals.append(res["value"])
-        value = float(np.mean(vals))
-        line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": 0, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": value * 1e3, "higher_is_better": False,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": dict(cfg, l2="inputs larger than L2"), "impl": "reference",
-                "cpu_baseline": cpu_baseline_obj(dict(res, value=value)),
-                "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-        print(json.dumps(line))
+        if rank == 0:
+            reference_arm(args, cfg)
         return
 
     import torch
@@ -461,34 +544,40 @@ def main():
 
         dist.init_process_group("nccl")
     pkg.lib()
-    precision = pkg.DH2_MIXED if args.precision == "mixed" else pkg.DH2_FP64
+    form = args.form
     v, f = workload_mesh(args.workload)
     n = len(f)
-    x = synth.random_vector(n, 1809_0002)
-    xdt = torch.complex64 if precision == pkg.DH2_MIXED else torch.complex128
+    x = synth.random_vector(n, ERROR_SEED)
+    xdt = torch.complex128 if form == "fp64" else torch.complex64
     x_dev = torch.from_numpy(x).to(xdt).cuda()
     stream = torch.cuda.current_stream()
-    main_model = pkg.Model.load() if args.learned else None
+    model = pkg.Model.load() if args.order == "learned" else None
+    if args.order not in ("learned", "configured"):
+        cfg = dict(cfg, m=int(args.order), k=int(args.order) ** 3)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    side = {}
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
+    # FP32 weight-QR tiles for the all-FP32 builds (outside the timed region)
     if args.qr_tpc:
         TILES.update(qr_tpc=tuple(int(t) for t in args.qr_tpc.split(",")), qr_group_rows=args.qr_group_rows)
-        tuning = {"qr_threads_per_column": list(TILES["qr_tpc"]), "qr_group_rows": args.qr_group_rows,
-                  "note": "fixed on the command line"}
-    else:
-        tuning = None if args.no_autotune else autotune(pkg, v, f, cfg, precision, stream)
+        side["autotune"] = {"qr_threads_per_column": list(TILES["qr_tpc"]), "qr_group_rows": args.qr_group_rows,
+                            "note": "fixed on the command line"}
+    elif not args.no_autotune:
+        leg(side, "autotune", lambda: autotune(pkg, v, f, cfg, stream))
 
     # warm-up and timed steps (one replica per GPU: the path is not sharded)
     launches0 = pkg.lib().dh2_kernel_launches()
     barrier()
     with ClockSampler(local) as clk:
         t_wall0 = time.perf_counter()
-        build_ms, mv_ms, mats = time_steps(pkg, torch, v, f, cfg, precision, x_dev, args.steps, args.warmup,
-                                           stream, main_model)
+        build_ms, mv_ms, ktimes, stimes, mat = time_steps(pkg, torch, v, f, cfg, form, x_dev, args.steps,
+                                                          args.warmup, stream, model)
         barrier()
         t_wall = time.perf_counter() - t_wall0
     launches = pkg.lib().dh2_kernel_launches() - launches0
@@ -496,142 +585,132 @@ def main():
     build_s = float(np.mean(build_ms)) / 1e3
     step_ms = float(np.mean(np.array(build_ms) + np.array(mv_ms)))
     build_s, step_ms = max_over_ranks([build_s, step_ms], torch, world, "cuda")
-    mat = mats[-1]
     info = mat.get_info()
+    order = info.m
+    cfg_run = dict(cfg, m=order, k=order ** 3)
     free_b, total_b = torch.cuda.mem_get_info()
     device_used_gb = (total_b - free_b) / 1e9
 
     # matvec throughput: algorithmic bytes / device time, repeated launches
     mv_rep_ms = matvec_repeat_ms(torch, mat, x_dev, 20, stream)
     mv_gbs = info.matvec_bytes / (mv_rep_ms * 1e-3) / 1e9
-
-    # per-kernel device times summed over the timed builds
-    ktimes = {}
-    for m_ in mats:
-        for name, (ms, cnt) in m_.kernel_times().items():
-            a, b = ktimes.get(name, (0.0, 0))
-            ktimes[name] = (a + ms, b + cnt)
-    # matvec kernels with timing on
     mat.set_timing(True)
     for _ in range(10):
         mat.matvec(x_dev, torch.empty_like(x_dev), stream=stream)
     torch.cuda.synchronize()
     mv_kernels = {k: v_ for k, v_ in mat.kernel_times().items() if k.startswith("mv_")}
     mat.set_timing(False)
-    work = kernel_work(mat, info, cfg)
-    peaks = load_peaks()
+    work = mat.kernel_work()
+    peaks = load_peaks(sms)
     build_kernels = {k: v_ for k, v_ in ktimes.items() if not k.startswith("mv_") and v_[1] > 0}
     dom = max(build_kernels, key=lambda k: build_kernels[k][0])
-    roof = roofline_obj(dom, build_kernels[dom], work, peaks, len(mats),
-                        measured_traffic(cfg["workload"], dom, args.precision))
+    roof = roofline_obj(dom, build_kernels[dom], work, peaks, args.steps,
+                        measured_traffic(cfg["workload"], dom, form))
     leaf_ms, leaf_cnt = mv_kernels.get("mv_leaf_out", (0.0, 0))
     mv_roof = roofline_obj("mv_leaf_out", (leaf_ms, leaf_cnt), work, peaks, 10,
-                           measured_traffic(cfg["workload"], "mv_leaf_out", args.precision))
-
-    # e2e: host mesh in, host vector in/out, through the C ABI
-    xh = np.ascontiguousarray(x.astype(np.complex128))
-    e2e = []
-    for i in range(0 if args.no_e2e else 1 + min(args.steps, 3)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        m2 = gpu_build(pkg, v, f, cfg, precision, None)
-        m2.matvec_host(xh)
-        torch.cuda.synchronize()
-        if i > 0:
-            e2e.append(time.perf_counter() - t0)
-        m2.close()
-    h2d = v.nbytes + f.astype(np.int32).nbytes + xh.nbytes
-    d2h = xh.nbytes
+                           measured_traffic(cfg["workload"], "mv_leaf_out", form))
 
     # accuracy against sampled dense rows (outside the timed region)
+    rows = error_rows(n, args.error_rows)
     ref_tree = pkg.Tree(v, f, leaf_max=cfg["leaf"])
-    err = sampled_dense_error(pkg, torch, mat, ref_tree, cfg["kappa"], x, args.error_rows, 1809_0002)
+    ref = pkg.dh2_dense_rows(ref_tree.handle, cfg["kappa"], rows, torch.from_numpy(x).cuda())
+    ref_tree.close()
+    err = sampled_dense_error(pkg, torch, mat, ref, rows, x)
+    minfo = {"gbs": mv_gbs, "ms": mv_rep_ms, "bytes": info.matvec_bytes, "relerr_sampled_dense": err,
+             "rows_sampled": len(rows),
+             "kernel_ms": {k: round(v_[0] / max(v_[1], 1) * (v_[1] / 10), 4) for k, v_ in mv_kernels.items()}}
+    headline = {
+        "ranks": {"max_row": info.max_rank_row, "mean_row": info.mean_rank_row,
+                  "max_col": info.max_rank_col, "mean_col": info.mean_rank_col},
+        "storage": {"near_entries": info.near_entries, "coupling_entries": info.coupling_entries,
+                    "basis_entries": info.basis_entries, "nadm": info.nadm, "nnear": info.nnear},
+        "stage_ms_per_build": {k: round(v_ / args.steps, 3) for k, v_ in stimes.items()},
+        "kernel_ms_per_build": {k: round(v_[0] / args.steps, 3) for k, v_ in build_kernels.items()},
+        "truncation_MB": info.truncation_bytes / 1e6, "rank_cap_retries": info.rank_cap_retries,
+    }
+    mat.close()
+    release(pkg, torch)
 
-    # plain FP64 GPU form of the same build
-    fp64 = None
-    if precision == pkg.DH2_MIXED and not args.no_fp64:
-        x64 = torch.from_numpy(x).cuda()
-        b64, m64, mats64 = time_steps(pkg, torch, v, f, cfg, pkg.DH2_FP64, x64, 2, 1, stream)
-        mv64 = matvec_repeat_ms(torch, mats64[-1], x64, 10, stream)
-        err64 = sampled_dense_error(pkg, torch, mats64[-1], ref_tree, cfg["kappa"], x, args.error_rows, 1809_0002)
-        fp64 = {"build_s": float(np.mean(b64)) / 1e3, "matvec_ms": mv64,
-                "matvec_gbs": mats64[-1].get_info().matvec_bytes / (mv64 * 1e-3) / 1e9,
-                "matvec_relerr_sampled_dense": err64,
-                "speedup_build_mixed_vs_fp64": float(np.mean(b64)) / 1e3 / build_s}
-        for m_ in mats64:
-            m_.close()
+    # e2e: host mesh in, host vector in/out, through the C ABI, copies inside the timed region
+    def e2e_leg():
+        xh = np.ascontiguousarray(x.astype(np.complex128))
+        times = []
+        for i in range(1 + min(args.steps, 3)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            m2 = gpu_build(pkg, v, f, cfg, form, None, model)
+            m2.matvec_host(xh)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+            m2.close()
+        return {"value": float(np.mean(times)), "unit": "s",
+                "h2d_bytes_per_step": int(v.nbytes + f.astype(np.int32).nbytes + xh.nbytes),
+                "d2h_bytes_per_step": int(xh.nbytes)}
 
-    learned = None
-    if precision == pkg.DH2_MIXED and not args.no_learned and not args.learned:
-        learned = learned_measure(pkg, torch, v, f, cfg, x, ref_tree, args.error_rows, err, stream,
-                                  with_fp64=not args.no_fp64)
-
-    batch = None
+    if not args.no_e2e:
+        leg(side, "e2e", e2e_leg)
+        release(pkg, torch)
+    # the configured order of the workload in the same form (reported beside the headline order)
+    if args.order != "configured" and order != WORKLOADS[args.workload][5]:
+        leg(side, "configured_order", lambda: side_build(pkg, torch, v, f, dict(cfg, m=WORKLOADS[args.workload][5]),
+                                                         form, x, ref, rows, stream))
+        release(pkg, torch)
+    if form != "mixed32" and not args.no_fp32:
+        leg(side, "all_fp32", lambda: side_build(pkg, torch, v, f, cfg_run, "mixed32", x, ref, rows, stream))
+        release(pkg, torch)
+    if form != "fp64" and not args.no_fp64:
+        leg(side, "plain_fp64", lambda: side_build(pkg, torch, v, f, cfg_run, "fp64", x, ref, rows, stream))
+        release(pkg, torch)
+    if model is not None and not args.no_learned:
+        leg(side, "plain_same_order", lambda: side_build(pkg, torch, v, f, cfg_run, form, x, ref, rows, stream))
+        release(pkg, torch)
     if not args.no_batch:
-        batch = batch_measure(pkg, torch, args.batch_meshes, stream)
-
-    baseline = None
+        leg(side, "batch", lambda: batch_measure(pkg, torch, args.batch_meshes, stream, form))
+        release(pkg, torch)
     if rank == 0 and not args.no_baseline:
-        try:
-            baseline = cpu_baseline_obj(run_oracle_child(args.workload))
-        except Exception as e:  # reported, never silently replaced
-            baseline = {"value": None, "unit": "s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+        leg(side, "cpu_baseline", lambda: cpu_baseline_obj(run_oracle_child("oracle_sample_seconds", args.workload)))
 
+    pf = side.get("plain_fp64", {})
+    if "build_s" in pf:
+        pf["speedup_build_vs_fp64"] = pf["build_s"] / build_s
     if rank == 0:
+        e2e = side.pop("e2e", None)
         line = {
-            "metric": METRIC, "value": build_s * world / world, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "metric": METRIC, "value": build_s, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "c64+f64" if precision == pkg.DH2_MIXED else "c128",
-            "data": "synthetic",
-            "config": dict(cfg, precision=args.precision, parallelism=f"replicas{world}",
-                           order=("learned: " + str(info.m)) if args.learned else "configured",
+            "vs_baseline": None, "dtype": DTYPES[form], "data": "synthetic",
+            "config": dict(cfg_run, precision=FORMS[form], parallelism=f"replicas{world}",
+                           order=(f"learned model: m = {order}" if model is not None else f"m = {order}"),
+                           configured_order=WORKLOADS[args.workload][5],
                            l2="inputs larger than L2 (nearfield alone > 1 GB)"),
-            "build_s": build_s,
-            "matvec": {"gbs": mv_gbs, "ms": mv_rep_ms, "bytes": info.matvec_bytes,
-                       "relerr_sampled_dense": err, "rows_sampled": args.error_rows,
-                       "kernel_ms": {k: round(v_[0] / max(v_[1], 1) * (v_[1] / 10), 4)
-                                     for k, v_ in mv_kernels.items()}},
-            "ranks": {"max_row": info.max_rank_row, "mean_row": info.mean_rank_row,
-                      "max_col": info.max_rank_col, "mean_col": info.mean_rank_col},
-            "storage": {"near_entries": info.near_entries, "coupling_entries": info.coupling_entries,
-                        "basis_entries": info.basis_entries, "nadm": info.nadm, "nnear": info.nnear},
-            "stage_ms": {k: round(v_, 3) for k, v_ in mat.stage_ms().items()},
-            "kernel_ms_per_step": {k: round(v_[0] / len(mats), 3) for k, v_ in build_kernels.items()},
+            "build_s": build_s, "meets_eps": bool(err <= cfg["eps"]),
+            "matvec": minfo, **headline,
             "roofline": roof,
             "matvec_roofline": mv_roof,
-            "plain_fp64": fp64,
-            "autotune": tuning,
-            "learned": learned,
-            "batch": batch,
-            "cpu_baseline": baseline,
-            "e2e": ({"value": float(np.mean(e2e)), "unit": "s", "h2d_bytes_per_step": int(h2d),
-                     "d2h_bytes_per_step": int(d2h)} if e2e else None),
-            "device_memory_used_gb": device_used_gb,
+            **{k: side.get(k) for k in ("configured_order", "all_fp32", "plain_fp64", "plain_same_order", "batch",
+                                         "autotune")},
+            "cpu_baseline": side.get("cpu_baseline"),
+            "e2e": (e2e if e2e and "value" in e2e else {"error": (e2e or {}).get("error", "not run")}),
+            "device_memory_used_gb": device_used_gb, "sm_count": sms,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "clocks": clk.summary(),
             "wall_s_timed_region": t_wall,
         }
         print(json.dumps(line))
-    for m_ in mats:
-        m_.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
 # ----------------------------------------------------------------------------- roofline
 
-def load_peaks():
+def load_peaks(sms=152):
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
         return dict(hbm_gbs=d["hbm_gbs"], bf16=d["bf16_tflops"], sm_max_mhz=d.get("sm_max_mhz", 2070.0),
-                    source="measured")
-    return dict(hbm_gbs=6800.0, bf16=1900.0, sm_max_mhz=2070.0, source="fallback")
-
-
-def kernel_work(mat, info, cfg):
-    """Algorithmic work per kernel over one build / one matvec (library counters)."""
-    return mat.kernel_work()
+                    source="measured", sms=sms)
+    return dict(hbm_gbs=6800.0, bf16=1900.0, sm_max_mhz=2070.0, source="fallback", sms=sms)
 
 
 KERNEL_SOURCES = ["paper_1809_04384_gb300/csrc/numeric.cu", "paper_1809_04384_gb300/csrc/linalg.cuh",
@@ -675,14 +754,15 @@ def roofline_obj(name, timing, work, peaks, nsteps, traffic=None):
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peaks["source"] + " copy bandwidth",
                 "algorithmic_bytes_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
-    # FP32 / FP64 SIMT arithmetic: peak from unit counts and the maximum SM clock
+    # FP32 / FP64 SIMT arithmetic: peak from unit counts (FMA per SM per clock) and the maximum SM clock
     lanes = {"flop32": 128, "flop64": 2}[kind]
-    peak = 152 * lanes * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    sms = peaks.get("sms", 152)
+    peak = sms * lanes * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
     achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
     return {"kernel": name, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "peak_source": f"derived: 152 SMs x {lanes} {'FP32' if lanes == 128 else 'FP64'} FMA lanes x 2 x "
-                           f"{peaks['sm_max_mhz']:.0f} MHz",
+            "peak_source": f"derived: {sms} SMs (device properties) x {lanes} {'FP32' if lanes == 128 else 'FP64'} "
+                           f"FMA per SM per clock x 2 flop x {peaks['sm_max_mhz']:.0f} MHz",
             "algorithmic_flop_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
 
 

@@ -47,6 +47,7 @@ typedef enum {
 enum { DH2_FP64 = 0, DH2_MIXED = 1 };                 /* dh2_options.precision */
 enum { DH2_C64 = 1, DH2_C128 = 2 };                   /* vector dtypes */
 enum { DH2_RANK_BLOCKREL = 0, DH2_RANK_GLOBAL = 1, DH2_RANK_SPECTRAL = 2 };  /* dh2_options.rank_rule */
+enum { DH2_FAULT_NONE = 0, DH2_FAULT_TIMEOUT = 1, DH2_FAULT_NONFINITE = 2, DH2_FAULT_ALLOC = 3 };  /* dh2_options.fault */
 
 typedef struct dh2_tree_s* dh2_tree;
 typedef struct dh2_matrix_s* dh2_matrix;
@@ -56,15 +57,22 @@ typedef struct {
     double eta1;            /* direction parameter eta_1 of Eq. (3a)/(4); paper: 10 (Section 5) */
     int32_t leaf_max;       /* clusters with at most leaf_max elements are leaves; paper: 32 */
     int32_t precision;      /* DH2_FP64: complex FP64 everywhere.  DH2_MIXED: complex FP32
-                               kernel evaluation, GEMMs, weight QRs and matvec storage; FP64
-                               SVD truncation (Gram + Jacobi) and basis-change matrices */
+                               kernel evaluation, coupling and projection GEMMs (3xTF32 on the
+                               tensor cores) and matvec storage; the weight QRs and the SVD
+                               truncation in FP64 (qr_fp64 = svd_fp64 = 1, the defaults) or,
+                               with both set to 0, in FP32 (the all-FP32 variant) */
     int32_t rank_rule;      /* DH2_RANK_BLOCKREL: sum_{i>k} sigma_i^2 <= eps^2 with every block
                                weighted by 1/|G_b|_F (blockwise relative Frobenius, Section 5);
                                DH2_RANK_GLOBAL: <= eps^2 sum_i sigma_i^2, unweighted;
                                DH2_RANK_SPECTRAL: sigma_{k+1} <= eps with the block weights
                                of DH2_RANK_BLOCKREL (error control in the spectral norm,
                                Section 5) */
-    int32_t qr_fp64;        /* DH2_MIXED only: 1 = run the weight QRs (R, Z-hat) in FP64 */
+    int32_t qr_fp64;        /* weight QRs (R, Z-hat) and the orthogonalisation of the leaf bases:
+                               1 (default) = FP64 Cholesky QR: the FP64 Gram matrix Z^* Z of the
+                               stack and its pivoted Cholesky factor R (R^* R = Z^* Z; pivots below
+                               16 u_64 max diag(Z^* Z) are dropped as rounding noise), FP64 Jacobi
+                               for the leaves; 2 = FP64 Householder; 0 = FP32 Householder and FP32
+                               one-sided Jacobi (DH2_MIXED only; the FP64 form treats 0 as 1) */
     int32_t qr_group_rows;  /* stacks taller than this are factored in row groups whose R
                                factors are stacked and factored again (0 = 1024 rows; never
                                below twice the stack's columns) */
@@ -80,14 +88,21 @@ typedef struct {
                                with `model` (see "Learned order and rank" below); the m argument
                                of the build is then ignored.  0 (default) = the plain fixed-order
                                method */
-    int32_t reserved0;      /* must be 0 */
+    int32_t svd_fp64;       /* DH2_MIXED only: 1 (default) = SVD truncation through the FP64 Gram
+                               matrix and an FP64 Hermitian Jacobi eigensolver; 0 = FP32
+                               one-sided Jacobi on the rows of A */
     dh2_model model;        /* the model used when learned = 1 (not owned) */
     int32_t qr_tpc[3];      /* FP32 weight QRs of at most 32, 64 and 128 columns: threads per
                                column of the column-parallel kernel, which sets the rows per
                                chunk (16 x threads); 0 = the defaults 8, 4, 2; allowed
                                1, 2, 4, 8 with threads x class width <= 256 (dh2_autotune
                                picks them) */
-    int32_t reserved1;      /* must be 0 */
+    int32_t fault;          /* test hook, 0 in normal use: DH2_FAULT_TIMEOUT / DH2_FAULT_NONFINITE
+                               make the host find that device error bit set after the projection
+                               stage (the build then fails as it would after a real device-side
+                               timeout or non-finite value); DH2_FAULT_ALLOC makes the first
+                               device allocation of the build fail.  Nothing is injected on the
+                               GPU itself */
 } dh2_options;
 
 typedef struct {
@@ -123,8 +138,8 @@ typedef struct {
                                (Q / F, C, U', singular values), which the learned rank caps size */
 } dh2_matrix_info;
 
-/* Fills *opt with the paper's parameters: eta1 = 10, leaf_max = 32, DH2_MIXED,
- * blockwise relative rank rule, FP32 weight QRs, default workspace. */
+/* Fills *opt with the paper's parameters: eta1 = 10, leaf_max = 32, DH2_MIXED with FP64
+ * weight QRs and FP64 SVD truncation, blockwise relative rank rule, default workspace. */
 dh2_status dh2_options_default(dh2_options* opt);
 
 /*
@@ -252,6 +267,14 @@ int64_t dh2_kernel_launches(void);
 
 /* Waits for `stream` and reports deferred device errors. */
 dh2_status dh2_sync(void* stream);
+
+/* Waits for the current device, then returns the freed device memory that the library's
+ * stream-ordered pool keeps for reuse to the driver (the pool keeps up to a quarter of the
+ * device otherwise).  For processes that also allocate through another allocator (e.g.
+ * PyTorch's caching allocator), which cannot use memory the pool holds.  A device
+ * allocation of the library that fails does the same once and retries before it reports
+ * DH2_ENOMEM.  Errors: DH2_ECUDA. */
+dh2_status dh2_release_cached(void);
 
 /*
  * Autotuner (no counterpart in the paper): picks the tile shapes of the FP32 weight

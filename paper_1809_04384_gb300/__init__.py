@@ -23,6 +23,7 @@ DH2_OK, DH2_EINVAL, DH2_ENOMEM, DH2_ECUDA, DH2_ETIMEOUT, DH2_ENUMERIC, DH2_EUNSU
 DH2_FP64, DH2_MIXED = 0, 1
 DH2_C64, DH2_C128 = 1, 2
 DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL, DH2_RANK_SPECTRAL = 0, 1, 2
+DH2_FAULT_NONE, DH2_FAULT_TIMEOUT, DH2_FAULT_NONFINITE, DH2_FAULT_ALLOC = 0, 1, 2, 3
 (DH2_X_R, DH2_X_ZROW, DH2_X_ZCOL, DH2_X_SROW, DH2_X_SCOL, DH2_X_QROW, DH2_X_QCOL,
  DH2_X_CROW, DH2_X_CCOL, DH2_X_P) = range(10)
 DH2_MLP_IN, DH2_MLP_HIDDEN, DH2_MLP_OUT, DH2_MLP_NPARAMS, DH2_PROBE_ORDERS = 8, 128, 2, 17922, 6
@@ -37,8 +38,8 @@ class dh2_options(C.Structure):
     _fields_ = [("eta1", C.c_double), ("leaf_max", C.c_int32), ("precision", C.c_int32),
                 ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("qr_group_rows", C.c_int32),
                 ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32),
-                ("learned", C.c_int32), ("reserved0", C.c_int32), ("model", C.c_void_p),
-                ("qr_tpc", C.c_int32 * 3), ("reserved1", C.c_int32)]
+                ("learned", C.c_int32), ("svd_fp64", C.c_int32), ("model", C.c_void_p),
+                ("qr_tpc", C.c_int32 * 3), ("fault", C.c_int32)]
 
 
 class dh2_tree_info(C.Structure):
@@ -79,6 +80,7 @@ _SIGS = {
     "dh2_matvec_host": (C.c_int, [_P, _P, _P, _P]),
     "dh2_set_timing": (C.c_int, [_P, C.c_int32]),
     "dh2_sync": (C.c_int, [_P]),
+    "dh2_release_cached": (C.c_int, []),
     "dh2_tree_get_info": (C.c_int, [_P, C.POINTER(dh2_tree_info)]),
     "dh2_tree_export": (C.c_int, [_P] + [_P] * 9),
     "dh2_matrix_get_info": (C.c_int, [_P, C.POINTER(dh2_matrix_info)]),
@@ -279,6 +281,11 @@ def dh2_dense_rows(tree, kappa, rows, x, stream=None):
     return out
 
 
+def dh2_release_cached():
+    """Hands the freed device memory the library's pool keeps back to the driver."""
+    _check(lib().dh2_release_cached())
+
+
 def dh2_free_tree(tree):
     lib().dh2_free_tree(tree)
 
@@ -327,11 +334,11 @@ class Matrix:
     build chooses the order and sizes the truncation by the learned model (m is ignored)."""
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                 qr_fp64=0, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None, qr_tpc=(0, 0, 0),
-                 stream=None):
+                 qr_fp64=1, svd_fp64=1, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None,
+                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
-                       qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes, tensor_cores=tensor_cores,
-                       kb_store=kb_store, qr_tpc=qr_tpc)
+                       svd_fp64=svd_fp64, qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes,
+                       tensor_cores=tensor_cores, kb_store=kb_store, qr_tpc=qr_tpc, fault=fault)
         if model is not None:
             opts.learned = 1
             opts.model = model.handle
@@ -446,10 +453,10 @@ class Matrix:
 
 
 def build_batch(trees, kappas, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                nstreams=0, model=None, qr_tpc=(0, 0, 0), qr_group_rows=0):
+                nstreams=0, model=None, qr_tpc=(0, 0, 0), qr_group_rows=0, qr_fp64=1, svd_fp64=1):
     """Concurrent builds (dh2_build_dh2_batch) wrapped as Matrix objects, in order."""
     opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_tpc=qr_tpc,
-                   qr_group_rows=qr_group_rows)
+                   qr_group_rows=qr_group_rows, qr_fp64=qr_fp64, svd_fp64=svd_fp64)
     if model is not None:
         opts.learned = 1
         opts.model = model.handle

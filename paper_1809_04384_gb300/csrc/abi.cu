@@ -105,6 +105,9 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.qr_group_rows < 0) throw Error{DH2_EINVAL, f + ": qr_group_rows must be >= 0"};
     if (o.tensor_cores != 0 && o.tensor_cores != 1) throw Error{DH2_EINVAL, f + ": tensor_cores must be 0 or 1"};
     if (o.kb_store < 0 || o.kb_store > 2) throw Error{DH2_EINVAL, f + ": kb_store must be 0, 1 or 2"};
+    if (o.qr_fp64 < 0 || o.qr_fp64 > 2) throw Error{DH2_EINVAL, f + ": qr_fp64 must be 0, 1 or 2"};
+    if (o.svd_fp64 != 0 && o.svd_fp64 != 1) throw Error{DH2_EINVAL, f + ": svd_fp64 must be 0 or 1"};
+    if (o.fault < DH2_FAULT_NONE || o.fault > DH2_FAULT_ALLOC) throw Error{DH2_EINVAL, f + ": bad fault hook"};
     static const int width[3] = {32, 64, 128};
     for (int c = 0; c < 3; ++c) {
         const int v = o.qr_tpc[c];
@@ -124,6 +127,10 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
 // The whole build of one matrix on stream s (arguments already checked); blocks until done.
 dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, double eps, const dh2_options& o,
                         cudaStream_t s) {
+    struct FaultScope {   // the allocation hook never outlives this build
+        explicit FaultScope(bool on) { fault_alloc_pending() = on; }
+        ~FaultScope() { fault_alloc_pending() = false; }
+    } fault_scope(o.fault == DH2_FAULT_ALLOC);
     auto mat = std::make_unique<dh2_matrix_s>();
     cudaEvent_t e0, e1;
     DH2_CHECK_CUDA(cudaEventCreate(&e0));
@@ -142,7 +149,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
                           o.workspace_bytes, o.tensor_cores, o.kb_store, {o.qr_tpc[0], o.qr_tpc[1], o.qr_tpc[2]},
-                          {}};
+                          {}, o.svd_fp64, o.fault};
     if (o.learned) {
         int32_t ml = m;
         learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);
@@ -208,9 +215,33 @@ void* dev_alloc(size_t bytes) {
         }
         if (dev < 64) seen |= uint64_t(1) << dev;
     }
+    if (fault_alloc_pending()) {
+        fault_alloc_pending() = false;
+        throw Error{DH2_ENOMEM, "dev_alloc: injected allocation failure (dh2_options.fault)"};
+    }
     void* p = nullptr;
-    DH2_CHECK_CUDA(cudaMallocAsync(&p, bytes, alloc_stream()));
+    cudaError_t e = cudaMallocAsync(&p, bytes, alloc_stream());
+    if (e == cudaErrorMemoryAllocation) {
+        // the pool may hold freed blocks of other streams, or blocks still in flight: wait
+        // for the device, hand the pool's cached memory back to the driver and retry once
+        cudaGetLastError();
+        DH2_CHECK_CUDA(cudaDeviceSynchronize());
+        cudaMemPool_t pool;
+        DH2_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+        DH2_CHECK_CUDA(cudaMemPoolTrimTo(pool, 0));
+        e = cudaMallocAsync(&p, bytes, alloc_stream());
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{e == cudaErrorMemoryAllocation ? DH2_ENOMEM : DH2_ECUDA,
+                    "cudaMallocAsync(" + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e)};
+    }
     return p;
+}
+
+bool& fault_alloc_pending() {
+    thread_local bool pending = false;
+    return pending;
 }
 
 void ensure_smem(const void* fn, size_t bytes) {
@@ -266,7 +297,9 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->leaf_max = 32;
     opt->precision = DH2_MIXED;
     opt->rank_rule = DH2_RANK_BLOCKREL;
-    opt->qr_fp64 = 0;
+    opt->qr_fp64 = 1;
+    opt->svd_fp64 = 1;
+    opt->fault = DH2_FAULT_NONE;
     opt->qr_group_rows = 0;
     opt->workspace_bytes = 0;
     opt->tensor_cores = 1;
@@ -482,6 +515,17 @@ dh2_status dh2_set_timing(dh2_matrix mat, int32_t on) {
 
 dh2_status dh2_sync(void* stream) {
     return guarded([&] { DH2_CHECK_CUDA(cudaStreamSynchronize(as_stream(stream))); });
+}
+
+dh2_status dh2_release_cached(void) {
+    return guarded([&] {
+        int dev = 0;
+        DH2_CHECK_CUDA(cudaGetDevice(&dev));
+        DH2_CHECK_CUDA(cudaDeviceSynchronize());
+        cudaMemPool_t pool;
+        DH2_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+        DH2_CHECK_CUDA(cudaMemPoolTrimTo(pool, 0));
+    });
 }
 
 dh2_status dh2_dense_rows(dh2_tree tree, double kappa, const int32_t* rows, int32_t count, const double* x,

@@ -75,6 +75,7 @@ struct AllocScope {
 };
 
 void* dev_alloc(size_t bytes);   // throws Error (DH2_ENOMEM / DH2_ECUDA)
+bool& fault_alloc_pending();     // test hook: the calling thread's next dev_alloc fails
 void dev_free(void* p);          // errors are ignored (used from destructors)
 
 // Owning device allocation (see above); moves only.

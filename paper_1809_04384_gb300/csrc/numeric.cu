@@ -1062,6 +1062,269 @@ __global__ void __launch_bounds__(256, 3) k_tsqr_cols(const QRTask* __restrict__
     }
 }
 
+// A stack with no more rows than columns is its own R factor: R = Z gives R^* R = Z^* Z
+// exactly, which is all the method uses of R.  (Merging such a stack into a zero R by
+// Householder reflections and keeping min(rows, cols) rows would drop the rounding noise
+// that the reflections leave in the further rows; with ill-conditioned leading columns
+// that noise is amplified far above u |Z|.)  One CTA per stack, rows converted to TDst.
+template <class TSrc, class TDst>
+__global__ void k_copy_rows(const QRTask* __restrict__ tasks, const cx<TSrc>* __restrict__ src,
+                            cx<TDst>* __restrict__ dst, unsigned* err) {
+    const QRTask tk = tasks[blockIdx.x];
+    bool bad = false;
+    for (int idx = threadIdx.x; idx < tk.rout * tk.ncols; idx += blockDim.x) {
+        const int i = idx / tk.ncols, l = idx - i * tk.ncols;
+        const cx<TSrc> u = i < tk.nrows ? src[tk.src + (int64_t)i * tk.ld + l] : zero<TSrc>();
+        bad |= !isfinite(u.x) || !isfinite(u.y);
+        dst[tk.dst + idx] = cx<TDst>{TDst(u.x), TDst(u.y)};
+    }
+    if (bad) raise_err(err, ERR_TSQR_INPUT);
+}
+
+// ----------------------------------------------------------------------------- FP64 Cholesky QR
+
+// R-factor of a stacked matrix Z (H x c) in FP64 through its Gram matrix: G = Z^* Z
+// accumulated in FP64 (Hermitian, upper tiles only), then a pivoted Cholesky G = R^* R
+// with R (rout x c) dense rows: row j holds the j-th pivot's entries in the original
+// column order.  Only R^* R = Z^* Z enters the method (the stacks of Eq. basis_weights_def
+// and Eq. recomp_weight_full and the truncation use R through products whose Gram is
+// that of Z), so R may differ from a Householder R by a unitary left factor.  The Gram
+// has absolute rounding error ~ u_64 |Z|^2, which moves the squared singular values that
+// the rank rule sums by the same absolute amount, far below eps^2 |Z|^2.
+
+// One tile of the Gram matrix: columns [i0, i0 + TB) x [j0, j0 + TB), i0 <= j0, over the
+// stacked rows [r0, r1).
+struct GramItem {
+    int64_t src;              // element offset of the stack's first row
+    int64_t out;              // cx<double> offset of this partial tile (TB x TB, row-major)
+    int32_t ld, ncols, r0, r1;
+    int32_t i0, j0;
+};
+
+// TB = 16 * BS: each of up to 256 threads accumulates a BS x BS block of the tile in
+// FP64 registers; on a diagonal tile only the blocks on or above the diagonal are
+// computed, handed out to consecutive threads so that whole warps of the rest stay idle.
+// Rows are staged RC at a time in shared memory, converted to FP64 once.
+template <int BS, class TSrc>
+__global__ void __launch_bounds__(256) k_gram64(const GramItem* __restrict__ items, const cx<TSrc>* __restrict__ src,
+                                                cx<double>* __restrict__ part, unsigned* err) {
+    constexpr int TB = 16 * BS, RC = 16;
+    __shared__ cx<double> sa[RC][TB], sb[RC][TB];
+    const GramItem it = items[blockIdx.x];
+    const bool diag = it.i0 == it.j0;
+    const int nbi = min(16, (it.ncols - it.i0 + BS - 1) / BS);
+    const int nbj = min(16, (it.ncols - it.j0 + BS - 1) / BS);
+    int bi = -1, bj = -1;
+    {
+        int t = threadIdx.x;
+        if (diag) {
+            for (int r = 0; r < nbi; ++r) {   // block row r holds nbi - r blocks
+                const int cnt = nbi - r;
+                if (t < cnt) {
+                    bi = r;
+                    bj = r + t;
+                    break;
+                }
+                t -= cnt;
+            }
+        } else if (t < nbi * nbj) {
+            bi = t / nbj;
+            bj = t - bi * nbj;
+        }
+    }
+    const bool active = bi >= 0;
+    cx<double> acc[BS][BS];
+#pragma unroll
+    for (int p = 0; p < BS; ++p)
+#pragma unroll
+        for (int q = 0; q < BS; ++q) acc[p][q] = zero<double>();
+    const cx<TSrc>* S = src + it.src;
+    bool bad = false;
+    for (int h0 = it.r0; h0 < it.r1; h0 += RC) {
+        const int hh = min(RC, it.r1 - h0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < RC * TB; idx += blockDim.x) {
+            const int r = idx / TB, c = idx - r * TB;
+            cx<double> a = zero<double>(), b = zero<double>();
+            if (r < hh) {
+                const int64_t row = (int64_t)(h0 + r) * it.ld;
+                if (it.i0 + c < it.ncols) {
+                    const cx<TSrc> u = S[row + it.i0 + c];
+                    bad |= !isfinite(u.x) || !isfinite(u.y);
+                    a = cx<double>{double(u.x), double(u.y)};
+                }
+                if (!diag && it.j0 + c < it.ncols) {
+                    const cx<TSrc> u = S[row + it.j0 + c];
+                    bad |= !isfinite(u.x) || !isfinite(u.y);
+                    b = cx<double>{double(u.x), double(u.y)};
+                }
+            }
+            sa[r][c] = a;
+            if (!diag) sb[r][c] = b;
+        }
+        __syncthreads();
+        if (active) {
+            const cx<double>(*B)[TB] = diag ? sa : sb;
+            for (int r = 0; r < hh; ++r) {
+                cx<double> a[BS], b[BS];
+#pragma unroll
+                for (int q = 0; q < BS; ++q) {
+                    a[q] = sa[r][bi * BS + q];
+                    b[q] = B[r][bj * BS + q];
+                }
+#pragma unroll
+                for (int p = 0; p < BS; ++p)
+#pragma unroll
+                    for (int q = 0; q < BS; ++q) fma_cjx(acc[p][q], a[p], b[q]);
+            }
+        }
+    }
+    if (bad) raise_err(err, ERR_TSQR_INPUT);
+    if (active) {
+        cx<double>* O = part + it.out;
+#pragma unroll
+        for (int p = 0; p < BS; ++p)
+#pragma unroll
+            for (int q = 0; q < BS; ++q) O[(bi * BS + p) * TB + bj * BS + q] = acc[p][q];
+    }
+}
+
+// One stack's Gram assembly and pivoted Cholesky (one CTA).
+struct CholTask {
+    int64_t part;      // cx<double> offset of the stack's first partial tile
+    int64_t g;         // cx<double> offset of its c x c working matrix (upper triangle used)
+    int64_t dst;       // element offset of the output rows (rout x c, pitch c)
+    int32_t ncols, rout, ntile, ngroups;
+};
+
+// Pivot threshold relative to the largest diagonal entry of G: the Gram carries absolute
+// rounding errors of a few u_64 |Z|^2, so smaller remaining pivots are rounding noise.
+constexpr double kCholPivotTol = 16.0 * 2.220446049250313e-16;
+
+template <int TB, class TDst>
+__global__ void __launch_bounds__(256) k_pchol64(const CholTask* __restrict__ tasks, const cx<double>* __restrict__ part,
+                                                 cx<double>* __restrict__ gscr, cx<TDst>* __restrict__ dst,
+                                                 unsigned* err) {
+    constexpr int CMAX = 512;
+    __shared__ double s_d[CMAX];
+    __shared__ int s_perm[CMAX];
+    __shared__ cx<double> s_w[CMAX];
+    __shared__ double s_rv[32];
+    __shared__ int s_ri[32];
+    __shared__ double s_tol;
+    const CholTask tk = tasks[blockIdx.x];
+    const int c = tk.ncols, nt = tk.ntile, ng = tk.ngroups;
+    cx<double>* G = gscr + tk.g;
+    cx<TDst>* R = dst + tk.dst;
+    // G (upper triangle) = sum of the row groups' partial tiles, in group order
+    for (int idx = threadIdx.x; idx < c * c; idx += blockDim.x) {
+        const int i = idx / c, j = idx - i * c;
+        if (i > j) continue;
+        const int I = i / TB, J = j / TB;
+        const int pr = I * nt - (I * (I - 1)) / 2 + (J - I);   // index of tile pair (I, J), I <= J
+        const cx<double>* P = part + tk.part + ((int64_t)pr * ng) * TB * TB + (i - I * TB) * TB + (j - J * TB);
+        cx<double> v = zero<double>();
+        for (int g = 0; g < ng; ++g) v = v + P[(int64_t)g * TB * TB];
+        G[idx] = v;
+    }
+    for (int l = threadIdx.x; l < c; l += blockDim.x) s_perm[l] = l;
+    __syncthreads();
+    for (int l = threadIdx.x; l < c; l += blockDim.x) s_d[l] = G[(int64_t)l * c + l].x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int l = 0; l < c; ++l) m = fmax(m, s_d[l]);
+        s_tol = kCholPivotTol * m;
+    }
+    __syncthreads();
+    const double tol = s_tol;
+    int j = 0;
+    for (; j < tk.rout; ++j) {
+        // pivot: the largest remaining diagonal entry (lowest position on ties)
+        double bv = -1.0;
+        int bp = c;
+        for (int l = j + threadIdx.x; l < c; l += blockDim.x) {
+            const double v = s_d[l];
+            if (!(v == v)) raise_err(err, ERR_TSQR_NONFINITE);
+            if (v > bv) {
+                bv = v;
+                bp = l;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+            const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+            if (ov > bv || (ov == bv && op < bp)) {
+                bv = ov;
+                bp = op;
+            }
+        }
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) {
+            s_rv[w] = bv;
+            s_ri[w] = bp;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = s_rv[0];
+            int p = s_ri[0];
+            for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
+                if (s_rv[q] > v || (s_rv[q] == v && s_ri[q] < p)) {
+                    v = s_rv[q];
+                    p = s_ri[q];
+                }
+            s_rv[0] = v;
+            s_ri[0] = p;
+            if (v > tol && p < c) {   // swap positions j and p
+                const int t = s_perm[j];
+                s_perm[j] = s_perm[p];
+                s_perm[p] = t;
+                const double dt = s_d[j];
+                s_d[j] = s_d[p];
+                s_d[p] = dt;
+            }
+        }
+        __syncthreads();
+        if (!(s_rv[0] > tol)) break;   // the rest of G is rounding noise (or the stack is exhausted)
+        const int pj = s_perm[j];
+        const double rjj = sqrt(s_d[j]), inv = 1.0 / rjj;
+        // row j of R: w_l = G'(pj, perm l) / r_jj for positions l > j
+        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
+            const int a = s_perm[l];
+            const cx<double> gv = pj <= a ? G[(int64_t)pj * c + a] : conj(G[(int64_t)a * c + pj]);
+            s_w[l] = inv * gv;
+        }
+        __syncthreads();
+        for (int col = threadIdx.x; col < c; col += blockDim.x) R[(int64_t)j * c + col] = zero<TDst>();
+        __syncthreads();
+        if (threadIdx.x == 0) R[(int64_t)j * c + pj] = cx<TDst>{TDst(rjj), TDst(0)};
+        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
+            const cx<double> v = s_w[l];
+            R[(int64_t)j * c + s_perm[l]] = cx<TDst>{TDst(v.x), TDst(v.y)};
+        }
+        // Schur complement: G'(a, b) -= conj(w_a) w_b on the upper triangle, positions > j
+        const int rem = c - j - 1;
+        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+            const int l = j + 1 + idx / rem, m = j + 1 + idx % rem;
+            const int a = s_perm[l], b = s_perm[m];
+            if (a > b) continue;
+            cx<double>& g = G[(int64_t)a * c + b];
+            cx<double> v = g;
+            fma_cjx(v, cx<double>{-s_w[l].x, -s_w[l].y}, s_w[m]);
+            g = v;
+        }
+        __syncthreads();
+        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
+            const int a = s_perm[l];
+            s_d[l] = G[(int64_t)a * c + a].x;
+        }
+        __syncthreads();
+    }
+    // rows past the numerical rank are zero
+    for (int idx = j * c + threadIdx.x; idx < tk.rout * c; idx += blockDim.x) R[idx] = zero<TDst>();
+}
+
 template <class TQ, int RPL>
 size_t tsqr_smem_bytes(int k) {
     return ((size_t)k * (32 * RPL + 1) + (size_t)kQRNB * k + 2 * kQRNB * kQRNB + kQRNB) * sizeof(cx<TQ>) +
@@ -1146,7 +1409,7 @@ struct TruncTask {
     int32_t rows, rz, qld, leaf, a, pad;
 };
 
-template <class T, class FV>
+template <class T, bool F64, class FV>
 __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<T>* __restrict__ Z,
                               cx<T>* Ascr, cx<double>* M, cx<double>* U, JRot<double>* rot,
                               double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct,
@@ -1159,11 +1422,12 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
     cta_gemm_fit<T>(n, rz, k, V, [&](int nu, int j) { return conj(Zt[(int64_t)j * k + nu]); },
                 [&](int i, int j, cx<T> v) { Ascr[(int64_t)i * rz + j] = v; });
     __syncthreads();
-    // left singular vectors of A: FP32 one-sided Jacobi on the rows of A (mixed form), or the
-    // FP64 Gram A A^* and a Hermitian Jacobi eigensolver (FP64 form); u(i, r) is entry i of
+    // left singular vectors of A: FP32 one-sided Jacobi on the rows of A (all-FP32 mixed
+    // form), or the FP64 Gram A A^* and a Hermitian Jacobi eigensolver (F64: the FP64 form
+    // and the mixed form with FP64 truncation); u(i, r) is entry i of
     // the r-th vector by descending singular value, s_lam[s_order[r]] its squared value
     cx<float>* Jt = reinterpret_cast<cx<float>*>(M);
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value && !F64) {
         __shared__ int s_flag;
         rowjac_f32(n, rz, Ascr, rz, Jt, s_lam, s_order, &s_flag, kJacobiSweepsF32, kJacobiTolF32);
         for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -1176,7 +1440,7 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
         eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err);
     }
     auto u = [&](int i, int r) -> cx<T> {
-        if constexpr (std::is_same<T, float>::value) {
+        if constexpr (std::is_same<T, float>::value && !F64) {
             return Jt[(int64_t)s_order[r] * n + i];
         } else {
             const cx<double> v = U[(int64_t)i * n + s_order[r]];
@@ -1227,7 +1491,7 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
 
 // Truncation of a non-leaf pair: V-hat = [C_t1 E_t1c; C_t2 E_t2c] (working precision),
 // A = V-hat Z^*, SVD of A through the FP64 Gram A A^* and a Hermitian Jacobi eigensolver.
-template <class T>
+template <class T, bool F64>
 __global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Vhat,
                            const cx<T>* __restrict__ Z, cx<T>* ascr, cx<double>* gscr, int smem_n, double eps,
                            int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig, int32_t* rank,
@@ -1236,7 +1500,7 @@ __global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<
     const TruncTask tk = tasks[blockIdx.x];
     const int n = tk.rows;
     EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.gslot);
-    truncate_body<T>(tk, Dense<T>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch, e.M, e.U, e.rot,
+    truncate_body<T, F64>(tk, Dense<T>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch, e.M, e.U, e.rot,
                      eps, rule, Q, Cd, Ct, sig, rank, e.order, e.lam, err);
 }
 
@@ -1248,7 +1512,7 @@ struct OrthTask {
 // Leaf basis weights with an explicit orthonormal factor: V V^* = U diag(lam) U^* (FP64
 // Gram, Hermitian Jacobi); P = U[:, :rt] (descending eigenvalues), R = P^* V, so V = P R
 // and R^* R = V^* V (Eq. basis_weights_def up to a unitary left factor).
-template <class T>
+template <class T, bool F64>
 __global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, cx<T>* V,
                             cx<double>* gscr, int smem_n, cx<T>* P, cx<T>* R, unsigned* err) {
     extern __shared__ unsigned char smraw[];
@@ -1257,7 +1521,7 @@ __global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, cx<T>* V,
     const int n = tk.n, rt = tk.rt;
     EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.scr);
     cx<T>* Vt = V + tk.v;
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value && !F64) {
         // FP32 one-sided Jacobi on the rows of V (rotated in place, V is not used later):
         // V = J W with orthogonal rows w_i, so P = J[:, order], R = W[order, :]
         __shared__ int s_flag;
@@ -1301,7 +1565,7 @@ struct LeafTruncTask {
 // Truncation of a leaf pair in the coordinates of its orthonormal basis P: with V = P R,
 // A = V Z^* has the left singular vectors P U' and the singular values of Z' R-projected,
 // where Z'^* Z' = R Z Z^* R^*.  Q = P U'[:, :k_tc], C = Q^* V = U'[:, :k_tc]^* R.
-template <class T>
+template <class T, bool F64>
 __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, const cx<T>* __restrict__ Z,
                              const cx<T>* __restrict__ P, const cx<T>* __restrict__ R, cx<double>* gscr,
                              int smem_n, double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct, double* sig,
@@ -1314,7 +1578,7 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
     EigSpace e = eig_space(rt, smem_n, smraw, gscr + tk.scr);
     const cx<T>* Zt = Z + tk.z;
     cx<float>* Jt = reinterpret_cast<cx<float>*>(e.M);
-    if constexpr (std::is_same<T, float>::value) {
+    if constexpr (std::is_same<T, float>::value && !F64) {
         // W = Z'^* (rt x rz, rz <= rt) in the U area; FP32 one-sided Jacobi on its rows
         __shared__ int s_flag;
         cx<float>* Wl = reinterpret_cast<cx<float>*>(e.U);
@@ -1340,7 +1604,7 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
     }
     // entry j of the r-th left singular vector of Z'^* (descending)
     auto u = [&](int j, int r) -> cx<T> {
-        if constexpr (std::is_same<T, float>::value) {
+        if constexpr (std::is_same<T, float>::value && !F64) {
             return Jt[(int64_t)e.order[r] * rt + j];
         } else {
             const cx<double> v = e.U[(int64_t)j * rt + e.order[r]];
@@ -1892,7 +2156,8 @@ struct StageTimer {
 
 const char* const kKernelNames[K_COUNT] = {
     "nearfield", "leaf_basis", "transfer", "kron", "stack_blocks", "tsqr", "truncate", "project",
-    "mv_gather", "mv_forward", "mv_coupling", "mv_backward", "mv_leaf_out", "tsqr_narrow", "leaf_orth"};
+    "mv_gather", "mv_forward", "mv_coupling", "mv_backward", "mv_leaf_out", "tsqr_narrow", "leaf_orth",
+    "wqr_chol"};
 
 namespace {
 // CUDA-event pairs around individual launches, summed per kernel id on collect().
@@ -1965,6 +2230,31 @@ void download_structure(const Tree& tr, const Structure& st, HostStructure& hs, 
 }
 
 // ============================================================================= Num<T>
+
+// Bytes of K_b stores that builds running now have decided to keep (per process); a build
+// holds its share from the decision until its K_b buffer is released.
+std::mutex& kb_reserve_mu() {
+    static std::mutex mu;
+    return mu;
+}
+int64_t& kb_reserved() {
+    static int64_t bytes = 0;
+    return bytes;
+}
+struct KbHold {
+    int64_t bytes = 0;
+    void acquire(int64_t b) {   // called with kb_reserve_mu() held
+        kb_reserved() += b;
+        bytes += b;
+    }
+    void release() {
+        if (bytes == 0) return;
+        std::lock_guard<std::mutex> lk(kb_reserve_mu());
+        kb_reserved() -= bytes;
+        bytes = 0;
+    }
+    ~KbHold() { release(); }
+};
 
 template <class T>
 class Num : public NumBase {
@@ -2056,7 +2346,16 @@ private:
     DBuf<unsigned> err_;
     void check_err(cudaStream_t s, const char* where) {
         unsigned e = read_scalar(err_.p, s);
+        if (e & ERR_TC_TIMEOUT)
+            throw Error{DH2_ETIMEOUT, std::string("a bounded tensor-core wait gave up in ") + where + " (code " +
+                                          std::to_string(e) + "); the matrix is not usable"};
         if (e) throw Error{DH2_ENUMERIC, std::string("non-finite value in ") + where + " (code " + std::to_string(e) + ")"};
+    }
+    // test hook (dh2_options.fault): the host sets the device error bit that a device-side
+    // timeout or a non-finite value would have set, so that the stage's check reports it
+    void inject_fault(cudaStream_t s) {
+        unsigned bit = bp_.fault == DH2_FAULT_TIMEOUT ? ERR_TC_TIMEOUT : bp_.fault == DH2_FAULT_NONFINITE ? ERR_TSQR_NONFINITE : 0u;
+        if (bit) DH2_CHECK_CUDA(cudaMemcpyAsync(err_.p, &bit, sizeof(bit), cudaMemcpyHostToDevice, s));
     }
     double work_[K_COUNT] = {0};     // algorithmic work accumulated while planning launches
     static constexpr double kEvalFlops = 20.0;   // flop-equivalents per kernel evaluation
@@ -2088,12 +2387,30 @@ private:
     MatvecGraph graph_[2];          // complex64, complex128 vectors
     cudaStream_t capture_stream_ = nullptr, side_stream_ = nullptr;
     bool kstore_ = true;            // K_b kept for the column pass / leaf-pair projection
+    KbHold kb_hold_;                // this build's share of the K_b stores of concurrent builds
     cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
     void truncate(int pass, cudaStream_t s);
     bool truncate_once(int pass, cudaStream_t s);
     void project(cudaStream_t s);
+    void project_checked(cudaStream_t s);
     void plan_matvec(cudaStream_t s);
     void tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s, const char* where);
+    // weight factorisations in FP64 through the Gram matrix and a pivoted Cholesky (the
+    // FP64 form and the mixed form with qr_fp64 = 1); qr_fp64 = 2 keeps FP64 Householder
+    bool chol_qr() const {
+        return std::is_same<T, double>::value ? bp_.qr_fp64 != 2 : bp_.qr_fp64 == 1;
+    }
+    // algorithmic flops of one weight factorisation of a stack of `rows` x `cols`
+    void qr_work(int64_t rows, int32_t cols) {
+        if (rows <= cols) return;   // copied: R = Z
+        if (chol_qr()) {   // Hermitian Gram (c(c+1)/2 complex FMA per row) + pivoted Cholesky
+            work_[cols <= 32 ? K_TSQR_NARROW : K_TSQR] += 4.0 * rows * cols * (cols + 1.0);
+            const double r = (double)std::min<int64_t>(rows, cols);
+            work_[K_WQR_CHOL] += 8.0 * (r * cols * cols - r * r * cols + r * r * r / 3.0) / 2.0;
+        } else {
+            work_[cols <= 32 ? K_TSQR_NARROW : K_TSQR] += 8.0 * rows * cols * cols;
+        }
+    }
 };
 
 // ----------------------------------------------------------------------------- layout
@@ -2489,11 +2806,16 @@ void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>*
         const int64_t m0 = mel;
         int32_t mrows = 0;
         for (int32_t r0 = 0; r0 < t.nrows; r0 += g) {
-            const int32_t h = std::min(g, t.nrows - r0);
+            // a short last part joins the group before it: every group keeps all its R rows
+            // (a group with fewer rows than columns would drop the rows that carry its
+            // rounding noise, see k_copy_rows)
+            int32_t h = std::min(g, t.nrows - r0);
+            if (t.nrows - (r0 + h) > 0 && t.nrows - (r0 + h) < t.ncols) h = t.nrows - r0;
             const int32_t ro = std::min(h, t.ncols);
             groups.push_back(QRTask{t.src + (int64_t)r0 * t.ld, mel, h, ro, t.ncols, t.ld});
             mel += (int64_t)ro * t.ncols;
             mrows += ro;
+            if (r0 + h >= t.nrows) break;
         }
         merges.push_back(QRTask{m0, t.dst, mrows, t.rout, t.ncols, t.ncols});
     }
@@ -2506,19 +2828,105 @@ void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>*
     }
 }
 
+// FP64 Cholesky QR of every stack of a level: stacks of at most 32 columns use 32-column
+// Gram tiles (2 x 2 per thread), wider ones 64-column tiles (4 x 4 per thread).  Each
+// stack's upper tile pairs are cut into row groups so that the launch has enough CTAs; the
+// partial tiles of a stack are summed in group order by the Cholesky kernel (no atomics,
+// deterministic).  Stacks are processed in chunks whose scratch stays under 1 GiB.
+template <class TS, class TD>
+void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>* dst, cudaStream_t s, EventLog& ev,
+                    unsigned* err) {
+    constexpr int64_t kScratchElems = (int64_t(1) << 30) / (int64_t)sizeof(cx<double>);
+    for (int cls = 0; cls < 2; ++cls) {
+        const int TB = cls == 0 ? 32 : 64;
+        std::vector<QRTask> ts;
+        for (const QRTask& t : tasks)
+            if ((t.ncols <= 32) == (cls == 0) && t.nrows > 0) ts.push_back(t);
+        if (ts.empty()) continue;
+        double units = 0;
+        for (const QRTask& t : ts) {
+            const int nt = (t.ncols + TB - 1) / TB;
+            units += (double)nt * (nt + 1) / 2 * t.nrows;
+        }
+        const int64_t want_items = 152 * 12;
+        int64_t grows = std::max<int64_t>(128, (int64_t)std::ceil(units / want_items));
+        grows = (grows + 15) / 16 * 16;
+        size_t i0 = 0;
+        while (i0 < ts.size()) {
+            std::vector<GramItem> items;
+            std::vector<CholTask> ct;
+            int64_t pel = 0, gel = 0;
+            size_t i1 = i0;
+            for (; i1 < ts.size(); ++i1) {
+                const QRTask& t = ts[i1];
+                const int nt = (t.ncols + TB - 1) / TB;
+                const int ng = (int)((t.nrows + grows - 1) / grows);
+                const int64_t tp = (int64_t)nt * (nt + 1) / 2;
+                const int64_t need = tp * ng * TB * TB + (int64_t)t.ncols * t.ncols;
+                if (i1 > i0 && pel + gel + need > kScratchElems) break;
+                CholTask c{pel, gel, t.dst, t.ncols, t.rout, nt, ng};
+                for (int I = 0; I < nt; ++I)
+                    for (int J = I; J < nt; ++J)
+                        for (int g = 0; g < ng; ++g) {
+                            const int32_t r0 = (int32_t)(g * grows), r1 = (int32_t)std::min<int64_t>(t.nrows, r0 + grows);
+                            items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB});
+                            pel += (int64_t)TB * TB;
+                        }
+                gel += (int64_t)t.ncols * t.ncols;
+                ct.push_back(c);
+            }
+            for (auto& c : ct) c.g += pel;   // working matrices follow the partial tiles
+            DBuf<GramItem> di;
+            DBuf<CholTask> dc;
+            upload_vec(di, items, s);
+            upload_vec(dc, ct, s);
+            DBuf<cx<double>> scr((size_t)(pel + gel));
+            ev.begin(cls == 0 ? K_TSQR_NARROW : K_TSQR, s);
+            if (cls == 0)
+                k_gram64<2, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
+            else
+                k_gram64<4, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
+            ev.end(s);
+            DH2_CHECK_LAUNCH("k_gram64");
+            ev.begin(K_WQR_CHOL, s);
+            if (cls == 0)
+                k_pchol64<32, TD><<<(unsigned)ct.size(), 256, 0, s>>>(dc.p, scr.p, scr.p, dst, err);
+            else
+                k_pchol64<64, TD><<<(unsigned)ct.size(), 256, 0, s>>>(dc.p, scr.p, scr.p, dst, err);
+            ev.end(s);
+            DH2_CHECK_LAUNCH("k_pchol64");
+            i0 = i1;
+        }
+    }
+}
+
 template <class T>
 void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst, cudaStream_t s,
                   const char* where) {
     (void)where;   // the device error word is sticky: the stage that ran this QR reads it once
+    // stacks with no more rows than columns are copied (R = Z), the others factored
+    std::vector<QRTask> copies, rest;
+    for (const QRTask& t : tasks) (t.nrows <= t.ncols ? copies : rest).push_back(t);
+    if (!copies.empty()) {
+        DBuf<QRTask> d;
+        upload_vec(d, copies, s);
+        k_copy_rows<T, T><<<(unsigned)copies.size(), 128, 0, s>>>(d.p, src, dst, err_.p);
+        DH2_CHECK_LAUNCH("k_copy_rows");
+    }
+    if (rest.empty()) return;
+    if (chol_qr()) {
+        chol_qr_launch<T, T>(rest, src, dst, s, ev_, err_.p);
+        return;
+    }
     const bool fp64 = std::is_same<T, double>::value || bp_.qr_fp64;
     if (fp64) {
         if (tsqr_smem_bytes<double, 1>(k_) > 200 * 1024)
             throw Error{DH2_EUNSUPPORTED, "FP64 weight QR supports m <= 6"};
-        tsqr_tree<T, double, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
+        tsqr_tree<T, double, T, 1>(rest, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
     } else if (tsqr_smem_bytes<float, 2>(k_) <= 100 * 1024) {
-        tsqr_tree<T, float, T, 2>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
+        tsqr_tree<T, float, T, 2>(rest, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
     } else {
-        tsqr_tree<T, float, T, 1>(tasks, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
+        tsqr_tree<T, float, T, 1>(rest, k_, bp_.qr_group_rows, src, dst, s, ev_, err_.p, bp_.qr_tpc);
     }
 }
 
@@ -2550,7 +2958,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
                 kron.push_back(KronTask{offR_[s0], offE_[a], srow * kk, rR_[s0], 0});
                 kron.push_back(KronTask{offR_[s1], offE_[a] + 3 * m_ * m_, (srow + rR_[s0]) * kk, rR_[s1], 0});
                 innerq.push_back(QRTask{srow * kk, offR_[a], rR_[s0] + rR_[s1], rR_[a], kk, kk});
-                work_[K_TSQR] += 8.0 * (rR_[s0] + rR_[s1]) * kk * kk;
+                qr_work(rR_[s0] + rR_[s1], kk);
                 work_[K_KRON] += 24.0 * m_ * kk * (rR_[s0] + rR_[s1]);
                 srow += rR_[s0] + rR_[s1];
             }
@@ -2560,7 +2968,8 @@ void Num<T>::basis_weights(cudaStream_t s) {
             DBuf<OrthTask> d;
             upload_vec(d, leafo, s);
             const size_t smem = eig_smem_bytes(smem_n);
-            auto kern = k_leaf_orth<T>;
+            // FP64 orthogonalisation with the FP64 weight QRs (and in the FP64 form)
+            auto kern = bp_.qr_fp64 ? k_leaf_orth<T, true> : k_leaf_orth<T, false>;
             ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_LEAF_ORTH, s);
             kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, V_.p, gscr.p, smem_n, P_.p, R_.p, err_.p);
@@ -2626,10 +3035,15 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
         bool can_recompute = false;
         if constexpr (std::is_same<T, float>::value) can_recompute = bp_.tensor_cores && k_ <= 128;
         if (can_recompute && bp_.kb_store != 1) {
+            // concurrent builds (the batch) decide one at a time, each against the free memory
+            // less what the stores of the others still hold
+            std::lock_guard<std::mutex> lk(kb_reserve_mu());
             size_t free_b = 0, total_b = 0;
             DH2_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
             const double bytes = (double)offK_.back() * sizeof(cx<T>);
-            kstore_ = !(bp_.kb_store == 2 || bytes > 0.25 * (double)free_b);
+            const double avail = std::max(0.0, (double)free_b - (double)kb_reserved());
+            kstore_ = !(bp_.kb_store == 2 || bytes > 0.25 * avail);
+            if (kstore_) kb_hold_.acquire((int64_t)bytes);
         }
         K_.alloc(kstore_ ? std::max<int64_t>(offK_.back(), 1) : 1);
     }
@@ -2688,7 +3102,7 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
                     srow += rZ_[pass][ap];
                 }
                 qtasks.push_back(QRTask{r0 * kk, offZ_[pass][a], (int32_t)(srow - r0), rZ_[pass][a], zc, kk});
-                work_[zc <= 32 ? K_TSQR_NARROW : K_TSQR] += 8.0 * (srow - r0) * zc * zc;
+                qr_work(srow - r0, zc);
             }
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             if (!btasks.empty()) {
@@ -2839,7 +3253,7 @@ bool Num<T>::truncate_once(int pass, cudaStream_t s) {
             DBuf<LeafTruncTask> d;
             upload_vec(d, lt, s);
             const size_t smem = eig_smem_bytes(smem_l);
-            auto kern = k_trunc_leaf<T>;
+            auto kern = bp_.svd_fp64 ? k_trunc_leaf<T, true> : k_trunc_leaf<T, false>;
             ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_TRUNCATE, s);
             kern<<<(unsigned)lt.size(), kThreads, smem, s>>>(d.p, kk, Z_[pass].p, P_.p, R_.p, lscr.p, smem_l,
@@ -2861,7 +3275,7 @@ bool Num<T>::truncate_once(int pass, cudaStream_t s) {
             DBuf<TruncTask> d;
             upload_vec(d, tt, s);
             size_t smem = eig_smem_bytes(smem_n);
-            auto kern = k_truncate<T>;
+            auto kern = bp_.svd_fp64 ? k_truncate<T, true> : k_truncate<T, false>;
             ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_TRUNCATE, s);
             kern<<<(unsigned)tt.size(), kThreads, smem, s>>>(d.p, kk, vhat.p, Z_[pass].p, ascr.p, gscr.p, smem_n,
@@ -2995,6 +3409,17 @@ void Num<T>::project(cudaStream_t s) {
     ev_.end(s);
     DH2_CHECK_LAUNCH("k_project");
     DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+}
+
+// the projection stage, then its device error check (a tensor-core wait that gave up leaves
+// S~ partly written)
+template <class T>
+void Num<T>::project_checked(cudaStream_t s) {
+    project(s);
+    inject_fault(s);
+    check_err(s, "projection");
+    K_.release();   // read by nothing after the projection
+    kb_hold_.release();
 }
 
 // ----------------------------------------------------------------------------- matvec plan
@@ -3202,7 +3627,7 @@ void Num<T>::build(cudaStream_t s) {
     truncate(1, s);
     tm.end(ST_TRUNCATE_COL);
     tm.begin(ST_PROJECT);
-    project(s);
+    project_checked(s);
     tm.end(ST_PROJECT);
     tm.begin(ST_MATVEC_PLAN);
     plan_matvec(s);
@@ -3217,9 +3642,10 @@ void Num<T>::build(cudaStream_t s) {
     info.kernel_work_kind[K_KRON] = w32;
     info.kernel_work_kind[K_STACK_BLOCKS] = w32;
     info.kernel_work_kind[K_TSQR] = wqr;
-    info.kernel_work_kind[K_TRUNCATE] = W_FLOP64;
-    info.kernel_work_kind[K_LEAF_ORTH] = W_FLOP64;
+    info.kernel_work_kind[K_TRUNCATE] = (std::is_same<T, double>::value || bp_.svd_fp64) ? W_FLOP64 : W_FLOP32;
+    info.kernel_work_kind[K_LEAF_ORTH] = wqr;
     info.kernel_work_kind[K_TSQR_NARROW] = info.kernel_work_kind[K_TSQR];
+    info.kernel_work_kind[K_WQR_CHOL] = W_FLOP64;
     info.kernel_work_kind[K_PROJECT] = w32;
     // matvec leaf kernel: nearfield panels + leaf row bases streamed once, x and y once
     int64_t qleaf = 0;

@@ -37,11 +37,14 @@ struct BuildParams {
     // empty = the structural bound min(rows, k).  A pair whose truncation rank exceeds its
     // cap sends the whole pass back to the structural bound.
     std::vector<int32_t> rank_cap;
+    int32_t svd_fp64 = 0;   // mixed form: FP64 Gram + Hermitian Jacobi truncation
+    int32_t fault = 0;      // dh2_options.fault (test hook)
 };
 
 enum KernelId {
     K_NEARFIELD = 0, K_LEAF_BASIS, K_TRANSFER, K_KRON, K_STACK_BLOCKS, K_TSQR, K_TRUNCATE, K_PROJECT,
-    K_MV_GATHER, K_MV_FORWARD, K_MV_COUPLING, K_MV_BACKWARD, K_MV_LEAF_OUT, K_TSQR_NARROW, K_LEAF_ORTH, K_COUNT
+    K_MV_GATHER, K_MV_FORWARD, K_MV_COUPLING, K_MV_BACKWARD, K_MV_LEAF_OUT, K_TSQR_NARROW, K_LEAF_ORTH, K_WQR_CHOL,
+    K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 

@@ -16,6 +16,9 @@ CASES = {
     "mixed1280": (3, 8.0, 16, 5.0, 2.0, 3, 1e-4),      # directional levels above D = {0} levels
     "dir1280": (3, 8.0, 8, 1.0, 2.0, 4, 1e-4),         # directional, levels 7-9
     "dir320m6": (2, 3.0, 8, 1.0, 4.0, 6, 1e-4),        # k = 216: weight stacks of 129-256 columns
+    "dir320m5": (2, 3.0, 8, 1.0, 4.0, 5, 1e-4),        # k = 125: the headline's order, 65-128 column stacks
+    "plain5120m5": (4, 8.0, 32, 10.0, 1.0, 5, 1e-4),   # paper parameters, kappa h as the 20480 workload;
+                                                       # nearfield panels up to 5120 columns (several parts)
 }
 
 

@@ -13,8 +13,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_noalloc_matvec_matches_matvec_twice(precision):
+@pytest.mark.parametrize("precision, vec", [("mixed", "c64"), ("mixed", "c128"), ("fp64", "c128")])
+def test_noalloc_matvec_matches_matvec_twice(precision, vec):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -31,7 +31,7 @@ def test_noalloc_matvec_matches_matvec_twice(precision):
     tree = dh2.Tree(v, f, leaf_max=p["leaf"])
     prec = dh2.DH2_FP64 if precision == "fp64" else dh2.DH2_MIXED
     mat = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], precision=prec, eta1=p["eta1"])
-    dt = torch.complex128 if precision == "fp64" else torch.complex64
+    dt = torch.complex128 if vec == "c128" else torch.complex64
     tol = TOL[precision]["matvec_same_ranks"]
     for seed in (11, 12):   # two calls in a row, different inputs
         x = torch.from_numpy(synth.random_vector(len(f), seed)).to(dt).cuda()
@@ -42,3 +42,4 @@ def test_noalloc_matvec_matches_matvec_twice(precision):
         b = y_ref.cpu().numpy().astype(np.complex128)
         assert np.all(np.isfinite(a))
         assert rel(a, b) <= tol
+
