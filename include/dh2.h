@@ -103,6 +103,15 @@ typedef struct {
                                timeout or non-finite value); DH2_FAULT_ALLOC makes the first
                                device allocation of the build fail.  Nothing is injected on the
                                GPU itself */
+    int32_t symmetry;       /* 1 (default): use the complex symmetry G^T = G of the Galerkin
+                               matrix (Eq. 1, 2) with the point-symmetric direction sets D_l = -D_l
+                               (Remark "construction of directions"): the basis weights of (t, -c)
+                               and the column-pass total weights, truncated bases and basis-change
+                               matrices of (t, c) are the complex conjugates of the row pass at
+                               (t, -c), so they are copied instead of computed.  Used only when the
+                               host finds the directions, son maps, block tree and sizes symmetric
+                               (dh2_matrix_info.symmetric); 0 = compute both passes */
+    int32_t reserved2;      /* must be 0 */
 } dh2_options;
 
 typedef struct {
@@ -136,6 +145,9 @@ typedef struct {
     int32_t rank_cap_retries; /* truncation passes redone because a rank exceeded its learned cap */
     int64_t truncation_bytes; /* device bytes of the truncated bases of both passes as allocated
                                (Q / F, C, U', singular values), which the learned rank caps size */
+    int32_t symmetric;      /* 1 when the build derived the column pass from the row pass
+                               (dh2_options.symmetry) */
+    int32_t reserved;
 } dh2_matrix_info;
 
 /* Fills *opt with the paper's parameters: eta1 = 10, leaf_max = 32, DH2_MIXED with FP64

@@ -108,6 +108,8 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.qr_fp64 < 0 || o.qr_fp64 > 2) throw Error{DH2_EINVAL, f + ": qr_fp64 must be 0, 1 or 2"};
     if (o.svd_fp64 != 0 && o.svd_fp64 != 1) throw Error{DH2_EINVAL, f + ": svd_fp64 must be 0 or 1"};
     if (o.fault < DH2_FAULT_NONE || o.fault > DH2_FAULT_ALLOC) throw Error{DH2_EINVAL, f + ": bad fault hook"};
+    if (o.symmetry != 0 && o.symmetry != 1) throw Error{DH2_EINVAL, f + ": symmetry must be 0 or 1"};
+    if (o.reserved2 != 0) throw Error{DH2_EINVAL, f + ": reserved2 must be 0"};
     static const int width[3] = {32, 64, 128};
     for (int c = 0; c < 3; ++c) {
         const int v = o.qr_tpc[c];
@@ -149,7 +151,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
                           o.workspace_bytes, o.tensor_cores, o.kb_store, {o.qr_tpc[0], o.qr_tpc[1], o.qr_tpc[2]},
-                          {}, o.svd_fp64, o.fault};
+                          {}, o.svd_fp64, o.fault, o.symmetry};
     if (o.learned) {
         int32_t ml = m;
         learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);
@@ -300,6 +302,7 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->qr_fp64 = 1;
     opt->svd_fp64 = 1;
     opt->fault = DH2_FAULT_NONE;
+    opt->symmetry = 1;
     opt->qr_group_rows = 0;
     opt->workspace_bytes = 0;
     opt->tensor_cores = 1;
@@ -607,6 +610,7 @@ dh2_status dh2_matrix_get_info(dh2_matrix mat, dh2_matrix_info* out) {
         out->learned_m = mat->learned_m;
         out->rank_cap_retries = in.rank_cap_retries;
         out->truncation_bytes = in.truncation_bytes;
+        out->symmetric = in.symmetric;
     });
 }
 

@@ -15,7 +15,9 @@
 // T is the working precision: float for DH2_MIXED, double for DH2_FP64.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <mutex>
+#include <array>
 #include <string>
 
 #include "numeric.cuh"
@@ -2118,12 +2120,46 @@ __global__ void __launch_bounds__(256) k_leaf_out2(const LeafOut2* __restrict__ 
     }
 }
 
+// ----------------------------------------------------------------------------- complex symmetry
+
+// Copies of per-pair arrays between a pair (t, c) and its mirror (t, -c): the column pass of
+// (t, c) is the complex conjugate of the row pass of (t, -c) (G^T = G, D_l = -D_l), and the
+// basis weights of (t, -c) are the conjugates of those of (t, c).  One CTA per segment.
+struct MirrorSeg {
+    int64_t src, dst, n;
+};
+
+__global__ void k_mirror_real(const MirrorSeg* __restrict__ segs, const double* __restrict__ src,
+                              double* __restrict__ dst) {
+    const MirrorSeg m = segs[blockIdx.x];
+    for (int64_t i = threadIdx.x; i < m.n; i += blockDim.x) dst[m.dst + i] = src[m.src + i];
+}
+
+template <class E, bool CONJ>
+__global__ void k_mirror(const MirrorSeg* __restrict__ segs, const E* __restrict__ src, E* __restrict__ dst) {
+    const MirrorSeg m = segs[blockIdx.x];
+    for (int64_t i = threadIdx.x; i < m.n; i += blockDim.x) {
+        E v = src[m.src + i];
+        if constexpr (CONJ) v.y = -v.y;
+        dst[m.dst + i] = v;
+    }
+}
+
 // ----------------------------------------------------------------------------- helpers
 
 template <class T>
 void upload_vec(DBuf<T>& d, const std::vector<T>& h, cudaStream_t s) {
     d.alloc(h.size());
     d.upload(h.data(), h.size(), s);
+}
+
+template <class E, bool CONJ>
+void mirror_copy(const std::vector<MirrorSeg>& segs, const E* src, E* dst, cudaStream_t s) {
+    if (segs.empty()) return;
+    DBuf<MirrorSeg> d;
+    upload_vec(d, segs, s);
+    k_mirror<E, CONJ><<<(unsigned)segs.size(), 128, 0, s>>>(d.p, src, dst);
+    DH2_CHECK_LAUNCH("k_mirror");
 }
 
 struct StageTimer {
@@ -2369,6 +2405,16 @@ private:
 
     void layout();
     void layout_trunc(int pass);
+    void offsets_trunc(int pass);
+    // complex symmetry (dh2_options.symmetry): mirror_[a] is the active pair (t, -c) of the pair
+    // a = (t, c); sym_ when the structure is symmetric and the column pass is mirrored.  Of
+    // each mirrored couple the pair with the smaller index computes its basis weights.
+    std::vector<int32_t> mirror_;
+    bool sym_ = false;
+    void setup_symmetry(cudaStream_t s);
+    bool canonical(int64_t a) const { return !sym_ || mirror_[a] >= a; }
+    void mirror_total_weights(cudaStream_t s);
+    void mirror_truncation(cudaStream_t s);
     bool capped_[2] = {false, false};
     void analytic(cudaStream_t s);
     void nearfield(cudaStream_t s);
@@ -2515,6 +2561,12 @@ void Num<T>::layout_trunc(int pass) {
         ub_[pass][a] = std::min(rows, rZ_[pass][a]);
         if (capped_[pass]) ub_[pass][a] = std::min(ub_[pass][a], std::max(bp_.rank_cap[a], 1));
     }
+    offsets_trunc(pass);
+}
+
+// Offsets of Q, C, U' and the singular values of one pass from its column bounds ub_.
+template <class T>
+void Num<T>::offsets_trunc(int pass) {
     auto scan = [&](std::vector<int64_t>& off, auto sizef) {
         off.resize(na_ + 1);
         int64_t acc = 0;
@@ -2536,6 +2588,83 @@ void Num<T>::layout_trunc(int pass) {
         return leaf_[a] ? rows_[a] : ub_[pass][sons_[0][a]] + ub_[pass][sons_[1][a]];
     });
     rank_[pass].assign(na_, 0);
+}
+
+// ----------------------------------------------------------------------------- complex symmetry
+
+// The Galerkin matrix is complex symmetric (g(x, y) = g(y, x) in Eq. 1 and the same basis
+// functions on both sides of Eq. 2), the direction sets are point-symmetric (the cube-face
+// grid of Remark "construction of directions" is), c_st = -c_ts, and W = V with
+// V_{t,-c} = conj(V_{t,c}) (real Lagrange polynomials and weights): then block (s, t, -c) is
+// the transpose of block (t, s, c), and the column-pass total weight of (t, c) is the
+// conjugate of the row-pass total weight of (t, -c), with everything that the truncation
+// derives from it.  The host checks every ingredient on the actual structure (directions up
+// to 1e-12, the son maps of the active pairs, the block tree, stack sizes); one failure
+// keeps both passes.  (Ties in the nearest-direction rules of the son map and of c_ts go to
+// the lowest index, which is not symmetric under c -> -c: directional block trees can fail
+// the check.)
+template <class T>
+void Num<T>::setup_symmetry(cudaStream_t s) {
+    sym_ = false;
+    mirror_.clear();
+    if (!bp_.symmetry || na_ == 0) return;
+    const auto& h = hs_;
+    const std::vector<double> dirs = st_.dirs.to_host(s);
+    const int L = h.depth;
+    std::vector<std::vector<int32_t>> mir(L + 1);
+    for (int l = 0; l <= L; ++l) {
+        const int32_t d0 = h.dir_off[l], nd = h.dir_off[l + 1] - d0;
+        mir[l].assign(nd, -1);
+        // exact lookup of the negated direction by its coordinates rounded to 2^-30
+        std::map<std::array<int64_t, 3>, int32_t> key;
+        auto kf = [&](const double* d, double sg) {
+            return std::array<int64_t, 3>{std::llround(sg * d[0] * 1073741824.0), std::llround(sg * d[1] * 1073741824.0),
+                                          std::llround(sg * d[2] * 1073741824.0)};
+        };
+        for (int32_t c = 0; c < nd; ++c) key[kf(&dirs[3 * (size_t)(d0 + c)], 1.0)] = c;
+        for (int32_t c = 0; c < nd; ++c) {   // -1: no mirror (fails only if an active pair needs it)
+            const double* a = &dirs[3 * (size_t)(d0 + c)];
+            auto it = key.find(kf(a, -1.0));
+            if (it == key.end()) continue;
+            const double* b = &dirs[3 * (size_t)(d0 + it->second)];
+            if (std::fabs(a[0] + b[0]) <= 1e-12 && std::fabs(a[1] + b[1]) <= 1e-12 && std::fabs(a[2] + b[2]) <= 1e-12)
+                mir[l][c] = it->second;
+        }
+    }
+    // active pairs, their sizes, stack heights and sons (the son maps of the active pairs
+    // commute with the mirror; ties in the son map elsewhere do not matter)
+    std::vector<int32_t> mr(na_);
+    for (int64_t a = 0; a < na_; ++a) {
+        const int32_t t = h.a_t[a], c = h.a_c[a];
+        const int32_t cm = mir[h.level[t]][c];
+        if (cm < 0) return;
+        const int32_t am = h.pair_of(t, cm);
+        if (am < 0) return;
+        mr[a] = am;
+    }
+    for (int64_t a = 0; a < na_; ++a) {
+        const int32_t am = mr[a];
+        if (mr[am] != a || rR_[am] != rR_[a] || rZ_[1][a] != rZ_[0][am] || rZ_[0][a] != rZ_[1][am]) return;
+        if (!leaf_[a] && (sons_[0][am] != mr[sons_[0][a]] || sons_[1][am] != mr[sons_[1][a]])) return;
+    }
+    // every admissible block (t, s, c) has its transpose (s, t, -c)
+    const int64_t nb = (int64_t)h.adm_t.size();
+    int64_t dmax = 1;
+    for (int l = 0; l <= L; ++l) dmax = std::max<int64_t>(dmax, h.dir_off[l + 1] - h.dir_off[l]);
+    const uint64_t ncl = (uint64_t)h.nc;
+    auto bkey = [&](int32_t t, int32_t s2, int32_t c) { return ((uint64_t)t * ncl + (uint64_t)s2) * (uint64_t)dmax + c; };
+    std::vector<uint64_t> keys(nb);
+    for (int64_t b = 0; b < nb; ++b) keys[b] = bkey(h.adm_t[b], h.adm_s[b], h.adm_c[b]);
+    std::sort(keys.begin(), keys.end());
+    for (int64_t b = 0; b < nb; ++b) {
+        const int32_t t = h.adm_t[b], s2 = h.adm_s[b];
+        const int32_t cm = mir[h.level[t]][h.adm_c[b]];
+        if (cm < 0) return;
+        const uint64_t k2 = bkey(s2, t, cm);
+        if (!std::binary_search(keys.begin(), keys.end(), k2)) return;
+    }
+    mirror_.swap(mr);
+    sym_ = true;
 }
 
 // ----------------------------------------------------------------------------- analytic stage
@@ -2947,7 +3076,14 @@ void Num<T>::basis_weights(cudaStream_t s) {
         int smem_n = 0;
         for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a)
             if (leaf_[a]) smem_n = std::max(smem_n, std::min(rows_[a], 64));
+        std::vector<MirrorSeg> mR, mP;   // pairs (t, -c) whose weights are the conjugates of (t, c)'s
         for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a) {
+            if (!canonical(a)) {
+                const int32_t am = mirror_[a];
+                mR.push_back(MirrorSeg{offR_[am], offR_[a], (int64_t)rR_[a] * kk});
+                if (leaf_[a]) mP.push_back(MirrorSeg{offP_[am], offP_[a], (int64_t)rows_[a] * rR_[a]});
+                continue;
+            }
             if (leaf_[a]) {
                 OrthTask o{offV_[a], offP_[a], offR_[a], gel, rows_[a], rR_[a]};
                 if (rows_[a] > smem_n) gel += eig_global_elems(rows_[a]);
@@ -2988,6 +3124,8 @@ void Num<T>::basis_weights(cudaStream_t s) {
             DH2_CHECK_LAUNCH("k_kron");
             tsqr(innerq, stack.p, R_.p, s, "basis weights");
         }
+        mirror_copy<cx<T>, true>(mR, R_.p, R_.p, s);
+        mirror_copy<cx<T>, true>(mP, P_.p, P_.p, s);
     }
     std::vector<int32_t> rr(rR_.begin(), rR_.end());
     upload_vec(rR_d_, rr, s);
@@ -3021,8 +3159,23 @@ void Num<T>::launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pas
 }
 
 template <class T>
+void Num<T>::mirror_total_weights(cudaStream_t s) {
+    Z_[1].alloc(std::max<int64_t>(offZ_[1][na_], 1));
+    std::vector<MirrorSeg> segs;
+    for (int64_t a = 0; a < na_; ++a) {
+        const int64_t n = (int64_t)rZ_[1][a] * zcols(a);
+        if (n) segs.push_back(MirrorSeg{offZ_[0][mirror_[a]], offZ_[1][a], n});
+    }
+    mirror_copy<cx<T>, true>(segs, Z_[0].p, Z_[1].p, s);
+}
+
+template <class T>
 void Num<T>::total_weights(int pass, cudaStream_t s) {
     const auto& h = hs_;
+    if (pass == 1 && sym_) {
+        mirror_total_weights(s);
+        return;
+    }
     const auto& ptr = pass == 0 ? h.row_ptr : h.col_ptr;
     const auto& idx = pass == 0 ? h.row_idx : h.col_idx;
     Z_[pass].alloc(std::max<int64_t>(offZ_[pass][na_], 1));
@@ -3153,8 +3306,55 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
 
 // ----------------------------------------------------------------------------- truncation
 
+// The column pass as the conjugate of the row pass at the mirrored pairs: bounds, ranks,
+// Q / F, C, U' and singular values.
+template <class T>
+void Num<T>::mirror_truncation(cudaStream_t s) {
+    for (int64_t a = 0; a < na_; ++a) ub_[1][a] = ub_[0][mirror_[a]];
+    offsets_trunc(1);
+    Q_[1].alloc(std::max<int64_t>(offQ_[1][na_], 1));
+    Up_[1].alloc(std::max<int64_t>(offUp_[1][na_], 1));
+    Cd_[1].alloc(std::max<int64_t>(offC_[1][na_], 1));
+    if constexpr (std::is_same<T, float>::value) Ct_[1].alloc(std::max<int64_t>(offC_[1][na_], 1));
+    sig_[1].alloc(std::max<int64_t>(offSig_[1][na_], 1));
+    std::vector<MirrorSeg> q, c, u, g;
+    for (int64_t a = 0; a < na_; ++a) {
+        const int32_t am = mirror_[a];
+        rank_[1][a] = rank_[0][am];
+        auto seg = [&](std::vector<MirrorSeg>& v, const std::vector<int64_t>* off) {
+            const int64_t n = off[0][am + 1] - off[0][am];
+            if (n != off[1][a + 1] - off[1][a]) throw Error{DH2_ECUDA, "mirrored truncation: sizes differ"};
+            if (n) v.push_back(MirrorSeg{off[0][am], off[1][a], n});
+        };
+        seg(q, offQ_);
+        seg(c, offC_);
+        seg(u, offUp_);
+        seg(g, offSig_);
+    }
+    mirror_copy<cx<T>, true>(q, Q_[0].p, Q_[1].p, s);
+    mirror_copy<cx<T>, true>(u, Up_[0].p, Up_[1].p, s);
+    mirror_copy<cx<double>, true>(c, Cd_[0].p, Cd_[1].p, s);
+    if constexpr (std::is_same<T, float>::value) mirror_copy<cx<float>, true>(c, Ct_[0].p, Ct_[1].p, s);
+    {
+        if (!g.empty()) {   // singular values (real)
+            DBuf<MirrorSeg> d;
+            upload_vec(d, g, s);
+            k_mirror_real<<<(unsigned)g.size(), 128, 0, s>>>(d.p, sig_[0].p, sig_[1].p);
+            DH2_CHECK_LAUNCH("k_mirror");
+        }
+    }
+    upload_vec(rank_d_[1], rank_[1], s);
+}
+
 template <class T>
 void Num<T>::truncate(int pass, cudaStream_t s) {
+    if (pass == 1 && sym_) {
+        mirror_truncation(s);
+        const int64_t cb = std::is_same<T, float>::value ? (int64_t)sizeof(cx<float>) : 0;
+        info.truncation_bytes += offQ_[1][na_] * (int64_t)sizeof(cx<T>) + offUp_[1][na_] * (int64_t)sizeof(cx<T>) +
+                                 offC_[1][na_] * ((int64_t)sizeof(cx<double>) + cb) + offSig_[1][na_] * 8;
+        return;
+    }
     while (!truncate_once(pass, s)) {
         // a rank exceeded its learned cap: redo the pass with the structural bounds
         err_.zero(s);
@@ -3605,6 +3805,8 @@ void Num<T>::build(cudaStream_t s) {
     err_.alloc(1);
     err_.zero(s);
     layout();
+    setup_symmetry(s);
+    info.symmetric = sym_ ? 1 : 0;
     tm.begin(ST_ANALYTIC);
     analytic(s);
     tm.end(ST_ANALYTIC);

@@ -39,6 +39,7 @@ struct BuildParams {
     std::vector<int32_t> rank_cap;
     int32_t svd_fp64 = 0;   // mixed form: FP64 Gram + Hermitian Jacobi truncation
     int32_t fault = 0;      // dh2_options.fault (test hook)
+    int32_t symmetry = 1;   // derive the column pass from the row pass when the structure allows
 };
 
 enum KernelId {
@@ -59,6 +60,7 @@ struct MatrixInfoAcc {
     int32_t kernel_work_kind[16] = {0};
     int32_t rank_cap_retries = 0;
     int64_t truncation_bytes = 0;
+    int32_t symmetric = 0;
 };
 enum WorkKind { W_NONE = 0, W_FLOP32 = 1, W_FLOP64 = 2, W_BYTES = 3 };
 

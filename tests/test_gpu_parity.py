@@ -394,3 +394,47 @@ def test_cholesky_qr_and_householder_agree(name, precision):
     yo = oracle_matvec(name)
     for y in ys:
         assert rel(y, yo) <= max(mv_tol, 2 * rc.eps if precision != "fp64" else 0)
+
+
+@pytest.mark.parametrize("name, expect", [("lowfreq1280", 1), ("plain5120m5", 1), ("laplace1280", 1), ("dir320", 0)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_symmetric_column_pass_matches_computed(name, expect, precision):
+    """Where the structure is symmetric (no directional admissible block) the build takes the
+    column pass as the conjugated row pass at (t, -c) (dh2_matrix_info.symmetric = 1) and
+    gives the column Grams, singular values, ranks and product of a build that computes
+    both passes; directional block trees with ties in the nearest-direction rules fall back."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    rc = oracle_recompression(name)
+    v, f, p, *_ = oracle_structure(name)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    mats = [dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"], symmetry=sy,
+                       **form_kwargs(precision)) for sy in (1, 0)]
+    assert mats[0].get_info().symmetric == expect and mats[1].get_info().symmetric == 0
+    tol = TOL[precision]
+    act = np.nonzero(rc.pairs.active)[0]
+    for tc in act:
+        for which in (dh2.DH2_X_R, dh2.DH2_X_ZCOL):
+            a, b = mats[0].pair(which, tc), mats[1].pair(which, tc)
+            if which == dh2.DH2_X_ZCOL and rc.tree.is_leaf(int(np.searchsorted(rc.pairs.base, tc, side="right") - 1)):
+                pa, pb = mats[0].pair(dh2.DH2_X_P, tc), mats[1].pair(dh2.DH2_X_P, tc)
+                ga, gb = pa @ (a.conj().T @ a) @ pa.conj().T, pb @ (b.conj().T @ b) @ pb.conj().T
+            else:
+                ga, gb = a.conj().T @ a, b.conj().T @ b
+            if np.linalg.norm(gb) > 0:
+                assert rel(ga, gb) <= tol["gram"], (which, tc)
+        sa, sb = mats[0].pair(dh2.DH2_X_SCOL, tc).real.ravel(), mats[1].pair(dh2.DH2_X_SCOL, tc).real.ravel()
+        n = min(len(sa), len(sb))
+        if n:
+            assert np.abs(sa[:n] ** 2 - sb[:n] ** 2).max() <= tol["sigma2"] * max(sb[0], 1e-300) ** 2, tc
+    r0, c0 = mats[0].ranks()
+    r1, c1 = mats[1].ranks()
+    assert np.mean(c0[act] != c1[act]) <= 0.01
+    x = x_vector(rc.tree.n)
+    ys = [m.matvec(torch.from_numpy(x).to(vec_dtype(precision)).cuda()).cpu().numpy().astype(np.complex128)
+          for m in mats]
+    same = np.array_equal(c0[act], c1[act]) and np.array_equal(r0[act], r1[act])
+    assert rel(ys[0], ys[1]) <= (tol["matvec_same_ranks"] if same else 2 * rc.eps)
+    assert rel(ys[0], oracle_matvec(name)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision != "fp64" else 0)
