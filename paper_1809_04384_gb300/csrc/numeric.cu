@@ -1110,7 +1110,9 @@ struct GramItem {
 template <int BS, class TSrc>
 __global__ void __launch_bounds__(256) k_gram64(const GramItem* __restrict__ items, const cx<TSrc>* __restrict__ src,
                                                 cx<double>* __restrict__ part, unsigned* err) {
-    constexpr int TB = 16 * BS, RC = 16;
+    // rows per staged chunk: 16 for 64-column tiles (1024 FP64 FMA per thread per chunk),
+    // 32 for 32-column tiles, whose threads do a quarter of that per row
+    constexpr int TB = 16 * BS, RC = BS >= 4 ? 16 : 32;
     __shared__ cx<double> sa[RC][TB], sb[RC][TB];
     const GramItem it = items[blockIdx.x];
     const bool diag = it.i0 == it.j0;
@@ -1873,28 +1875,6 @@ struct Coup {
     int32_t kt, ks;
 };
 
-// y^_tc = sum_{b in row(t,c)} S~_b x^_sc ; one warp per row pair, blocks in CSR order
-template <class T>
-__global__ void k_coupling(const int32_t* __restrict__ ptr, const Coup* __restrict__ items,
-                           const int64_t* __restrict__ yh_off, const int32_t* __restrict__ krow,
-                           int64_t npairs, const cx<T>* __restrict__ St, const cx<T>* __restrict__ xh,
-                           cx<T>* yh) {
-    const int warps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    int64_t a = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
-    if (a >= npairs) return;
-    const int kt = krow[a];
-    for (int i = 0; i < kt; ++i) {
-        cx<T> acc = zero<T>();
-        for (int e = ptr[a]; e < ptr[a + 1]; ++e) {
-            const Coup it = items[e];
-            const cx<T>* row = St + it.st + (int64_t)i * it.ks;
-            for (int j = lane; j < it.ks; j += 32) fma_cx(acc, row[j], xh[it.xh + j]);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) yh[yh_off[a] + i] = acc;
-    }
-}
-
 struct Bwd {
     int64_t q, yhp;      // parent Q-hat offset (at this son's first row), parent y^ offset
     int32_t ld, kp;      // parent pitch and rank
@@ -1965,42 +1945,98 @@ __global__ void k_leaf_out(const LeafOut* __restrict__ leaves, const LeafQ* __re
     }
 }
 
-// y^_tc = sum_{b in row(t,c)} S~_b x^_sc: one CTA per row pair, one thread per (block, row)
-// dot product, partial sums reduced per row in a fixed order (deterministic).  The couplings
-// of one row pair are contiguous (stored in row-list order).
+// y^_tc = sum_{b in row(t,c)} S~_b x^_sc in two launches.  The couplings of one row pair are
+// contiguous (row-list order); the host cuts them into tiles, runs of whole blocks of at
+// most kCoupTile bytes (a block larger than that is a tile of its own).  k_coupling_tile:
+// one CTA per tile copies it to shared memory with cp.async (many copies in flight per
+// thread), forms every (block, row) dot product from shared memory and writes the tile's
+// row sums (blocks added in order).  k_coupling_sum: one thread per row of a row pair adds
+// its tiles' sums in tile order.  Tiles of similar size balance the load across the SMs;
+// every sum has a fixed order (deterministic).
+constexpr size_t kCoupTile = 16 * 1024;
+
+struct CoupTile {
+    int32_t e0, e1;     // blocks [e0, e1) of the item list
+    int32_t kt, pad;    // rows of the row pair
+    int64_t out;        // offset of the tile's kt row sums
+};
+
 template <class T>
-__global__ void k_coupling2(const int32_t* __restrict__ ptr, const Coup* __restrict__ items,
-                            const int64_t* __restrict__ yh_off, const int32_t* __restrict__ krow,
-                            const cx<T>* __restrict__ St, const cx<T>* __restrict__ xh, cx<T>* yh) {
-    extern __shared__ unsigned char smraw[];
-    cx<T>* part = reinterpret_cast<cx<T>*>(smraw);
-    const int a = blockIdx.x;
-    const int kt = krow[a];
-    if (kt == 0) return;
-    const int e_begin = ptr[a], e_end = ptr[a + 1];
-    const int cb = max(1, (int)blockDim.x / kt);       // blocks per round
+__device__ __forceinline__ void cp_async_elem(cx<T>* dst, const cx<T>* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(cx<T>) == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+
+template <class T, int TILE>
+__global__ void __launch_bounds__(256) k_coupling_tile(const CoupTile* __restrict__ tiles,
+                                                       const Coup* __restrict__ items, const cx<T>* __restrict__ St,
+                                                       const cx<T>* __restrict__ xh, cx<T>* __restrict__ psum) {
+    __shared__ __align__(16) cx<T> tile[TILE];
+    __shared__ cx<T> part[256];
+    const CoupTile tl = tiles[blockIdx.x];
+    const int kt = tl.kt, e0 = tl.e0, e1 = tl.e1;
+    const Coup first = items[e0], last = items[e1 - 1];
+    const int64_t base = first.st, nel = last.st + (int64_t)kt * last.ks - base;
+    const bool staged = nel <= TILE;
+    if (staged) {
+        for (int w = threadIdx.x; w < (int)nel; w += blockDim.x) cp_async_elem<T>(tile + w, St + base + w);
+        asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
     cx<T> acc0 = zero<T>(), acc1 = zero<T>();
-    for (int e0 = e_begin; e0 < e_end; e0 += cb) {
-        const int nb = min(cb, e_end - e0);
-        for (int w = threadIdx.x; w < nb * kt; w += blockDim.x) {
+    const int nw = (e1 - e0) * kt;
+    for (int w0 = 0; w0 < nw; w0 += blockDim.x) {
+        const int w = w0 + threadIdx.x;
+        cx<T> d = zero<T>();
+        if (w < nw) {
             const int q = w / kt, i = w - q * kt;
             const Coup it = items[e0 + q];
-            const cx<T>* row = St + it.st + (int64_t)i * it.ks;
+            const cx<T>* row = staged ? tile + (it.st - base) + (int64_t)i * it.ks : St + it.st + (int64_t)i * it.ks;
             const cx<T>* xv = xh + it.xh;
-            cx<T> d = zero<T>();
 #pragma unroll 4
             for (int j = 0; j < it.ks; ++j) fma_cx(d, row[j], xv[j]);
-            part[w] = d;
         }
+        part[threadIdx.x] = d;
         __syncthreads();
-        for (int q = 0; q < nb; ++q) {
-            if (threadIdx.x < kt) acc0 = acc0 + part[q * kt + threadIdx.x];
-            if (threadIdx.x + blockDim.x < kt) acc1 = acc1 + part[q * kt + threadIdx.x + blockDim.x];
+        for (int r = threadIdx.x; r < kt; r += blockDim.x) {   // partials (q, r) of this round, in block order
+            const int q = (w0 - r + kt - 1) / kt;
+            cx<T> sum = zero<T>();
+            for (int idx = q * kt + r; idx < w0 + (int)blockDim.x && idx < nw; idx += kt) sum = sum + part[idx - w0];
+            if (r < (int)blockDim.x) acc0 = acc0 + sum;
+            else acc1 = acc1 + sum;
         }
         __syncthreads();
     }
-    if (threadIdx.x < kt) yh[yh_off[a] + threadIdx.x] = acc0;
-    if (threadIdx.x + blockDim.x < kt) yh[yh_off[a] + threadIdx.x + blockDim.x] = acc1;
+    if (threadIdx.x < kt) psum[tl.out + threadIdx.x] = acc0;
+    if (threadIdx.x + blockDim.x < kt) psum[tl.out + threadIdx.x + blockDim.x] = acc1;
+}
+
+// rows of the row pairs with couplings: (row pair offset in y^, first tile sum, tiles, kt)
+struct CoupRow {
+    int64_t yh, out;
+    int32_t ntile, kt;
+};
+
+template <class T>
+__global__ void k_coupling_sum(const CoupRow* __restrict__ rows, int64_t nrows, int64_t nentries,
+                               const int64_t* __restrict__ row_first, const cx<T>* __restrict__ psum, cx<T>* yh) {
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= nentries) return;
+    // row pair of entry g: binary search in row_first (first entry index of each row pair)
+    int64_t lo = 0, hi = nrows - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (row_first[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    const CoupRow r = rows[lo];
+    const int i = (int)(g - row_first[lo]);
+    cx<T> acc = zero<T>();
+    for (int t = 0; t < r.ntile; ++t) acc = acc + psum[r.out + (int64_t)t * r.kt + i];
+    yh[r.yh + i] = acc;
 }
 
 struct LeafOut2 {
@@ -2354,6 +2390,20 @@ private:
     std::vector<std::pair<int64_t, int64_t>> fwd_up_lv_;      // per level range in fwd_up_
     DBuf<FwdUp> fwd_up_;
     DBuf<int32_t> coup_ptr_, krow_d_;
+    DBuf<CoupTile> coup_tiles_;         // coupling tiles (k_coupling_tile) and row sums (k_coupling_sum)
+    DBuf<CoupRow> coup_rows_;
+    DBuf<int64_t> coup_first_;
+    DBuf<cx<T>> coup_psum_;
+    int64_t n_coup_tiles_ = 0, n_coup_rows_ = 0, n_coup_entries_ = 0;
+    void launch_coupling(const cx<T>* xh, cx<T>* yh, cudaStream_t s) {
+        if (n_coup_tiles_ == 0) return;
+        k_coupling_tile<T, kCoupTile / sizeof(cx<T>)><<<(unsigned)n_coup_tiles_, 256, 0, s>>>(
+            coup_tiles_.p, coup_.p, St_.p, xh, coup_psum_.p);
+        DH2_CHECK_LAUNCH("k_coupling_tile");
+        k_coupling_sum<T><<<grid_for(n_coup_entries_, 256), 256, 0, s>>>(coup_rows_.p, n_coup_rows_, n_coup_entries_,
+                                                                        coup_first_.p, coup_psum_.p, yh);
+        DH2_CHECK_LAUNCH("k_coupling_sum");
+    }
     DBuf<Coup> coup_;
     DBuf<int64_t> yh_off_;
     std::vector<std::pair<int64_t, int64_t>> bwd_lv_;
@@ -2375,7 +2425,6 @@ private:
     DBuf<NearPart> near_parts_;   // column chunks of the nearfield panels (graph product)
     DBuf<cx<T>> near_pbuf_;       // their partial row sums
     int64_t n_near_parts_ = 0;
-    int32_t kmax_row_ = 0;
 
     bool timing_on_ = false;
     EventLog ev_;
@@ -3676,6 +3725,42 @@ void Num<T>::plan_matvec(cudaStream_t s) {
     }
     upload_vec(coup_ptr_, cptr, s);
     upload_vec(coup_, items, s);
+    {   // tiles of the coupling products: runs of whole blocks of at most kCoupTile bytes per row pair
+        const int64_t cap = (int64_t)(kCoupTile / sizeof(cx<T>));
+        std::vector<CoupTile> tiles;
+        std::vector<CoupRow> crow;
+        std::vector<int64_t> first;
+        int64_t out = 0, entries = 0;
+        for (int64_t a = 0; a < na_; ++a) {
+            const int32_t e_beg = cptr[a], e_end = cptr[a + 1], kt = rank_[0][a];
+            if (kt == 0) continue;
+            const int64_t t0 = (int64_t)tiles.size(), out0 = out;
+            int32_t e = e_beg;
+            while (e < e_end) {
+                int64_t tot = 0;
+                int32_t e1 = e;
+                while (e1 < e_end) {
+                    const int64_t sz = (int64_t)kt * items[e1].ks;
+                    if (e1 > e && tot + sz > cap) break;
+                    tot += sz;
+                    ++e1;
+                }
+                tiles.push_back(CoupTile{e, e1, kt, 0, out});
+                out += kt;
+                e = e1;
+            }
+            crow.push_back(CoupRow{yh_off[a], out0, (int32_t)((int64_t)tiles.size() - t0), kt});
+            first.push_back(entries);
+            entries += kt;
+        }
+        n_coup_tiles_ = (int64_t)tiles.size();
+        n_coup_rows_ = (int64_t)crow.size();
+        n_coup_entries_ = entries;
+        upload_vec(coup_tiles_, tiles, s);
+        upload_vec(coup_rows_, crow, s);
+        upload_vec(coup_first_, first, s);
+        coup_psum_.alloc(std::max<int64_t>(out, 1));
+    }
     std::vector<int32_t> kr(rank_[0].begin(), rank_[0].end());
     upload_vec(krow_d_, kr, s);
     std::vector<int64_t> yo(yh_off.begin(), yh_off.end() - 1);
@@ -3777,8 +3862,6 @@ void Num<T>::plan_matvec(cudaStream_t s) {
     upload_vec(near_parts_, np, s);
     near_pbuf_.alloc(std::max<int64_t>(pofs, 1));
     upload_vec(leaf_out2_, lo2, s);
-    kmax_row_ = 0;
-    for (int64_t a = 0; a < na_; ++a) kmax_row_ = std::max(kmax_row_, rank_[0][a]);
     const int64_t cs = sizeof(cx<T>);
     info.matvec_bytes = (info.near_entries + info.coupling_entries + info.basis_entries) * cs +
                         2 * n_ * cs + 2 * (xh_off[na_] + yh_off[na_]) * cs;
@@ -3952,10 +4035,8 @@ void Num<T>::launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bo
     }
     if (na_) {
         if (timing_on_) ev_.begin(K_MV_COUPLING, s);
-        k_coupling2<T><<<(unsigned)na_, 256, std::max(256, kmax_row_) * sizeof(cx<T>), s>>>(
-            coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, St_.p, xh_.p, yh_.p);
+        launch_coupling(xh_.p, yh_.p, s);
         if (timing_on_) ev_.end(s);
-        DH2_CHECK_LAUNCH("k_coupling");
     }
     off = 0;
     for (int l = 1; l <= hs_.depth; ++l) {
@@ -4075,9 +4156,7 @@ void Num<T>::matvec_noalloc(const void* x, void* y, int dtype, cudaStream_t s) {
         off += cnt;
     }
     if (na_) {
-        k_coupling2<T><<<(unsigned)na_, 256, std::max(256, kmax_row_) * sizeof(cx<T>), s>>>(
-            coup_ptr_.p, coup_.p, yh_off_.p, krow_d_.p, St_.p, xh, yh);
-        DH2_CHECK_LAUNCH("k_coupling");
+        launch_coupling(xh, yh, s);
     }
     off = 0;
     for (int l = 1; l <= hs_.depth; ++l) {
