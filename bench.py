@@ -88,6 +88,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end builds")
     ap.add_argument("--batch-meshes", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="skip the plain build at the learned order")
+    ap.add_argument("--no-direct", action="store_true", help="skip the direct-recompression build")
     ap.add_argument("--m", type=int, default=0, help="override the workload's configured order")
     ap.add_argument("--no-autotune", action="store_true", help="library default tile shapes, no autotuning")
     ap.add_argument("--qr-tpc", default="", help="fixed FP32 weight-QR threads per column 'a,b,c' (skips autotuning)")
@@ -270,14 +271,16 @@ def cpu_baseline_obj(res):
 TILES = {}   # FP32 weight-QR tile shapes chosen by the autotuner for this run (empty: library defaults)
 
 
-def gpu_build(pkg, v, f, cfg, form, stream, model=None):
+def gpu_build(pkg, v, f, cfg, form, stream, model=None, **extra):
     """Tree + DH^2 build of one workload.  form: 'mixed' (FP32 products and storage, FP64
-    weight factorisations and SVD), 'mixed32' (all FP32) or 'fp64'."""
+    weight factorisations and SVD), 'mixed32' (all FP32) or 'fp64'.  extra: further Matrix
+    options (e.g. direct=1)."""
     tree = pkg.Tree(v, f, leaf_max=cfg["leaf"], stream=stream)
     prec = pkg.DH2_FP64 if form == "fp64" else pkg.DH2_MIXED
     f64 = 0 if form == "mixed32" else 1
     mat = pkg.Matrix(tree, cfg["kappa"], cfg["m"], cfg["eta2"], cfg["eps"], precision=prec, eta1=cfg["eta1"],
-                     qr_fp64=f64, svd_fp64=f64, model=model, stream=stream, **(TILES if form == "mixed32" else {}))
+                     qr_fp64=f64, svd_fp64=f64, model=model, stream=stream, **(TILES if form == "mixed32" else {}),
+                     **extra)
     tree.close()
     return mat
 
@@ -305,7 +308,7 @@ def autotune(pkg, v, f, cfg, stream):
             "note": "0 = library default (8, 4, 2 threads per column; 1024-row groups)"}
 
 
-def time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, warmup, stream, model=None):
+def time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, warmup, stream, model=None, **extra):
     """Device-timed steps: build (tree + DH^2) and one matvec, CUDA events on `stream`.
     Only the last matrix is kept (returned open); the per-kernel and per-stage device
     times of the timed builds are summed as they go."""
@@ -317,7 +320,7 @@ def time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, warmup, stream, model=
         y = torch.empty_like(x_dev)
         torch.cuda.synchronize()
         e0.record(stream)
-        mat = gpu_build(pkg, v, f, cfg, form, stream, model)
+        mat = gpu_build(pkg, v, f, cfg, form, stream, model, **extra)
         e1.record(stream)
         mat.matvec(x_dev, y, stream=stream)
         e2.record(stream)
@@ -366,16 +369,17 @@ def sampled_dense_error(pkg, torch, mat, ref, rows, x):
     return float(np.linalg.norm(y[rows] - ref) / np.linalg.norm(ref))
 
 
-def side_build(pkg, torch, v, f, cfg, form, x, ref, rows, stream, model=None, steps=2):
+def side_build(pkg, torch, v, f, cfg, form, x, ref, rows, stream, model=None, steps=2, **extra):
     """One warm-up and `steps` timed builds of a variant; its product error and sizes."""
     x_dev = torch.from_numpy(x).to(torch.complex128 if form == "fp64" else torch.complex64).cuda()
-    b, mv, kt, _, mat = time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, 1, stream, model)
+    b, mv, kt, _, mat = time_steps(pkg, torch, v, f, cfg, form, x_dev, steps, 1, stream, model, **extra)
     info = mat.get_info()
     mv_ms = matvec_repeat_ms(torch, mat, x_dev, 10, stream)
     out = {"form": form, "m": info.m, "build_s": float(np.mean(b)) / 1e3,
            "relerr_sampled_dense": sampled_dense_error(pkg, torch, mat, ref, rows, x),
            "matvec_ms": mv_ms, "matvec_gbs": info.matvec_bytes / (mv_ms * 1e-3) / 1e9,
            "truncation_MB": info.truncation_bytes / 1e6, "rank_cap_retries": info.rank_cap_retries,
+           "peak_pool_GB": info.peak_pool_bytes / 1e9, "symmetric": info.symmetric,
            "kernel_ms_per_build": {k: round(a / steps, 2) for k, (a, c) in kt.items() if c}}
     out["meets_eps"] = bool(out["relerr_sampled_dense"] <= cfg["eps"])
     mat.close()
@@ -627,6 +631,7 @@ def main():
         "stage_ms_per_build": {k: round(v_ / args.steps, 3) for k, v_ in stimes.items()},
         "kernel_ms_per_build": {k: round(v_[0] / args.steps, 3) for k, v_ in build_kernels.items()},
         "truncation_MB": info.truncation_bytes / 1e6, "rank_cap_retries": info.rank_cap_retries,
+        "peak_pool_GB": info.peak_pool_bytes / 1e9, "symmetric": info.symmetric,
     }
     mat.close()
     release(pkg, torch)
@@ -665,6 +670,10 @@ def main():
     if model is not None and not args.no_learned:
         leg(side, "plain_same_order", lambda: side_build(pkg, torch, v, f, cfg_run, form, x, ref, rows, stream))
         release(pkg, torch)
+    if not args.no_direct:
+        leg(side, "direct_recompression", lambda: side_build(pkg, torch, v, f, cfg_run, form, x, ref, rows, stream,
+                                                             direct=1))
+        release(pkg, torch)
     if not args.no_batch:
         leg(side, "batch", lambda: batch_measure(pkg, torch, args.batch_meshes, stream, form))
         release(pkg, torch)
@@ -688,8 +697,8 @@ def main():
             "matvec": minfo, **headline,
             "roofline": roof,
             "matvec_roofline": mv_roof,
-            **{k: side.get(k) for k in ("configured_order", "all_fp32", "plain_fp64", "plain_same_order", "batch",
-                                         "autotune")},
+            **{k: side.get(k) for k in ("configured_order", "all_fp32", "plain_fp64", "plain_same_order",
+                                         "direct_recompression", "batch", "autotune")},
             "cpu_baseline": side.get("cpu_baseline"),
             "e2e": (e2e if e2e and "value" in e2e else {"error": (e2e or {}).get("error", "not run")}),
             "device_memory_used_gb": device_used_gb, "sm_count": sms,

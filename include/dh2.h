@@ -111,7 +111,16 @@ typedef struct {
                                (t, -c), so they are copied instead of computed.  Used only when the
                                host finds the directions, son maps, block tree and sizes symmetric
                                (dh2_matrix_info.symmetric); 0 = compute both passes */
-    int32_t reserved2;      /* must be 0 */
+    int32_t direct;         /* 1 = direct recompression during the set-up (Section 5, the low-memory
+                               variant of the Boeing run): the leaf bases of each tree level are
+                               evaluated and orthogonalised at once and never held for the whole
+                               tree, and the intermediates of the recompression (basis weights R,
+                               leaf factors P, total weights, transfers, block products K_b) are
+                               released as soon as the last stage that reads them is done; the
+                               stacked-weight workspace per level defaults to 2 GiB.  The matrix and
+                               its products are those of direct = 0; dh2_export_pair of R, P and
+                               the total weights then reports DH2_EUNSUPPORTED.  0 (default) =
+                               keep them for inspection */
 } dh2_options;
 
 typedef struct {
@@ -147,7 +156,10 @@ typedef struct {
                                (Q / F, C, U', singular values), which the learned rank caps size */
     int32_t symmetric;      /* 1 when the build derived the column pass from the row pass
                                (dh2_options.symmetry) */
-    int32_t reserved;
+    int32_t direct;         /* 1 for a build with dh2_options.direct */
+    int64_t peak_pool_bytes;  /* high-water mark of the device memory the library's stream-ordered
+                               pool had handed out during the build (process-wide: concurrent
+                               builds count together) */
 } dh2_matrix_info;
 
 /* Fills *opt with the paper's parameters: eta1 = 10, leaf_max = 32, DH2_MIXED with FP64

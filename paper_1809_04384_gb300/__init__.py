@@ -39,7 +39,7 @@ class dh2_options(C.Structure):
                 ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("qr_group_rows", C.c_int32),
                 ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32),
                 ("learned", C.c_int32), ("svd_fp64", C.c_int32), ("model", C.c_void_p),
-                ("qr_tpc", C.c_int32 * 3), ("fault", C.c_int32), ("symmetry", C.c_int32), ("reserved2", C.c_int32)]
+                ("qr_tpc", C.c_int32 * 3), ("fault", C.c_int32), ("symmetry", C.c_int32), ("direct", C.c_int32)]
 
 
 class dh2_tree_info(C.Structure):
@@ -55,7 +55,8 @@ class dh2_matrix_info(C.Structure):
                 ("stage_ms", C.c_double * 16), ("kernel_ms", C.c_double * 16),
                 ("kernel_launches", C.c_int64 * 16), ("kernel_work", C.c_double * 16),
                 ("kernel_work_kind", C.c_int32 * 16), ("learned_m", C.c_int32), ("rank_cap_retries", C.c_int32),
-                ("truncation_bytes", C.c_int64), ("symmetric", C.c_int32), ("reserved", C.c_int32)]
+                ("truncation_bytes", C.c_int64), ("symmetric", C.c_int32), ("direct", C.c_int32),
+                ("peak_pool_bytes", C.c_int64)]
 
 
 class DH2Error(RuntimeError):
@@ -335,10 +336,11 @@ class Matrix:
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
                  qr_fp64=1, svd_fp64=1, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None,
-                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, symmetry=1, stream=None):
+                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, symmetry=1, direct=0, stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
                        svd_fp64=svd_fp64, qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes,
-                       tensor_cores=tensor_cores, kb_store=kb_store, qr_tpc=qr_tpc, fault=fault, symmetry=symmetry)
+                       tensor_cores=tensor_cores, kb_store=kb_store, qr_tpc=qr_tpc, fault=fault, symmetry=symmetry,
+                       direct=direct)
         if model is not None:
             opts.learned = 1
             opts.model = model.handle

@@ -109,7 +109,7 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.svd_fp64 != 0 && o.svd_fp64 != 1) throw Error{DH2_EINVAL, f + ": svd_fp64 must be 0 or 1"};
     if (o.fault < DH2_FAULT_NONE || o.fault > DH2_FAULT_ALLOC) throw Error{DH2_EINVAL, f + ": bad fault hook"};
     if (o.symmetry != 0 && o.symmetry != 1) throw Error{DH2_EINVAL, f + ": symmetry must be 0 or 1"};
-    if (o.reserved2 != 0) throw Error{DH2_EINVAL, f + ": reserved2 must be 0"};
+    if (o.direct != 0 && o.direct != 1) throw Error{DH2_EINVAL, f + ": direct must be 0 or 1"};
     static const int width[3] = {32, 64, 128};
     for (int c = 0; c < 3; ++c) {
         const int v = o.qr_tpc[c];
@@ -134,6 +134,15 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
         ~FaultScope() { fault_alloc_pending() = false; }
     } fault_scope(o.fault == DH2_FAULT_ALLOC);
     auto mat = std::make_unique<dh2_matrix_s>();
+    // high-water mark of the pool's handed-out memory over this build
+    int pdev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&pdev));
+    cudaMemPool_t pool;
+    DH2_CHECK_CUDA(cudaDeviceGetDefaultMemPool(&pool, pdev));
+    {
+        uint64_t zero = 0;
+        DH2_CHECK_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
     cudaEvent_t e0, e1;
     DH2_CHECK_CUDA(cudaEventCreate(&e0));
     DH2_CHECK_CUDA(cudaEventCreate(&e1));
@@ -151,7 +160,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
                           o.workspace_bytes, o.tensor_cores, o.kb_store, {o.qr_tpc[0], o.qr_tpc[1], o.qr_tpc[2]},
-                          {}, o.svd_fp64, o.fault, o.symmetry};
+                          {}, o.svd_fp64, o.fault, o.symmetry, o.direct};
     if (o.learned) {
         int32_t ml = m;
         learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);
@@ -162,6 +171,11 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->num->build(s);
     mat->num->info.stage_ms[ST_STRUCTURE] += ms;
     DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+    {
+        uint64_t high = 0;
+        DH2_CHECK_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &high));
+        mat->num->info.peak_pool_bytes = (int64_t)high;
+    }
     return mat.release();
 }
 
@@ -611,6 +625,8 @@ dh2_status dh2_matrix_get_info(dh2_matrix mat, dh2_matrix_info* out) {
         out->rank_cap_retries = in.rank_cap_retries;
         out->truncation_bytes = in.truncation_bytes;
         out->symmetric = in.symmetric;
+        out->direct = mat->bp.direct;
+        out->peak_pool_bytes = in.peak_pool_bytes;
     });
 }
 

@@ -2734,7 +2734,8 @@ void Num<T>::analytic(cudaStream_t s) {
         int32_t t = h.a_t[a], c = h.a_c[a];
         int32_t g = h.dir_off[h.level[t]] + c;
         if (leaf_[a]) {
-            lt.push_back(LeafTask{t, g, h.offset[t], h.size[t], offV_[a]});
+            // direct recompression: the leaf bases are evaluated level by level in basis_weights
+            if (!bp_.direct) lt.push_back(LeafTask{t, g, h.offset[t], h.size[t], offV_[a]});
         } else {
             int32_t c1 = h.son_dir(t, c);
             int32_t g1 = h.dir_off[h.level[t] + 1] + c1;
@@ -2742,7 +2743,7 @@ void Num<T>::analytic(cudaStream_t s) {
             tt.push_back(TransferTask{t, h.son1[t], g, g1, offE_[a] + 3 * m_ * m_});
         }
     }
-    V_.alloc(std::max<int64_t>(offV_[na_], 1));
+    V_.alloc(bp_.direct ? 1 : std::max<int64_t>(offV_[na_], 1));
     E_.alloc(std::max<int64_t>(offE_[na_], 1));
     if (!lt.empty()) {
         DBuf<LeafTask> d;
@@ -3126,6 +3127,8 @@ void Num<T>::basis_weights(cudaStream_t s) {
         for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a)
             if (leaf_[a]) smem_n = std::max(smem_n, std::min(rows_[a], 64));
         std::vector<MirrorSeg> mR, mP;   // pairs (t, -c) whose weights are the conjugates of (t, c)'s
+        std::vector<LeafTask> vtasks;      // direct recompression: this level's leaf bases
+        int64_t vlev = 0;
         for (int64_t a = hs_.alevel_start[l]; a < hs_.alevel_start[l + 1]; ++a) {
             if (!canonical(a)) {
                 const int32_t am = mirror_[a];
@@ -3134,7 +3137,14 @@ void Num<T>::basis_weights(cudaStream_t s) {
                 continue;
             }
             if (leaf_[a]) {
-                OrthTask o{offV_[a], offP_[a], offR_[a], gel, rows_[a], rR_[a]};
+                int64_t voff = offV_[a];
+                if (bp_.direct) {
+                    const int32_t t = hs_.a_t[a];
+                    voff = vlev;
+                    vtasks.push_back(LeafTask{t, hs_.dir_off[hs_.level[t]] + hs_.a_c[a], hs_.offset[t], hs_.size[t], voff});
+                    vlev += (int64_t)rows_[a] * kk;
+                }
+                OrthTask o{voff, offP_[a], offR_[a], gel, rows_[a], rR_[a]};
                 if (rows_[a] > smem_n) gel += eig_global_elems(rows_[a]);
                 leafo.push_back(o);
                 work_[K_LEAF_ORTH] += 8.0 * rows_[a] * rows_[a] * kk + 8.0 * rR_[a] * kk * rows_[a];
@@ -3148,6 +3158,18 @@ void Num<T>::basis_weights(cudaStream_t s) {
                 srow += rR_[s0] + rR_[s1];
             }
         }
+        DBuf<cx<T>> vl;   // direct recompression: evaluated here and orthogonalised at once
+        if (!vtasks.empty()) {
+            vl.alloc((size_t)vlev);
+            DBuf<LeafTask> d;
+            upload_vec(d, vtasks, s);
+            ev_.begin(K_LEAF_BASIS, s);
+            k_leaf_basis<T><<<(unsigned)vtasks.size(), 128, 0, s>>>(d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p,
+                                                                    st_.dirs.p, m_, bp_.kappa, vl.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_leaf_basis");
+        }
+        cx<T>* Vsrc = bp_.direct ? vl.p : V_.p;
         if (!leafo.empty()) {
             gscr.reserve(std::max<int64_t>(gel, 1));
             DBuf<OrthTask> d;
@@ -3157,7 +3179,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
             auto kern = bp_.qr_fp64 ? k_leaf_orth<T, true> : k_leaf_orth<T, false>;
             ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_LEAF_ORTH, s);
-            kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, V_.p, gscr.p, smem_n, P_.p, R_.p, err_.p);
+            kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, Vsrc, gscr.p, smem_n, P_.p, R_.p, err_.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_leaf_orth");
             check_err(s, "leaf basis weights");
@@ -3251,7 +3273,8 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
     }
     const int kk = k_;
     const int64_t cap_rows = std::max<int64_t>(
-        64, (bp_.workspace_bytes > 0 ? bp_.workspace_bytes : (int64_t(16) << 30)) / ((int64_t)kk * sizeof(cx<T>)));
+        64, (bp_.workspace_bytes > 0 ? bp_.workspace_bytes : (int64_t(bp_.direct ? 2 : 16) << 30)) /
+                ((int64_t)kk * sizeof(cx<T>)));
     DBuf<cx<T>> stack;
     for (int l = 0; l <= h.depth; ++l) {
         int64_t a = h.alevel_start[l];
@@ -3911,6 +3934,15 @@ void Num<T>::build(cudaStream_t s) {
     tm.begin(ST_TRUNCATE_COL);
     truncate(1, s);
     tm.end(ST_TRUNCATE_COL);
+    if (bp_.direct) {   // read by nothing after the truncation (the projection uses C, U' and K_b)
+        DH2_CHECK_CUDA(cudaStreamSynchronize(s));
+        V_.release();
+        E_.release();
+        R_.release();
+        P_.release();
+        Z_[0].release();
+        Z_[1].release();
+    }
     tm.begin(ST_PROJECT);
     project_checked(s);
     tm.end(ST_PROJECT);
@@ -4190,6 +4222,8 @@ void Num<T>::export_pair(int which, int64_t tc, double* out, int64_t cap, int32_
     const int32_t a = hs_.aidx[tc];
     if (a < 0) return;
     const int pass = (which == DH2_X_ZCOL || which == DH2_X_SCOL || which == DH2_X_QCOL || which == DH2_X_CCOL) ? 1 : 0;
+    if (bp_.direct && (which == DH2_X_R || which == DH2_X_ZROW || which == DH2_X_ZCOL || which == DH2_X_P))
+        throw Error{DH2_EUNSUPPORTED, "a direct-recompression build releases R, P and the total weights"};
     int64_t r = 0, c = 0, ld = 0, off = 0;
     const void* src = nullptr;
     bool is_double = std::is_same<T, double>::value, is_real = false;

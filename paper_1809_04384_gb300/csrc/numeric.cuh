@@ -40,6 +40,7 @@ struct BuildParams {
     int32_t svd_fp64 = 0;   // mixed form: FP64 Gram + Hermitian Jacobi truncation
     int32_t fault = 0;      // dh2_options.fault (test hook)
     int32_t symmetry = 1;   // derive the column pass from the row pass when the structure allows
+    int32_t direct = 0;     // direct recompression: leaf bases per level, intermediates released early
 };
 
 enum KernelId {
@@ -61,6 +62,7 @@ struct MatrixInfoAcc {
     int32_t rank_cap_retries = 0;
     int64_t truncation_bytes = 0;
     int32_t symmetric = 0;
+    int64_t peak_pool_bytes = 0;
 };
 enum WorkKind { W_NONE = 0, W_FLOP32 = 1, W_FLOP64 = 2, W_BYTES = 3 };
 

@@ -438,3 +438,45 @@ def test_symmetric_column_pass_matches_computed(name, expect, precision):
     same = np.array_equal(c0[act], c1[act]) and np.array_equal(r0[act], r1[act])
     assert rel(ys[0], ys[1]) <= (tol["matvec_same_ranks"] if same else 2 * rc.eps)
     assert rel(ys[0], oracle_matvec(name)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision != "fp64" else 0)
+
+
+@pytest.mark.parametrize("name", ["lowfreq1280", "dir1280", "plain5120m5"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_direct_recompression_matches_default(name, precision):
+    """Direct recompression during the set-up (leaf bases evaluated and orthogonalised level by
+    level, intermediates released after their last use) gives the ranks and product of the
+    default build, matches the oracle, refuses exports of what it released, and holds no more
+    device memory at its peak."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    rc = oracle_recompression(name)
+    v, f, p, *_ = oracle_structure(name)
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    x = torch.from_numpy(x_vector(rc.tree.n)).to(vec_dtype(precision)).cuda()
+    act = np.nonzero(rc.pairs.active)[0]
+    tc = int(act[0])
+    out = []
+    for d in (0, 1):   # one matrix at a time: the pool's high-water mark is process-wide
+        torch.cuda.synchronize()
+        dh2.dh2_release_cached()
+        m = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"], direct=d,
+                       **form_kwargs(precision))
+        info = m.get_info()
+        y = m.matvec(x).cpu().numpy().astype(np.complex128)
+        out.append((info.direct, info.peak_pool_bytes, m.ranks(), y, m.pair(dh2.DH2_X_SROW, tc).shape))
+        if d == 1:
+            with pytest.raises(dh2.DH2Error) as ei:
+                m.pair(dh2.DH2_X_R, tc)
+            assert ei.value.status == dh2.DH2_EUNSUPPORTED
+        m.close()
+    (d0, p0, (r0, c0), y0, sh0), (d1, p1, (r1, c1), y1, sh1) = out
+    assert d0 == 0 and d1 == 1
+    assert 0 < p1 <= p0
+    assert np.mean(r0[act] != r1[act]) <= 0.01 and np.mean(c0[act] != c1[act]) <= 0.01
+    tol = TOL[precision]
+    same = np.array_equal(r0[act], r1[act]) and np.array_equal(c0[act], c1[act])
+    assert rel(y1, y0) <= (tol["matvec_same_ranks"] if same else 2 * rc.eps)
+    assert rel(y1, oracle_matvec(name)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision != "fp64" else 0)
+    assert sh1 == sh0
