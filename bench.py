@@ -89,6 +89,7 @@ def parse():
     ap.add_argument("--batch-meshes", type=int, default=64)
     ap.add_argument("--no-learned", action="store_true", help="skip the plain build at the learned order")
     ap.add_argument("--no-direct", action="store_true", help="skip the direct-recompression build")
+    ap.add_argument("--no-dlp", action="store_true", help="skip the double-layer build")
     ap.add_argument("--m", type=int, default=0, help="override the workload's configured order")
     ap.add_argument("--no-autotune", action="store_true", help="library default tile shapes, no autotuning")
     ap.add_argument("--qr-tpc", default="", help="fixed FP32 weight-QR threads per column 'a,b,c' (skips autotuning)")
@@ -376,12 +377,15 @@ def side_build(pkg, torch, v, f, cfg, form, x, ref, rows, stream, model=None, st
     info = mat.get_info()
     mv_ms = matvec_repeat_ms(torch, mat, x_dev, 10, stream)
     out = {"form": form, "m": info.m, "build_s": float(np.mean(b)) / 1e3,
-           "relerr_sampled_dense": sampled_dense_error(pkg, torch, mat, ref, rows, x),
+           "relerr_sampled_dense": (sampled_dense_error(pkg, torch, mat, ref, rows, x) if ref is not None
+                                    else None),
            "matvec_ms": mv_ms, "matvec_gbs": info.matvec_bytes / (mv_ms * 1e-3) / 1e9,
            "truncation_MB": info.truncation_bytes / 1e6, "rank_cap_retries": info.rank_cap_retries,
            "peak_pool_GB": info.peak_pool_bytes / 1e9, "symmetric": info.symmetric,
            "kernel_ms_per_build": {k: round(a / steps, 2) for k, (a, c) in kt.items() if c}}
-    out["meets_eps"] = bool(out["relerr_sampled_dense"] <= cfg["eps"])
+    if ref is not None:
+        out["meets_eps"] = bool(out["relerr_sampled_dense"] <= cfg["eps"])
+    out["mean_rank_row"], out["mean_rank_col"] = info.mean_rank_row, info.mean_rank_col
     mat.close()
     return out
 
@@ -670,6 +674,12 @@ def main():
     if model is not None and not args.no_learned:
         leg(side, "plain_same_order", lambda: side_build(pkg, torch, v, f, cfg_run, form, x, ref, rows, stream))
         release(pkg, torch)
+    if not args.no_dlp:
+        # the double layer operator on the same mesh and order (no dense reference rows: its
+        # error is checked against the oracle in the tests)
+        leg(side, "double_layer", lambda: side_build(pkg, torch, v, f, cfg_run, form, x, None, rows, stream,
+                                                     layer=pkg.DH2_DOUBLE_LAYER))
+        release(pkg, torch)
     if not args.no_direct:
         leg(side, "direct_recompression", lambda: side_build(pkg, torch, v, f, cfg_run, form, x, ref, rows, stream,
                                                              direct=1))
@@ -698,7 +708,7 @@ def main():
             "roofline": roof,
             "matvec_roofline": mv_roof,
             **{k: side.get(k) for k in ("configured_order", "all_fp32", "plain_fp64", "plain_same_order",
-                                         "direct_recompression", "batch", "autotune")},
+                                         "direct_recompression", "double_layer", "batch", "autotune")},
             "cpu_baseline": side.get("cpu_baseline"),
             "e2e": (e2e if e2e and "value" in e2e else {"error": (e2e or {}).get("error", "not run")}),
             "device_memory_used_gb": device_used_gb, "sm_count": sms,

@@ -48,6 +48,7 @@ enum { DH2_FP64 = 0, DH2_MIXED = 1 };                 /* dh2_options.precision *
 enum { DH2_C64 = 1, DH2_C128 = 2 };                   /* vector dtypes */
 enum { DH2_RANK_BLOCKREL = 0, DH2_RANK_GLOBAL = 1, DH2_RANK_SPECTRAL = 2 };  /* dh2_options.rank_rule */
 enum { DH2_FAULT_NONE = 0, DH2_FAULT_TIMEOUT = 1, DH2_FAULT_NONFINITE = 2, DH2_FAULT_ALLOC = 3 };  /* dh2_options.fault */
+enum { DH2_SINGLE_LAYER = 0, DH2_DOUBLE_LAYER = 1 };  /* dh2_options.layer */
 
 typedef struct dh2_tree_s* dh2_tree;
 typedef struct dh2_matrix_s* dh2_matrix;
@@ -121,6 +122,18 @@ typedef struct {
                                its products are those of direct = 0; dh2_export_pair of R, P and
                                the total weights then reports DH2_EUNSUPPORTED.  0 (default) =
                                keep them for inspection */
+    int32_t layer;          /* DH2_SINGLE_LAYER (default): the single layer operator, kernel g of
+                               Eq. (1).  DH2_DOUBLE_LAYER: the double layer operator of the paper's
+                               second experiment (Section 5), kernel d/dn_y g(x, y) =
+                               exp(i kappa r)(1 - i kappa r) <x - y, n_y> / (4 pi r^3) with the unit
+                               normal n_y = (v1 - v0) x (v2 - v0) / |.| of the y element (vertex
+                               order); the nearfield by the 3 x 3 interior rule (0 on the diagonal,
+                               where x - y lies in the element's plane); rows interpolated as for the
+                               single layer (V), columns with the normal derivative of the modified
+                               Lagrange polynomials, W_sc = int phi_j d/dn_y [exp(i kappa <y, c>)
+                               L_{s,mu}(y)], and separate basis weights for V and W (Section 3.2 with
+                               W != V).  The matrix is not symmetric: both passes are computed */
+    int32_t reserved3;      /* must be 0 */
 } dh2_options;
 
 typedef struct {
@@ -420,7 +433,9 @@ enum {
     DH2_X_QCOL = 6,
     DH2_X_CROW = 7,     /* basis change C_tc = Q_tc^* V_tc, k_tc x k */
     DH2_X_CCOL = 8,
-    DH2_X_P = 9         /* leaf pair: orthonormal P with V_tc = P R_tc (#t x r_t) */
+    DH2_X_P = 9,        /* leaf pair: orthonormal P with V_tc = P R_tc (#t x r_t) */
+    DH2_X_RW = 10,      /* column basis weight R_W,tc (double layer; equals DH2_X_R otherwise) */
+    DH2_X_PW = 11       /* leaf pair: orthonormal P_W with W_tc = P_W R_W,tc (double layer) */
 };
 /* Copies one per-pair matrix as complex128 (interleaved, row-major) into out
  * (capacity `cap` complex values; singular values are stored as (sigma, 0)).

@@ -24,8 +24,9 @@ DH2_FP64, DH2_MIXED = 0, 1
 DH2_C64, DH2_C128 = 1, 2
 DH2_RANK_BLOCKREL, DH2_RANK_GLOBAL, DH2_RANK_SPECTRAL = 0, 1, 2
 DH2_FAULT_NONE, DH2_FAULT_TIMEOUT, DH2_FAULT_NONFINITE, DH2_FAULT_ALLOC = 0, 1, 2, 3
+DH2_SINGLE_LAYER, DH2_DOUBLE_LAYER = 0, 1
 (DH2_X_R, DH2_X_ZROW, DH2_X_ZCOL, DH2_X_SROW, DH2_X_SCOL, DH2_X_QROW, DH2_X_QCOL,
- DH2_X_CROW, DH2_X_CCOL, DH2_X_P) = range(10)
+ DH2_X_CROW, DH2_X_CCOL, DH2_X_P, DH2_X_RW, DH2_X_PW) = range(12)
 DH2_MLP_IN, DH2_MLP_HIDDEN, DH2_MLP_OUT, DH2_MLP_NPARAMS, DH2_PROBE_ORDERS = 8, 128, 2, 17922, 6
 # the trained weights of the learned order/rank model (FP32, little endian, packed order of dh2.h)
 LEARNED_WEIGHTS = os.path.join(HERE, "learned_order_rank.f32")
@@ -39,7 +40,8 @@ class dh2_options(C.Structure):
                 ("rank_rule", C.c_int32), ("qr_fp64", C.c_int32), ("qr_group_rows", C.c_int32),
                 ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32),
                 ("learned", C.c_int32), ("svd_fp64", C.c_int32), ("model", C.c_void_p),
-                ("qr_tpc", C.c_int32 * 3), ("fault", C.c_int32), ("symmetry", C.c_int32), ("direct", C.c_int32)]
+                ("qr_tpc", C.c_int32 * 3), ("fault", C.c_int32), ("symmetry", C.c_int32), ("direct", C.c_int32),
+                ("layer", C.c_int32), ("reserved3", C.c_int32)]
 
 
 class dh2_tree_info(C.Structure):
@@ -336,11 +338,11 @@ class Matrix:
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
                  qr_fp64=1, svd_fp64=1, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None,
-                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, symmetry=1, direct=0, stream=None):
+                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, symmetry=1, direct=0, layer=DH2_SINGLE_LAYER, stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
                        svd_fp64=svd_fp64, qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes,
                        tensor_cores=tensor_cores, kb_store=kb_store, qr_tpc=qr_tpc, fault=fault, symmetry=symmetry,
-                       direct=direct)
+                       direct=direct, layer=layer)
         if model is not None:
             opts.learned = 1
             opts.model = model.handle

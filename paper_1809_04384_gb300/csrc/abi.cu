@@ -110,6 +110,8 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.fault < DH2_FAULT_NONE || o.fault > DH2_FAULT_ALLOC) throw Error{DH2_EINVAL, f + ": bad fault hook"};
     if (o.symmetry != 0 && o.symmetry != 1) throw Error{DH2_EINVAL, f + ": symmetry must be 0 or 1"};
     if (o.direct != 0 && o.direct != 1) throw Error{DH2_EINVAL, f + ": direct must be 0 or 1"};
+    if (o.layer != DH2_SINGLE_LAYER && o.layer != DH2_DOUBLE_LAYER) throw Error{DH2_EINVAL, f + ": bad layer"};
+    if (o.reserved3 != 0) throw Error{DH2_EINVAL, f + ": reserved3 must be 0"};
     static const int width[3] = {32, 64, 128};
     for (int c = 0; c < 3; ++c) {
         const int v = o.qr_tpc[c];
@@ -160,7 +162,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
                           o.workspace_bytes, o.tensor_cores, o.kb_store, {o.qr_tpc[0], o.qr_tpc[1], o.qr_tpc[2]},
-                          {}, o.svd_fp64, o.fault, o.symmetry, o.direct};
+                          {}, o.svd_fp64, o.fault, o.symmetry, o.direct, o.layer};
     if (o.learned) {
         int32_t ml = m;
         learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);

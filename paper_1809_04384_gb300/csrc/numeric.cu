@@ -63,6 +63,32 @@ __device__ __forceinline__ double lagrange1(const double* xi, int m, int j, doub
     return v;
 }
 
+// derivative of the Lagrange polynomial l_j of the m nodes xi at x (product rule):
+// l_j'(x) = sum_{q != j} 1 / (xi_j - xi_q) prod_{i != j, q} (x - xi_i) / (xi_j - xi_i)
+__device__ __forceinline__ double lagrange1_d(const double* xi, int m, int j, double x) {
+    double s = 0.0;
+    for (int q = 0; q < m; ++q) {
+        if (q == j) continue;
+        double v = 1.0 / (xi[j] - xi[q]);
+        for (int i = 0; i < m; ++i)
+            if (i != j && i != q) v *= (x - xi[i]) / (xi[j] - xi[i]);
+        s += v;
+    }
+    return s;
+}
+
+// d/dn_y g(x, y) = exp(i kappa r) (1 - i kappa r) <x - y, n_y> / (4 pi r^3) for d = x - y
+template <class T>
+__device__ __forceinline__ cx<T> dlp_d(T dx, T dy, T dz, T n0, T n1, T n2, T kappa) {
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    const T r = sqrt(r2);
+    T s, c;
+    sc(kappa * r, &s, &c);
+    const T kr = kappa * r;
+    const T f = (dx * n0 + dy * n1 + dz * n2) / (T(4.0 * kPi) * r2 * r);
+    return cx<T>{(c + kr * s) * f, (s - kr * c) * f};
+}
+
 // ----------------------------------------------------------------------------- analytic stage
 
 // nodes[t][a][j] = mid_a + half_a cos(pi (2j+1) / (2m)), half padded to >= 1e-3 max half
@@ -88,12 +114,33 @@ struct LeafTask {
     int64_t voff;
 };
 
-// V_tc for leaf pairs: v_{i nu} = |T_i|/3 sum_q exp(i kappa <x_q, c>) L_{t,nu}(x_q)  (FP64, stored as T)
-template <class T>
+// unit normals of the elements (original order): n = (v1 - v0) x (v2 - v0) / |.| (vertex order)
+__global__ void k_normals(const double* __restrict__ vert, const int32_t* __restrict__ tri, int64_t n,
+                          double* __restrict__ nrm) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double* a = vert + 3 * (int64_t)tri[3 * e];
+    const double* b = vert + 3 * (int64_t)tri[3 * e + 1];
+    const double* c = vert + 3 * (int64_t)tri[3 * e + 2];
+    const double u0 = b[0] - a[0], u1 = b[1] - a[1], u2 = b[2] - a[2];
+    const double v0 = c[0] - a[0], v1 = c[1] - a[1], v2 = c[2] - a[2];
+    const double x = u1 * v2 - u2 * v1, y = u2 * v0 - u0 * v2, z = u0 * v1 - u1 * v0;
+    const double inv = 1.0 / sqrt(x * x + y * y + z * z);
+    nrm[3 * e] = x * inv;
+    nrm[3 * e + 1] = y * inv;
+    nrm[3 * e + 2] = z * inv;
+}
+
+// Leaf bases (FP64, stored as T).  Row basis V_tc (W = false):
+//   v_{i nu} = |T_i|/3 sum_q exp(i kappa <x_q, c>) L_{t,nu}(x_q);
+// column basis of the double layer W_tc (W = true), the normal derivative of the same
+// functions along the element normal n_i:
+//   w_{i nu} = |T_i|/3 sum_q exp(i kappa <x_q, c>) (i kappa <n_i, c> L_{t,nu}(x_q) + <n_i, grad L_{t,nu}(x_q)>).
+template <class T, bool W>
 __global__ void k_leaf_basis(const LeafTask* __restrict__ tasks, const int32_t* __restrict__ perm,
                              const double* __restrict__ area, const double* __restrict__ x3,
                              const double* __restrict__ nodes, const double* __restrict__ dirs,
-                             int m, double kappa, cx<T>* V) {
+                             int m, double kappa, const double* __restrict__ nrm, cx<T>* V) {
     const LeafTask tk = tasks[blockIdx.x];
     const int k = m * m * m;
     __shared__ double xi[3][8];
@@ -108,12 +155,23 @@ __global__ void k_leaf_basis(const LeafTask* __restrict__ tasks, const int32_t* 
         double ar = 0.0, ai = 0.0;
         for (int q = 0; q < 3; ++q) {
             const double* x = x3 + ((int64_t)e * 3 + q) * 3;
-            double L = lagrange1(xi[0], m, nx, x[0]) * lagrange1(xi[1], m, ny, x[1]) *
-                       lagrange1(xi[2], m, nz, x[2]);
+            const double lx = lagrange1(xi[0], m, nx, x[0]), ly = lagrange1(xi[1], m, ny, x[1]),
+                         lz = lagrange1(xi[2], m, nz, x[2]);
+            const double L = lx * ly * lz;
             double s, c;
             sincos(kappa * (x[0] * c0 + x[1] * c1 + x[2] * c2), &s, &c);
-            ar += c * L;
-            ai += s * L;
+            if constexpr (W) {
+                const double n0 = nrm[3 * e], n1 = nrm[3 * e + 1], n2 = nrm[3 * e + 2];
+                const double dn = n0 * lagrange1_d(xi[0], m, nx, x[0]) * ly * lz +
+                                  n1 * lx * lagrange1_d(xi[1], m, ny, x[1]) * lz +
+                                  n2 * lx * ly * lagrange1_d(xi[2], m, nz, x[2]);
+                const double kl = kappa * (n0 * c0 + n1 * c1 + n2 * c2) * L;   // imaginary part of the factor
+                ar += c * dn - s * kl;
+                ai += s * dn + c * kl;
+            } else {
+                ar += c * L;
+                ai += s * L;
+            }
         }
         V[tk.voff + idx] = cx<T>{T(w * ar), T(w * ai)};
     }
@@ -197,11 +255,14 @@ struct QuadRows<double> {
 
 __constant__ double c_w7[7];
 
-template <class T>
+// Nearfield entries by quadrature: single layer (DLP = false) g_ij as in Eq. (2), the
+// diagonal by the 7-point rule in x against the 3-point rule in y; double layer (DLP = true)
+// the normal derivative along the column element's normal, 3 x 3 rule, 0 on the diagonal.
+template <class T, bool DLP>
 __global__ void k_nearfield(const NearSeg* __restrict__ segs, QuadRows<T> qr,
                             const int32_t* __restrict__ perm, const double* __restrict__ area,
                             const double* __restrict__ x3, const double* __restrict__ x7, double kappa,
-                            cx<T>* P, int32_t* colidx) {
+                            const double* __restrict__ nrm, cx<T>* P, int32_t* colidx) {
     const NearSeg sg = segs[blockIdx.x];
     const T kap = (T)kappa;
     // the panel's column -> x~ index list, read by the matvec
@@ -211,15 +272,25 @@ __global__ void k_nearfield(const NearSeg* __restrict__ segs, QuadRows<T> qr,
         int64_t r = sg.roff + i, c = sg.coff + j;
         int e = perm[r], f = perm[c];
         cx<T> v;
-        if (e != f) {
+        if (DLP && e == f) {
+            v = zero<T>();
+        } else if (e != f) {
             T acc_r = 0, acc_i = 0;
+            T n0 = 0, n1 = 0, n2 = 0;
+            if constexpr (DLP) {
+                n0 = T(nrm[3 * f]);
+                n1 = T(nrm[3 * f + 1]);
+                n2 = T(nrm[3 * f + 2]);
+            }
 #pragma unroll
             for (int p = 0; p < 3; ++p)
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     T d[3];
                     qr.diff(r, p, c, q, d);
-                    cx<T> g = helmholtz_d<T>(d[0], d[1], d[2], kap);
+                    cx<T> g;
+                    if constexpr (DLP) g = dlp_d<T>(d[0], d[1], d[2], n0, n1, n2, kap);
+                    else g = helmholtz_d<T>(d[0], d[1], d[2], kap);
                     acc_r += g.x;
                     acc_i += g.y;
                 }
@@ -744,9 +815,9 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
                                const int32_t* __restrict__ adm_c, const int32_t* __restrict__ tc_level,
                                const int32_t* __restrict__ dir_off, const double* __restrict__ dirs,
                                const double* __restrict__ nodes, int m, double kappa,
-                               const cx<T>* __restrict__ R, const int64_t* __restrict__ roff,
-                               const int32_t* __restrict__ rrows, double* bnorm, cx<T>* stack,
-                               cx<T>* Kst, unsigned* err) {
+                               const cx<T>* __restrict__ Rv, const cx<T>* __restrict__ Rw,
+                               const int64_t* __restrict__ roff, const int32_t* __restrict__ rrows, double* bnorm,
+                               cx<T>* stack, cx<T>* Kst, unsigned* err) {
     extern __shared__ unsigned char smraw[];
     __shared__ T red[32];
     const BlockRowTask tk = tasks[blockIdx.x];
@@ -754,7 +825,11 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
     const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
     const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
     const int ro = rrows[tk.other];
-    const cx<T>* Ro = R + roff[tk.other];
+    // Rv: weights of the row basis V, Rw: of the column basis W (the same array for the
+    // single layer).  The "other" pair is a column cluster s in the rows pass and in the
+    // recomputed K_b rows, a row cluster t otherwise; the "own" pair is always a row cluster.
+    const cx<T>* R = Rv;
+    const cx<T>* Ro = ((rows_pass || tk.own_leaf == 2) ? Rw : Rv) + roff[tk.other];
     cx<T>* out = stack + tk.dst;
     if constexpr (NT > 0) {
         // node tables (2 x 128 float4), then the tensor-core operands on a 128-byte boundary
@@ -2377,6 +2452,13 @@ private:
     DBuf<int32_t> tc_level_;
     DBuf<double> nodes_;
     DBuf<cx<T>> V_, E_, R_, P_, K_, Z_[2], Q_[2], Ct_[2], Up_[2], St_, near_;
+    // double layer: leaf column bases W and their weights R_W, P_W (same offsets as V, R, P),
+    // element normals (FP64, original order)
+    DBuf<cx<T>> W_, RW_, PW_;
+    DBuf<double> normals_;
+    bool dlp() const { return bp_.layer == DH2_DOUBLE_LAYER; }
+    const cx<T>* Rcol() const { return dlp() ? RW_.p : R_.p; }
+    const cx<T>* Pcol() const { return dlp() ? PW_.p : P_.p; }
     DBuf<cx<double>> Cd_[2];
     DBuf<double> sig_[2], bnorm_;
     DBuf<int64_t> offR_d_;
@@ -2468,6 +2550,7 @@ private:
     void analytic(cudaStream_t s);
     void nearfield(cudaStream_t s);
     void basis_weights(cudaStream_t s);
+    void basis_weights_of(bool col, cudaStream_t s);
     void total_weights(int pass, cudaStream_t s);
     template <int NT>
     void launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pass, cx<T>* stack, cudaStream_t s);
@@ -2656,7 +2739,7 @@ template <class T>
 void Num<T>::setup_symmetry(cudaStream_t s) {
     sym_ = false;
     mirror_.clear();
-    if (!bp_.symmetry || na_ == 0) return;
+    if (!bp_.symmetry || na_ == 0 || dlp()) return;   // the double layer is not symmetric
     const auto& h = hs_;
     const std::vector<double> dirs = st_.dirs.to_host(s);
     const int L = h.depth;
@@ -2745,14 +2828,28 @@ void Num<T>::analytic(cudaStream_t s) {
     }
     V_.alloc(bp_.direct ? 1 : std::max<int64_t>(offV_[na_], 1));
     E_.alloc(std::max<int64_t>(offE_[na_], 1));
+    if (dlp()) {
+        normals_.alloc((size_t)3 * std::max<int64_t>(n_, 1));
+        k_normals<<<grid_for(n_, kThreads), kThreads, 0, s>>>(tr_.vert.p, tr_.tri.p, n_, normals_.p);
+        DH2_CHECK_LAUNCH("k_normals");
+        W_.alloc(bp_.direct ? 1 : std::max<int64_t>(offV_[na_], 1));
+    }
     if (!lt.empty()) {
         DBuf<LeafTask> d;
         upload_vec(d, lt, s);
         ev_.begin(K_LEAF_BASIS, s);
-        k_leaf_basis<T><<<(unsigned)lt.size(), 128, 0, s>>>(d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p,
-                                                            st_.dirs.p, m_, bp_.kappa, V_.p);
+        k_leaf_basis<T, false><<<(unsigned)lt.size(), 128, 0, s>>>(d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p,
+                                                                   st_.dirs.p, m_, bp_.kappa, nullptr, V_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_leaf_basis");
+        if (dlp()) {   // the column bases of the double layer, same layout
+            ev_.begin(K_LEAF_BASIS, s);
+            k_leaf_basis<T, true><<<(unsigned)lt.size(), 128, 0, s>>>(d.p, tr_.perm.p, tr_.area.p, tr_.x3.p,
+                                                                      nodes_.p, st_.dirs.p, m_, bp_.kappa, normals_.p,
+                                                                      W_.p);
+            ev_.end(s);
+            DH2_CHECK_LAUNCH("k_leaf_basis");
+        }
         DH2_CHECK_CUDA(cudaStreamSynchronize(s));
     }
     if (!tt.empty()) {
@@ -2864,8 +2961,14 @@ void Num<T>::nearfield(cudaStream_t s) {
     for (int64_t b0 = 0; b0 < (int64_t)all.size(); b0 += chunk) {
         int64_t cnt = std::min<int64_t>(chunk, (int64_t)all.size() - b0);
         ev_.begin(K_NEARFIELD, s);
-        k_nearfield<T><<<(unsigned)cnt, kThreads, 0, s>>>(dseg.p + b0, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
-                                                          tr_.x7.p, bp_.kappa, near_.p, colidx_.p);
+        if (dlp())
+            k_nearfield<T, true><<<(unsigned)cnt, kThreads, 0, s>>>(dseg.p + b0, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
+                                                                    tr_.x7.p, bp_.kappa, normals_.p, near_.p,
+                                                                    colidx_.p);
+        else
+            k_nearfield<T, false><<<(unsigned)cnt, kThreads, 0, s>>>(dseg.p + b0, qr, tr_.perm.p, tr_.area.p,
+                                                                     tr_.x3.p, tr_.x7.p, bp_.kappa, nullptr, near_.p,
+                                                                     colidx_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_nearfield");
     }
@@ -3111,10 +3214,25 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
 
 // ----------------------------------------------------------------------------- basis weights
 
+// Basis weights of one basis, bottom-up (Eq. basis_weights_def): col = false the row basis V
+// (R_, P_), col = true the column basis W of the double layer (RW_, PW_); the two have the
+// same sizes and offsets.
 template <class T>
 void Num<T>::basis_weights(cudaStream_t s) {
-    R_.alloc(std::max<int64_t>(offR_[na_], 1));
-    P_.alloc(std::max<int64_t>(offP_[na_], 1));
+    basis_weights_of(false, s);
+    if (dlp()) basis_weights_of(true, s);
+    std::vector<int32_t> rr(rR_.begin(), rR_.end());
+    upload_vec(rR_d_, rr, s);
+    upload_vec(offR_d_, offR_, s);
+    check_err(s, "basis weights");
+}
+
+template <class T>
+void Num<T>::basis_weights_of(bool col, cudaStream_t s) {
+    DBuf<cx<T>>& Rb = col ? RW_ : R_;
+    DBuf<cx<T>>& Pb = col ? PW_ : P_;
+    Rb.alloc(std::max<int64_t>(offR_[na_], 1));
+    Pb.alloc(std::max<int64_t>(offP_[na_], 1));
     DBuf<cx<T>> stack;
     DBuf<cx<double>> gscr;
     const int kk = k_;
@@ -3164,12 +3282,16 @@ void Num<T>::basis_weights(cudaStream_t s) {
             DBuf<LeafTask> d;
             upload_vec(d, vtasks, s);
             ev_.begin(K_LEAF_BASIS, s);
-            k_leaf_basis<T><<<(unsigned)vtasks.size(), 128, 0, s>>>(d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p,
-                                                                    st_.dirs.p, m_, bp_.kappa, vl.p);
+            if (col)
+                k_leaf_basis<T, true><<<(unsigned)vtasks.size(), 128, 0, s>>>(
+                    d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p, st_.dirs.p, m_, bp_.kappa, normals_.p, vl.p);
+            else
+                k_leaf_basis<T, false><<<(unsigned)vtasks.size(), 128, 0, s>>>(
+                    d.p, tr_.perm.p, tr_.area.p, tr_.x3.p, nodes_.p, st_.dirs.p, m_, bp_.kappa, nullptr, vl.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_leaf_basis");
         }
-        cx<T>* Vsrc = bp_.direct ? vl.p : V_.p;
+        cx<T>* Vsrc = bp_.direct ? vl.p : (col ? W_.p : V_.p);
         if (!leafo.empty()) {
             gscr.reserve(std::max<int64_t>(gel, 1));
             DBuf<OrthTask> d;
@@ -3179,7 +3301,7 @@ void Num<T>::basis_weights(cudaStream_t s) {
             auto kern = bp_.qr_fp64 ? k_leaf_orth<T, true> : k_leaf_orth<T, false>;
             ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_LEAF_ORTH, s);
-            kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, Vsrc, gscr.p, smem_n, P_.p, R_.p, err_.p);
+            kern<<<(unsigned)leafo.size(), kThreads, smem, s>>>(d.p, kk, Vsrc, gscr.p, smem_n, Pb.p, Rb.p, err_.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_leaf_orth");
             check_err(s, "leaf basis weights");
@@ -3190,18 +3312,14 @@ void Num<T>::basis_weights(cudaStream_t s) {
             upload_vec(d, kron, s);
             size_t smem = (2 * (size_t)kk + 3 * m_ * m_) * sizeof(cx<T>);
             ev_.begin(K_KRON, s);
-            k_kron<T, T, T, T><<<(unsigned)kron.size(), kThreads, smem, s>>>(d.p, m_, R_.p, E_.p, stack.p);
+            k_kron<T, T, T, T><<<(unsigned)kron.size(), kThreads, smem, s>>>(d.p, m_, Rb.p, E_.p, stack.p);
             ev_.end(s);
             DH2_CHECK_LAUNCH("k_kron");
-            tsqr(innerq, stack.p, R_.p, s, "basis weights");
+            tsqr(innerq, stack.p, Rb.p, s, "basis weights");
         }
-        mirror_copy<cx<T>, true>(mR, R_.p, R_.p, s);
-        mirror_copy<cx<T>, true>(mP, P_.p, P_.p, s);
+        mirror_copy<cx<T>, true>(mR, Rb.p, Rb.p, s);
+        mirror_copy<cx<T>, true>(mP, Pb.p, Pb.p, s);
     }
-    std::vector<int32_t> rr(rR_.begin(), rR_.end());
-    upload_vec(rR_d_, rr, s);
-    upload_vec(offR_d_, offR_, s);
-    check_err(s, "basis weights");
 }
 
 // ----------------------------------------------------------------------------- total weights
@@ -3222,8 +3340,8 @@ void Num<T>::launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pas
         ev_.begin(K_STACK_BLOCKS, s);
         kern<<<(unsigned)tasks.size(), kThreads, smem, s>>>(d.p, pass == 0, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p,
                                                           tc_level_.p, st_.dir_off_d.p, st_.dirs.p, nodes_.p, m_,
-                                                          bp_.kappa, R_.p, offR_d_.p, rR_d_.p, bnorm_.p, stack,
-                                                          kstore_ ? K_.p : nullptr, err_.p);
+                                                          bp_.kappa, R_.p, Rcol(), offR_d_.p, rR_d_.p, bnorm_.p,
+                                                          stack, kstore_ ? K_.p : nullptr, err_.p);
         ev_.end(s);
         DH2_CHECK_LAUNCH("k_stack_blocks");
     }
@@ -3366,8 +3484,9 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
             if (!rhtasks.empty()) {
                 DBuf<RhTask> d;
                 upload_vec(d, rhtasks, s);
-                k_rows_rh<T><<<(unsigned)rhtasks.size(), kThreads, (size_t)kk * sizeof(cx<T>), s>>>(d.p, kk, R_.p,
-                                                                                                   stack.p);
+                // the leaf's own basis: V in the rows pass, W in the columns pass
+                k_rows_rh<T><<<(unsigned)rhtasks.size(), kThreads, (size_t)kk * sizeof(cx<T>), s>>>(
+                    d.p, kk, pass == 0 ? R_.p : Rcol(), stack.p);
                 DH2_CHECK_LAUNCH("k_rows_rh");
             }
             tsqr(qtasks, stack.p, Z_[pass].p, s, pass == 0 ? "total weights (rows)" : "total weights (columns)");
@@ -3528,7 +3647,8 @@ bool Num<T>::truncate_once(int pass, cudaStream_t s) {
             auto kern = bp_.svd_fp64 ? k_trunc_leaf<T, true> : k_trunc_leaf<T, false>;
             ensure_smem(reinterpret_cast<const void*>(kern), smem);
             ev_.begin(K_TRUNCATE, s);
-            kern<<<(unsigned)lt.size(), kThreads, smem, s>>>(d.p, kk, Z_[pass].p, P_.p, R_.p, lscr.p, smem_l,
+            kern<<<(unsigned)lt.size(), kThreads, smem, s>>>(d.p, kk, Z_[pass].p, pass == 0 ? P_.p : Pcol(),
+                                                              pass == 0 ? R_.p : Rcol(), lscr.p, smem_l,
                                                               bp_.eps, bp_.rank_rule, Q_[pass].p, Cd_[pass].p, Ct,
                                                               sig_[pass].p, rank_d_[pass].p, Up_[pass].p, err_.p);
             ev_.end(s);
@@ -3937,9 +4057,12 @@ void Num<T>::build(cudaStream_t s) {
     if (bp_.direct) {   // read by nothing after the truncation (the projection uses C, U' and K_b)
         DH2_CHECK_CUDA(cudaStreamSynchronize(s));
         V_.release();
+        W_.release();
         E_.release();
         R_.release();
         P_.release();
+        RW_.release();
+        PW_.release();
         Z_[0].release();
         Z_[1].release();
     }
@@ -4222,7 +4345,8 @@ void Num<T>::export_pair(int which, int64_t tc, double* out, int64_t cap, int32_
     const int32_t a = hs_.aidx[tc];
     if (a < 0) return;
     const int pass = (which == DH2_X_ZCOL || which == DH2_X_SCOL || which == DH2_X_QCOL || which == DH2_X_CCOL) ? 1 : 0;
-    if (bp_.direct && (which == DH2_X_R || which == DH2_X_ZROW || which == DH2_X_ZCOL || which == DH2_X_P))
+    if (bp_.direct && (which == DH2_X_R || which == DH2_X_ZROW || which == DH2_X_ZCOL || which == DH2_X_P ||
+                       which == DH2_X_RW || which == DH2_X_PW))
         throw Error{DH2_EUNSUPPORTED, "a direct-recompression build releases R, P and the total weights"};
     int64_t r = 0, c = 0, ld = 0, off = 0;
     const void* src = nullptr;
@@ -4230,6 +4354,10 @@ void Num<T>::export_pair(int which, int64_t tc, double* out, int64_t cap, int32_
     const int rowsA = leaf_[a] ? rows_[a] : rank_[pass][sons_[0][a]] + rank_[pass][sons_[1][a]];
     switch (which) {
         case DH2_X_R: r = rR_[a]; c = k_; ld = k_; off = offR_[a]; src = R_.p; break;
+        case DH2_X_RW: r = rR_[a]; c = k_; ld = k_; off = offR_[a]; src = Rcol(); break;
+        case DH2_X_PW:
+            if (!leaf_[a]) return;
+            r = rows_[a]; c = rR_[a]; ld = c; off = offP_[a]; src = Pcol(); break;
         case DH2_X_ZROW: case DH2_X_ZCOL:
             r = rZ_[pass][a]; c = zcols(a); ld = c; off = offZ_[pass][a]; src = Z_[pass].p; break;
         case DH2_X_P:

@@ -41,6 +41,7 @@ struct BuildParams {
     int32_t fault = 0;      // dh2_options.fault (test hook)
     int32_t symmetry = 1;   // derive the column pass from the row pass when the structure allows
     int32_t direct = 0;     // direct recompression: leaf bases per level, intermediates released early
+    int32_t layer = 0;      // DH2_SINGLE_LAYER / DH2_DOUBLE_LAYER
 };
 
 enum KernelId {
