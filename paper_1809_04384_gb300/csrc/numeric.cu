@@ -493,9 +493,10 @@ __device__ void tc_product(TcState& st, uint32_t col0, int K, const GA& genA, co
     tc::fence_after_sync();
 }
 
+// ncols: TMEM columns of the CTA (a power of two, 32 ... 512), 2 NT by default
 template <int NT>
-__device__ void tc_begin(TcState& st, float* buf, uint64_t* mbar, uint32_t* tmem_slot) {
-    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(tmem_slot, 2 * NT);
+__device__ void tc_begin(TcState& st, float* buf, uint64_t* mbar, uint32_t* tmem_slot, uint32_t ncols = 2 * NT) {
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(tmem_slot, ncols);
     if (threadIdx.x == 0) tc::mbar_init(mbar, 1);
     tc::fence_before_sync();
     __syncthreads();
@@ -505,14 +506,14 @@ __device__ void tc_begin(TcState& st, float* buf, uint64_t* mbar, uint32_t* tmem
 
 // releases the TMEM; after a timeout, first lets committed products finish (bounded)
 template <int NT>
-__device__ void tc_end(TcState& st, unsigned* err) {
+__device__ void tc_end(TcState& st, unsigned* err, uint32_t ncols = 2 * NT) {
     if (!st.ok) {
         if (threadIdx.x == 0) raise_err(err, ERR_TC_TIMEOUT);
         if (st.phase > 0) tc::mbar_wait(st.mbar, (st.phase - 1) & 1, kTcWaitPolls);
     }
     tc::fence_before_sync();
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(st.tmem, 2 * NT);
+    if ((threadIdx.x >> 5) == 0) tc::tmem_dealloc(st.tmem, ncols);
 }
 
 // Operand generators.  A chunk of an M = 128 operand is written at float offset idx
@@ -544,10 +545,11 @@ __device__ __forceinline__ cx<float> coupling_value(float4 p, float4 q, float ka
 
 template <int NT>
 struct GenS {
-    const float4* P;   // 128 entries (row side), zero-padded past k
+    const float4* P;   // 128 entries (row side: rows nu of this M tile)
     const float4* Q;   // k entries (column side)
-    int k;
+    int k;             // contraction length (columns mu)
     float kappa;
+    int nk;            // rows of this M tile that exist (rows nu >= nk are zero)
     __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
         constexpr int KC = TcTile<NT>::KC;
         constexpr int GROUPS = KC / 4;                          // 4-wide groups of a chunk
@@ -563,7 +565,7 @@ struct GenS {
             for (int e = 0; e < 4; ++e) {
                 const int mu = mu0 + 4 * g + e;
                 cx<float> v = zero<float>();
-                if (nu < k && mu < k) v = coupling_value(p, Q[mu], kappa);
+                if (nu < nk && mu < k) v = coupling_value(p, Q[mu], kappa);
                 tc::split_tf32(v.x, ph1[e], pl1[e]);
                 tc::split_tf32(v.y, ph2[e], pl2[e]);
             }
@@ -586,9 +588,10 @@ __device__ void load_node_tables(int32_t t, int32_t s, const double* __restrict_
     const double* np_ = nodes + (int64_t)cp * 3 * m;
     const double* nq_ = nodes + (int64_t)cq * 3 * m;
     const double rx = nq_[0], ry = nq_[m], rz = nq_[2 * m];
-    for (int idx = threadIdx.x; idx < 128 + k; idx += blockDim.x) {
-        const bool isp = idx < 128;
-        const int nu = isp ? idx : idx - 128;
+    // P: 256 entries (two M tiles of 128 rows), zero past k; Q: k entries
+    for (int idx = threadIdx.x; idx < 256 + k; idx += blockDim.x) {
+        const bool isp = idx < 256;
+        const int nu = isp ? idx : idx - 256;
         const double* nn = isp ? np_ : nq_;
         float4 v = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         if (nu < k) {
@@ -666,16 +669,17 @@ struct GenRowsB {
 // (quarter + 4) may read; each of the two reads half of the columns j.
 template <int NT>
 struct GenFromTmem {
-    uint32_t d1;   // TMEM address of D1 (lane 0, first column)
+    uint32_t d1;   // TMEM address of D1 (lane 0, first column); rows nu >= 128 in the next NT columns
     int ro;
     bool conj_d;
     __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
         constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int q = mu0 >> 5;                 // TMEM lane quarter of this chunk (KC <= 32)
+        const int z = mu0 >> 7;                 // M tile of D1 holding rows mu0 ... (KC divides 128)
+        const int q = (mu0 & 127) >> 5;         // TMEM lane quarter of this chunk (KC <= 32)
         if ((warp & 3) != q) return;
         const int sub = lane - (mu0 & 31);      // row of the chunk held by this lane
-        const uint32_t trow = d1 + ((uint32_t)(32 * q) << 16);
+        const uint32_t trow = d1 + (uint32_t)(z * NT) + ((uint32_t)(32 * q) << 16);
         const int half = warp >> 2;
         for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2); c0 += 16) {
             float re[16], im[16];
@@ -697,9 +701,11 @@ struct GenFromTmem {
 };
 
 // Tensor-core form of one block task (both passes; see the comment of k_stack_blocks).
-// Rows pass: D1 = (R_s S_b^*)^T (TMEM columns [0, NT)), then K_b = R_t conj(D1)
-// (columns [NT, 2 NT)); |G_b|_F = |K_b|_F; the stack rows are written once, scaled:
-// w K_b^* for a leaf row cluster, w R_s S_b^* otherwise.  Cols pass: (R_t S_b)^T, scaled.
+// Rows pass: D1 = (R_s S_b^*)^T, then K_b = R_t conj(D1); |G_b|_F = |K_b|_F; the stack rows
+// are written once, scaled: w K_b^* for a leaf row cluster, w R_s S_b^* otherwise.  Cols
+// pass: (R_t S_b)^T, scaled.  An MMA tile has M = 128 rows, so k <= 256 takes nz = 1 or 2
+// tiles of rows nu of D1 (TMEM columns [z NT, (z + 1) NT)) and of rows a of K_b (columns
+// [(nz + y) NT, ...)); the CTA holds 2 nz NT TMEM columns.
 template <int NT>
 __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const float4* Ptab, const float4* Qtab,
                                 float kappa, int k,
@@ -710,101 +716,107 @@ __device__ void stack_blocks_tc(const BlockRowTask& tk, bool rows_pass, const fl
     constexpr int RP = TcTile<NT>::RP;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = warp & 3, half = warp >> 2;
-    const int row = 32 * q + lane;   // TMEM lane (D row) read by this thread
+    const int nz = k > 128 ? 2 : 1;
+    const uint32_t ncols = (uint32_t)(2 * nz * NT);
     TcState st;
-    tc_begin<NT>(st, tcbuf, mbar, tmem_slot);
-    const uint32_t trow = st.tmem + ((uint32_t)(32 * q) << 16);
+    tc_begin<NT>(st, tcbuf, mbar, tmem_slot, ncols);
+    const uint32_t tq = st.tmem + ((uint32_t)(32 * q) << 16);   // this warp's lane quarter
     const bool kmode = !rows_pass && tk.own_leaf == 2;   // column stack rows w K_b, recomputed
+    // D1 = (R_o S^*)^T (sign +1) or (R_o S)^T (cols pass, sign -1), tile by tile
+    const float sgn = (!rows_pass && !kmode) ? -1.0f : 1.0f;
+    for (int z = 0; z < nz; ++z)
+        tc_product<NT>(st, (uint32_t)(z * NT), k, GenS<NT>{Ptab + 128 * z, Qtab, k, kappa, k - 128 * z},
+                       GenRowsB<NT>{Ro, ro, k, sgn});
     if (!rows_pass && !kmode) {
         const float sc_ = bnorm[tk.b] > 0.0 ? float(1.0 / bnorm[tk.b]) : 0.0f;
-        tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, kappa}, GenRowsB<NT>{Ro, ro, k, -1.0f});
         if (st.ok) {
-            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
-                float re[16], im[16];
-                tc::tmem_ld16(trow + (uint32_t)c0, re);
-                tc::tmem_ld16(trow + (uint32_t)(c0 + RP), im);
-                if (row < k)
+            for (int z = 0; z < nz; ++z) {
+                const int row = 128 * z + 32 * q + lane;   // nu
+                for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                    float re[16], im[16];
+                    tc::tmem_ld16(tq + (uint32_t)(z * NT + c0), re);
+                    tc::tmem_ld16(tq + (uint32_t)(z * NT + c0 + RP), im);
+                    if (row < k)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < ro) out[(int64_t)(c0 + j) * k + row] = cx<float>{sc_ * re[j], sc_ * im[j]};
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < ro) out[(int64_t)(c0 + j) * k + row] = cx<float>{sc_ * re[j], sc_ * im[j]};
+                }
             }
         }
-        tc_end<NT>(st, err);
+        tc_end<NT>(st, err, ncols);
         return;
     }
-    tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, kappa}, GenRowsB<NT>{Ro, ro, k, 1.0f});
     const int rt = rrows[tk.own];
+    const int ny = rt > 128 ? 2 : 1;   // rt <= k <= 128 nz
     const cx<float>* Rt = R + roff[tk.own];
     cx<float>* Kb = (Kst && !kmode) ? Kst + tk.koff : nullptr;   // stored only if there is a store
-    tc_product<NT>(st, NT, k, GenRowsA<NT>{Rt, rt, k, k}, GenFromTmem<NT>{st.tmem, ro, true});
-    // K_b (rows a = TMEM lanes, columns j < ro) and |K_b|_F
+    for (int y = 0; y < ny; ++y)
+        tc_product<NT>(st, (uint32_t)((nz + y) * NT), k, GenRowsA<NT>{Rt + (int64_t)128 * y * k, rt - 128 * y, k, k},
+                       GenFromTmem<NT>{st.tmem, ro, true});
+    // K_b (rows a = TMEM lanes of tile y, columns j < ro) and |K_b|_F
     float acc = 0.0f;
     if (st.ok) {
-        for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
-            float re[16], im[16];
-            tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
-            tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
-            if (row < rt)
+        for (int y = 0; y < ny; ++y) {
+            const int row = 128 * y + 32 * q + lane;   // a
+            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(tq + (uint32_t)((nz + y) * NT + c0), re);
+                tc::tmem_ld16(tq + (uint32_t)((nz + y) * NT + c0 + RP), im);
+                if (row < rt)
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (c0 + j < ro) {
-                        if (Kb) Kb[(int64_t)row * ro + c0 + j] = cx<float>{re[j], im[j]};
-                        acc += re[j] * re[j] + im[j] * im[j];
-                    }
+                    for (int j = 0; j < 16; ++j)
+                        if (c0 + j < ro) {
+                            if (Kb) Kb[(int64_t)row * ro + c0 + j] = cx<float>{re[j], im[j]};
+                            acc += re[j] * re[j] + im[j] * im[j];
+                        }
+            }
         }
     }
     const float nrm = sqrtf(block_sum(acc, red));
     if (threadIdx.x == 0 && !kmode) bnorm[tk.b] = (double)nrm;
     const float sc_ = nrm > 0.0f ? 1.0f / nrm : 0.0f;
     if (st.ok) {
-        if (kmode) {
-            // w K_b: column-stack row a (< rt), column j (< ro), pitch k
-            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
-                float re[16], im[16];
-                tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
-                tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
-                if (row < rt)
+        if (kmode || tk.own_leaf) {
+            // kmode: w K_b, column-stack row a (< rt), column j (< ro), pitch k;
+            // leaf row cluster: w K_b^*, stack row j (< ro), column a (< rt), pitch k
+            for (int y = 0; y < ny; ++y) {
+                const int row = 128 * y + 32 * q + lane;   // a
+                for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                    float re[16], im[16];
+                    tc::tmem_ld16(tq + (uint32_t)((nz + y) * NT + c0), re);
+                    tc::tmem_ld16(tq + (uint32_t)((nz + y) * NT + c0 + RP), im);
+                    if (row < rt)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < ro) {
-                            const cx<float> v{sc_ * re[j], sc_ * im[j]};
-                            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
-                            out[(int64_t)row * k + c0 + j] = v;
-                        }
-            }
-        } else if (tk.own_leaf) {
-            // w K_b^*: stack row j (< ro), column a (< rt), pitch k
-            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
-                float re[16], im[16];
-                tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
-                tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
-                if (row < rt)
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < ro) {
-                            const cx<float> v{sc_ * re[j], -sc_ * im[j]};
-                            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
-                            out[(int64_t)(c0 + j) * k + row] = v;
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < ro) {
+                                const cx<float> v{sc_ * re[j], (kmode ? sc_ : -sc_) * im[j]};
+                                if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                                if (kmode) out[(int64_t)row * k + c0 + j] = v;
+                                else out[(int64_t)(c0 + j) * k + row] = v;
+                            }
+                }
             }
         } else {
             // w R_s S_b^*: stack row i (< ro), column nu (< k)
-            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
-                float re[16], im[16];
-                tc::tmem_ld16(trow + (uint32_t)c0, re);
-                tc::tmem_ld16(trow + (uint32_t)(c0 + RP), im);
-                if (row < k)
+            for (int z = 0; z < nz; ++z) {
+                const int row = 128 * z + 32 * q + lane;   // nu
+                for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < ro; c0 += 16) {
+                    float re[16], im[16];
+                    tc::tmem_ld16(tq + (uint32_t)(z * NT + c0), re);
+                    tc::tmem_ld16(tq + (uint32_t)(z * NT + c0 + RP), im);
+                    if (row < k)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (c0 + j < ro) {
-                            const cx<float> v{sc_ * re[j], sc_ * im[j]};
-                            if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
-                            out[(int64_t)(c0 + j) * k + row] = v;
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            if (c0 + j < ro) {
+                                const cx<float> v{sc_ * re[j], sc_ * im[j]};
+                                if (!isfinite(v.x) || !isfinite(v.y)) raise_err(err, ERR_STACK_NONFINITE);
+                                out[(int64_t)(c0 + j) * k + row] = v;
+                            }
+                }
             }
         }
     }
-    tc_end<NT>(st, err);
+    tc_end<NT>(st, err, ncols);
 }
 
 // rows pass: R_sc S_b^*, then |G_b|_F = |R_tc S_b R_sc^*|_F, rows scaled by 1/|G_b|.
@@ -837,8 +849,8 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
         __shared__ uint32_t tc_tmem;
         float4* Ptab = reinterpret_cast<float4*>(
             (reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
-        float4* Qtab = Ptab + 128;
-        float* tcbuf = reinterpret_cast<float*>(Qtab + 128);
+        float4* Qtab = Ptab + 256;
+        float* tcbuf = reinterpret_cast<float*>(Qtab + 256);
         load_node_tables(t, s, cd, nodes, m, rows_pass || tk.own_leaf == 2, Ptab, Qtab);
         stack_blocks_tc<NT>(tk, rows_pass, Ptab, Qtab, (float)kappa, k, Ro, ro, R, roff, rrows, bnorm, out, Kst,
                             tcbuf, &tc_mbar, &tc_tmem, red, err);
@@ -1861,31 +1873,40 @@ __global__ void __launch_bounds__(256, 2) k_project_tc(const ProjTask* __restric
     const int32_t t = adm_t[tk.b], s = adm_s[tk.b], c = adm_c[tk.b];
     const double* cd = dirs + 3 * (dir_off[tc_level[t]] + c);
     float4* Ptab = reinterpret_cast<float4*>((reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
-    float4* Qtab = Ptab + 128;
-    float* tcbuf = reinterpret_cast<float*>(Qtab + 128);
+    float4* Qtab = Ptab + 256;
+    float* tcbuf = reinterpret_cast<float*>(Qtab + 256);
     load_node_tables(t, s, cd, nodes, m, false, Ptab, Qtab);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int q = warp & 3, half = warp >> 2;
-    const int row = 32 * q + lane;
     const int kt = tk.kt, ks = tk.ks;
+    // k <= 256: nz tiles of 128 rows nu of D1 = (C_t S)^T, ny tiles of 128 rows of S~^T
+    const int nz = k > 128 ? 2 : 1, ny = ks > 128 ? 2 : 1;
+    const uint32_t ncols = (uint32_t)(2 * nz * NT);
     TcState st;
-    tc_begin<NT>(st, tcbuf, &tc_mbar, &tc_tmem);
-    tc_product<NT>(st, 0, k, GenS<NT>{Ptab, Qtab, k, (float)kappa}, GenRowsB<NT>{Crow + tk.crow, kt, k, -1.0f});
-    tc_product<NT>(st, NT, k, GenRowsA<NT>{Ccol + tk.ccol, ks, k, k}, GenFromTmem<NT>{st.tmem, kt, false});
+    tc_begin<NT>(st, tcbuf, &tc_mbar, &tc_tmem, ncols);
+    for (int z = 0; z < nz; ++z)
+        tc_product<NT>(st, (uint32_t)(z * NT), k, GenS<NT>{Ptab + 128 * z, Qtab, k, (float)kappa, k - 128 * z},
+                       GenRowsB<NT>{Crow + tk.crow, kt, k, -1.0f});
+    for (int y = 0; y < ny; ++y)
+        tc_product<NT>(st, (uint32_t)((nz + y) * NT), k, GenRowsA<NT>{Ccol + tk.ccol + (int64_t)128 * y * k, ks - 128 * y, k, k},
+                       GenFromTmem<NT>{st.tmem, kt, false});
     if (st.ok) {
-        const uint32_t trow = st.tmem + ((uint32_t)(32 * q) << 16);
+        const uint32_t tq = st.tmem + ((uint32_t)(32 * q) << 16);
         cx<float>* out = Stilde + tk.dst;
-        for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < kt; c0 += 16) {
-            float re[16], im[16];
-            tc::tmem_ld16(trow + (uint32_t)(NT + c0), re);
-            tc::tmem_ld16(trow + (uint32_t)(NT + c0 + RP), im);
-            if (row < ks)
+        for (int y = 0; y < ny; ++y) {
+            const int row = 128 * y + 32 * q + lane;
+            for (int c0 = half * (RP / 2); c0 < (half + 1) * (RP / 2) && c0 < kt; c0 += 16) {
+                float re[16], im[16];
+                tc::tmem_ld16(tq + (uint32_t)((nz + y) * NT + c0), re);
+                tc::tmem_ld16(tq + (uint32_t)((nz + y) * NT + c0 + RP), im);
+                if (row < ks)
 #pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    if (c0 + i < kt) out[(int64_t)(c0 + i) * ks + row] = cx<float>{re[i], im[i]};
+                    for (int i = 0; i < 16; ++i)
+                        if (c0 + i < kt) out[(int64_t)(c0 + i) * ks + row] = cx<float>{re[i], im[i]};
+            }
         }
     }
-    tc_end<NT>(st, err);
+    tc_end<NT>(st, err, ncols);
 }
 
 // ----------------------------------------------------------------------------- matvec kernels
@@ -3334,7 +3355,7 @@ void Num<T>::launch_stack_blocks(const std::vector<BlockRowTask>& tasks, int pas
         DBuf<BlockRowTask> d;
         upload_vec(d, tasks, s);
         size_t smem = sgen_smem_bytes<T>(m_);
-        if constexpr (NT > 0) smem = 128 + 2 * 128 * sizeof(float4) + TcTile<NT>::kOperandBytes;   // 128: alignment
+        if constexpr (NT > 0) smem = 128 + 2 * 256 * sizeof(float4) + TcTile<NT>::kOperandBytes;   // 128: alignment
         auto kern = k_stack_blocks<T, NT>;
         ensure_smem(reinterpret_cast<const void*>(kern), smem);
         ev_.begin(K_STACK_BLOCKS, s);
@@ -3375,7 +3396,14 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
         // recomputes it instead
         kstore_ = true;
         bool can_recompute = false;
-        if constexpr (std::is_same<T, float>::value) can_recompute = bp_.tensor_cores && k_ <= 128;
+        if constexpr (std::is_same<T, float>::value) {
+            // the recomputed rows run on the tensor cores only: k <= 128, or k <= 256 with leaf
+            // ranks of at most 64 (a TMEM budget of 4 NT columns, NT <= 128)
+            int32_t leaf_rank = 0;
+            for (int64_t a = 0; a < na_; ++a)
+                if (leaf_[a]) leaf_rank = std::max(leaf_rank, rR_[a]);
+            can_recompute = bp_.tensor_cores && (k_ <= 128 || (k_ <= 256 && leaf_rank <= 64));
+        }
         if (can_recompute && bp_.kb_store != 1) {
             // concurrent builds (the batch) decide one at a time, each against the free memory
             // less what the stores of the others still hold
@@ -3450,17 +3478,21 @@ void Num<T>::total_weights(int pass, cudaStream_t s) {
             stack.reserve(std::max<int64_t>(srow * kk, 1));
             if (!btasks.empty()) {
                 bool tcore = false;
-                if constexpr (std::is_same<T, float>::value) tcore = bp_.tensor_cores && kk <= 128;
+                if constexpr (std::is_same<T, float>::value) tcore = bp_.tensor_cores && kk <= 256;
                 if (tcore) {
-                    // tensor-core tiles by the rank of the R factor: N = 2 x (32 | 64 | 128)
-                    std::vector<BlockRowTask> cls[3];
+                    // tensor-core tiles by the rank of the R factor: N = 2 x (32 | 64 | 128); with
+                    // k > 128 (two M tiles, 4 NT TMEM columns) ranks above 64 stay on the CUDA cores
+                    std::vector<BlockRowTask> cls[3], simt;
                     for (const BlockRowTask& b : btasks) {
                         const int32_t ro = rR_[b.other];
-                        cls[ro <= 32 ? 0 : ro <= 64 ? 1 : 2].push_back(b);
+                        const int c = ro <= 32 ? 0 : ro <= 64 ? 1 : 2;
+                        if (c == 2 && kk > 128) simt.push_back(b);
+                        else cls[c].push_back(b);
                     }
                     launch_stack_blocks<64>(cls[0], pass, stack.p, s);
                     launch_stack_blocks<128>(cls[1], pass, stack.p, s);
                     launch_stack_blocks<256>(cls[2], pass, stack.p, s);
+                    launch_stack_blocks<0>(simt, pass, stack.p, s);
                 } else {
                     launch_stack_blocks<0>(btasks, pass, stack.p, s);
                 }
@@ -3698,7 +3730,7 @@ void Num<T>::launch_project_tc(const std::vector<ProjTask>& tasks, cudaStream_t 
     if constexpr (std::is_same<T, float>::value) {
         DBuf<ProjTask> d;
         upload_vec(d, tasks, s);
-        const size_t smem = 128 + 2 * 128 * sizeof(float4) + TcTile<NT>::kOperandBytes;
+        const size_t smem = 128 + 2 * 256 * sizeof(float4) + TcTile<NT>::kOperandBytes;
         auto kern = k_project_tc<NT>;
         ensure_smem(reinterpret_cast<const void*>(kern), smem);
         kern<<<(unsigned)tasks.size(), kThreads, smem, s>>>(d.p, st_.adm_t.p, st_.adm_s.p, st_.adm_c.p, tc_level_.p,
@@ -3759,12 +3791,14 @@ void Num<T>::project(cudaStream_t s) {
     St_.alloc(std::max<int64_t>(off, 1));
     if (nb == 0) return;
     if constexpr (std::is_same<T, float>::value) {
-        if (bp_.tensor_cores && k_ <= 128) {
-            // blocks whose clusters are not both leaves: tensor-core tiles by k_t
+        if (bp_.tensor_cores && k_ <= 256) {
+            // blocks whose clusters are not both leaves: tensor-core tiles by k_t (with k > 128
+            // only k_t <= 64, see total_weights)
             std::vector<ProjTask> rest, cls[3];
             for (const ProjTask& p : pt) {
-                if (p.leafpair || p.kt == 0 || p.ks == 0) rest.push_back(p);
-                else cls[p.kt <= 32 ? 0 : p.kt <= 64 ? 1 : 2].push_back(p);
+                const int c = p.kt <= 32 ? 0 : p.kt <= 64 ? 1 : 2;
+                if (p.leafpair || p.kt == 0 || p.ks == 0 || (c == 2 && k_ > 128)) rest.push_back(p);
+                else cls[c].push_back(p);
             }
             ev_.begin(K_PROJECT, s);
             launch_project_tc<64>(cls[0], s);

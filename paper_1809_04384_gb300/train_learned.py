@@ -5,8 +5,10 @@
 Data (every step on the GPU through the library):
 
 * meshes: ``synth.batch_meshes`` (spheres and ellipsoids of 1280-20480 triangles,
-  semi-axes U[0.5, 2], kappa U[4, 16]; the configurations the model is meant for),
-  leaf 32, eta1 10, eta2 1, eps 1e-4;
+  semi-axes U[0.5, 2], kappa U[4, 16]; the configurations the model is meant for) and
+  ``synth.directional_meshes`` (20480 triangles, kappa U[28, 40], whose admissible blocks
+  reach directional levels, as those of larger meshes at higher kappa do), leaf 32, eta1 10,
+  eta2 1, eps 1e-4;
 * features of every active pair (dh2_learned_features);
 * the x-side interpolation error of every pair at m = 3..8 (dh2_learned_probe);
 * the order each mesh needs: the smallest m in 4..7 whose built matrix has a
@@ -99,9 +101,10 @@ def mesh_data(v, f, kappa, m_ref, eps=EPS, nrows=64, seed=0):
     return out
 
 
-def collect(count, seed, m_ref, log=print):
+def collect(count, seed, m_ref, log=print, directional=0):
     data = []
-    for i, (v, f, kappa) in enumerate(synth.batch_meshes(count, seed)):
+    meshes = synth.batch_meshes(count, seed) + synth.directional_meshes(directional, seed + 7)
+    for i, (v, f, kappa) in enumerate(meshes):
         t0 = time.perf_counter()
         d = mesh_data(v, f, kappa, m_ref, seed=seed + 100 + i)
         if d["pairs"]:
@@ -222,6 +225,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--meshes", type=int, default=40)
     ap.add_argument("--val", type=int, default=6, help="meshes held out for validation")
+    ap.add_argument("--directional", type=int, default=8, help="directional meshes added to the training meshes")
     ap.add_argument("--seed", type=int, default=TRAIN_SEED)
     ap.add_argument("--m-ref", type=int, default=6)
     ap.add_argument("--steps", type=int, default=4000)
@@ -233,9 +237,13 @@ def main(argv=None):
 
     build()
     t0 = time.perf_counter()
-    data = collect(args.meshes, args.seed, args.m_ref, log=lambda s: print(s, file=sys.stderr))
+    data = collect(args.meshes, args.seed, args.m_ref, log=lambda s: print(s, file=sys.stderr),
+                   directional=args.directional)
     t_data = time.perf_counter() - t0
-    tr, va = data[: args.meshes - args.val], data[args.meshes - args.val:]
+    # validation: the last args.val meshes of the sphere/ellipsoid family; every directional
+    # mesh trains
+    tr = data[: args.meshes - args.val] + data[args.meshes:]
+    va = data[args.meshes - args.val: args.meshes]
     c = calibrate(tr, EPS)
     Xtr, Ttr = samples(tr, c, EPS)
     Xva, Tva = samples(va, c, EPS)
@@ -249,7 +257,8 @@ def main(argv=None):
     model = dh2.Model(params)
     model.save(args.out)
     print(json.dumps({
-        "samples_train": int(len(Xtr)), "samples_val": int(len(Xva)), "meshes": args.meshes, "m_ref": args.m_ref,
+        "samples_train": int(len(Xtr)), "samples_val": int(len(Xva)), "meshes": args.meshes,
+        "directional_meshes": args.directional, "m_ref": args.m_ref,
         "label_threshold_eps": c, "order_offset": delta, "data_s": round(t_data, 2), "train_s": round(t_train, 2), "steps": args.steps,
         "batch": args.batch, "loss_first": hist[0][1], "loss_last": hist[-1][1],
         "train": stats_tr, "val": stats_va,

@@ -137,3 +137,18 @@ def batch_meshes(count: int, seed: int):
         v, f = ellipsoid(level, axes)
         out.append((v, f, kappa))
     return out
+
+
+def directional_meshes(count: int, seed: int):
+    """Meshes whose admissible blocks reach directional levels at eta1 = 10: spheres and
+    ellipsoids of 20480 triangles (refinement level 5; ellipsoid with probability 1/2,
+    semi-axes U[0.8, 1.25]^3) with wave number U[28, 40].  Returns (vertices, triangles, kappa)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        is_ell = bool(rng.random() < 0.5)
+        axes = rng.uniform(0.8, 1.25, size=3) if is_ell else np.ones(3)
+        kappa = float(rng.uniform(28.0, 40.0))
+        v, f = ellipsoid(5, axes)
+        out.append((v, f, kappa))
+    return out

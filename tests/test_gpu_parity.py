@@ -227,7 +227,7 @@ def test_grouped_weight_qr_matches_oracle(name, precision):
     assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision != "fp64" else 0)
 
 
-@pytest.mark.parametrize("name", ["mixed1280", "dir1280"])
+@pytest.mark.parametrize("name", ["mixed1280", "dir1280", "dir320m6", "dir320m5"])
 def test_tensor_core_and_cuda_core_products_agree(name):
     """The coupling products of the total weights on the tcgen05 tensor cores (3xTF32) and
     on the CUDA cores (FP32) give the same ranks and, within the mixed tolerance, the same
@@ -283,7 +283,7 @@ def test_spectral_rank_rule_matches_oracle(precision):
     assert rel(y, rc.matvec(x)) <= max(tol["matvec_same_ranks"], 2 * rc.eps if precision != "fp64" else 0)
 
 
-@pytest.mark.parametrize("name", ["mixed1280", "dir1280"])
+@pytest.mark.parametrize("name", ["mixed1280", "dir1280", "dir320m6"])
 def test_recomputed_block_products_match_stored(name):
     """K_b = R_t S_b R_s^* recomputed on the tensor cores (column pass of leaf columns,
     leaf-pair projection through C_t S_b C_s^*) instead of kept: same ranks, same product,
