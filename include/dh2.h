@@ -341,7 +341,9 @@ dh2_status dh2_autotune(dh2_tree tree, double kappa, int32_t m, double eta, doub
  * to [3, 8] (the transfer matrices E of Eq. nested tie the orders of a cluster and
  * its sons, so one order serves the matrix; the training calibrates the order
  * unit's offset so that this reaches the order the training meshes need) and sizes
- * the truncated bases by the predicted ranks (1.25 x + 4 columns per pair).  The
+ * the truncated bases by the predicted ranks (1.25 x + 4 columns per pair) on the
+ * levels with D_l = {0}, the kind of pair the training meshes provide; directional
+ * pairs keep the structural bound.  The
  * SVD truncation still decides every rank: a pass in which one exceeds its cap is
  * redone with the structural bounds (dh2_matrix_info.rank_cap_retries).
  *

@@ -529,8 +529,13 @@ void choose(const Tree& tr, const Structure& st, const HostStructure& hs, Model&
         const double m = (double)y[(size_t)tc * kOut] * kMScale;
         const double rh = std::max(0.0, (double)y[(size_t)tc * kOut + 1] * kRankScale);
         mh[a] = std::isfinite(m) ? m : 8.0;
-        // slack over the estimate: a quarter plus four columns
-        caps[a] = std::isfinite(rh) ? (int32_t)std::ceil(1.25 * rh) + 4 : (1 << 30);
+        // slack over the estimate: a quarter plus four columns.  Only pairs of levels with
+        // D_l = {0}, the kind the training meshes provide, are capped; a directional pair keeps
+        // the structural bound (its ranks lie outside the training data, and one rank over its
+        // cap would send the whole pass back to the structural bounds)
+        const int32_t lv = hs.level[hs.a_t[a]];
+        const bool directional = hs.dir_off[lv + 1] - hs.dir_off[lv] > 1;
+        caps[a] = (std::isfinite(rh) && !directional) ? (int32_t)std::ceil(1.25 * rh) + 4 : (1 << 30);
     }
     // the order of the matrix: the 99th percentile (nearest rank, from below) of the
     // predicted orders, rounded down; the model's order unit carries the calibrated offset

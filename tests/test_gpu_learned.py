@@ -148,10 +148,12 @@ def _const_model(dh2, m, rank):
     return dh2.Model(p)
 
 
-@pytest.mark.parametrize("name", ["dir1280", "mixed1280"])
+@pytest.mark.parametrize("name", ["lowfreq1280", "mixed1280"])
 def test_learned_build_rank_caps_and_fallback(dh2, name):
     """Caps below the ranks redo the truncation with the structural bounds; caps above them
-    shrink the truncation buffers.  Either way ranks and product equal the plain build's."""
+    shrink the truncation buffers.  Either way ranks and product equal the plain build's.
+    (The caps apply to the pairs of levels with D_l = {0}; both cases have such pairs of
+    rank above 4.)"""
     import torch
 
     v, f, p, *_ = oracle_structure(name)
@@ -162,9 +164,11 @@ def test_learned_build_rank_caps_and_fallback(dh2, name):
     b0 = plain.info.truncation_bytes
     maxr = int(max(rr0.max(), rc0.max()))
     assert maxr > 4
-    # caps of 4 columns (estimate 0) are exceeded in both passes; caps of exactly the
-    # largest rank (estimate (maxr - 4) / 1.25) never are
-    for cap_rank, retries in ((0.0, 2), ((maxr - 4) / 1.25, 0)):
+    # caps of 4 columns (estimate 0) are exceeded in both passes (in the row pass only where
+    # the column pass is its mirror); caps of exactly the largest rank (estimate
+    # (maxr - 4) / 1.25) never are
+    passes = 1 if plain.get_info().symmetric else 2
+    for cap_rank, retries in ((0.0, passes), ((maxr - 4) / 1.25, 0)):
         model = _const_model(dh2, p["m"], cap_rank)
         mat = dh2.Matrix(tree, p["kappa"], 1, p["eta2"], p["eps"], eta1=p["eta1"], model=model)
         info = mat.get_info()
@@ -221,3 +225,46 @@ def test_trained_model_gain(dh2):
     assert abs(err(learned) - err(plain_m)) <= 1e-3 * err(plain_m)
     np.testing.assert_array_equal(learned.ranks()[0], plain_m.ranks()[0])
     assert learned.info.truncation_bytes < plain_m.info.truncation_bytes
+
+
+def test_learned_build_on_a_directional_mesh(dh2):
+    """A mesh outside the training set whose admissible blocks reach directional levels (the
+    20480-triangle sphere at kappa 36): the learned build caps only the pairs of levels with
+    D_l = {0}, so no rank exceeds its cap (no truncation pass is redone), its truncated bases
+    take less memory than a plain build at the same order, its ranks are the plain ones and
+    its product meets eps on sampled rows."""
+    import torch
+
+    import synth
+
+    v, f = synth.icosphere(5)
+    kappa, eps = 36.0, 1e-4
+    tree = dh2.Tree(v, f)
+    learned = dh2.Matrix(tree, kappa, 5, 1.0, eps, model=dh2.Model.load())
+    m = learned.info.m
+    plain_m = dh2.Matrix(tree, kappa, m, 1.0, eps)
+    # the structure has directional pairs
+    adm, _, active = learned.blocks()
+    assert any(learned.directions(l)[0] > 0 for l in range(learned.info.depth + 1))
+    assert learned.info.rank_cap_retries == 0
+    assert learned.info.truncation_bytes < plain_m.info.truncation_bytes
+    np.testing.assert_array_equal(learned.ranks()[0], plain_m.ranks()[0])
+    x = synth.random_vector(len(f), 1809_0001)
+    rows = np.sort(np.random.default_rng(1809_0002).choice(len(f), size=128, replace=False))
+    ref = dh2.dh2_dense_rows(tree.handle, kappa, rows, torch.from_numpy(x).cuda())
+    y = learned.matvec(torch.from_numpy(x).to(torch.complex64).cuda()).cpu().numpy()[rows]
+    assert rel(y, ref) <= eps
+
+
+def test_learned_caps_leave_directional_pairs_alone(dh2):
+    """On a block tree whose pairs of rank above 4 all lie on directional levels (dir1280),
+    caps of 4 columns are never exceeded: directional pairs keep the structural bound."""
+    import torch
+
+    v, f, p, *_ = oracle_structure("dir1280")
+    tree, plain = gpu_matrix("dir1280", "mixed")
+    mat = dh2.Matrix(tree, p["kappa"], 1, p["eta2"], p["eps"], eta1=p["eta1"], model=_const_model(dh2, p["m"], 0.0))
+    assert mat.get_info().rank_cap_retries == 0
+    np.testing.assert_array_equal(mat.ranks()[0], plain.ranks()[0])
+    x = torch.from_numpy(x_vector(plain.n)).to(torch.complex64).cuda()
+    assert rel(mat.matvec(x).cpu().numpy(), plain.matvec(x).cpu().numpy()) <= 1e-6
