@@ -773,6 +773,13 @@ def roofline_obj(name, timing, work, peaks, nsteps, traffic=None):
         return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "peak_source": peaks["source"] + " copy bandwidth",
                 "algorithmic_bytes_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
+    if kind == "tc_bf16":   # BF16 tensor-core products (the integer-digit Gram): the measured BF16 peak
+        achieved = per_launch_work / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks["bf16"]
+        return {"kernel": name, "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_source": peaks["source"] + " dense BF16 (cuBLAS, burst)",
+                "algorithmic_flop_per_launch": per_launch_work, "avg_launch_ms": per_launch_ms}
     # FP32 / FP64 SIMT arithmetic: peak from unit counts (FMA per SM per clock) and the maximum SM clock
     lanes = {"flop32": 128, "flop64": 2}[kind]
     sms = peaks.get("sms", 152)

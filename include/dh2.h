@@ -133,7 +133,13 @@ typedef struct {
                                Lagrange polynomials, W_sc = int phi_j d/dn_y [exp(i kappa <y, c>)
                                L_{s,mu}(y)], and separate basis weights for V and W (Section 3.2 with
                                W != V).  The matrix is not symmetric: both passes are computed */
-    int32_t reserved3;      /* must be 0 */
+    int32_t gram_tc;        /* DH2_MIXED with qr_fp64 = 1: 1 (default) = the Gram matrices Z^* Z of
+                               weight stacks wider than 32 columns from exact integer products on
+                               the tensor cores: each real column, scaled by a power of two, is
+                               split into 8 signed base-64 digits (BF16), the digit products of
+                               one weight summed exactly in FP32 (at most 2048 rows per sum) and
+                               combined in FP64; error at most about 2^-43 max|z_m| max|z_n| per
+                               row.  0 = FP64 FMAs on the CUDA cores */
 } dh2_options;
 
 typedef struct {
@@ -162,7 +168,8 @@ typedef struct {
     int64_t kernel_launches[16]; /* number of timed launches per kernel */
     double kernel_work[16]; /* algorithmic work of each kernel in one build (build kernels) or
                                one matvec (matvec kernels), in the unit of kernel_work_kind */
-    int32_t kernel_work_kind[16]; /* 0 none, 1 FP32 flop, 2 FP64 flop, 3 bytes moved */
+    int32_t kernel_work_kind[16]; /* 0 none, 1 FP32 flop, 2 FP64 flop, 3 bytes moved,
+                                   4 BF16 tensor-core flop */
     int32_t learned_m;      /* the order the learned model chose (0 for a plain build) */
     int32_t rank_cap_retries; /* truncation passes redone because a rank exceeded its learned cap */
     int64_t truncation_bytes; /* device bytes of the truncated bases of both passes as allocated
@@ -291,6 +298,20 @@ dh2_status dh2_matvec_host(dh2_matrix mat, const double* x_host, double* y_host,
  * pointers, count < 0, a point-mode tree, a row out of range or kappa < 0; DH2_ECUDA. */
 dh2_status dh2_dense_rows(dh2_tree tree, double kappa, const int32_t* rows, int32_t count, const double* x,
                           double* out, void* stream);
+
+/* The Gram matrix G = Z^* Z of a complex FP32 matrix, formed as the weight factorisations of
+ * the mixed form form it (the first step of their Cholesky QR, Section 3.2's QR of the stacked
+ * weights): the real and imaginary parts of Z in FP64 FMAs (gram_tc = 0), or, for more than
+ * 32 columns with gram_tc = 1, from exact integer digit products on the tensor cores (see
+ * dh2_options.gram_tc), in both cases summed over row groups in FP64.  Exposed so that the
+ * product can be checked on its own.
+ * z: DEVICE complex64 [rows x ld], row-major (column j of row i at i * ld + j), read only;
+ * g: DEVICE complex128 [cols x cols], row-major, written (both triangles; G(i, j) =
+ * conj(G(j, i)) exactly).  Blocks until done.  Errors: DH2_EINVAL for NULL pointers, rows
+ * outside [1, 2^31), cols outside [1, 512], ld < cols or gram_tc not 0/1; DH2_ENUMERIC if z
+ * holds a non-finite value (g is then unspecified); DH2_ETIMEOUT if a bounded tensor-core
+ * wait gives up; DH2_ENOMEM; DH2_ECUDA. */
+dh2_status dh2_gram(const void* z, int64_t rows, int32_t cols, int64_t ld, int32_t gram_tc, void* g, void* stream);
 
 /* Turns per-launch CUDA-event timing of the matvec kernels on (1) or off (0);
  * the sums are reported in dh2_matrix_info.kernel_ms / kernel_launches (matvec

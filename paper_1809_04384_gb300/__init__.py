@@ -41,7 +41,7 @@ class dh2_options(C.Structure):
                 ("workspace_bytes", C.c_int64), ("tensor_cores", C.c_int32), ("kb_store", C.c_int32),
                 ("learned", C.c_int32), ("svd_fp64", C.c_int32), ("model", C.c_void_p),
                 ("qr_tpc", C.c_int32 * 3), ("fault", C.c_int32), ("symmetry", C.c_int32), ("direct", C.c_int32),
-                ("layer", C.c_int32), ("reserved3", C.c_int32)]
+                ("layer", C.c_int32), ("gram_tc", C.c_int32)]
 
 
 class dh2_tree_info(C.Structure):
@@ -104,6 +104,7 @@ _SIGS = {
     "dh2_model_train_step": (C.c_int, [_P, _P, _P, C.c_int64, C.c_float, _P, _P]),
     "dh2_free_model": (None, [_P]),
     "dh2_dense_rows": (C.c_int, [_P, C.c_double, _P, C.c_int32, _P, _P, _P]),
+    "dh2_gram": (C.c_int, [_P, C.c_int64, C.c_int32, C.c_int64, C.c_int32, _P, _P]),
     "dh2_autotune": (C.c_int, [_P, C.c_double, C.c_int32, C.c_double, C.c_double, C.POINTER(dh2_options), C.c_int32,
                                _P, C.POINTER(dh2_options), C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "dh2_learned_features": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(dh2_options), _P, _P, C.c_int64,
@@ -284,6 +285,21 @@ def dh2_dense_rows(tree, kappa, rows, x, stream=None):
     return out
 
 
+def dh2_gram(z, gram_tc=1, stream=None):
+    """G = Z^* Z in FP64 (complex128 CUDA tensor) of a complex64 CUDA matrix z (rows x cols,
+    row pitch z.stride(0)), as the weight factorisations form it."""
+    import torch
+    if not (z.is_cuda and z.dtype == torch.complex64 and z.dim() == 2 and z.stride(1) == 1):
+        raise TypeError("z must be a complex64 CUDA matrix with unit column stride")
+    rows, cols = z.shape
+    g = torch.empty((cols, cols), dtype=torch.complex128, device=z.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(z.device)
+    _check(lib().dh2_gram(C.c_void_p(z.data_ptr()), rows, cols, z.stride(0), int(gram_tc), C.c_void_p(g.data_ptr()),
+                          _stream(stream)))
+    return g
+
+
 def dh2_release_cached():
     """Hands the freed device memory the library's pool keeps back to the driver."""
     _check(lib().dh2_release_cached())
@@ -338,11 +354,12 @@ class Matrix:
 
     def __init__(self, tree: Tree, kappa, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
                  qr_fp64=1, svd_fp64=1, workspace_bytes=0, qr_group_rows=0, tensor_cores=1, kb_store=0, model=None,
-                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, symmetry=1, direct=0, layer=DH2_SINGLE_LAYER, stream=None):
+                 qr_tpc=(0, 0, 0), fault=DH2_FAULT_NONE, symmetry=1, direct=0, layer=DH2_SINGLE_LAYER, gram_tc=1,
+                 stream=None):
         opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_fp64=qr_fp64,
                        svd_fp64=svd_fp64, qr_group_rows=qr_group_rows, workspace_bytes=workspace_bytes,
                        tensor_cores=tensor_cores, kb_store=kb_store, qr_tpc=qr_tpc, fault=fault, symmetry=symmetry,
-                       direct=direct, layer=layer)
+                       direct=direct, layer=layer, gram_tc=gram_tc)
         if model is not None:
             opts.learned = 1
             opts.model = model.handle
@@ -388,9 +405,9 @@ class Matrix:
         return out
 
     def kernel_work(self):
-        """{kernel name: (kind, amount)}: kind 'flop32' | 'flop64' | 'byte'."""
+        """{kernel name: (kind, amount)}: kind 'flop32' | 'flop64' | 'byte' | 'tc_bf16'."""
         info = self.get_info()
-        kinds = {1: "flop32", 2: "flop64", 3: "byte"}
+        kinds = {1: "flop32", 2: "flop64", 3: "byte", 4: "tc_bf16"}
         out = {}
         for i in range(16):
             name = lib().dh2_kernel_name(i)
@@ -457,10 +474,12 @@ class Matrix:
 
 
 def build_batch(trees, kappas, m, eta, eps, precision=DH2_MIXED, eta1=10.0, rank_rule=DH2_RANK_BLOCKREL,
-                nstreams=0, model=None, qr_tpc=(0, 0, 0), qr_group_rows=0, qr_fp64=1, svd_fp64=1, symmetry=1):
+                nstreams=0, model=None, qr_tpc=(0, 0, 0), qr_group_rows=0, qr_fp64=1, svd_fp64=1, symmetry=1,
+                gram_tc=1):
     """Concurrent builds (dh2_build_dh2_batch) wrapped as Matrix objects, in order."""
     opts = options(eta1=eta1, leaf_max=32, precision=precision, rank_rule=rank_rule, qr_tpc=qr_tpc,
-                   qr_group_rows=qr_group_rows, qr_fp64=qr_fp64, svd_fp64=svd_fp64, symmetry=symmetry)
+                   qr_group_rows=qr_group_rows, qr_fp64=qr_fp64, svd_fp64=svd_fp64, symmetry=symmetry,
+                   gram_tc=gram_tc)
     if model is not None:
         opts.learned = 1
         opts.model = model.handle

@@ -111,7 +111,7 @@ void check_build_args(dh2_tree tree, double kappa, int32_t m, double eta, double
     if (o.symmetry != 0 && o.symmetry != 1) throw Error{DH2_EINVAL, f + ": symmetry must be 0 or 1"};
     if (o.direct != 0 && o.direct != 1) throw Error{DH2_EINVAL, f + ": direct must be 0 or 1"};
     if (o.layer != DH2_SINGLE_LAYER && o.layer != DH2_DOUBLE_LAYER) throw Error{DH2_EINVAL, f + ": bad layer"};
-    if (o.reserved3 != 0) throw Error{DH2_EINVAL, f + ": reserved3 must be 0"};
+    if (o.gram_tc != 0 && o.gram_tc != 1) throw Error{DH2_EINVAL, f + ": gram_tc must be 0 or 1"};
     static const int width[3] = {32, 64, 128};
     for (int c = 0; c < 3; ++c) {
         const int v = o.qr_tpc[c];
@@ -162,7 +162,7 @@ dh2_matrix build_matrix(dh2_tree tree, double kappa, int32_t m, double eta, doub
     mat->depth = mat->tr.depth;
     mat->bp = BuildParams{kappa, eta, eps, m, o.precision, o.rank_rule, o.qr_fp64, o.qr_group_rows,
                           o.workspace_bytes, o.tensor_cores, o.kb_store, {o.qr_tpc[0], o.qr_tpc[1], o.qr_tpc[2]},
-                          {}, o.svd_fp64, o.fault, o.symmetry, o.direct, o.layer};
+                          {}, o.svd_fp64, o.fault, o.symmetry, o.direct, o.layer, o.gram_tc};
     if (o.learned) {
         int32_t ml = m;
         learned::choose(mat->tr, mat->st, mat->hs, o.model->md, s, &ml, mat->bp.rank_cap);
@@ -317,6 +317,7 @@ dh2_status dh2_options_default(dh2_options* opt) {
     opt->rank_rule = DH2_RANK_BLOCKREL;
     opt->qr_fp64 = 1;
     opt->svd_fp64 = 1;
+    opt->gram_tc = 1;
     opt->fault = DH2_FAULT_NONE;
     opt->symmetry = 1;
     opt->qr_group_rows = 0;
@@ -560,6 +561,19 @@ dh2_status dh2_dense_rows(dh2_tree tree, double kappa, const int32_t* rows, int3
         cudaStream_t s = as_stream(stream);
         AllocScope scope(s);
         dense_rows(tree->tr, kappa, rows, count, x, out, s);
+    });
+}
+
+dh2_status dh2_gram(const void* z, int64_t rows, int32_t cols, int64_t ld, int32_t gram_tc, void* g, void* stream) {
+    return guarded([&] {
+        DH2_REQUIRE(z != nullptr && g != nullptr, "dh2_gram: NULL");
+        DH2_REQUIRE(rows >= 1 && rows <= INT32_MAX, "dh2_gram: rows must be in [1, 2^31)");
+        DH2_REQUIRE(cols >= 1 && cols <= 512, "dh2_gram: cols must be in [1, 512]");
+        DH2_REQUIRE(ld >= cols && ld <= INT32_MAX, "dh2_gram: ld must be in [cols, 2^31)");
+        DH2_REQUIRE(gram_tc == 0 || gram_tc == 1, "dh2_gram: gram_tc must be 0 or 1");
+        cudaStream_t s = as_stream(stream);
+        AllocScope scope(s);
+        gram_matrix(z, rows, cols, ld, gram_tc != 0, g, s);
     });
 }
 

@@ -174,5 +174,8 @@ void prepare_quadrature(Tree& tr, cudaStream_t s);
 // out_host[i] = (G x)[rows_host[i]] in FP64 (dense.cu); x_dev complex128, original order
 void dense_rows(const Tree& tr, double kappa, const int32_t* rows_host, int32_t count, const double* x_dev,
                 double* out_host, cudaStream_t s);
+// g = Z^* Z (cols x cols complex FP64) of a complex FP32 matrix (numeric.cu); tc: tensor-core
+// digit products for more than 32 columns
+void gram_matrix(const void* z, int64_t rows, int32_t cols, int64_t ld, bool tc, void* g, cudaStream_t s);
 
 }  // namespace dh2

@@ -1188,6 +1188,7 @@ struct GramItem {
     int64_t out;              // cx<double> offset of this partial tile (TB x TB, row-major)
     int32_t ld, ncols, r0, r1;
     int32_t i0, j0;
+    int32_t half, pad;        // k_gram_slices: the real (0) or imaginary (1) parts of columns j0..
 };
 
 // TB = 16 * BS: each of up to 256 threads accumulates a BS x BS block of the tile in
@@ -1278,6 +1279,255 @@ __global__ void __launch_bounds__(256) k_gram64(const GramItem* __restrict__ ite
 #pragma unroll
             for (int q = 0; q < BS; ++q) O[(bi * BS + p) * TB + bj * BS + q] = acc[p][q];
     }
+}
+
+// ----------------------------------------------------------------------------- Gram from integer slices
+
+// The Gram tile G = Z_I^* Z_J of an FP32 stack (I, J: 64 complex columns each) from exact
+// integer products on the BF16 tensor cores.  Each real column m of the tile (the real and
+// the imaginary parts of a complex column are two real columns) is scaled by 2^-e_m, e_m the
+// exponent of its largest magnitude over the CTA's rows, and written as 8 signed base-64
+// digits, x 2^-e_m = sum_i d_i 2^(1 - 6 i) + rest, |d_i| <= 32, |rest| <= 2^-48: each digit is
+// the rounded remainder of the previous one times 64, so every step is exact in FP32 and every
+// digit exact in BF16.  A dot product of two columns is then sum_{i,j} (d_i . d'_j) 2^(2 - 6(i+j));
+// the digit products with one i + j = g share that scale and are summed in one FP32 TMEM
+// accumulator, whose partial sums are integers of magnitude at most 8 * 32 * 32 * rows <= 2^24
+// for rows <= 2048, so the tensor cores add them exactly.  Products with i + j > 9 are dropped;
+// with the rests this leaves an error of at most about 2^-43 max|z_m| max|z_n| per row (an FP64
+// accumulation: 2^-53 |z_m| |z_n|), far below the FP32 rounding of the stack's own entries.
+//
+// The real product is split by the column part of J: a CTA with half = 0 forms D = Y_I^T Re Z_J
+// and one with half = 1 forms D = Y_I^T Im Z_J, Y_I = [Re Z_I, Im Z_I] (M = 128, N = 64), and
+// each writes one complex partial tile: half 0 (Re G, Im G) = (D_top, -D_bottom), half 1
+// (D_bottom, D_top).  The 8 group accumulators take all 512 TMEM columns (one CTA per SM); the
+// digits of 32 rows are staged per step in two shared-memory buffers, so the digits of the next
+// rows are formed while the tensor cores work on the current ones.
+namespace gram_tc {
+constexpr int kDigits = 8;
+constexpr int kMaxRows = 2048;
+constexpr int kSub = 32;
+constexpr int kABytes = kDigits * 128 * kSub * 2;   // digits of Y_I, 128 rows x kSub
+constexpr int kBBytes = kDigits * 64 * kSub * 2;    // digits of one part of Z_J, 64 rows x kSub
+constexpr int kHeader = 2048;
+constexpr size_t kSmemBytes = 1024 + kHeader + 2 * (size_t)(kABytes + kBBytes);   // 1024: alignment
+
+// digits of 8 consecutive rows (y = x 2^(5 - e), |y| <= 32) of operand row r, stored as one
+// 16-byte core-matrix row per digit (K-major layout of an operand with R rows)
+template <int R>
+__device__ __forceinline__ void store_digits(float (&y)[8], unsigned char* buf, int r, int q) {
+    constexpr float kRound = 12582912.0f;   // 1.5 * 2^23: (y + kRound) - kRound = rint(y), |y| < 2^22
+    constexpr int kDigitBytes = R * kSub * 2;
+    const int off = tc::kmaj_off16(r, 8 * q, R) * 2;
+#pragma unroll
+    for (int d = 0; d < kDigits; ++d) {
+        uint32_t bits[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const float s = __fsub_rn(__fadd_rn(y[t], kRound), kRound);
+            y[t] = __fmul_rn(__fsub_rn(y[t], s), 64.0f);
+            bits[t] = __float_as_uint(s);   // an integer of at most 6 bits: the low half is zero
+        }
+        uint4 v;
+        v.x = __byte_perm(bits[0], bits[1], 0x7632);
+        v.y = __byte_perm(bits[2], bits[3], 0x7632);
+        v.z = __byte_perm(bits[4], bits[5], 0x7632);
+        v.w = __byte_perm(bits[6], bits[7], 0x7632);
+        *reinterpret_cast<uint4*>(buf + d * kDigitBytes + off) = v;
+    }
+}
+
+// FP32 -> FP64 with e added to the exponent, by integer operations (f normal or zero)
+__device__ __forceinline__ double widen(float f, int e) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t E = (b >> 23) & 0xFFu;
+    if (E == 0) return 0.0;
+    const uint32_t hi = (b & 0x80000000u) | ((E + 896u + (uint32_t)e) << 20) | ((b >> 3) & 0xFFFFFu);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+}  // namespace gram_tc
+
+__global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restrict__ items,
+                                                        const cx<float>* __restrict__ src,
+                                                        cx<double>* __restrict__ part, unsigned* err) {
+    using namespace gram_tc;
+    extern __shared__ unsigned char g_smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(g_smem_raw) + 1023) &
+                                                           ~static_cast<uintptr_t>(1023));
+    uint32_t* colbits = reinterpret_cast<uint32_t*>(base);   // 192: column maxima, then exponents
+    int* ex = reinterpret_cast<int*>(base);
+    float* scl = reinterpret_cast<float*>(base + 768);        // 192: 2^(5 - e)
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 1536);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(base + 1552);
+    unsigned char* ops = base + kHeader;
+
+    const GramItem it = items[blockIdx.x];
+    const bool diag = it.i0 == it.j0;
+    const int h = it.half;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const cx<float>* S = src + it.src;
+    if (tid < 192) colbits[tid] = 0u;
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    // column scales from the largest magnitude of each real column over the CTA's rows
+    const int p = tid & 63, q = tid >> 6;
+    const bool colA = it.i0 + p < it.ncols, colB = !diag && it.j0 + p < it.ncols;
+    {
+        float ar = 0.0f, ai = 0.0f, bm = 0.0f;
+        bool bad = false;
+        for (int r = it.r0 + q; r < it.r1; r += 4) {
+            const cx<float>* row = S + (int64_t)r * it.ld;
+            if (colA) {
+                const cx<float> u = row[it.i0 + p];
+                bad |= !isfinite(u.x) || !isfinite(u.y);
+                ar = fmaxf(ar, fabsf(u.x));
+                ai = fmaxf(ai, fabsf(u.y));
+            }
+            if (colB) {
+                const cx<float> u = row[it.j0 + p];
+                const float v = h ? u.y : u.x;
+                bad |= !isfinite(v);
+                bm = fmaxf(bm, fabsf(v));
+            }
+        }
+        if (bad) raise_err(err, ERR_TSQR_INPUT);
+        atomicMax(&colbits[p], __float_as_uint(ar));
+        atomicMax(&colbits[64 + p], __float_as_uint(ai));
+        if (!diag) atomicMax(&colbits[128 + p], __float_as_uint(bm));
+    }
+    __syncthreads();
+    if (tid < 192) {
+        const int E = (int)(colbits[tid] >> 23);   // biased exponent of the maximum (>= 0)
+        int e = E - 126;                           // maximum < 2^e
+        float sc = 0.0f;
+        if (E == 0 || E == 255 || e < -100) e = 0;   // zero, negligible or non-finite (flagged) column
+        else sc = __int_as_float((127 + 5 - e) << 23);
+        ex[tid] = e;
+        scl[tid] = sc;
+    }
+    __syncthreads();
+
+    const int nsub = (it.r1 - it.r0 + kSub - 1) / kSub;
+    const uint32_t idesc = tc::idesc_bf16(128, 64);
+    bool ok = true;
+    int committed = -1;
+    for (int sc = 0; sc < nsub; ++sc) {
+        const int b = sc & 1;
+        if (sc >= 2) {   // the tensor cores are done with this buffer (step sc - 2)
+            ok = __syncthreads_and(tc::mbar_wait(&mbar[b], ((sc - 2) >> 1) & 1, kTcWaitPolls));
+            if (!ok) break;
+        }
+        unsigned char* Ab = ops + b * (kABytes + kBBytes);
+        unsigned char* Bb = Ab + kABytes;
+        const int row0 = it.r0 + sc * kSub + 8 * q;
+        {
+            float re[8], im[8];
+            const float sr = scl[p], si = scl[64 + p];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                cx<float> u{0.0f, 0.0f};
+                if (colA && row0 + t < it.r1) u = S[(int64_t)(row0 + t) * it.ld + it.i0 + p];
+                re[t] = u.x * sr;
+                im[t] = u.y * si;
+            }
+            store_digits<128>(re, Ab, p, q);
+            store_digits<128>(im, Ab, 64 + p, q);
+        }
+        if (!diag) {
+            float v[8];
+            const float sb = scl[128 + p];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                float x = 0.0f;
+                if (colB && row0 + t < it.r1) {
+                    const cx<float> u = S[(int64_t)(row0 + t) * it.ld + it.j0 + p];
+                    x = h ? u.y : u.x;
+                }
+                v[t] = x * sb;
+            }
+            store_digits<64>(v, Bb, p, q);
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t a0 = tc::smem_u32(Ab), b0 = tc::smem_u32(Bb);
+            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (64 / 8) * 128, sbo = 128;
+            constexpr uint32_t dA = 128 * kSub * 2, dB = 64 * kSub * 2;
+#pragma unroll 1
+            for (int g = 2; g <= kDigits + 1; ++g) {
+                const int ilo = max(1, g - kDigits), ihi = min(kDigits, g - 1);
+#pragma unroll 1
+                for (int i = ilo; i <= ihi; ++i) {
+                    const int j = g - i;
+#pragma unroll
+                    for (int ks = 0; ks < kSub / 16; ++ks) {
+                        const uint64_t da = tc::sdesc(a0 + (i - 1) * dA + ks * 2 * lboA, lboA, sbo);
+                        const uint64_t db =
+                            diag ? tc::sdesc(a0 + (j - 1) * dA + h * 8 * 128 + ks * 2 * lboA, lboA, sbo)
+                                 : tc::sdesc(b0 + (j - 1) * dB + ks * 2 * lboB, lboB, sbo);
+                        tc::mma_bf16(tmem + (uint32_t)((g - 2) * 64), da, db, idesc, sc > 0 || i > ilo || ks > 0);
+                    }
+                }
+            }
+            tc::commit(&mbar[b]);
+        }
+        committed = sc;
+    }
+    if (ok && committed >= 0)
+        ok = __syncthreads_and(tc::mbar_wait(&mbar[committed & 1], (committed >> 1) & 1, kTcWaitPolls));
+    tc::fence_after_sync();
+
+    if (ok && committed >= 0) {
+        // warp (quarter qd, column half ch): TMEM lane m = row m of D, columns 32 ch .. 32 ch + 31
+        const int qd = warp & 3, ch = warp >> 2;
+        const int m = 32 * qd + lane;
+        const uint32_t tq = tmem + ((uint32_t)(32 * qd) << 16);
+        float hi[32], lo[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.0f;
+#pragma unroll 1
+        for (int g = 2; g <= kDigits + 1; ++g) {
+            float v0[16], v1[16];
+            tc::tmem_ld16(tq + (uint32_t)((g - 2) * 64 + 32 * ch), v0);
+            tc::tmem_ld16(tq + (uint32_t)((g - 2) * 64 + 32 * ch + 16), v1);
+            const float w = __int_as_float((127 + 2 - 6 * g) << 23);   // 2^(2 - 6 g)
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const float x = (j < 16 ? v0[j] : v1[j - 16]) * w;   // exact
+                const float s = __fadd_rn(hi[j], x);                 // two-sum: hi + x = s + e
+                const float bb = __fsub_rn(s, hi[j]);
+                const float e = __fadd_rn(__fsub_rn(hi[j], __fsub_rn(s, bb)), __fsub_rn(x, bb));
+                hi[j] = s;
+                lo[j] = __fadd_rn(lo[j], e);
+            }
+        }
+        const int em = ex[m];
+        const int i = m & 63;
+        const bool top = m < 64;
+        const int comp = (h == 0) != top ? 1 : 0;
+        const double sgn = (h == 0 && !top) ? -1.0 : 1.0;
+        double* o = reinterpret_cast<double*>(part + it.out + (int64_t)i * 64 + 32 * ch) + comp;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int e = em + ex[(diag ? 64 * h : 128) + 32 * ch + j];
+            o[2 * j] = sgn * (widen(hi[j], e) + widen(lo[j], e));
+        }
+    }
+    if (!ok) {
+        if (tid == 0) raise_err(err, ERR_TC_TIMEOUT);
+        if (committed >= 0) tc::mbar_wait(&mbar[committed & 1], (committed >> 1) & 1, kTcWaitPolls);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 512);
 }
 
 // One stack's Gram assembly and pivoted Cholesky (one CTA).
@@ -1414,6 +1664,14 @@ __global__ void __launch_bounds__(256) k_pchol64(const CholTask* __restrict__ ta
     }
     // rows past the numerical rank are zero
     for (int idx = j * c + threadIdx.x; idx < tk.rout * c; idx += blockDim.x) R[idx] = zero<TDst>();
+}
+
+// G (c x c) from its upper triangle: G(i, j) = conj(G(j, i)) below the diagonal
+__global__ void k_gram_full(const cx<double>* __restrict__ up, int c, cx<double>* __restrict__ g) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)c * c) return;
+    const int i = (int)(idx / c), j = (int)(idx - (int64_t)i * c);
+    g[idx] = i <= j ? up[idx] : conj(up[(int64_t)j * c + i]);
 }
 
 template <class TQ, int RPL>
@@ -2599,6 +2857,9 @@ private:
     bool chol_qr() const {
         return std::is_same<T, double>::value ? bp_.qr_fp64 != 2 : bp_.qr_fp64 == 1;
     }
+    // Gram tiles of wide FP32 stacks from exact integer digit products on the tensor cores
+    bool gram_slices() const { return std::is_same<T, float>::value && chol_qr() && bp_.gram_tc != 0; }
+    double gram_mma_flops_ = 0.0;   // tensor-core work of k_gram_slices in this build
     // algorithmic flops of one weight factorisation of a stack of `rows` x `cols`
     void qr_work(int64_t rows, int32_t cols) {
         if (rows <= cols) return;   // copied: R = Z
@@ -3136,12 +3397,20 @@ void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>*
 // stack's upper tile pairs are cut into row groups so that the launch has enough CTAs; the
 // partial tiles of a stack are summed in group order by the Cholesky kernel (no atomics,
 // deterministic).  Stacks are processed in chunks whose scratch stays under 1 GiB.
+// Gram matrices (FP64 partial tiles per row group) and pivoted Cholesky factors of the
+// stacks.  slices: stacks of more than 32 FP32 columns take their Gram tiles from
+// k_gram_slices (exact integer products on the tensor cores, two CTAs per tile and row
+// group of at most 2048 rows); otherwise k_gram64 forms them with FP64 FMAs.  *mma_flops
+// gains the tensor-core work of k_gram_slices.
 template <class TS, class TD>
 void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>* dst, cudaStream_t s, EventLog& ev,
-                    unsigned* err) {
+                    unsigned* err, bool slices = false, double* mma_flops = nullptr,
+                    cx<double>* gram_out = nullptr) {
     constexpr int64_t kScratchElems = (int64_t(1) << 30) / (int64_t)sizeof(cx<double>);
     for (int cls = 0; cls < 2; ++cls) {
         const int TB = cls == 0 ? 32 : 64;
+        const bool tcg = slices && cls == 1 && std::is_same<TS, float>::value;
+        const int halves = tcg ? 2 : 1;
         std::vector<QRTask> ts;
         for (const QRTask& t : tasks)
             if ((t.ncols <= 32) == (cls == 0) && t.nrows > 0) ts.push_back(t);
@@ -3151,9 +3420,16 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
             const int nt = (t.ncols + TB - 1) / TB;
             units += (double)nt * (nt + 1) / 2 * t.nrows;
         }
-        const int64_t want_items = 152 * 12;
-        int64_t grows = std::max<int64_t>(128, (int64_t)std::ceil(units / want_items));
-        grows = (grows + 15) / 16 * 16;
+        int64_t grows;
+        if (tcg) {   // one CTA per SM: about four waves of CTAs, at most 2048 rows each
+            grows = std::min<int64_t>(gram_tc::kMaxRows,
+                                      std::max<int64_t>(256, (int64_t)std::ceil(units / (152 * 2))));
+            grows = (grows + 31) / 32 * 32;
+        } else {
+            const int64_t want_items = 152 * 12;
+            grows = std::max<int64_t>(128, (int64_t)std::ceil(units / want_items));
+            grows = (grows + 15) / 16 * 16;
+        }
         size_t i0 = 0;
         while (i0 < ts.size()) {
             std::vector<GramItem> items;
@@ -3165,16 +3441,23 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                 const int nt = (t.ncols + TB - 1) / TB;
                 const int ng = (int)((t.nrows + grows - 1) / grows);
                 const int64_t tp = (int64_t)nt * (nt + 1) / 2;
-                const int64_t need = tp * ng * TB * TB + (int64_t)t.ncols * t.ncols;
+                const int64_t need = tp * ng * halves * TB * TB + (int64_t)t.ncols * t.ncols;
                 if (i1 > i0 && pel + gel + need > kScratchElems) break;
-                CholTask c{pel, gel, t.dst, t.ncols, t.rout, nt, ng};
+                CholTask c{pel, gel, t.dst, t.ncols, t.rout, nt, ng * halves};
                 for (int I = 0; I < nt; ++I)
                     for (int J = I; J < nt; ++J)
-                        for (int g = 0; g < ng; ++g) {
-                            const int32_t r0 = (int32_t)(g * grows), r1 = (int32_t)std::min<int64_t>(t.nrows, r0 + grows);
-                            items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB});
-                            pel += (int64_t)TB * TB;
-                        }
+                        for (int g = 0; g < ng; ++g)
+                            for (int hf = 0; hf < halves; ++hf) {
+                                const int32_t r0 = (int32_t)(g * grows);
+                                const int32_t r1 = (int32_t)std::min<int64_t>(t.nrows, r0 + grows);
+                                items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB, hf, 0});
+                                pel += (int64_t)TB * TB;
+                                if (tcg && mma_flops) {   // 36 digit products of 128 x 64 real columns
+                                    const double mi = 2.0 * std::min(TB, t.ncols - I * TB);
+                                    const double nj = std::min(TB, t.ncols - J * TB);
+                                    *mma_flops += 2.0 * 36.0 * mi * nj * (r1 - r0);
+                                }
+                            }
                 gel += (int64_t)t.ncols * t.ncols;
                 ct.push_back(c);
             }
@@ -3185,12 +3468,18 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
             upload_vec(dc, ct, s);
             DBuf<cx<double>> scr((size_t)(pel + gel));
             ev.begin(cls == 0 ? K_TSQR_NARROW : K_TSQR, s);
-            if (cls == 0)
+            if (cls == 0) {
                 k_gram64<2, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
-            else
+            } else if (tcg) {
+                if constexpr (std::is_same<TS, float>::value) {
+                    ensure_smem(reinterpret_cast<const void*>(k_gram_slices), gram_tc::kSmemBytes);
+                    k_gram_slices<<<(unsigned)items.size(), 256, gram_tc::kSmemBytes, s>>>(di.p, src, scr.p, err);
+                }
+            } else {
                 k_gram64<4, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
+            }
             ev.end(s);
-            DH2_CHECK_LAUNCH("k_gram64");
+            DH2_CHECK_LAUNCH(tcg ? "k_gram_slices" : "k_gram64");
             ev.begin(K_WQR_CHOL, s);
             if (cls == 0)
                 k_pchol64<32, TD><<<(unsigned)ct.size(), 256, 0, s>>>(dc.p, scr.p, scr.p, dst, err);
@@ -3198,6 +3487,11 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                 k_pchol64<64, TD><<<(unsigned)ct.size(), 256, 0, s>>>(dc.p, scr.p, scr.p, dst, err);
             ev.end(s);
             DH2_CHECK_LAUNCH("k_pchol64");
+            if (gram_out) {   // the summed Gram matrix of the (single) stack, both triangles
+                const int c = ct[0].ncols;
+                k_gram_full<<<(unsigned)((int64_t(c) * c + 255) / 256), 256, 0, s>>>(scr.p + ct[0].g, c, gram_out);
+                DH2_CHECK_LAUNCH("k_gram_full");
+            }
             i0 = i1;
         }
     }
@@ -3218,7 +3512,7 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
     }
     if (rest.empty()) return;
     if (chol_qr()) {
-        chol_qr_launch<T, T>(rest, src, dst, s, ev_, err_.p);
+        chol_qr_launch<T, T>(rest, src, dst, s, ev_, err_.p, gram_slices(), &gram_mma_flops_);
         return;
     }
     const bool fp64 = std::is_same<T, double>::value || bp_.qr_fp64;
@@ -4119,6 +4413,10 @@ void Num<T>::build(cudaStream_t s) {
     info.kernel_work_kind[K_TRUNCATE] = (std::is_same<T, double>::value || bp_.svd_fp64) ? W_FLOP64 : W_FLOP32;
     info.kernel_work_kind[K_LEAF_ORTH] = wqr;
     info.kernel_work_kind[K_TSQR_NARROW] = info.kernel_work_kind[K_TSQR];
+    if (gram_slices()) {   // the wide Gram tiles ran on the tensor cores: their BF16 work
+        info.kernel_work[K_TSQR] = gram_mma_flops_;
+        info.kernel_work_kind[K_TSQR] = W_FLOP_BF16;
+    }
     info.kernel_work_kind[K_WQR_CHOL] = W_FLOP64;
     info.kernel_work_kind[K_PROJECT] = w32;
     // matvec leaf kernel: nearfield panels + leaf row bases streamed once, x and y once
@@ -4452,6 +4750,20 @@ std::unique_ptr<NumBase> make_numeric(const Tree& tr, Structure& st, const HostS
                                       const BuildParams& bp) {
     if (bp.precision == DH2_FP64) return std::unique_ptr<NumBase>(new Num<double>(tr, st, hs, bp));
     return std::unique_ptr<NumBase>(new Num<float>(tr, st, hs, bp));
+}
+
+// The Gram matrix Z^* Z of one complex FP32 matrix in FP64, as the weight factorisations
+// form it (dh2_gram)
+void gram_matrix(const void* z, int64_t rows, int32_t cols, int64_t ld, bool tc, void* g, cudaStream_t s) {
+    DBuf<unsigned> err(1);
+    DH2_CHECK_CUDA(cudaMemsetAsync(err.p, 0, sizeof(unsigned), s));
+    const QRTask t{0, 0, (int32_t)rows, 0, cols, (int32_t)ld};
+    EventLog ev;
+    chol_qr_launch<float, float>({t}, static_cast<const cx<float>*>(z), nullptr, s, ev, err.p, tc, nullptr,
+                                 static_cast<cx<double>*>(g));
+    const unsigned e = read_scalar(err.p, s);
+    if (e & ERR_TC_TIMEOUT) throw Error{DH2_ETIMEOUT, "dh2_gram: a bounded tensor-core wait gave up"};
+    if (e) throw Error{DH2_ENUMERIC, "dh2_gram: non-finite input"};
 }
 
 }  // namespace dh2

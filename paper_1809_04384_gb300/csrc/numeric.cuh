@@ -42,6 +42,7 @@ struct BuildParams {
     int32_t symmetry = 1;   // derive the column pass from the row pass when the structure allows
     int32_t direct = 0;     // direct recompression: leaf bases per level, intermediates released early
     int32_t layer = 0;      // DH2_SINGLE_LAYER / DH2_DOUBLE_LAYER
+    int32_t gram_tc = 0;    // mixed form: Gram tiles of wide FP32 stacks from integer digit products
 };
 
 enum KernelId {
@@ -65,7 +66,7 @@ struct MatrixInfoAcc {
     int32_t symmetric = 0;
     int64_t peak_pool_bytes = 0;
 };
-enum WorkKind { W_NONE = 0, W_FLOP32 = 1, W_FLOP64 = 2, W_BYTES = 3 };
+enum WorkKind { W_NONE = 0, W_FLOP32 = 1, W_FLOP64 = 2, W_BYTES = 3, W_FLOP_BF16 = 4 };
 
 class NumBase {
 public:

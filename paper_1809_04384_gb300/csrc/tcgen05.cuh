@@ -1,4 +1,4 @@
-// Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) of sm_103a: TF32
+// Inline-PTX helpers for the 5th-generation tensor cores (tcgen05) of sm_103a: TF32 and BF16
 // matrix products from shared-memory operands into Tensor Memory (TMEM), completion
 // through an mbarrier, and TMEM reads.
 //
@@ -45,6 +45,25 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 // instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major
 __host__ __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// instruction descriptor of kind::f16 with BF16 A and B, FP32 accumulator, both K-major
+__host__ __device__ __forceinline__ uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+// The K-major layout for 16-bit operands: a core matrix is 8 rows x 8 values (16 B), one MMA
+// of K = 16 reads two core matrices along K.  Offset in 16-bit elements.
+__host__ __device__ __forceinline__ int kmaj_off16(int r, int k, int R) {
+    return ((k >> 3) * (R >> 3) + (r >> 3)) * 64 + (r & 7) * 8 + (k & 7);
+}
+
+// D (TMEM) (+)= A * B with BF16 operands (kind::f16); issued by one thread
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, bool accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(tmem_d), "l"(da), "l"(db), "r"(idesc), "r"(accumulate ? 1u : 0u));
 }
 
 // D (TMEM) (+)= A * B; issued by one thread

@@ -51,6 +51,8 @@ def test_library_loads_and_binds(libpath):
 
 
 def test_invalid_arguments_rejected_before_gpu_work(libpath):
+    import ctypes as C
+
     import numpy as np
 
     import paper_1809_04384_gb300 as pkg
@@ -65,6 +67,17 @@ def test_invalid_arguments_rejected_before_gpu_work(libpath):
     with pytest.raises(pkg.DH2Error) as e:
         pkg.dh2_build_dh2(None, 1.0, 4, 1.0, 1e-4)
     assert e.value.status == pkg.DH2_EINVAL
+    # dh2_gram: NULL pointers, sizes and the mode are checked before any device work
+    L = pkg.lib()
+    buf = (C.c_double * 4)()
+    assert L.dh2_gram(None, 8, 4, 4, 1, buf, None) == pkg.DH2_EINVAL
+    assert L.dh2_gram(buf, 8, 4, 4, 1, None, None) == pkg.DH2_EINVAL
+    assert L.dh2_gram(buf, 0, 4, 4, 1, buf, None) == pkg.DH2_EINVAL
+    assert L.dh2_gram(buf, 8, 513, 513, 1, buf, None) == pkg.DH2_EINVAL
+    assert L.dh2_gram(buf, 8, 4, 3, 1, buf, None) == pkg.DH2_EINVAL
+    assert L.dh2_gram(buf, 8, 4, 4, 2, buf, None) == pkg.DH2_EINVAL
+    # the option defaults to the tensor-core Gram and takes only 0 / 1
+    assert pkg.options().gram_tc == 1
 
 
 def test_batch_arguments_rejected_before_gpu_work(libpath):
