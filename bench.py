@@ -614,6 +614,13 @@ def main():
     dom = max(build_kernels, key=lambda k: build_kernels[k][0])
     roof = roofline_obj(dom, build_kernels[dom], work, peaks, args.steps,
                         measured_traffic(cfg["workload"], dom, form))
+    # every build kernel against its own bound (compact: bound, achieved, unit, frac)
+    kernel_roofs = {}
+    for kname in sorted(build_kernels):
+        r = roofline_obj(kname, build_kernels[kname], work, peaks, args.steps)
+        if r is not None:
+            kernel_roofs[kname] = {"bound": r["bound"], "achieved": round(r["achieved"], 3), "unit": r["unit"],
+                                   "frac": round(r["frac"], 4)}
     leaf_ms, leaf_cnt = mv_kernels.get("mv_leaf_out", (0.0, 0))
     mv_roof = roofline_obj("mv_leaf_out", (leaf_ms, leaf_cnt), work, peaks, 10,
                            measured_traffic(cfg["workload"], "mv_leaf_out", form))
@@ -707,6 +714,7 @@ def main():
             "matvec": minfo, **headline,
             "roofline": roof,
             "matvec_roofline": mv_roof,
+            "build_kernel_rooflines": kernel_roofs,
             **{k: side.get(k) for k in ("configured_order", "all_fp32", "plain_fp64", "plain_same_order",
                                          "direct_recompression", "double_layer", "batch", "autotune")},
             "cpu_baseline": side.get("cpu_baseline"),

@@ -1189,7 +1189,57 @@ struct GramItem {
     int32_t ld, ncols, r0, r1;
     int32_t i0, j0;
     int32_t half, pad;        // k_gram_slices: the real (0) or imaginary (1) parts of columns j0..
+    int64_t cmax;             // k_gram_slices: offset of the row group's column maxima (2 ncols)
 };
+
+// Column maxima of a stack's row group for k_gram_slices: max |Re z_c| at cmax[2 c] and
+// max |Im z_c| at cmax[2 c + 1] over rows r0 .. r1 - 1 (FP32 bit patterns, combined by
+// atomicMax over the slices of a group; the buffer starts at zero).
+struct ColMaxTask {
+    int64_t src, cmax;
+    int32_t ld, ncols, r0, r1;
+};
+
+// max |Re|, |Im| of one column over rows r, r + step, ... < r1 (eight loads in flight)
+__device__ __forceinline__ void colmax_rows(const cx<float>* S, int64_t ld, int r, int r1, int step, uint32_t* out,
+                                            unsigned* err) {
+    float mr = 0.0f, mi = 0.0f;
+    bool bad = false;
+    for (; r + 7 * step < r1; r += 8 * step) {
+        cx<float> u[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) u[t] = S[(int64_t)(r + t * step) * ld];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            bad |= !isfinite(u[t].x) || !isfinite(u[t].y);
+            mr = fmaxf(mr, fabsf(u[t].x));
+            mi = fmaxf(mi, fabsf(u[t].y));
+        }
+    }
+    for (; r < r1; r += step) {
+        const cx<float> u = S[(int64_t)r * ld];
+        bad |= !isfinite(u.x) || !isfinite(u.y);
+        mr = fmaxf(mr, fabsf(u.x));
+        mi = fmaxf(mi, fabsf(u.y));
+    }
+    if (bad) raise_err(err, ERR_TSQR_INPUT);
+    atomicMax(&out[0], __float_as_uint(mr));   // non-negative floats order as their bit patterns
+    atomicMax(&out[1], __float_as_uint(mi));
+}
+
+__global__ void __launch_bounds__(256) k_gram_colmax(const ColMaxTask* __restrict__ tasks,
+                                                     const cx<float>* __restrict__ src, uint32_t* cmax,
+                                                     unsigned* err) {
+    const ColMaxTask tk = tasks[blockIdx.x];
+    const int C = tk.ncols, t = threadIdx.x, nt = blockDim.x;
+    const cx<float>* S = src + tk.src;
+    if (C <= nt) {   // nt / C threads per column, consecutive threads on consecutive columns
+        const int tpc = nt / C, c = t % C, ph = t / C;
+        if (ph < tpc) colmax_rows(S + c, tk.ld, tk.r0 + ph, tk.r1, tpc, cmax + tk.cmax + 2 * c, err);
+    } else {
+        for (int c = t; c < C; c += nt) colmax_rows(S + c, tk.ld, tk.r0, tk.r1, 1, cmax + tk.cmax + 2 * c, err);
+    }
+}
 
 // TB = 16 * BS: each of up to 256 threads accumulates a BS x BS block of the tile in
 // FP64 registers; on a diagonal tile only the blocks on or above the diagonal are
@@ -1286,53 +1336,78 @@ __global__ void __launch_bounds__(256) k_gram64(const GramItem* __restrict__ ite
 // The Gram tile G = Z_I^* Z_J of an FP32 stack (I, J: 64 complex columns each) from exact
 // integer products on the BF16 tensor cores.  Each real column m of the tile (the real and
 // the imaginary parts of a complex column are two real columns) is scaled by 2^-e_m, e_m the
-// exponent of its largest magnitude over the CTA's rows, and written as 8 signed base-64
+// exponent of its largest magnitude over the row group, and written as 8 signed base-64
 // digits, x 2^-e_m = sum_i d_i 2^(1 - 6 i) + rest, |d_i| <= 32, |rest| <= 2^-48: each digit is
-// the rounded remainder of the previous one times 64, so every step is exact in FP32 and every
-// digit exact in BF16.  A dot product of two columns is then sum_{i,j} (d_i . d'_j) 2^(2 - 6(i+j));
-// the digit products with one i + j = g share that scale and are summed in one FP32 TMEM
-// accumulator, whose partial sums are integers of magnitude at most 8 * 32 * 32 * rows <= 2^24
-// for rows <= 2048, so the tensor cores add them exactly.  Products with i + j > 9 are dropped;
+// the remainder rounded to the next grid 2^(-6 i), so every step is exact in FP32 and every
+// digit (kept at its weight) exact in BF16.  A dot product of two columns is then
+// sum_{i,j} (d_i . d'_j) 2^(2 - 6(i+j)); the digit products with one i + j = g share that grid
+// and are summed in one FP32 TMEM accumulator, whose partial sums are integer multiples of it
+// of magnitude at most 8 * 32 * 32 * rows <= 2^24 units for rows <= 2048, so the tensor cores
+// add them exactly.  Products with i + j > 9 are dropped;
 // with the rests this leaves an error of at most about 2^-43 max|z_m| max|z_n| per row (an FP64
 // accumulation: 2^-53 |z_m| |z_n|), far below the FP32 rounding of the stack's own entries.
 //
 // The real product is split by the column part of J: a CTA with half = 0 forms D = Y_I^T Re Z_J
-// and one with half = 1 forms D = Y_I^T Im Z_J, Y_I = [Re Z_I, Im Z_I] (M = 128, N = 64), and
-// each writes one complex partial tile: half 0 (Re G, Im G) = (D_top, -D_bottom), half 1
-// (D_bottom, D_top).  The 8 group accumulators take all 512 TMEM columns (one CTA per SM); the
-// digits of 32 rows are staged per step in two shared-memory buffers, so the digits of the next
-// rows are formed while the tensor cores work on the current ones.
+// and one with half = 1 forms D = Y_I^T Im Z_J, Y_I = [Re Z_I, Im Z_I] (M = 128 rows), and each
+// writes one complex partial tile: half 0 (Re G, Im G) = (D_top, -D_bottom), half 1
+// (D_bottom, D_top).  The 8 group accumulators (64 columns each) take all 512 TMEM columns (one
+// CTA per SM).  The digits of J's part are stored digit after digit as one operand of 512 rows,
+// so one MMA multiplies digit i of Y_I by up to four consecutive digits j of Z_J (N <= 256) and
+// writes the consecutive groups i + j: 14 MMAs per 16 rows, each accumulator run starting at a
+// TMEM column that is a multiple of its width.  The digits of 32 rows are
+// staged per step in two shared-memory buffers; the rows of the next step are loaded into
+// registers and the digits of the next step formed while the tensor cores work on the current.
 namespace gram_tc {
 constexpr int kDigits = 8;
 constexpr int kMaxRows = 2048;
 constexpr int kSub = 32;
-constexpr int kABytes = kDigits * 128 * kSub * 2;   // digits of Y_I, 128 rows x kSub
-constexpr int kBBytes = kDigits * 64 * kSub * 2;    // digits of one part of Z_J, 64 rows x kSub
+constexpr int kABytes = kDigits * 128 * kSub * 2;   // digits of Y_I: per digit 128 rows x kSub
+constexpr int kBBytes = kDigits * 64 * kSub * 2;    // digits of one part of Z_J: 512 rows x kSub
 constexpr int kHeader = 2048;
 constexpr size_t kSmemBytes = 1024 + kHeader + 2 * (size_t)(kABytes + kBBytes);   // 1024: alignment
 
-// digits of 8 consecutive rows (y = x 2^(5 - e), |y| <= 32) of operand row r, stored as one
-// 16-byte core-matrix row per digit (K-major layout of an operand with R rows)
-template <int R>
-__device__ __forceinline__ void store_digits(float (&y)[8], unsigned char* buf, int r, int q) {
-    constexpr float kRound = 12582912.0f;   // 1.5 * 2^23: (y + kRound) - kRound = rint(y), |y| < 2^22
-    constexpr int kDigitBytes = R * kSub * 2;
-    const int off = tc::kmaj_off16(r, 8 * q, R) * 2;
+// two FP32 lanes at once (Blackwell packed arithmetic): rows t and t + 1 of a column
+__device__ __forceinline__ uint64_t fadd2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fsub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t pack2(float a, float b) {
+    return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+
+// The digits of 8 consecutive rows (y = x 2^(5 - e), |y| <= 32) of one real column, each at its
+// own weight: digit d is y's remainder rounded to the grid 2^(-6 d) (adding and subtracting
+// 1.5 * 2^(23 - 6 d) rounds to that grid; the remainder then loses the digit exactly), so
+// digit d = s 2^(-6 d) with an integer |s| <= 32 and y = sum of the digits + rest, |rest| <=
+// 2^-43.  Stored as one 16-byte core-matrix row per digit (K-major layouts, see tcgen05.cuh):
+// at row r of digit d's 128-row block of A (a != nullptr) and at row 64 d + rb of the 512-row
+// B (b != nullptr).
+__device__ __forceinline__ void store_digits(float (&y)[8], unsigned char* a, int r, unsigned char* b, int rb, int q) {
+    const int offa = tc::kmaj_off16(r, 8 * q, 128) * 2;
+    uint64_t v2[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) v2[t] = pack2(y[2 * t], y[2 * t + 1]);
 #pragma unroll
     for (int d = 0; d < kDigits; ++d) {
-        uint32_t bits[8];
+        const float R = 12582912.0f * __int_as_float((127 - 6 * d) << 23);   // 1.5 * 2^(23 - 6 d)
+        const uint64_t R2 = pack2(R, R);
+        uint32_t w[4];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const float s = __fsub_rn(__fadd_rn(y[t], kRound), kRound);
-            y[t] = __fmul_rn(__fsub_rn(y[t], s), 64.0f);
-            bits[t] = __float_as_uint(s);   // an integer of at most 6 bits: the low half is zero
+        for (int t = 0; t < 4; ++t) {
+            const uint64_t sd = fsub2(fadd2(v2[t], R2), R2);   // the digits of rows 2t, 2t + 1
+            v2[t] = fsub2(v2[t], sd);
+            // each digit has at most 6 significant bits: its FP32 pattern's low half is zero
+            w[t] = __byte_perm((uint32_t)sd, (uint32_t)(sd >> 32), 0x7632);
         }
-        uint4 v;
-        v.x = __byte_perm(bits[0], bits[1], 0x7632);
-        v.y = __byte_perm(bits[2], bits[3], 0x7632);
-        v.z = __byte_perm(bits[4], bits[5], 0x7632);
-        v.w = __byte_perm(bits[6], bits[7], 0x7632);
-        *reinterpret_cast<uint4*>(buf + d * kDigitBytes + off) = v;
+        const uint4 v{w[0], w[1], w[2], w[3]};
+        if (a) *reinterpret_cast<uint4*>(a + d * (128 * kSub * 2) + offa) = v;
+        if (b) *reinterpret_cast<uint4*>(b + tc::kmaj_off16(64 * d + rb, 8 * q, 512) * 2) = v;
     }
 }
 
@@ -1346,8 +1421,12 @@ __device__ __forceinline__ double widen(float f, int e) {
 }
 }  // namespace gram_tc
 
-__global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restrict__ items,
+// 288 threads: warps 0-7 form the digits (and drain the accumulators), warp 8 issues the MMAs.
+// Per buffer, `full` counts the 8 producer warps' arrivals and `empty` is signalled by the
+// tensor cores (tcgen05.commit) once the MMAs reading it are done; every wait is bounded.
+__global__ void __launch_bounds__(288, 1) k_gram_slices(const GramItem* __restrict__ items,
                                                         const cx<float>* __restrict__ src,
+                                                        const uint32_t* __restrict__ cmax,
                                                         cx<double>* __restrict__ part, unsigned* err) {
     using namespace gram_tc;
     extern __shared__ unsigned char g_smem_raw[];
@@ -1356,8 +1435,10 @@ __global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restri
     uint32_t* colbits = reinterpret_cast<uint32_t*>(base);   // 192: column maxima, then exponents
     int* ex = reinterpret_cast<int*>(base);
     float* scl = reinterpret_cast<float*>(base + 768);        // 192: 2^(5 - e)
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + 1536);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(base + 1552);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + 1536);
+    uint64_t* empty = reinterpret_cast<uint64_t*>(base + 1552);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(base + 1568);
+    int* s_committed = reinterpret_cast<int*>(base + 1572);
     unsigned char* ops = base + kHeader;
 
     const GramItem it = items[blockIdx.x];
@@ -1365,44 +1446,26 @@ __global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restri
     const int h = it.half;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const cx<float>* S = src + it.src;
-    if (tid < 192) colbits[tid] = 0u;
+    // column scales from the largest magnitude of each real column over the row group
+    // (k_gram_colmax): rows 0..63 of A the real parts of I, 64..127 the imaginary parts, B
+    // the part `half` of J
+    if (tid < 192) {
+        const int col = tid < 128 ? it.i0 + (tid & 63) : it.j0 + (tid - 128);
+        const int part_ = tid < 64 ? 0 : tid < 128 ? 1 : h;
+        colbits[tid] = (col < it.ncols && (tid < 128 || !diag)) ? cmax[it.cmax + 2 * col + part_] : 0u;
+    }
     if (warp == 0) tc::tmem_alloc(tslot, 512);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_init(&full[0], 8);
+        tc::mbar_init(&full[1], 8);
+        tc::mbar_init(&empty[0], 1);
+        tc::mbar_init(&empty[1], 1);
+        *s_committed = -1;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
-
-    // column scales from the largest magnitude of each real column over the CTA's rows
-    const int p = tid & 63, q = tid >> 6;
-    const bool colA = it.i0 + p < it.ncols, colB = !diag && it.j0 + p < it.ncols;
-    {
-        float ar = 0.0f, ai = 0.0f, bm = 0.0f;
-        bool bad = false;
-        for (int r = it.r0 + q; r < it.r1; r += 4) {
-            const cx<float>* row = S + (int64_t)r * it.ld;
-            if (colA) {
-                const cx<float> u = row[it.i0 + p];
-                bad |= !isfinite(u.x) || !isfinite(u.y);
-                ar = fmaxf(ar, fabsf(u.x));
-                ai = fmaxf(ai, fabsf(u.y));
-            }
-            if (colB) {
-                const cx<float> u = row[it.j0 + p];
-                const float v = h ? u.y : u.x;
-                bad |= !isfinite(v);
-                bm = fmaxf(bm, fabsf(v));
-            }
-        }
-        if (bad) raise_err(err, ERR_TSQR_INPUT);
-        atomicMax(&colbits[p], __float_as_uint(ar));
-        atomicMax(&colbits[64 + p], __float_as_uint(ai));
-        if (!diag) atomicMax(&colbits[128 + p], __float_as_uint(bm));
-    }
-    __syncthreads();
     if (tid < 192) {
         const int E = (int)(colbits[tid] >> 23);   // biased exponent of the maximum (>= 0)
         int e = E - 126;                           // maximum < 2^e
@@ -1415,77 +1478,111 @@ __global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restri
     __syncthreads();
 
     const int nsub = (it.r1 - it.r0 + kSub - 1) / kSub;
-    const uint32_t idesc = tc::idesc_bf16(128, 64);
     bool ok = true;
-    int committed = -1;
-    for (int sc = 0; sc < nsub; ++sc) {
-        const int b = sc & 1;
-        if (sc >= 2) {   // the tensor cores are done with this buffer (step sc - 2)
-            ok = __syncthreads_and(tc::mbar_wait(&mbar[b], ((sc - 2) >> 1) & 1, kTcWaitPolls));
-            if (!ok) break;
-        }
-        unsigned char* Ab = ops + b * (kABytes + kBBytes);
-        unsigned char* Bb = Ab + kABytes;
-        const int row0 = it.r0 + sc * kSub + 8 * q;
-        {
-            float re[8], im[8];
-            const float sr = scl[p], si = scl[64 + p];
+    if (warp < 8) {
+        // producers: thread (p, q) forms rows 8 q .. 8 q + 7 of a step for complex column p
+        // of I and (off the diagonal) column p of J's part
+        const int p = tid & 63, q = tid >> 6;
+        const bool colA = it.i0 + p < it.ncols, colB = !diag && it.j0 + p < it.ncols;
+        const float sr = scl[p], si = scl[64 + p], sb = diag ? 0.0f : scl[128 + p];
+        auto load = [&](int step, cx<float> (&za)[8], float (&zb)[8]) {
+            const int row0 = it.r0 + step * kSub + 8 * q;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                cx<float> u{0.0f, 0.0f};
-                if (colA && row0 + t < it.r1) u = S[(int64_t)(row0 + t) * it.ld + it.i0 + p];
-                re[t] = u.x * sr;
-                im[t] = u.y * si;
-            }
-            store_digits<128>(re, Ab, p, q);
-            store_digits<128>(im, Ab, 64 + p, q);
-        }
-        if (!diag) {
-            float v[8];
-            const float sb = scl[128 + p];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
+                const bool in = row0 + t < it.r1;
+                const cx<float>* row = S + (int64_t)(row0 + t) * it.ld;
+                za[t] = (colA && in) ? row[it.i0 + p] : cx<float>{0.0f, 0.0f};
                 float x = 0.0f;
-                if (colB && row0 + t < it.r1) {
-                    const cx<float> u = S[(int64_t)(row0 + t) * it.ld + it.j0 + p];
+                if (colB && in) {
+                    const cx<float> u = row[it.j0 + p];
                     x = h ? u.y : u.x;
                 }
-                v[t] = x * sb;
+                zb[t] = x;
             }
-            store_digits<64>(v, Bb, p, q);
-        }
-        tc::fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t a0 = tc::smem_u32(Ab), b0 = tc::smem_u32(Bb);
-            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (64 / 8) * 128, sbo = 128;
-            constexpr uint32_t dA = 128 * kSub * 2, dB = 64 * kSub * 2;
-#pragma unroll 1
-            for (int g = 2; g <= kDigits + 1; ++g) {
-                const int ilo = max(1, g - kDigits), ihi = min(kDigits, g - 1);
-#pragma unroll 1
-                for (int i = ilo; i <= ihi; ++i) {
-                    const int j = g - i;
+        };
+        cx<float> za[8];
+        float zb[8];
+        if (nsub > 0) load(0, za, zb);
+        for (int sc = 0; sc < nsub; ++sc) {
+            const int b = sc & 1;
+            cx<float> na[8];
+            float nb[8];
+            if (sc + 1 < nsub) load(sc + 1, na, nb);   // in flight while this step's digits are formed
+            if (sc >= 2 && !tc::mbar_wait(&empty[b], ((sc - 2) >> 1) & 1, kTcWaitPolls)) {
+                ok = false;   // the tensor cores never released this buffer
+                break;
+            }
+            unsigned char* Ab = ops + b * (kABytes + kBBytes);
+            unsigned char* Bb = Ab + kABytes;
+            {
+                float re[8], im[8];
 #pragma unroll
-                    for (int ks = 0; ks < kSub / 16; ++ks) {
-                        const uint64_t da = tc::sdesc(a0 + (i - 1) * dA + ks * 2 * lboA, lboA, sbo);
-                        const uint64_t db =
-                            diag ? tc::sdesc(a0 + (j - 1) * dA + h * 8 * 128 + ks * 2 * lboA, lboA, sbo)
-                                 : tc::sdesc(b0 + (j - 1) * dB + ks * 2 * lboB, lboB, sbo);
-                        tc::mma_bf16(tmem + (uint32_t)((g - 2) * 64), da, db, idesc, sc > 0 || i > ilo || ks > 0);
+                for (int t = 0; t < 8; ++t) {
+                    re[t] = za[t].x * sr;
+                    im[t] = za[t].y * si;
+                }
+                // on the diagonal, J's part is I's own: its digits go to B as well
+                store_digits(re, Ab, p, (diag && h == 0) ? Bb : nullptr, p, q);
+                store_digits(im, Ab, 64 + p, (diag && h == 1) ? Bb : nullptr, p, q);
+            }
+            if (!diag) {
+                float v[8];
+#pragma unroll
+                for (int t = 0; t < 8; ++t) v[t] = zb[t] * sb;
+                store_digits(v, nullptr, 0, Bb, p, q);
+            }
+            tc::fence_async_smem();   // the generic-proxy stores become visible to the tensor cores
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&full[b]);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                za[t] = na[t];
+                zb[t] = nb[t];
+            }
+        }
+        // every MMA has completed (they complete in order) before the accumulators are read
+        if (ok && nsub > 0) ok = tc::mbar_wait(&empty[(nsub - 1) & 1], ((nsub - 1) >> 1) & 1, kTcWaitPolls);
+    } else if (lane == 0) {
+        // the MMA issuer
+        for (int sc = 0; sc < nsub; ++sc) {
+            const int b = sc & 1;
+            if (!tc::mbar_wait(&full[b], (sc >> 1) & 1, kTcWaitPolls)) {
+                ok = false;
+                break;
+            }
+            tc::fence_after_sync();
+            unsigned char* Ab = ops + b * (kABytes + kBBytes);
+            const uint32_t a0 = tc::smem_u32(Ab), b0 = tc::smem_u32(Ab + kABytes);
+            constexpr uint32_t lboA = (128 / 8) * 128, lboB = (512 / 8) * 128, sbo = 128;
+            constexpr uint32_t dA = 128 * kSub * 2;   // bytes per digit of A
+#pragma unroll
+            for (int ks = 0; ks < kSub / 16; ++ks) {
+#pragma unroll 1
+                for (int i = 1; i <= kDigits; ++i) {
+                    const uint64_t da = tc::sdesc(a0 + (i - 1) * dA + ks * 2 * lboA, lboA, sbo);
+                    // the groups g = i + j (TMEM block g - 2) of digits j = 1 .. 9 - i, in runs of
+                    // 1, 2 or 4 blocks that start at a multiple of their length (N = 64, 128, 256)
+                    for (int blk = i - 1; blk < kDigits;) {
+                        int nd = 4;
+                        while (nd > 1 && ((blk & (nd - 1)) != 0 || blk + nd > kDigits)) nd >>= 1;
+                        const int j1 = blk - i + 2;
+                        const uint64_t db = tc::sdesc(b0 + (j1 - 1) * (64 / 8) * 128 + ks * 2 * lboB, lboB, sbo);
+                        // digit 1 against digits 1-4 and 5-8 writes all 8 groups: it starts the sums
+                        tc::mma_bf16(tmem + (uint32_t)(blk * 64), da, db, tc::idesc_bf16(128, 64 * nd),
+                                     sc > 0 || ks > 0 || i > 1);
+                        blk += nd;
                     }
                 }
             }
-            tc::commit(&mbar[b]);
+            tc::commit(&empty[b]);
+            *s_committed = sc;
         }
-        committed = sc;
     }
-    if (ok && committed >= 0)
-        ok = __syncthreads_and(tc::mbar_wait(&mbar[committed & 1], (committed >> 1) & 1, kTcWaitPolls));
+    ok = __syncthreads_and(ok) != 0;
     tc::fence_after_sync();
+    const int committed = *s_committed;
 
-    if (ok && committed >= 0) {
+    if (ok && committed >= 0 && warp < 8) {
         // warp (quarter qd, column half ch): TMEM lane m = row m of D, columns 32 ch .. 32 ch + 31
         const int qd = warp & 3, ch = warp >> 2;
         const int m = 32 * qd + lane;
@@ -1498,10 +1595,9 @@ __global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restri
             float v0[16], v1[16];
             tc::tmem_ld16(tq + (uint32_t)((g - 2) * 64 + 32 * ch), v0);
             tc::tmem_ld16(tq + (uint32_t)((g - 2) * 64 + 32 * ch + 16), v1);
-            const float w = __int_as_float((127 + 2 - 6 * g) << 23);   // 2^(2 - 6 g)
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const float x = (j < 16 ? v0[j] : v1[j - 16]) * w;   // exact
+                const float x = j < 16 ? v0[j] : v1[j - 16];
                 const float s = __fadd_rn(hi[j], x);                 // two-sum: hi + x = s + e
                 const float bb = __fsub_rn(s, hi[j]);
                 const float e = __fadd_rn(__fsub_rn(hi[j], __fsub_rn(s, bb)), __fsub_rn(x, bb));
@@ -1517,13 +1613,14 @@ __global__ void __launch_bounds__(256, 1) k_gram_slices(const GramItem* __restri
         double* o = reinterpret_cast<double*>(part + it.out + (int64_t)i * 64 + 32 * ch) + comp;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-            const int e = em + ex[(diag ? 64 * h : 128) + 32 * ch + j];
+            // x_m x_n = 2^(e_m + e_n - 10) y_m y_n
+            const int e = em + ex[(diag ? 64 * h : 128) + 32 * ch + j] - 10;
             o[2 * j] = sgn * (widen(hi[j], e) + widen(lo[j], e));
         }
     }
-    if (!ok) {
-        if (tid == 0) raise_err(err, ERR_TC_TIMEOUT);
-        if (committed >= 0) tc::mbar_wait(&mbar[committed & 1], (committed >> 1) & 1, kTcWaitPolls);
+    if (!ok && tid == 0) {
+        raise_err(err, ERR_TC_TIMEOUT);
+        if (committed >= 0) tc::mbar_wait(&empty[committed & 1], (committed >> 1) & 1, kTcWaitPolls);
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -3434,7 +3531,8 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
         while (i0 < ts.size()) {
             std::vector<GramItem> items;
             std::vector<CholTask> ct;
-            int64_t pel = 0, gel = 0;
+            std::vector<ColMaxTask> cmt;   // tcg: column maxima per row group, slices of 256 rows
+            int64_t pel = 0, gel = 0, coff = 0;
             size_t i1 = i0;
             for (; i1 < ts.size(); ++i1) {
                 const QRTask& t = ts[i1];
@@ -3444,13 +3542,24 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                 const int64_t need = tp * ng * halves * TB * TB + (int64_t)t.ncols * t.ncols;
                 if (i1 > i0 && pel + gel + need > kScratchElems) break;
                 CholTask c{pel, gel, t.dst, t.ncols, t.rout, nt, ng * halves};
+                std::vector<int64_t> gcm(ng, 0);
+                if (tcg)
+                    for (int g = 0; g < ng; ++g) {
+                        gcm[g] = coff;
+                        coff += 2 * (int64_t)t.ncols;
+                        const int32_t r0 = (int32_t)(g * grows);
+                        const int32_t r1 = (int32_t)std::min<int64_t>(t.nrows, r0 + grows);
+                        for (int32_t rs = r0; rs < r1; rs += 256)
+                            cmt.push_back(ColMaxTask{t.src, gcm[g], t.ld, t.ncols, rs, std::min(r1, rs + 256)});
+                    }
                 for (int I = 0; I < nt; ++I)
                     for (int J = I; J < nt; ++J)
                         for (int g = 0; g < ng; ++g)
                             for (int hf = 0; hf < halves; ++hf) {
                                 const int32_t r0 = (int32_t)(g * grows);
                                 const int32_t r1 = (int32_t)std::min<int64_t>(t.nrows, r0 + grows);
-                                items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB, hf, 0});
+                                items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB, hf, 0,
+                                                         gcm[g]});
                                 pel += (int64_t)TB * TB;
                                 if (tcg && mma_flops) {   // 36 digit products of 128 x 64 real columns
                                     const double mi = 2.0 * std::min(TB, t.ncols - I * TB);
@@ -3472,8 +3581,15 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                 k_gram64<2, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
             } else if (tcg) {
                 if constexpr (std::is_same<TS, float>::value) {
+                    DBuf<ColMaxTask> dcm;
+                    upload_vec(dcm, cmt, s);
+                    DBuf<uint32_t> cmb((size_t)std::max<int64_t>(coff, 1));
+                    DH2_CHECK_CUDA(cudaMemsetAsync(cmb.p, 0, (size_t)coff * sizeof(uint32_t), s));
+                    k_gram_colmax<<<(unsigned)cmt.size(), 256, 0, s>>>(dcm.p, src, cmb.p, err);
+                    DH2_CHECK_LAUNCH("k_gram_colmax");
                     ensure_smem(reinterpret_cast<const void*>(k_gram_slices), gram_tc::kSmemBytes);
-                    k_gram_slices<<<(unsigned)items.size(), 256, gram_tc::kSmemBytes, s>>>(di.p, src, scr.p, err);
+                    k_gram_slices<<<(unsigned)items.size(), 288, gram_tc::kSmemBytes, s>>>(di.p, src, cmb.p, scr.p,
+                                                                                          err);
                 }
             } else {
                 k_gram64<4, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);

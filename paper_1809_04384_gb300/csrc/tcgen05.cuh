@@ -85,6 +85,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// one arrival on the mbarrier (release at CTA scope)
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(mbar)) : "memory");
+}
+
 // waits for the phase of the given parity to complete; gives up after `limit` polls
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int limit) {
     uint32_t done = 0;
