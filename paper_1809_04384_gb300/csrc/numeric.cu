@@ -1188,7 +1188,8 @@ struct GramItem {
     int64_t out;              // cx<double> offset of this partial tile (TB x TB, row-major)
     int32_t ld, ncols, r0, r1;
     int32_t i0, j0;
-    int32_t half, pad;        // k_gram_slices: the real (0) or imaginary (1) parts of columns j0..
+    int32_t half;             // k_gram_slices: the real (0) or imaginary (1) parts of columns j0..
+    int32_t narrow;           // k_gram_slices: a stack of at most 32 columns, one CTA per tile
     int64_t cmax;             // k_gram_slices: offset of the row group's column maxima (2 ncols)
 };
 
@@ -1449,9 +1450,18 @@ __global__ void __launch_bounds__(288, 1) k_gram_slices(const GramItem* __restri
     // column scales from the largest magnitude of each real column over the row group
     // (k_gram_colmax): rows 0..63 of A the real parts of I, 64..127 the imaginary parts, B
     // the part `half` of J
+    // narrow (at most 32 columns, one tile): rows 0..31 of A the real parts, 32..63 the
+    // imaginary parts, and B the same 64 rows
+    const bool narrow = it.narrow != 0;
     if (tid < 192) {
-        const int col = tid < 128 ? it.i0 + (tid & 63) : it.j0 + (tid - 128);
-        const int part_ = tid < 64 ? 0 : tid < 128 ? 1 : h;
+        int col, part_;
+        if (narrow) {
+            col = tid < 64 ? (tid & 31) : it.ncols;
+            part_ = tid >> 5;
+        } else {
+            col = tid < 128 ? it.i0 + (tid & 63) : it.j0 + (tid - 128);
+            part_ = tid < 64 ? 0 : tid < 128 ? 1 : h;
+        }
         colbits[tid] = (col < it.ncols && (tid < 128 || !diag)) ? cmax[it.cmax + 2 * col + part_] : 0u;
     }
     if (warp == 0) tc::tmem_alloc(tslot, 512);
@@ -1482,9 +1492,12 @@ __global__ void __launch_bounds__(288, 1) k_gram_slices(const GramItem* __restri
     if (warp < 8) {
         // producers: thread (p, q) forms rows 8 q .. 8 q + 7 of a step for complex column p
         // of I and (off the diagonal) column p of J's part
-        const int p = tid & 63, q = tid >> 6;
-        const bool colA = it.i0 + p < it.ncols, colB = !diag && it.j0 + p < it.ncols;
-        const float sr = scl[p], si = scl[64 + p], sb = diag ? 0.0f : scl[128 + p];
+        // narrow: threads 0..127, p = column (< 32), q = row group; the others only keep step
+        const int p = narrow ? (tid & 31) : (tid & 63), q = narrow ? ((tid >> 5) & 3) : (tid >> 6);
+        const bool worker = !narrow || tid < 128;
+        const bool colA = worker && it.i0 + p < it.ncols, colB = !narrow && !diag && it.j0 + p < it.ncols;
+        const int rim = narrow ? 32 + p : 64 + p;   // A row of the imaginary part
+        const float sr = scl[p], si = scl[rim], sb = (diag || narrow) ? 0.0f : scl[128 + p];
         auto load = [&](int step, cx<float> (&za)[8], float (&zb)[8]) {
             const int row0 = it.r0 + step * kSub + 8 * q;
 #pragma unroll
@@ -1514,7 +1527,18 @@ __global__ void __launch_bounds__(288, 1) k_gram_slices(const GramItem* __restri
             }
             unsigned char* Ab = ops + b * (kABytes + kBBytes);
             unsigned char* Bb = Ab + kABytes;
-            {
+            if (narrow) {
+                if (worker) {   // B = A's 64 rows: [Re, Im] of the tile
+                    float re[8], im[8];
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        re[t] = za[t].x * sr;
+                        im[t] = za[t].y * si;
+                    }
+                    store_digits(re, Ab, p, Bb, p, q);
+                    store_digits(im, Ab, rim, Bb, rim, q);
+                }
+            } else {
                 float re[8], im[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) {
@@ -1523,9 +1547,9 @@ __global__ void __launch_bounds__(288, 1) k_gram_slices(const GramItem* __restri
                 }
                 // on the diagonal, J's part is I's own: its digits go to B as well
                 store_digits(re, Ab, p, (diag && h == 0) ? Bb : nullptr, p, q);
-                store_digits(im, Ab, 64 + p, (diag && h == 1) ? Bb : nullptr, p, q);
+                store_digits(im, Ab, rim, (diag && h == 1) ? Bb : nullptr, p, q);
             }
-            if (!diag) {
+            if (!diag && !narrow) {
                 float v[8];
 #pragma unroll
                 for (int t = 0; t < 8; ++t) v[t] = zb[t] * sb;
@@ -1582,7 +1606,46 @@ __global__ void __launch_bounds__(288, 1) k_gram_slices(const GramItem* __restri
     tc::fence_after_sync();
     const int committed = *s_committed;
 
-    if (ok && committed >= 0 && warp < 8) {
+    if (ok && committed >= 0 && narrow) {
+        // D (rows m < 64, columns n < 64; real parts first) through shared memory, scaled, then
+        // G = Z^* Z: Re G(i, j) = D(i, j) + D(32 + i, 32 + j), Im G(i, j) = D(i, 32 + j) - D(32 + i, j)
+        double* Dm = reinterpret_cast<double*>(ops);   // 64 x 64; the operand buffers are free now
+        const int qd = warp & 3, ch = warp >> 2;
+        if (warp < 8 && qd < 2) {
+            const int m = 32 * qd + lane;
+            const uint32_t tq = tmem + ((uint32_t)(32 * qd) << 16);
+            float hi[32], lo[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0.0f;
+#pragma unroll 1
+            for (int g = 2; g <= kDigits + 1; ++g) {
+                float v0[16], v1[16];
+                tc::tmem_ld16(tq + (uint32_t)((g - 2) * 64 + 32 * ch), v0);
+                tc::tmem_ld16(tq + (uint32_t)((g - 2) * 64 + 32 * ch + 16), v1);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float x = j < 16 ? v0[j] : v1[j - 16];
+                    const float s = __fadd_rn(hi[j], x);
+                    const float bb = __fsub_rn(s, hi[j]);
+                    const float e = __fadd_rn(__fsub_rn(hi[j], __fsub_rn(s, bb)), __fsub_rn(x, bb));
+                    hi[j] = s;
+                    lo[j] = __fadd_rn(lo[j], e);
+                }
+            }
+            const int em = ex[m];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int e = em + ex[32 * ch + j] - 10;
+                Dm[m * 64 + 32 * ch + j] = widen(hi[j], e) + widen(lo[j], e);
+            }
+        }
+        __syncthreads();
+        cx<double>* O = part + it.out;   // 32 x 32 tile
+        for (int idx = tid; idx < 32 * 32; idx += blockDim.x) {
+            const int i = idx >> 5, j = idx & 31;
+            O[idx] = cx<double>{Dm[i * 64 + j] + Dm[(32 + i) * 64 + 32 + j], Dm[i * 64 + 32 + j] - Dm[(32 + i) * 64 + j]};
+        }
+    } else if (ok && committed >= 0 && warp < 8) {
         // warp (quarter qd, column half ch): TMEM lane m = row m of D, columns 32 ch .. 32 ch + 31
         const int qd = warp & 3, ch = warp >> 2;
         const int m = 32 * qd + lane;
@@ -2956,7 +3019,7 @@ private:
     }
     // Gram tiles of wide FP32 stacks from exact integer digit products on the tensor cores
     bool gram_slices() const { return std::is_same<T, float>::value && chol_qr() && bp_.gram_tc != 0; }
-    double gram_mma_flops_ = 0.0;   // tensor-core work of k_gram_slices in this build
+    double gram_mma_flops_[2] = {0.0, 0.0};   // tensor-core work of k_gram_slices: narrow, wide stacks
     // algorithmic flops of one weight factorisation of a stack of `rows` x `cols`
     void qr_work(int64_t rows, int32_t cols) {
         if (rows <= cols) return;   // copied: R = Z
@@ -3495,10 +3558,10 @@ void tsqr_tree(const std::vector<QRTask>& tasks, int k, int group, const cx<TS>*
 // partial tiles of a stack are summed in group order by the Cholesky kernel (no atomics,
 // deterministic).  Stacks are processed in chunks whose scratch stays under 1 GiB.
 // Gram matrices (FP64 partial tiles per row group) and pivoted Cholesky factors of the
-// stacks.  slices: stacks of more than 32 FP32 columns take their Gram tiles from
-// k_gram_slices (exact integer products on the tensor cores, two CTAs per tile and row
-// group of at most 2048 rows); otherwise k_gram64 forms them with FP64 FMAs.  *mma_flops
-// gains the tensor-core work of k_gram_slices.
+// stacks.  slices: FP32 stacks take their Gram tiles from k_gram_slices (exact integer
+// products on the tensor cores; row groups of at most 2048 rows; two CTAs per tile of a
+// stack wider than 32 columns, one for a narrower stack); otherwise k_gram64 forms them
+// with FP64 FMAs.  mma_flops[0 | 1] gain the tensor-core work of the narrow | wide stacks.
 template <class TS, class TD>
 void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>* dst, cudaStream_t s, EventLog& ev,
                     unsigned* err, bool slices = false, double* mma_flops = nullptr,
@@ -3506,8 +3569,8 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
     constexpr int64_t kScratchElems = (int64_t(1) << 30) / (int64_t)sizeof(cx<double>);
     for (int cls = 0; cls < 2; ++cls) {
         const int TB = cls == 0 ? 32 : 64;
-        const bool tcg = slices && cls == 1 && std::is_same<TS, float>::value;
-        const int halves = tcg ? 2 : 1;
+        const bool tcg = slices && std::is_same<TS, float>::value;
+        const int halves = (tcg && cls == 1) ? 2 : 1;
         std::vector<QRTask> ts;
         for (const QRTask& t : tasks)
             if ((t.ncols <= 32) == (cls == 0) && t.nrows > 0) ts.push_back(t);
@@ -3520,7 +3583,7 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
         int64_t grows;
         if (tcg) {   // one CTA per SM: about four waves of CTAs, at most 2048 rows each
             grows = std::min<int64_t>(gram_tc::kMaxRows,
-                                      std::max<int64_t>(256, (int64_t)std::ceil(units / (152 * 2))));
+                                      std::max<int64_t>(256, (int64_t)std::ceil(units * halves / (152 * 4))));
             grows = (grows + 31) / 32 * 32;
         } else {
             const int64_t want_items = 152 * 12;
@@ -3558,13 +3621,13 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                             for (int hf = 0; hf < halves; ++hf) {
                                 const int32_t r0 = (int32_t)(g * grows);
                                 const int32_t r1 = (int32_t)std::min<int64_t>(t.nrows, r0 + grows);
-                                items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB, hf, 0,
-                                                         gcm[g]});
+                                items.push_back(GramItem{t.src, pel, t.ld, t.ncols, r0, r1, I * TB, J * TB, hf,
+                                                         cls == 0 ? 1 : 0, gcm[g]});
                                 pel += (int64_t)TB * TB;
-                                if (tcg && mma_flops) {   // 36 digit products of 128 x 64 real columns
+                                if (tcg && mma_flops) {   // 36 digit products of the real columns
                                     const double mi = 2.0 * std::min(TB, t.ncols - I * TB);
-                                    const double nj = std::min(TB, t.ncols - J * TB);
-                                    *mma_flops += 2.0 * 36.0 * mi * nj * (r1 - r0);
+                                    const double nj = (cls == 0 ? 2.0 : 1.0) * std::min(TB, t.ncols - J * TB);
+                                    mma_flops[cls] += 2.0 * 36.0 * mi * nj * (r1 - r0);
                                 }
                             }
                 gel += (int64_t)t.ncols * t.ncols;
@@ -3577,9 +3640,7 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
             upload_vec(dc, ct, s);
             DBuf<cx<double>> scr((size_t)(pel + gel));
             ev.begin(cls == 0 ? K_TSQR_NARROW : K_TSQR, s);
-            if (cls == 0) {
-                k_gram64<2, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
-            } else if (tcg) {
+            if (tcg) {
                 if constexpr (std::is_same<TS, float>::value) {
                     DBuf<ColMaxTask> dcm;
                     upload_vec(dcm, cmt, s);
@@ -3591,6 +3652,8 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                     k_gram_slices<<<(unsigned)items.size(), 288, gram_tc::kSmemBytes, s>>>(di.p, src, cmb.p, scr.p,
                                                                                           err);
                 }
+            } else if (cls == 0) {
+                k_gram64<2, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
             } else {
                 k_gram64<4, TS><<<(unsigned)items.size(), 256, 0, s>>>(di.p, src, scr.p, err);
             }
@@ -3628,7 +3691,7 @@ void Num<T>::tsqr(const std::vector<QRTask>& tasks, const cx<T>* src, cx<T>* dst
     }
     if (rest.empty()) return;
     if (chol_qr()) {
-        chol_qr_launch<T, T>(rest, src, dst, s, ev_, err_.p, gram_slices(), &gram_mma_flops_);
+        chol_qr_launch<T, T>(rest, src, dst, s, ev_, err_.p, gram_slices(), gram_mma_flops_);
         return;
     }
     const bool fp64 = std::is_same<T, double>::value || bp_.qr_fp64;
@@ -4529,8 +4592,10 @@ void Num<T>::build(cudaStream_t s) {
     info.kernel_work_kind[K_TRUNCATE] = (std::is_same<T, double>::value || bp_.svd_fp64) ? W_FLOP64 : W_FLOP32;
     info.kernel_work_kind[K_LEAF_ORTH] = wqr;
     info.kernel_work_kind[K_TSQR_NARROW] = info.kernel_work_kind[K_TSQR];
-    if (gram_slices()) {   // the wide Gram tiles ran on the tensor cores: their BF16 work
-        info.kernel_work[K_TSQR] = gram_mma_flops_;
+    if (gram_slices()) {   // the Gram tiles ran on the tensor cores: their BF16 work
+        info.kernel_work[K_TSQR_NARROW] = gram_mma_flops_[0];
+        info.kernel_work[K_TSQR] = gram_mma_flops_[1];
+        info.kernel_work_kind[K_TSQR_NARROW] = W_FLOP_BF16;
         info.kernel_work_kind[K_TSQR] = W_FLOP_BF16;
     }
     info.kernel_work_kind[K_WQR_CHOL] = W_FLOP64;

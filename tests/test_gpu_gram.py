@@ -55,7 +55,7 @@ def _exact_gram(re, im, k, cols):
 
 
 @pytest.mark.parametrize("rows,cols,ld", [(5000, 125, 125), (2100, 216, 216), (777, 40, 48), (4099, 64, 64),
-                                          (3000, 32, 32), (300, 100, 128)])
+                                          (3000, 32, 32), (300, 100, 128), (2500, 17, 24), (6000, 5, 5)])
 @pytest.mark.parametrize("gram_tc", [1, 0])
 def test_gram_exact_on_integer_data(rows, cols, ld, gram_tc):
     import torch
@@ -79,7 +79,7 @@ def _float_matrix(rows, cols, seed):
     return z.astype(np.complex64)
 
 
-@pytest.mark.parametrize("rows,cols", [(3000, 125), (1500, 216), (5000, 64), (600, 33)])
+@pytest.mark.parametrize("rows,cols", [(3000, 125), (1500, 216), (5000, 64), (600, 33), (4000, 32), (2000, 9)])
 def test_gram_tc_error_bound_on_float_data(rows, cols):
     import torch
 
@@ -130,9 +130,12 @@ def test_build_with_either_gram(name):
     tree = dh2.Tree(v, f, leaf_max=p["leaf"])
     mats = [dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"], gram_tc=t) for t in (1, 0)]
     info = mats[0].get_info()
+    # K_TSQR (wide stacks) and K_TSQR_NARROW (at most 32 columns) on the tensor cores or in FP64
     assert info.kernel_work_kind[5] == 4 and mats[1].get_info().kernel_work_kind[5] == 2
-    # where wide stacks taller than wide occurred, their Gram ran on the tensor cores
+    assert info.kernel_work_kind[13] == 4 and mats[1].get_info().kernel_work_kind[13] == 2
+    # where stacks taller than wide occurred, their Gram ran on the tensor cores
     assert (info.kernel_launches[5] > 0) == (info.kernel_work[5] > 0)
+    assert (info.kernel_launches[13] > 0) == (info.kernel_work[13] > 0)
     (r1, c1), (r0, c0) = mats[0].ranks(), mats[1].ranks()
     assert np.mean(r1 != r0) <= 0.01 and np.mean(c1 != c0) <= 0.01
     x = torch.from_numpy(x_vector(tree.n)).to(torch.complex64).cuda()
