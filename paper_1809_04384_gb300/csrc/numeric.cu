@@ -418,7 +418,9 @@ struct BlockRowTask {
 // Every operand is split into TF32 hi + lo and each real product is hi*hi + hi*lo + lo*hi.
 // K runs in chunks of KC: the operands of a chunk are generated into shared memory
 // (K-major core-matrix layout, see tcgen05.cuh) once the tensor cores are done with the
-// previous chunk; one thread issues the chunk's MMAs and commits them to an mbarrier.
+// previous chunk; one thread issues the chunk's MMAs and commits them to an mbarrier.  (Two
+// buffers, with or without block-wide barriers per chunk, measured slower: the chunk has to
+// shrink to 16 to fit them, and the generation of the couplings, not the MMAs, bounds it.)
 template <int NT>
 struct TcTile {
     static constexpr int KC = NT <= 128 ? 32 : 16;
@@ -453,21 +455,37 @@ __device__ __forceinline__ void tc_operands(float* buf, float*& A1h, float*& A1l
 }
 
 // D (TMEM columns [col0, col0 + NT)) = sum over K chunks of the generated operands.
-// genA(mu0, A1h, A1l, A2h, A2l) and genB(mu0, B1h, B1l, B2h, B2l) fill one chunk; they are
-// called by every thread of the block.  All threads of the block must call this.
+// gen.load(mu0, regs) fetches what a chunk needs from global memory into registers (the
+// next chunk's fetch is in flight while this chunk's operands are formed); gen(mu0, regs,
+// X1h, X1l, X2h, X2l) fills the chunk.  Both are called by every thread of the block.  All
+// threads of the block must call this.
 template <int NT, class GA, class GB>
 __device__ void tc_product(TcState& st, uint32_t col0, int K, const GA& genA, const GB& genB) {
     constexpr int KC = TcTile<NT>::KC;
     float *A1h, *A1l, *A2h, *A2l, *B1h, *B1l, *B2h, *B2l;
     tc_operands<NT>(st.buf, A1h, A1l, A2h, A2l, B1h, B1l, B2h, B2l);
     const int nchunks = (K + KC - 1) / KC;
+    typename GA::Regs ra;
+    typename GB::Regs rb;
+    if (nchunks > 0) {
+        genA.load(0, ra);
+        genB.load(0, rb);
+    }
     for (int ch = 0; ch < nchunks && st.ok; ++ch) {
+        typename GA::Regs na;
+        typename GB::Regs nb;
+        if (ch + 1 < nchunks) {
+            genA.load((ch + 1) * KC, na);
+            genB.load((ch + 1) * KC, nb);
+        }
         if (st.phase > 0) {   // the tensor cores are done with the previous operands
             st.ok = __syncthreads_and(tc::mbar_wait(st.mbar, (st.phase - 1) & 1, kTcWaitPolls));
             if (!st.ok) break;
         }
-        genA(ch * KC, A1h, A1l, A2h, A2l);
-        genB(ch * KC, B1h, B1l, B2h, B2l);
+        genA(ch * KC, ra, A1h, A1l, A2h, A2l);
+        genB(ch * KC, rb, B1h, B1l, B2h, B2l);
+        ra = na;
+        rb = nb;
         tc::fence_async_smem();
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -543,6 +561,64 @@ __device__ __forceinline__ cx<float> coupling_value(float4 p, float4 q, float ka
     return cx<float>{cs * f, sn * f};
 }
 
+// Two FP32 lanes per instruction (Blackwell packed arithmetic, round to nearest per lane).
+namespace f2 {
+__device__ __forceinline__ uint64_t pk(float a, float b) {
+    return (uint64_t)__float_as_uint(a) | ((uint64_t)__float_as_uint(b) << 32);
+}
+__device__ __forceinline__ float lo(uint64_t x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float hi(uint64_t x) { return __uint_as_float((uint32_t)(x >> 32)); }
+__device__ __forceinline__ uint64_t add(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+}  // namespace f2
+
+// coupling_value for the two column nodes q0, q1 of one row node p, two lanes at a time; the
+// same steps (the phase reduction's rint as (x + 1.5 * 2^23) - 1.5 * 2^23, equal for |x| < 2^22)
+__device__ __forceinline__ void coupling_pair(float4 p, float4 q0, float4 q1, float kappa, cx<float>& v0,
+                                              cx<float>& v1) {
+    constexpr double k2pi = 2.0 * kPi;
+    constexpr float hi = (float)k2pi;
+    constexpr float lo = (float)(k2pi - (double)hi);
+    constexpr float kRound = 12582912.0f;
+    const uint64_t dx = f2::sub(f2::pk(p.x, p.x), f2::pk(q0.x, q1.x));
+    const uint64_t dy = f2::sub(f2::pk(p.y, p.y), f2::pk(q0.y, q1.y));
+    const uint64_t dz = f2::sub(f2::pk(p.z, p.z), f2::pk(q0.z, q1.z));
+    const uint64_t r2 = f2::fma(dx, dx, f2::fma(dy, dy, f2::mul(dz, dz)));
+    const uint64_t ri = f2::pk(rsqrtf(f2::lo(r2)), rsqrtf(f2::hi(r2)));
+    const uint64_t w = f2::sub(f2::pk(p.w, p.w), f2::pk(q0.w, q1.w));
+    const uint64_t ph = f2::mul(f2::pk(kappa, kappa), f2::sub(f2::mul(r2, ri), w));
+    const uint64_t R2 = f2::pk(kRound, kRound);
+    const uint64_t j = f2::sub(f2::add(f2::mul(ph, f2::pk((float)(1.0 / k2pi), (float)(1.0 / k2pi))), R2), R2);
+    uint64_t red = f2::fma(j, f2::pk(-hi, -hi), ph);
+    red = f2::fma(j, f2::pk(-lo, -lo), red);
+    float s0, c0, s1, c1;
+    __sincosf(f2::lo(red), &s0, &c0);
+    __sincosf(f2::hi(red), &s1, &c1);
+    const float c4 = (float)(1.0 / (4.0 * kPi));
+    const uint64_t f = f2::mul(ri, f2::pk(c4, c4));
+    const uint64_t re = f2::mul(f2::pk(c0, c1), f), im = f2::mul(f2::pk(s0, s1), f);
+    v0 = cx<float>{f2::lo(re), f2::lo(im)};
+    v1 = cx<float>{f2::hi(re), f2::hi(im)};
+}
+
 template <int NT>
 struct GenS {
     const float4* P;   // 128 entries (row side: rows nu of this M tile)
@@ -550,7 +626,9 @@ struct GenS {
     int k;             // contraction length (columns mu)
     float kappa;
     int nk;            // rows of this M tile that exist (rows nu >= nk are zero)
-    __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
+    struct Regs {};
+    __device__ void load(int, Regs&) const {}
+    __device__ void operator()(int mu0, const Regs&, float* A1h, float* A1l, float* A2h, float* A2l) const {
         constexpr int KC = TcTile<NT>::KC;
         constexpr int GROUPS = KC / 4;                          // 4-wide groups of a chunk
         constexpr int IT = 128 * GROUPS / kThreads;             // the block has kThreads threads
@@ -562,12 +640,16 @@ struct GenS {
             float4 h1, l1, h2, l2;
             float* ph1 = &h1.x; float* pl1 = &l1.x; float* ph2 = &h2.x; float* pl2 = &l2.x;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int mu = mu0 + 4 * g + e;
-                cx<float> v = zero<float>();
-                if (nu < nk && mu < k) v = coupling_value(p, Q[mu], kappa);
-                tc::split_tf32(v.x, ph1[e], pl1[e]);
-                tc::split_tf32(v.y, ph2[e], pl2[e]);
+            for (int e = 0; e < 4; e += 2) {   // two columns per packed evaluation
+                const int mu = mu0 + 4 * g + e;   // Q holds 256 entries: mu + 1 < 256 is in range
+                cx<float> v0, v1;
+                coupling_pair(p, Q[mu], Q[mu + 1], kappa, v0, v1);
+                if (!(nu < nk && mu < k)) v0 = zero<float>();
+                if (!(nu < nk && mu + 1 < k)) v1 = zero<float>();
+                tc::split_tf32(v0.x, ph1[e], pl1[e]);
+                tc::split_tf32(v0.y, ph2[e], pl2[e]);
+                tc::split_tf32(v1.x, ph1[e + 1], pl1[e + 1]);
+                tc::split_tf32(v1.y, ph2[e + 1], pl2[e + 1]);
             }
             const int off = tc::kmaj_off(nu, 4 * g, 128);
             *reinterpret_cast<float4*>(A1h + off) = h1;
@@ -610,21 +692,24 @@ template <int NT>
 struct GenRowsA {
     const cx<float>* X;
     int rows, ld, kmax;
-    __device__ void operator()(int mu0, float* A1h, float* A1l, float* A2h, float* A2l) const {
-        constexpr int KC = TcTile<NT>::KC;
-        constexpr int IT = 128 * KC / kThreads;
+    static constexpr int IT = 128 * TcTile<NT>::KC / kThreads;
+    struct Regs {
         cx<float> v[IT];
+    };
+    __device__ void load(int mu0, Regs& r) const {
 #pragma unroll
         for (int it = 0; it < IT; ++it) {   // all loads of the chunk in flight together
             const int idx = threadIdx.x + it * kThreads, core = idx >> 5, w = idx & 31;
             const int a = (core & 15) * 8 + (w >> 2), mu = mu0 + (core >> 4) * 4 + (w & 3);
-            v[it] = (a < rows && mu < kmax) ? X[(int64_t)a * ld + mu] : zero<float>();
+            r.v[it] = (a < rows && mu < kmax) ? X[(int64_t)a * ld + mu] : zero<float>();
         }
+    }
+    __device__ void operator()(int, const Regs& r, float* A1h, float* A1l, float* A2h, float* A2l) const {
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
             const int idx = threadIdx.x + it * kThreads;
-            tc::split_tf32(v[it].x, A1h[idx], A1l[idx]);
-            tc::split_tf32(v[it].y, A2h[idx], A2l[idx]);
+            tc::split_tf32(r.v[it].x, A1h[idx], A1l[idx]);
+            tc::split_tf32(r.v[it].y, A2h[idx], A2l[idx]);
         }
     }
 };
@@ -636,21 +721,26 @@ struct GenRowsB {
     const cx<float>* Rm;
     int ro, k;
     float s;
-    __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
-        constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
-        constexpr int IT = RP * KC / kThreads;
+    static constexpr int IT = TcTile<NT>::RP * TcTile<NT>::KC / kThreads;
+    struct Regs {
         cx<float> rv[IT];
+    };
+    __device__ void load(int mu0, Regs& r) const {
+        constexpr int RP = TcTile<NT>::RP;
 #pragma unroll
         for (int it = 0; it < IT; ++it) {   // all loads of the chunk in flight together
             const int idx = threadIdx.x + it * kThreads, core = idx >> 5, w = idx & 31;
             const int i = (core % (RP / 8)) * 8 + (w >> 2), mu = mu0 + (core / (RP / 8)) * 4 + (w & 3);
-            rv[it] = (i < ro && mu < k) ? Rm[(int64_t)i * k + mu] : zero<float>();
+            r.rv[it] = (i < ro && mu < k) ? Rm[(int64_t)i * k + mu] : zero<float>();
         }
+    }
+    __device__ void operator()(int, const Regs& regs, float* B1h, float* B1l, float* B2h, float* B2l) const {
+        constexpr int RP = TcTile<NT>::RP;
 #pragma unroll
         for (int it = 0; it < IT; ++it) {
             const int idx = threadIdx.x + it * kThreads, core = idx >> 5, w = idx & 31;
             const int i = (core % (RP / 8)) * 8 + (w >> 2), kk = (core / (RP / 8)) * 4 + (w & 3);
-            const cx<float> r = rv[it];
+            const cx<float> r = regs.rv[it];
             const int o0 = tc::kmaj_off_pad(i, kk, NT), o1 = tc::kmaj_off_pad(i + RP, kk, NT);
             tc::split_tf32(r.x, B1h[o0], B1l[o0]);
             tc::split_tf32(r.y, B1h[o1], B1l[o1]);
@@ -672,7 +762,9 @@ struct GenFromTmem {
     uint32_t d1;   // TMEM address of D1 (lane 0, first column); rows nu >= 128 in the next NT columns
     int ro;
     bool conj_d;
-    __device__ void operator()(int mu0, float* B1h, float* B1l, float* B2h, float* B2l) const {
+    struct Regs {};
+    __device__ void load(int, Regs&) const {}
+    __device__ void operator()(int mu0, const Regs&, float* B1h, float* B1l, float* B2h, float* B2l) const {
         constexpr int KC = TcTile<NT>::KC, RP = TcTile<NT>::RP;
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int z = mu0 >> 7;                 // M tile of D1 holding rows mu0 ... (KC divides 128)
@@ -845,7 +937,7 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
     cx<T>* out = stack + tk.dst;
     if constexpr (NT > 0) {
         // node tables (2 x 128 float4), then the tensor-core operands on a 128-byte boundary
-        __shared__ __align__(8) uint64_t tc_mbar;
+        __shared__ __align__(8) uint64_t tc_mbar[1];
         __shared__ uint32_t tc_tmem;
         float4* Ptab = reinterpret_cast<float4*>(
             (reinterpret_cast<uintptr_t>(smraw) + 127) & ~uintptr_t(127));
@@ -853,7 +945,7 @@ __global__ void __launch_bounds__(256, 2) k_stack_blocks(const BlockRowTask* __r
         float* tcbuf = reinterpret_cast<float*>(Qtab + 256);
         load_node_tables(t, s, cd, nodes, m, rows_pass || tk.own_leaf == 2, Ptab, Qtab);
         stack_blocks_tc<NT>(tk, rows_pass, Ptab, Qtab, (float)kappa, k, Ro, ro, R, roff, rrows, bnorm, out, Kst,
-                            tcbuf, &tc_mbar, &tc_tmem, red, err);
+                            tcbuf, tc_mbar, &tc_tmem, red, err);
         return;
     }
     const SGen<T> S = load_sgen_tables<T>(t, s, cd, nodes, m, kappa, smraw);
@@ -2283,7 +2375,7 @@ __global__ void __launch_bounds__(256, 2) k_project_tc(const ProjTask* __restric
                                                        const cx<float>* __restrict__ Ccol, cx<float>* Stilde,
                                                        unsigned* err) {
     extern __shared__ unsigned char smraw[];
-    __shared__ __align__(8) uint64_t tc_mbar;
+    __shared__ __align__(8) uint64_t tc_mbar[1];
     __shared__ uint32_t tc_tmem;
     constexpr int RP = TcTile<NT>::RP;
     const ProjTask tk = tasks[blockIdx.x];
@@ -2301,7 +2393,7 @@ __global__ void __launch_bounds__(256, 2) k_project_tc(const ProjTask* __restric
     const int nz = k > 128 ? 2 : 1, ny = ks > 128 ? 2 : 1;
     const uint32_t ncols = (uint32_t)(2 * nz * NT);
     TcState st;
-    tc_begin<NT>(st, tcbuf, &tc_mbar, &tc_tmem, ncols);
+    tc_begin<NT>(st, tcbuf, tc_mbar, &tc_tmem, ncols);
     for (int z = 0; z < nz; ++z)
         tc_product<NT>(st, (uint32_t)(z * NT), k, GenS<NT>{Ptab + 128 * z, Qtab, k, (float)kappa, k - 128 * z},
                        GenRowsB<NT>{Crow + tk.crow, kt, k, -1.0f});
