@@ -544,22 +544,6 @@ __device__ void tc_end(TcState& st, unsigned* err, uint32_t ncols = 2 * NT) {
 // FP64, so that x_P - x_Q keeps full relative accuracy), and w = +-<node - ref, c> such that
 // <xi_t - xi_s, c> = P.w - Q.w.  Each thread keeps one row nu and writes four consecutive
 // mu with one 16-byte store per operand array.
-__device__ __forceinline__ cx<float> coupling_value(float4 p, float4 q, float kappa) {
-    const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-    constexpr double k2pi = 2.0 * kPi;
-    constexpr float hi = (float)k2pi;
-    constexpr float lo = (float)(k2pi - (double)hi);
-    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ri = rsqrtf(r2);
-    const float ph = kappa * (r2 * ri - (p.w - q.w));
-    const float j = rintf(ph * (float)(1.0 / k2pi));
-    float red = fmaf(-j, hi, ph);
-    red = fmaf(-j, lo, red);
-    float sn, cs;
-    __sincosf(red, &sn, &cs);
-    const float f = ri * (float)(1.0 / (4.0 * kPi));
-    return cx<float>{cs * f, sn * f};
-}
 
 // Two FP32 lanes per instruction (Blackwell packed arithmetic, round to nearest per lane).
 namespace f2 {
@@ -590,8 +574,10 @@ __device__ __forceinline__ uint64_t fma(uint64_t a, uint64_t b, uint64_t c) {
 }
 }  // namespace f2
 
-// coupling_value for the two column nodes q0, q1 of one row node p, two lanes at a time; the
-// same steps (the phase reduction's rint as (x + 1.5 * 2^23) - 1.5 * 2^23, equal for |x| < 2^22)
+// The coupling values S(p, q0), S(p, q1) of one row node p, two lanes at a time:
+// exp(i kappa (r - <xi_p - xi_q, c>)) / (4 pi r), r = |x_p - x_q| by rsqrt, the phase reduced
+// by the two-constant Cody-Waite reduction with 2 pi (rint as (x + 1.5 * 2^23) - 1.5 * 2^23,
+// exact for |x| < 2^22) before the hardware sine and cosine.
 __device__ __forceinline__ void coupling_pair(float4 p, float4 q0, float4 q1, float kappa, cx<float>& v0,
                                               cx<float>& v1) {
     constexpr double k2pi = 2.0 * kPi;
@@ -1793,36 +1779,52 @@ struct CholTask {
 // Pivot threshold relative to the largest diagonal entry of G: the Gram carries absolute
 // rounding errors of a few u_64 |Z|^2, so smaller remaining pivots are rounding noise.
 constexpr double kCholPivotTol = 16.0 * 2.220446049250313e-16;
+constexpr int kCholPanel = 8;   // pivots per panel of the blocked Cholesky
 
+// G (upper triangle) of every stack = the sum of its row groups' partial tiles, in group
+// order; grid (element blocks, stacks)
+template <int TB>
+__global__ void k_gram_sum(const CholTask* __restrict__ tasks, const cx<double>* __restrict__ part,
+                           cx<double>* __restrict__ gscr) {
+    const CholTask tk = tasks[blockIdx.y];
+    const int c = tk.ncols, nt = tk.ntile, ng = tk.ngroups;
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)c * c) return;
+    const int i = (int)(idx / c), j = (int)(idx - (int64_t)i * c);
+    if (i > j) return;
+    const int I = i / TB, J = j / TB;
+    const int pr = I * nt - (I * (I - 1)) / 2 + (J - I);   // index of tile pair (I, J), I <= J
+    const cx<double>* P = part + tk.part + ((int64_t)pr * ng) * TB * TB + (i - I * TB) * TB + (j - J * TB);
+    cx<double> v = zero<double>();
+    for (int g = 0; g < ng; ++g) v = v + P[(int64_t)g * TB * TB];
+    gscr[tk.g + idx] = v;
+}
+
+// Pivoted Cholesky of G (upper triangle in gscr, original column order), in panels of
+// kCholPanel pivots: within a panel, row j of R is row p_j of G corrected by the panel's
+// earlier rows (left-looking) and the remaining diagonal is updated at once; after the panel
+// the trailing upper triangle of the remaining columns takes one rank-kCholPanel update
+// (right-looking), row by row with consecutive columns per warp.  The panel's rows live in
+// shared memory (dynamic: kCholPanel x c complex values).
 template <int TB, class TDst>
 __global__ void __launch_bounds__(256) k_pchol64(const CholTask* __restrict__ tasks, const cx<double>* __restrict__ part,
                                                  cx<double>* __restrict__ gscr, cx<TDst>* __restrict__ dst,
                                                  unsigned* err) {
-    constexpr int CMAX = 512;
-    __shared__ double s_d[CMAX];
-    __shared__ int s_perm[CMAX];
-    __shared__ cx<double> s_w[CMAX];
+    constexpr int CMAX = 512, NB = kCholPanel;
+    __shared__ double s_d[CMAX];            // diagonal of the remaining Schur complement
+    __shared__ unsigned char s_rem[CMAX];   // 1 while the column is not a pivot
     __shared__ double s_rv[32];
     __shared__ int s_ri[32];
     __shared__ double s_tol;
+    extern __shared__ cx<double> s_W[];     // NB x c: the panel's rows of R
     const CholTask tk = tasks[blockIdx.x];
-    const int c = tk.ncols, nt = tk.ntile, ng = tk.ngroups;
-    cx<double>* G = gscr + tk.g;
+    const int c = tk.ncols;
+    cx<double>* G = gscr + tk.g;   // upper triangle summed by k_gram_sum
     cx<TDst>* R = dst + tk.dst;
-    // G (upper triangle) = sum of the row groups' partial tiles, in group order
-    for (int idx = threadIdx.x; idx < c * c; idx += blockDim.x) {
-        const int i = idx / c, j = idx - i * c;
-        if (i > j) continue;
-        const int I = i / TB, J = j / TB;
-        const int pr = I * nt - (I * (I - 1)) / 2 + (J - I);   // index of tile pair (I, J), I <= J
-        const cx<double>* P = part + tk.part + ((int64_t)pr * ng) * TB * TB + (i - I * TB) * TB + (j - J * TB);
-        cx<double> v = zero<double>();
-        for (int g = 0; g < ng; ++g) v = v + P[(int64_t)g * TB * TB];
-        G[idx] = v;
+    for (int l = threadIdx.x; l < c; l += blockDim.x) {
+        s_rem[l] = 1;
+        s_d[l] = G[(int64_t)l * c + l].x;
     }
-    for (int l = threadIdx.x; l < c; l += blockDim.x) s_perm[l] = l;
-    __syncthreads();
-    for (int l = threadIdx.x; l < c; l += blockDim.x) s_d[l] = G[(int64_t)l * c + l].x;
     __syncthreads();
     if (threadIdx.x == 0) {
         double m = 0.0;
@@ -1831,86 +1833,92 @@ __global__ void __launch_bounds__(256) k_pchol64(const CholTask* __restrict__ ta
     }
     __syncthreads();
     const double tol = s_tol;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     int j = 0;
-    for (; j < tk.rout; ++j) {
-        // pivot: the largest remaining diagonal entry (lowest position on ties)
-        double bv = -1.0;
-        int bp = c;
-        for (int l = j + threadIdx.x; l < c; l += blockDim.x) {
-            const double v = s_d[l];
-            if (!(v == v)) raise_err(err, ERR_TSQR_NONFINITE);
-            if (v > bv) {
-                bv = v;
-                bp = l;
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-            const int op = __shfl_xor_sync(0xffffffffu, bp, o);
-            if (ov > bv || (ov == bv && op < bp)) {
-                bv = ov;
-                bp = op;
-            }
-        }
-        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-        if (lane == 0) {
-            s_rv[w] = bv;
-            s_ri[w] = bp;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double v = s_rv[0];
-            int p = s_ri[0];
-            for (int q = 1; q < (int)(blockDim.x >> 5); ++q)
-                if (s_rv[q] > v || (s_rv[q] == v && s_ri[q] < p)) {
-                    v = s_rv[q];
-                    p = s_ri[q];
+    bool done = false;
+    while (j < tk.rout && !done) {
+        int i = 0;   // rows of this panel
+        for (; i < NB && j < tk.rout; ++i, ++j) {
+            // pivot: the largest remaining diagonal entry (lowest column on ties)
+            double bv = -1.0;
+            int bp = c;
+            for (int a = threadIdx.x; a < c; a += blockDim.x) {
+                if (!s_rem[a]) continue;
+                const double v = s_d[a];
+                if (!(v == v)) raise_err(err, ERR_TSQR_NONFINITE);
+                if (v > bv) {
+                    bv = v;
+                    bp = a;
                 }
-            s_rv[0] = v;
-            s_ri[0] = p;
-            if (v > tol && p < c) {   // swap positions j and p
-                const int t = s_perm[j];
-                s_perm[j] = s_perm[p];
-                s_perm[p] = t;
-                const double dt = s_d[j];
-                s_d[j] = s_d[p];
-                s_d[p] = dt;
             }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+                const int op = __shfl_xor_sync(0xffffffffu, bp, o);
+                if (ov > bv || (ov == bv && op < bp)) {
+                    bv = ov;
+                    bp = op;
+                }
+            }
+            if (lane == 0) {
+                s_rv[warp] = bv;
+                s_ri[warp] = bp;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double v = s_rv[0];
+                int p = s_ri[0];
+                for (int q = 1; q < nw; ++q)
+                    if (s_rv[q] > v || (s_rv[q] == v && s_ri[q] < p)) {
+                        v = s_rv[q];
+                        p = s_ri[q];
+                    }
+                s_rv[0] = v;
+                s_ri[0] = p;
+                if (v > tol && p < c) s_rem[p] = 0;
+            }
+            __syncthreads();
+            if (!(s_rv[0] > tol)) {   // the rest of G is rounding noise (or the stack is exhausted)
+                done = true;
+                break;
+            }
+            const int p = s_ri[0];
+            const double rjj = sqrt(s_rv[0]), inv = 1.0 / rjj;
+            cx<double>* W = s_W + (int64_t)i * c;
+            for (int a = threadIdx.x; a < c; a += blockDim.x) {
+                cx<double> v = zero<double>();
+                if (a == p) {
+                    v = cx<double>{rjj, 0.0};
+                } else if (s_rem[a]) {
+                    // G'(p, a): this panel's earlier rows are not yet in G
+                    v = p <= a ? G[(int64_t)p * c + a] : conj(G[(int64_t)a * c + p]);
+                    for (int i2 = 0; i2 < i; ++i2) {
+                        const cx<double> wp = s_W[(int64_t)i2 * c + p];
+                        fma_cjx(v, cx<double>{-wp.x, -wp.y}, s_W[(int64_t)i2 * c + a]);
+                    }
+                    v = inv * v;
+                    s_d[a] -= v.x * v.x + v.y * v.y;
+                }
+                W[a] = v;
+                R[(int64_t)j * c + a] = cx<TDst>{TDst(v.x), TDst(v.y)};
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (!(s_rv[0] > tol)) break;   // the rest of G is rounding noise (or the stack is exhausted)
-        const int pj = s_perm[j];
-        const double rjj = sqrt(s_d[j]), inv = 1.0 / rjj;
-        // row j of R: w_l = G'(pj, perm l) / r_jj for positions l > j
-        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
-            const int a = s_perm[l];
-            const cx<double> gv = pj <= a ? G[(int64_t)pj * c + a] : conj(G[(int64_t)a * c + pj]);
-            s_w[l] = inv * gv;
-        }
-        __syncthreads();
-        for (int col = threadIdx.x; col < c; col += blockDim.x) R[(int64_t)j * c + col] = zero<TDst>();
-        __syncthreads();
-        if (threadIdx.x == 0) R[(int64_t)j * c + pj] = cx<TDst>{TDst(rjj), TDst(0)};
-        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
-            const cx<double> v = s_w[l];
-            R[(int64_t)j * c + s_perm[l]] = cx<TDst>{TDst(v.x), TDst(v.y)};
-        }
-        // Schur complement: G'(a, b) -= conj(w_a) w_b on the upper triangle, positions > j
-        const int rem = c - j - 1;
-        for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
-            const int l = j + 1 + idx / rem, m = j + 1 + idx % rem;
-            const int a = s_perm[l], b = s_perm[m];
-            if (a > b) continue;
-            cx<double>& g = G[(int64_t)a * c + b];
-            cx<double> v = g;
-            fma_cjx(v, cx<double>{-s_w[l].x, -s_w[l].y}, s_w[m]);
-            g = v;
-        }
-        __syncthreads();
-        for (int l = j + 1 + threadIdx.x; l < c; l += blockDim.x) {
-            const int a = s_perm[l];
-            s_d[l] = G[(int64_t)a * c + a].x;
+        if (done || i == 0 || j >= tk.rout) break;
+        // trailing update of the remaining columns: G(a, b) -= sum_i conj(W_i(a)) W_i(b), a <= b
+        for (int a = warp; a < c; a += nw) {
+            if (!s_rem[a]) continue;
+            cx<double> wa[NB];
+#pragma unroll
+            for (int i2 = 0; i2 < NB; ++i2) wa[i2] = i2 < i ? s_W[(int64_t)i2 * c + a] : zero<double>();
+            for (int b = a + lane; b < c; b += 32) {
+                if (!s_rem[b]) continue;
+                cx<double> g = G[(int64_t)a * c + b];
+#pragma unroll
+                for (int i2 = 0; i2 < NB; ++i2)
+                    if (i2 < i) fma_cjx(g, cx<double>{-wa[i2].x, -wa[i2].y}, s_W[(int64_t)i2 * c + b]);
+                G[(int64_t)a * c + b] = g;
+            }
         }
         __syncthreads();
     }
@@ -3695,7 +3703,7 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
                 const int ng = (int)((t.nrows + grows - 1) / grows);
                 const int64_t tp = (int64_t)nt * (nt + 1) / 2;
                 const int64_t need = tp * ng * halves * TB * TB + (int64_t)t.ncols * t.ncols;
-                if (i1 > i0 && pel + gel + need > kScratchElems) break;
+                if (i1 > i0 && (pel + gel + need > kScratchElems || ct.size() >= 65535)) break;
                 CholTask c{pel, gel, t.dst, t.ncols, t.rout, nt, ng * halves};
                 std::vector<int64_t> gcm(ng, 0);
                 if (tcg)
@@ -3752,10 +3760,22 @@ void chol_qr_launch(const std::vector<QRTask>& tasks, const cx<TS>* src, cx<TD>*
             ev.end(s);
             DH2_CHECK_LAUNCH(tcg ? "k_gram_slices" : "k_gram64");
             ev.begin(K_WQR_CHOL, s);
-            if (cls == 0)
-                k_pchol64<32, TD><<<(unsigned)ct.size(), 256, 0, s>>>(dc.p, scr.p, scr.p, dst, err);
-            else
-                k_pchol64<64, TD><<<(unsigned)ct.size(), 256, 0, s>>>(dc.p, scr.p, scr.p, dst, err);
+            int cmax = 1;
+            for (const CholTask& c : ct) cmax = std::max(cmax, (int)c.ncols);
+            const size_t psm = (size_t)kCholPanel * cmax * sizeof(cx<double>);
+            {   // the Gram matrices from the partial tiles, all stacks at once (ct.size() < 65536 per launch)
+                const dim3 grid((unsigned)((int64_t(cmax) * cmax + 255) / 256), (unsigned)ct.size());
+                if (cls == 0) k_gram_sum<32><<<grid, 256, 0, s>>>(dc.p, scr.p, scr.p);
+                else k_gram_sum<64><<<grid, 256, 0, s>>>(dc.p, scr.p, scr.p);
+                DH2_CHECK_LAUNCH("k_gram_sum");
+            }
+            if (cls == 0) {
+                ensure_smem(reinterpret_cast<const void*>(k_pchol64<32, TD>), psm);
+                k_pchol64<32, TD><<<(unsigned)ct.size(), 256, psm, s>>>(dc.p, scr.p, scr.p, dst, err);
+            } else {
+                ensure_smem(reinterpret_cast<const void*>(k_pchol64<64, TD>), psm);
+                k_pchol64<64, TD><<<(unsigned)ct.size(), 256, psm, s>>>(dc.p, scr.p, scr.p, dst, err);
+            }
             ev.end(s);
             DH2_CHECK_LAUNCH("k_pchol64");
             if (gram_out) {   // the summed Gram matrix of the (single) stack, both triangles
