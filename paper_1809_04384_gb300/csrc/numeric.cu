@@ -16,7 +16,9 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <exception>
 #include <mutex>
+#include <thread>
 #include <array>
 #include <string>
 
@@ -2955,6 +2957,7 @@ public:
             if (g.exec) cudaGraphExecDestroy(g.exec);
         if (capture_stream_) cudaStreamDestroy(capture_stream_);
         if (side_stream_) cudaStreamDestroy(side_stream_);
+        if (near_stream_) cudaStreamDestroy(near_stream_);
         if (fork_ev_) cudaEventDestroy(fork_ev_);
         if (join_ev_) cudaEventDestroy(join_ev_);
     }
@@ -3087,7 +3090,9 @@ private:
     void mirror_truncation(cudaStream_t s);
     bool capped_[2] = {false, false};
     void analytic(cudaStream_t s);
-    void nearfield(cudaStream_t s);
+    void nearfield(cudaStream_t s, EventLog& ev);
+    void build_recompression(cudaStream_t s, StageTimer& tm);
+    void finish_info();
     void basis_weights(cudaStream_t s);
     void basis_weights_of(bool col, cudaStream_t s);
     void total_weights(int pass, cudaStream_t s);
@@ -3103,6 +3108,7 @@ private:
     };
     MatvecGraph graph_[2];          // complex64, complex128 vectors
     cudaStream_t capture_stream_ = nullptr, side_stream_ = nullptr;
+    cudaStream_t near_stream_ = nullptr;   // the nearfield stage, concurrent with the recompression
     bool kstore_ = true;            // K_b kept for the column pass / leaf-pair projection
     KbHold kb_hold_;                // this build's share of the K_b stores of concurrent builds
     cudaEvent_t fork_ev_ = nullptr, join_ev_ = nullptr;
@@ -3408,7 +3414,7 @@ void Num<T>::analytic(cudaStream_t s) {
 // ----------------------------------------------------------------------------- nearfield
 
 template <class T>
-void Num<T>::nearfield(cudaStream_t s) {
+void Num<T>::nearfield(cudaStream_t s, EventLog& ev) {
     const auto& h = hs_;
     // leaves in offset order: the leaves below a cluster form a contiguous range
     leaf_order_.clear();
@@ -3502,7 +3508,7 @@ void Num<T>::nearfield(cudaStream_t s) {
     const int64_t chunk = 1 << 22;   // segments (CTAs) per launch
     for (int64_t b0 = 0; b0 < (int64_t)all.size(); b0 += chunk) {
         int64_t cnt = std::min<int64_t>(chunk, (int64_t)all.size() - b0);
-        ev_.begin(K_NEARFIELD, s);
+        ev.begin(K_NEARFIELD, s);
         if (dlp())
             k_nearfield<T, true><<<(unsigned)cnt, kThreads, 0, s>>>(dseg.p + b0, qr, tr_.perm.p, tr_.area.p, tr_.x3.p,
                                                                     tr_.x7.p, bp_.kappa, normals_.p, near_.p,
@@ -3511,7 +3517,7 @@ void Num<T>::nearfield(cudaStream_t s) {
             k_nearfield<T, false><<<(unsigned)cnt, kThreads, 0, s>>>(dseg.p + b0, qr, tr_.perm.p, tr_.area.p,
                                                                      tr_.x3.p, tr_.x7.p, bp_.kappa, nullptr, near_.p,
                                                                      colidx_.p);
-        ev_.end(s);
+        ev.end(s);
         DH2_CHECK_LAUNCH("k_nearfield");
     }
 }
@@ -4655,9 +4661,68 @@ void Num<T>::build(cudaStream_t s) {
     tm.begin(ST_ANALYTIC);
     analytic(s);
     tm.end(ST_ANALYTIC);
-    tm.begin(ST_NEARFIELD);
-    nearfield(s);
-    tm.end(ST_NEARFIELD);
+    // The nearfield (read only by the matvec plan) is planned on a host thread and computed on
+    // its own stream while the recompression runs; it starts after the analytic stage (the
+    // double layer's normals) and the matvec plan waits for it.
+    int dev = 0;
+    DH2_CHECK_CUDA(cudaGetDevice(&dev));
+    if (!near_stream_) DH2_CHECK_CUDA(cudaStreamCreateWithFlags(&near_stream_, cudaStreamNonBlocking));
+    struct Events {   // destroyed on every path out of the build
+        cudaEvent_t e[3] = {nullptr, nullptr, nullptr};
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs;
+    DH2_CHECK_CUDA(cudaEventCreateWithFlags(&evs.e[0], cudaEventDisableTiming));
+    DH2_CHECK_CUDA(cudaEventCreate(&evs.e[1]));
+    DH2_CHECK_CUDA(cudaEventCreate(&evs.e[2]));
+    cudaEvent_t nf_fork = evs.e[0], nf_t0 = evs.e[1], nf_t1 = evs.e[2];
+    DH2_CHECK_CUDA(cudaEventRecord(nf_fork, s));
+    DH2_CHECK_CUDA(cudaStreamWaitEvent(near_stream_, nf_fork, 0));
+    EventLog nf_ev;
+    std::exception_ptr nf_err;
+    {
+        struct Joiner {   // joined on every path out of this scope
+            std::thread t;
+            ~Joiner() {
+                if (t.joinable()) t.join();
+            }
+        } nf;
+        nf.t = std::thread([&] {
+            try {
+                DH2_CHECK_CUDA(cudaSetDevice(dev));
+                AllocScope scope(near_stream_);
+                DH2_CHECK_CUDA(cudaEventRecord(nf_t0, near_stream_));
+                nearfield(near_stream_, nf_ev);
+                DH2_CHECK_CUDA(cudaEventRecord(nf_t1, near_stream_));
+            } catch (...) {
+                nf_err = std::current_exception();
+            }
+        });
+        build_recompression(s, tm);
+        nf.t.join();
+    }
+    if (nf_err) std::rethrow_exception(nf_err);
+    DH2_CHECK_CUDA(cudaEventRecord(nf_fork, near_stream_));
+    DH2_CHECK_CUDA(cudaStreamWaitEvent(s, nf_fork, 0));
+    tm.begin(ST_MATVEC_PLAN);
+    plan_matvec(s);
+    tm.end(ST_MATVEC_PLAN);
+    tm.collect(info.stage_ms);
+    {
+        float ms = 0;
+        DH2_CHECK_CUDA(cudaEventElapsedTime(&ms, nf_t0, nf_t1));
+        info.stage_ms[ST_NEARFIELD] += ms;
+    }
+    ev_.recs.insert(ev_.recs.end(), nf_ev.recs.begin(), nf_ev.recs.end());
+    nf_ev.recs.clear();
+    finish_info();
+}
+
+// The recompression stages of the build (Section 3.2) and the projection, on stream s.
+template <class T>
+void Num<T>::build_recompression(cudaStream_t s, StageTimer& tm) {
     tm.begin(ST_BASIS_WEIGHTS);
     basis_weights(s);
     tm.end(ST_BASIS_WEIGHTS);
@@ -4688,10 +4753,11 @@ void Num<T>::build(cudaStream_t s) {
     tm.begin(ST_PROJECT);
     project_checked(s);
     tm.end(ST_PROJECT);
-    tm.begin(ST_MATVEC_PLAN);
-    plan_matvec(s);
-    tm.end(ST_MATVEC_PLAN);
-    tm.collect(info.stage_ms);
+}
+
+// kernel times and work of the finished build
+template <class T>
+void Num<T>::finish_info() {
     ev_.collect(info);
     const int32_t w32 = std::is_same<T, float>::value ? W_FLOP32 : W_FLOP64;
     const int32_t wqr = (std::is_same<T, double>::value || bp_.qr_fp64) ? W_FLOP64 : W_FLOP32;
