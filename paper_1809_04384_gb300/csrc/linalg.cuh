@@ -529,13 +529,16 @@ struct JRot {
     cx<T> e;
 };
 
+// init_u = false: U already holds the unitary transform applied to M so far; the sweeps
+// continue it (U <- U J for every rotation J)
 template <class T>
 __device__ int herm_jacobi(int n, cx<T>* M, cx<T>* U, JRot<T>* rot, T* red, int max_sweeps,
-                           T tol) {
+                           T tol, bool init_u = true) {
     const int np = n + (n & 1);
     const int half = np / 2;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
-        U[idx] = (idx / n == idx % n) ? mk<T>(T(1), T(0)) : zero<T>();
+    if (init_u)
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+            U[idx] = (idx / n == idx % n) ? mk<T>(T(1), T(0)) : zero<T>();
     __syncthreads();
     T fro = 0;
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) fro += abs2(M[idx]);

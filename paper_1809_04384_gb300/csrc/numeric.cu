@@ -1948,10 +1948,127 @@ size_t tsqr_smem_bytes(int k) {
 
 // Hermitian eigensolver + descending order (NaN-safe): on return lam[i] are the
 // eigenvalues of M, order[r] the index of the r-th largest, U the eigenvectors.
+//
+// FP32 data (X32, Tw given, n >= 8): the sweeps start from an FP32 solution.  The Jacobi first
+// runs on an FP32 copy of M (the FP32 pipe is 64x the FP64 one); its eigenvectors U32 are made
+// unitary in FP64 by one Newton-Schulz step, U = U32 (I + E), E = (I - U32^* U32) / 2 (E is of
+// the order of the FP32 rounding, so it is kept in FP32; U^* U - I drops to ~1e-14), M is
+// rotated by U in FP64 (M <- U^* M U, a similarity to FP64 rounding, nearly diagonal) and the
+// FP64 sweeps continue from there, with U, to the same stopping rule.  The result is the FP64
+// eigendecomposition of M after about two FP64 sweeps instead of six to eight.  (Without the
+// Newton-Schulz step the rotation would be a congruence by a matrix unitary only to ~1e-7,
+// which moves the small eigenvalues by ~1e-7 |M|.)  X32: n x n complex FP32; Tw: one row of n
+// complex FP64 per warp.
 template <class T>
 __device__ void eig_desc(int n, cx<double>* M, cx<double>* U, JRot<double>* rot, double* red, double* lam,
-                         int* order, unsigned* err) {
-    herm_jacobi<double>(n, M, U, rot, red, 40, 1e-15);
+                         int* order, unsigned* err, cx<float>* X32 = nullptr, cx<double>* Tw = nullptr) {
+    bool warm = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (X32 != nullptr && Tw != nullptr && n >= 8) {
+            const int nn = n * n;
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+            cx<float>* M32 = reinterpret_cast<cx<float>*>(U);   // the U area is free until U is formed
+            // M scaled by a power of two to magnitudes below 1 (the weighted Grams reach far beyond
+            // the FP32 range, and squares of their entries appear in the rotations); the
+            // eigenvectors do not change
+            double mx = 0.0;
+            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) mx = fmax(mx, fmax(fabs(M[idx].x), fabs(M[idx].y)));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            __syncthreads();
+            if (lane == 0) red[warp] = mx;
+            __syncthreads();
+            mx = 0.0;
+            for (int q = 0; q < nw; ++q) mx = fmax(mx, red[q]);
+            __syncthreads();
+            int ex = 0;
+            if (mx > 0.0 && isfinite(mx)) frexp(mx, &ex);
+            const double scale = ldexp(1.0, -ex);   // |M| * scale < 1
+            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x)
+                M32[idx] = cx<float>{float(M[idx].x * scale), float(M[idx].y * scale)};
+            __syncthreads();
+            herm_jacobi<float>(n, M32, X32, reinterpret_cast<JRot<float>*>(rot), reinterpret_cast<float*>(red), 20,
+                               1e-6f);
+            __syncthreads();
+            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) U[idx] = cx<double>{double(X32[idx].x), double(X32[idx].y)};
+            __syncthreads();
+            // E = (I - U^* U) / 2, into the FP32 area
+            double emax = 0.0;
+            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+                const int i = idx / n, j = idx - i * n;
+                cx<double> g = zero<double>();
+                for (int l = 0; l < n; ++l) fma_cjx(g, U[(int64_t)l * n + i], U[(int64_t)l * n + j]);
+                const cx<double> ev{0.5 * ((i == j ? 1.0 : 0.0) - g.x), -0.5 * g.y};
+                emax = fmax(emax, fmax(fabs(ev.x), fabs(ev.y)));
+                if (!(emax <= 1.0)) emax = 2.0;   // NaN
+                X32[idx] = cx<float>{float(ev.x), float(ev.y)};
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+            __syncthreads();
+            if (lane == 0) red[warp] = emax;
+            __syncthreads();
+            emax = 0.0;
+            for (int q = 0; q < nw; ++q) emax = fmax(emax, red[q]);
+            __syncthreads();
+            // a start that one Newton-Schulz step cannot make unitary is dropped: the FP64 sweeps
+            // then start from the identity (M is untouched so far)
+            if (emax <= 1e-4) {
+            cx<double>* tmp = Tw + (int64_t)warp * n;
+            for (int i = warp; i < n; i += nw) {       // row i of U <- row i of U (I + E)
+                for (int j = lane; j < n; j += 32) {
+                    cx<double> acc = U[(int64_t)i * n + j];
+                    for (int l = 0; l < n; ++l) {
+                        const cx<float> e = X32[(int64_t)l * n + j];
+                        fma_cx(acc, U[(int64_t)i * n + l], cx<double>{double(e.x), double(e.y)});
+                    }
+                    tmp[j] = acc;
+                }
+                __syncwarp();
+                for (int j = lane; j < n; j += 32) U[(int64_t)i * n + j] = tmp[j];
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int i = warp; i < n; i += nw) {       // row i of M <- row i of M U
+                for (int j = lane; j < n; j += 32) {
+                    cx<double> acc = zero<double>();
+                    for (int l = 0; l < n; ++l) fma_cx(acc, M[(int64_t)i * n + l], U[(int64_t)l * n + j]);
+                    tmp[j] = acc;
+                }
+                __syncwarp();
+                for (int j = lane; j < n; j += 32) M[(int64_t)i * n + j] = tmp[j];
+                __syncwarp();
+            }
+            __syncthreads();
+            for (int j = warp; j < n; j += nw) {       // column j of M <- column j of U^* M
+                for (int i = lane; i < n; i += 32) {
+                    cx<double> acc = zero<double>();
+                    for (int l = 0; l < n; ++l) fma_cjx(acc, U[(int64_t)l * n + i], M[(int64_t)l * n + j]);
+                    tmp[i] = acc;
+                }
+                __syncwarp();
+                for (int i = lane; i < n; i += 32) M[(int64_t)i * n + j] = tmp[i];
+                __syncwarp();
+            }
+            __syncthreads();
+            // its Hermitian part (Hermitian up to rounding)
+            for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) {
+                const int i = idx / n, j = idx - i * n;
+                if (i < j) {
+                    const cx<double> a = M[idx], b = M[(int64_t)j * n + i];
+                    const cx<double> hh{0.5 * (a.x + b.x), 0.5 * (a.y - b.y)};
+                    M[idx] = hh;
+                    M[(int64_t)j * n + i] = conj(hh);
+                } else if (i == j) {
+                    M[idx].y = 0.0;
+                }
+            }
+            __syncthreads();
+            warm = true;
+            }
+        }
+    }
+    herm_jacobi<double>(n, M, U, rot, red, 40, 1e-15, !warm);
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double li = M[(int64_t)i * n + i].x;
@@ -1978,7 +2095,11 @@ struct EigSpace {
     JRot<double>* rot;
     double* lam;
     int* order;
+    cx<float>* X32;    // n x n FP32 scratch of the FP32 start (eig_desc)
+    cx<double>* Tw;    // kEigWarps rows of n: per-warp staging of the in-place transforms
 };
+
+constexpr int kEigWarps = 8;   // warps of the CTAs that call eig_desc (256 threads)
 
 __device__ __forceinline__ EigSpace eig_space(int n, int smem_n, unsigned char* smraw, cx<double>* gslot) {
     EigSpace e;
@@ -1988,24 +2109,34 @@ __device__ __forceinline__ EigSpace eig_space(int n, int smem_n, unsigned char* 
         e.rot = reinterpret_cast<JRot<double>*>(e.U + (int64_t)smem_n * smem_n);
         e.lam = reinterpret_cast<double*>(e.rot + (smem_n / 2 + 1));
         e.order = reinterpret_cast<int*>(e.lam + smem_n);
+        e.X32 = reinterpret_cast<cx<float>*>((reinterpret_cast<uintptr_t>(e.order + smem_n) + 15) &
+                                             ~static_cast<uintptr_t>(15));
+        e.Tw = reinterpret_cast<cx<double>*>((reinterpret_cast<uintptr_t>(e.X32 + (int64_t)smem_n * smem_n) + 15) &
+                                             ~static_cast<uintptr_t>(15));   // 8 smem_n^2 bytes: odd smem_n ends on 8
     } else {
         e.M = gslot;
         e.U = e.M + (int64_t)n * n;
         e.rot = reinterpret_cast<JRot<double>*>(e.U + (int64_t)n * n);
         e.lam = reinterpret_cast<double*>(e.rot + (n / 2 + 1));
         e.order = reinterpret_cast<int*>(e.lam + n);
+        e.X32 = reinterpret_cast<cx<float>*>((reinterpret_cast<uintptr_t>(e.order + n) + 15) &
+                                             ~static_cast<uintptr_t>(15));
+        e.Tw = reinterpret_cast<cx<double>*>((reinterpret_cast<uintptr_t>(e.X32 + (int64_t)n * n) + 15) &
+                                             ~static_cast<uintptr_t>(15));   // cx<double> needs 16-byte alignment
     }
     return e;
 }
 
 inline size_t eig_smem_bytes(int smem_n) {
     return smem_n > 0 ? 2 * (size_t)smem_n * smem_n * sizeof(cx<double>) + (smem_n / 2 + 1) * sizeof(JRot<double>) +
-                            smem_n * (sizeof(double) + sizeof(int)) + 64
+                            smem_n * (sizeof(double) + sizeof(int)) + 16 + (size_t)smem_n * smem_n * sizeof(cx<float>) +
+                            16 + (size_t)kEigWarps * smem_n * sizeof(cx<double>) + 64
                       : 64;
 }
 inline int64_t eig_global_elems(int n) {   // cx<double> elements of a global Jacobi slot
     int64_t bytes = 2 * (int64_t)n * n * sizeof(cx<double>) + (n / 2 + 1) * sizeof(JRot<double>) +
-                    n * (sizeof(double) + sizeof(int));
+                    n * (sizeof(double) + sizeof(int)) + 16 + (int64_t)n * n * sizeof(cx<float>) + 16 +
+                    (int64_t)kEigWarps * n * sizeof(cx<double>);
     return (bytes + sizeof(cx<double>) - 1) / sizeof(cx<double>) + 4;
 }
 
@@ -2024,7 +2155,8 @@ template <class T, bool F64, class FV>
 __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<T>* __restrict__ Z,
                               cx<T>* Ascr, cx<double>* M, cx<double>* U, JRot<double>* rot,
                               double eps, int rule, cx<T>* Q, cx<double>* Cd, cx<T>* Ct,
-                              double* sig, int32_t* rank, int* s_order, double* s_lam, unsigned* err) {
+                              double* sig, int32_t* rank, int* s_order, double* s_lam, unsigned* err,
+                              cx<float>* X32, cx<double>* Tw) {
     __shared__ double red[32];
     __shared__ int s_rank;
     const int n = tk.rows, rz = tk.rz;
@@ -2048,7 +2180,7 @@ __device__ void truncate_body(const TruncTask& tk, const FV& V, int k, const cx<
                              DenseCvt<double, T>{Ascr, rz, true, true},
                              [&](int i, int j, cx<double> v) { M[(int64_t)i * n + j] = v; });
         __syncthreads();
-        eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err);
+        eig_desc<T>(n, M, U, rot, red, s_lam, s_order, err, X32, Tw);
     }
     auto u = [&](int i, int r) -> cx<T> {
         if constexpr (std::is_same<T, float>::value && !F64) {
@@ -2112,7 +2244,7 @@ __global__ void k_truncate(const TruncTask* __restrict__ tasks, int k, const cx<
     const int n = tk.rows;
     EigSpace e = eig_space(n, smem_n, smraw, gscr + tk.gslot);
     truncate_body<T, F64>(tk, Dense<T>{Vhat + tk.vsrc, k, false, false}, k, Z, ascr + tk.ascratch, e.M, e.U, e.rot,
-                     eps, rule, Q, Cd, Ct, sig, rank, e.order, e.lam, err);
+                     eps, rule, Q, Cd, Ct, sig, rank, e.order, e.lam, err, e.X32, e.Tw);
 }
 
 struct OrthTask {
@@ -2153,7 +2285,7 @@ __global__ void k_leaf_orth(const OrthTask* __restrict__ tasks, int k, cx<T>* V,
     cta_gemm_fit<double>(n, n, k, DenseCvt<double, T>{Vt, k, false, false}, DenseCvt<double, T>{Vt, k, true, true},
                      [&](int i, int j, cx<double> v) { e.M[(int64_t)i * n + j] = v; });
     __syncthreads();
-    eig_desc<T>(n, e.M, e.U, e.rot, red, e.lam, e.order, err);
+    eig_desc<T>(n, e.M, e.U, e.rot, red, e.lam, e.order, err, e.X32, e.Tw);
     for (int idx = threadIdx.x; idx < n * rt; idx += blockDim.x) {
         const int i = idx / rt, j = idx - i * rt;
         const cx<double> u = e.U[(int64_t)i * n + e.order[j]];
@@ -2211,7 +2343,7 @@ __global__ void k_trunc_leaf(const LeafTruncTask* __restrict__ tasks, int k, con
                              DenseCvt<double, T>{Zt, rt, false, false},
                              [&](int i, int j, cx<double> v) { e.M[(int64_t)i * rt + j] = v; });
         __syncthreads();
-        eig_desc<T>(rt, e.M, e.U, e.rot, red, e.lam, e.order, err);
+        eig_desc<T>(rt, e.M, e.U, e.rot, red, e.lam, e.order, err, e.X32, e.Tw);
     }
     // entry j of the r-th left singular vector of Z'^* (descending)
     auto u = [&](int j, int r) -> cx<T> {
