@@ -5039,6 +5039,26 @@ void Num<T>::launch_matvec(const void* x, void* y, int dtype, cudaStream_t s, bo
                 leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y,
                 near_parts_.p, near_pbuf_.p);
         DH2_CHECK_LAUNCH("k_leaf_out2 (leaf bases)");
+    } else if (n_leaves_ && timing_on_ && n_near_parts_) {
+        // timed products run the graph's decomposition serially: the nearfield in panel column
+        // parts (balanced over the SMs), then the leaf bases plus the parts' sums; both launches
+        // count as the leaf output
+        ev_.begin(K_MV_LEAF_OUT, s);
+        k_near_part<T><<<(unsigned)n_near_parts_, 256, 0, s>>>(near_parts_.p, colidx_.p, near_.p, xt_.p,
+                                                                near_pbuf_.p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_near_part");
+        ev_.begin(K_MV_LEAF_OUT, s);
+        if (dtype == DH2_C64)
+            k_leaf_out2<T, float, 2><<<(unsigned)n_leaves_, 256, 0, s>>>(
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<float>*)y,
+                near_parts_.p, near_pbuf_.p);
+        else
+            k_leaf_out2<T, double, 2><<<(unsigned)n_leaves_, 256, 0, s>>>(
+                leaf_out2_.p, leaf_q_.p, colidx_.p, Q_[0].p, yh_.p, near_.p, xt_.p, tr_.perm.p, (cx<double>*)y,
+                near_parts_.p, near_pbuf_.p);
+        ev_.end(s);
+        DH2_CHECK_LAUNCH("k_leaf_out2 (leaf bases)");
     } else if (n_leaves_) {
         if (dtype == DH2_C64) {
             if (timing_on_) ev_.begin(K_MV_LEAF_OUT, s);

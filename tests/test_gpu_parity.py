@@ -199,6 +199,30 @@ def test_matvec_dtypes_agree(precision):
     assert rel(y64.astype(np.complex128), y128) <= 1e-5
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_timed_matvec_equals_graph_matvec(precision):
+    """With per-kernel timing on (dh2_set_timing), the product runs the CUDA graph's kernels one
+    after another on the caller's stream (nearfield panel parts, then the leaf bases plus the
+    parts' sums): the same arithmetic in the same order, so the same bits.  plain5120m5 has
+    panels of several parts."""
+    import torch
+
+    import paper_1809_04384_gb300 as dh2
+
+    v, f = mesh("plain5120m5")
+    p = params("plain5120m5")
+    tree = dh2.Tree(v, f, leaf_max=p["leaf"])
+    mat = dh2.Matrix(tree, p["kappa"], p["m"], p["eta2"], p["eps"], eta1=p["eta1"], **form_kwargs(precision))
+    x = torch.from_numpy(x_vector(mat.n)).to(vec_dtype(precision)).cuda()
+    y_graph = mat.matvec(x).cpu().numpy()
+    mat.set_timing(True)
+    y_timed = mat.matvec(x).cpu().numpy()
+    launches = mat.kernel_times()["mv_leaf_out"][1]
+    mat.set_timing(False)
+    assert launches == 2   # the panel parts and the leaf bases
+    assert np.array_equal(y_graph, y_timed)
+
+
 @pytest.mark.parametrize("name", ["mixed1280", "lowfreq1280"])
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_grouped_weight_qr_matches_oracle(name, precision):
